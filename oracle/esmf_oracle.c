@@ -1,0 +1,349 @@
+/*
+ * FP64 CPU oracle for the grouped generalized Coulomb / exchange builds.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or helper with the
+ * CUDA library; the two meet only in the seeded input generator.
+ *
+ * What it computes (plain definitions, no blocking or fusion):
+ *   - contracted s-type Gaussians normalised to <phi|phi> = 1 (textbook,
+ *     Szabo & Ostlund App. A, the text the paper cites for integrals);
+ *   - primitive (ss|ss) integrals through the Boys function F0 closed form;
+ *   - Schwarz factors Q_pq = sqrt((pq|pq));
+ *   - generalized J, K and F of Eq. (J_and_K), Sec. II.B.1:
+ *       J[D]_pq = sum_rs D_rs (rs|pq),  K[D]_pq = sum_rs D_rs (pr|qs),
+ *       F = 2J - K,  for non-symmetric D;
+ *   - the inner product D.F = sum_pq D_pq F_pq of Table I (notation table).
+ * Screening reading: a quartet (pq|rs) is kept iff Q_pq * Q_rs >= tol
+ * (tol = 0 keeps every quartet).  The paper's own rule (Sec. II.C) drops a
+ * pair whose largest integral is below a threshold; the Schwarz product
+ * rule is the bound-based form of the same idea.
+ *
+ * Every floating point operation is IEEE double.  erf() is the C library's.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* offsets of each function's primitives in the flat exps / weights arrays */
+static int64_t *prim_offsets(int n, const int32_t *nprim)
+{
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    off[0] = 0;
+    for (int i = 0; i < n; ++i) off[i + 1] = off[i] + nprim[i];
+    return off;
+}
+
+/*
+ * Normalisation (textbook): primitive g_k = (2 a_k / pi)^{3/4} exp(-a_k r^2)
+ * has <g_k|g_k> = 1; <g_k|g_l> on one center = (2 sqrt(a_k a_l)/(a_k+a_l))^{3/2}.
+ * phi = c sum_k d_k g_k with c chosen so that <phi|phi> = 1.
+ * Output w_k = c d_k (2 a_k/pi)^{3/4}: the weight of the raw exp(-a_k r^2).
+ */
+int oracle_normalize(int n, const int32_t *nprim, const double *exps,
+                     const double *coefs, double *w)
+{
+    if (n <= 0) return -1;
+    int64_t *off = prim_offsets(n, nprim);
+    for (int mu = 0; mu < n; ++mu) {
+        double s = 0.0;
+        for (int64_t k = off[mu]; k < off[mu + 1]; ++k)
+            for (int64_t l = off[mu]; l < off[mu + 1]; ++l) {
+                double ak = exps[k], al = exps[l];
+                double ov = pow(2.0 * sqrt(ak * al) / (ak + al), 1.5);
+                s += coefs[k] * coefs[l] * ov;
+            }
+        double c = 1.0 / sqrt(s);
+        for (int64_t k = off[mu]; k < off[mu + 1]; ++k)
+            w[k] = c * coefs[k] * pow(2.0 * exps[k] / OR_PI, 0.75);
+    }
+    free(off);
+    return 0;
+}
+
+/* Boys function of order zero, F0(T) = int_0^1 exp(-T u^2) du
+ *   = (1/2) sqrt(pi/T) erf(sqrt(T))  for T > 0, with the Taylor series
+ *   sum_k (-T)^k / (k! (2k+1)) for small T (four terms below 1e-6). */
+double oracle_boys0(double T)
+{
+    if (T < 1e-6) return 1.0 - T / 3.0 + T * T / 10.0 - T * T * T / 42.0;
+    return 0.5 * sqrt(OR_PI / T) * erf(sqrt(T));
+}
+
+/* [ab|cd] over raw Gaussians exp(-a|r-A|^2) ... (textbook, Boys 1950):
+ *   p = a+b, q = c+d, P = (aA+bB)/p, Q = (cC+dD)/q, rho = pq/(p+q)
+ *   [ab|cd] = 2 pi^{5/2} / (p q sqrt(p+q)) exp(-ab/p |AB|^2)
+ *             exp(-cd/q |CD|^2) F0(rho |PQ|^2) */
+static double prim_eri(double a, const double *A, double b, const double *B,
+                       double c, const double *C, double d, const double *D)
+{
+    double p = a + b, q = c + d;
+    double P[3], Q[3], ab2 = 0, cd2 = 0, pq2 = 0;
+    for (int x = 0; x < 3; ++x) {
+        P[x] = (a * A[x] + b * B[x]) / p;
+        Q[x] = (c * C[x] + d * D[x]) / q;
+        ab2 += (A[x] - B[x]) * (A[x] - B[x]);
+        cd2 += (C[x] - D[x]) * (C[x] - D[x]);
+        pq2 += (P[x] - Q[x]) * (P[x] - Q[x]);
+    }
+    double T = p * q / (p + q) * pq2;
+    return 2.0 * pow(OR_PI, 2.5) / (p * q * sqrt(p + q)) *
+           exp(-a * b / p * ab2) * exp(-c * d / q * cd2) * oracle_boys0(T);
+}
+
+typedef struct {
+    int n;
+    const double *center;
+    const int32_t *nprim;
+    const double *exps;
+    const double *w;
+    int64_t *off;
+} obasis;
+
+static obasis mk_basis(int n, const double *center, const int32_t *nprim,
+                       const double *exps, const double *w)
+{
+    obasis b;
+    b.n = n; b.center = center; b.nprim = nprim; b.exps = exps; b.w = w;
+    b.off = prim_offsets(n, nprim);
+    return b;
+}
+
+/* contracted (pq|rs): sum over all primitive products */
+static double eri_c(const obasis *b, int p, int q, int r, int s)
+{
+    double v = 0.0;
+    for (int64_t i = b->off[p]; i < b->off[p + 1]; ++i)
+        for (int64_t j = b->off[q]; j < b->off[q + 1]; ++j)
+            for (int64_t k = b->off[r]; k < b->off[r + 1]; ++k)
+                for (int64_t l = b->off[s]; l < b->off[s + 1]; ++l)
+                    v += b->w[i] * b->w[j] * b->w[k] * b->w[l] *
+                         prim_eri(b->exps[i], b->center + 3 * p,
+                                  b->exps[j], b->center + 3 * q,
+                                  b->exps[k], b->center + 3 * r,
+                                  b->exps[l], b->center + 3 * s);
+    return v;
+}
+
+double oracle_eri(int n, const double *center, const int32_t *nprim,
+                  const double *exps, const double *w, int p, int q, int r, int s)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    double v = eri_c(&b, p, q, r, s);
+    free(b.off);
+    return v;
+}
+
+/* full N^4 tensor, element [((p N + q) N + r) N + s] = (pq|rs), no symmetry used */
+int oracle_eri_tensor(int n, const double *center, const int32_t *nprim,
+                      const double *exps, const double *w, double *out)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q)
+            for (int r = 0; r < n; ++r)
+                for (int s = 0; s < n; ++s)
+                    out[(((int64_t)p * n + q) * n + r) * n + s] = eri_c(&b, p, q, r, s);
+    free(b.off);
+    return 0;
+}
+
+/* Q[p N + q] = sqrt((pq|pq)) */
+int oracle_schwarz(int n, const double *center, const int32_t *nprim,
+                   const double *exps, const double *w, double *Q)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q) {
+            double v = eri_c(&b, p, q, p, q);
+            Q[(int64_t)p * n + q] = sqrt(v > 0.0 ? v : 0.0);
+        }
+    free(b.off);
+    return 0;
+}
+
+static int kept(const double *Q, int n, int p, int q, int r, int s, double tol)
+{
+    return Q[(int64_t)p * n + q] * Q[(int64_t)r * n + s] >= tol;
+}
+
+/*
+ * Brute force over all ordered (p,q,r,s) with a precomputed full tensor:
+ *   J[p][q] += D[r][s] (pq|rs),  K[p][r] += D[q][s] (pq|rs).
+ * This is Eq. (J_and_K) with the dummy indices renamed.  J, K are zeroed.
+ */
+int oracle_jk_brute(int n, const double *eri, const double *Q, double tol,
+                    int m, const double *D, double *J, double *K)
+{
+    int64_t nn = (int64_t)n * n;
+    memset(J, 0, sizeof(double) * (size_t)(nn * m));
+    memset(K, 0, sizeof(double) * (size_t)(nn * m));
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q)
+            for (int r = 0; r < n; ++r)
+                for (int s = 0; s < n; ++s) {
+                    if (!kept(Q, n, p, q, r, s, tol)) continue;
+                    double v = eri[(((int64_t)p * n + q) * n + r) * n + s];
+                    for (int k = 0; k < m; ++k) {
+                        const double *Dk = D + k * nn;
+                        J[k * nn + (int64_t)p * n + q] += Dk[(int64_t)r * n + s] * v;
+                        K[k * nn + (int64_t)p * n + r] += Dk[(int64_t)q * n + s] * v;
+                    }
+                }
+    return 0;
+}
+
+/* pair index of (p >= q) */
+static int64_t pidx(int p, int q) { return (int64_t)p * (p + 1) / 2 + q; }
+
+/*
+ * Unique-quartet loop: each integral with p >= q, r >= s, pair(pq) >=
+ * pair(rs) is evaluated once and applied to every DISTINCT ordered tuple in
+ * its permutation orbit (p,q,r,s) (q,p,r,s) (p,q,s,r) (q,p,s,r) (r,s,p,q)
+ * (s,r,p,q) (r,s,q,p) (s,r,q,p), using the same ordered update as the brute
+ * loop.  No degeneracy factors are needed.
+ * Bra pairs pq in [pair_begin, pair_end) are processed (the full build is
+ * [0, N(N+1)/2)); J and K are accumulated, NOT zeroed, so that partial
+ * ranges can be summed.  If eri_list is non-NULL it supplies the integrals
+ * in loop order (stored mode) instead of evaluating them.
+ * Returns the number of kept unique quartets.
+ */
+int64_t oracle_jk_unique(int n, const double *center, const int32_t *nprim,
+                         const double *exps, const double *w, const double *Q,
+                         double tol, int m, const double *D, double *J, double *K,
+                         int64_t pair_begin, int64_t pair_end,
+                         const double *eri_list)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    int64_t nn = (int64_t)n * n;
+    int64_t nkept = 0, pos = 0;
+    /* walk all bra pairs, skip those outside the range */
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q <= p; ++q) {
+            int64_t pq = pidx(p, q);
+            if (pq < pair_begin || pq >= pair_end) continue;
+            for (int r = 0; r <= p; ++r)
+                for (int s = 0; s <= r; ++s) {
+                    int64_t rs = pidx(r, s);
+                    if (rs > pq) continue;
+                    if (!kept(Q, n, p, q, r, s, tol)) continue;
+                    double v = eri_list ? eri_list[pos++] : eri_c(&b, p, q, r, s);
+                    ++nkept;
+                    int t[8][4] = {{p, q, r, s}, {q, p, r, s}, {p, q, s, r}, {q, p, s, r},
+                                   {r, s, p, q}, {s, r, p, q}, {r, s, q, p}, {s, r, q, p}};
+                    for (int a = 0; a < 8; ++a) {
+                        int dup = 0;
+                        for (int c = 0; c < a; ++c)
+                            if (t[a][0] == t[c][0] && t[a][1] == t[c][1] &&
+                                t[a][2] == t[c][2] && t[a][3] == t[c][3]) { dup = 1; break; }
+                        if (dup) continue;
+                        int i0 = t[a][0], i1 = t[a][1], i2 = t[a][2], i3 = t[a][3];
+                        for (int k = 0; k < m; ++k) {
+                            const double *Dk = D + k * nn;
+                            J[k * nn + (int64_t)i0 * n + i1] += Dk[(int64_t)i2 * n + i3] * v;
+                            K[k * nn + (int64_t)i0 * n + i2] += Dk[(int64_t)i1 * n + i3] * v;
+                        }
+                    }
+                }
+        }
+    free(b.off);
+    return nkept;
+}
+
+/* The kept unique integrals in the loop order of oracle_jk_unique over
+ * [pair_begin, pair_end); returns how many were written (at most cap). */
+int64_t oracle_unique_list(int n, const double *center, const int32_t *nprim,
+                           const double *exps, const double *w, const double *Q,
+                           double tol, int64_t pair_begin, int64_t pair_end,
+                           double *out, int64_t cap)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    int64_t cnt = 0;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q <= p; ++q) {
+            int64_t pq = pidx(p, q);
+            if (pq < pair_begin || pq >= pair_end) continue;
+            for (int r = 0; r <= p; ++r)
+                for (int s = 0; s <= r; ++s) {
+                    if (pidx(r, s) > pq) continue;
+                    if (!kept(Q, n, p, q, r, s, tol)) continue;
+                    if (cnt < cap) out[cnt] = eri_c(&b, p, q, r, s);
+                    ++cnt;
+                }
+        }
+    free(b.off);
+    return cnt;
+}
+
+/* number of kept unique quartets for a Schwarz table */
+int64_t oracle_count_kept(int n, const double *Q, double tol)
+{
+    int64_t cnt = 0;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q <= p; ++q)
+            for (int r = 0; r <= p; ++r)
+                for (int s = 0; s <= r; ++s)
+                    if (pidx(r, s) <= pidx(p, q) && kept(Q, n, p, q, r, s, tol)) ++cnt;
+    return cnt;
+}
+
+/*
+ * Selected elements, each computed on its own from the definition:
+ *   J[k][p][q] = sum_{r,s} kept (pq|rs) D_k[r][s]      (jidx holds p,q pairs)
+ *   K[k][p][r] = sum_{q,s} kept (pq|rs) D_k[q][s]      (kidx holds p,r pairs)
+ * Outputs are laid out [k][element].
+ */
+int oracle_jk_elements(int n, const double *center, const int32_t *nprim,
+                       const double *exps, const double *w, const double *Q,
+                       double tol, int m, const double *D,
+                       int nj, const int32_t *jidx, double *Jout,
+                       int nk, const int32_t *kidx, double *Kout)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    int64_t nn = (int64_t)n * n;
+    for (int e = 0; e < nj; ++e) {
+        int p = jidx[2 * e], q = jidx[2 * e + 1];
+        for (int k = 0; k < m; ++k) Jout[(int64_t)k * nj + e] = 0.0;
+        for (int r = 0; r < n; ++r)
+            for (int s = 0; s < n; ++s) {
+                if (!kept(Q, n, p, q, r, s, tol)) continue;
+                double v = eri_c(&b, p, q, r, s);
+                for (int k = 0; k < m; ++k)
+                    Jout[(int64_t)k * nj + e] += D[k * nn + (int64_t)r * n + s] * v;
+            }
+    }
+    for (int e = 0; e < nk; ++e) {
+        int p = kidx[2 * e], r = kidx[2 * e + 1];
+        for (int k = 0; k < m; ++k) Kout[(int64_t)k * nk + e] = 0.0;
+        for (int q = 0; q < n; ++q)
+            for (int s = 0; s < n; ++s) {
+                if (!kept(Q, n, p, q, r, s, tol)) continue;
+                double v = eri_c(&b, p, q, r, s);
+                for (int k = 0; k < m; ++k)
+                    Kout[(int64_t)k * nk + e] += D[k * nn + (int64_t)q * n + s] * v;
+            }
+    }
+    free(b.off);
+    return 0;
+}
+
+/* F_k = 2 J_k - K_k and t_k = D_k . F_k = sum_pq D_k[pq] F_k[pq] (Table I) */
+int oracle_fock_traces(int n, int m, const double *D, const double *J,
+                       const double *K, double *F, double *t)
+{
+    int64_t nn = (int64_t)n * n;
+    for (int k = 0; k < m; ++k) {
+        double acc = 0.0;
+        for (int64_t e = 0; e < nn; ++e) {
+            double f = 2.0 * J[k * nn + e] - K[k * nn + e];
+            if (F) F[k * nn + e] = f;
+            acc += D[k * nn + e] * f;
+        }
+        t[k] = acc;
+    }
+    return 0;
+}

@@ -1,0 +1,166 @@
+"""ctypes wrapper around the FP64 CPU oracle (esmf_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU-baseline leg, never by the product library.  The compiled
+object is built here with gcc (no CUDA), in-tree, next to the source.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "esmf_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force=False):
+    """Compile the oracle shared library (plain C, -O2, IEEE double)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math",
+           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            dp = C.POINTER(C.c_double)
+            ip = C.POINTER(C.c_int32)
+            L.oracle_normalize.argtypes = [C.c_int, ip, dp, dp, dp]
+            L.oracle_boys0.argtypes = [C.c_double]
+            L.oracle_boys0.restype = C.c_double
+            L.oracle_eri.argtypes = [C.c_int, dp, ip, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
+            L.oracle_eri.restype = C.c_double
+            L.oracle_eri_tensor.argtypes = [C.c_int, dp, ip, dp, dp, dp]
+            L.oracle_schwarz.argtypes = [C.c_int, dp, ip, dp, dp, dp]
+            L.oracle_jk_brute.argtypes = [C.c_int, dp, dp, C.c_double, C.c_int, dp, dp, dp]
+            L.oracle_jk_unique.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double, C.c_int,
+                                           dp, dp, dp, C.c_int64, C.c_int64, dp]
+            L.oracle_jk_unique.restype = C.c_int64
+            L.oracle_unique_list.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double,
+                                             C.c_int64, C.c_int64, dp, C.c_int64]
+            L.oracle_unique_list.restype = C.c_int64
+            L.oracle_count_kept.argtypes = [C.c_int, dp, C.c_double]
+            L.oracle_count_kept.restype = C.c_int64
+            L.oracle_jk_elements.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double, C.c_int,
+                                             dp, C.c_int, ip, dp, C.c_int, ip, dp]
+            L.oracle_fock_traces.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp]
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class Oracle:
+    """FP64 oracle bound to one basis (host numpy arrays)."""
+
+    def __init__(self, basis):
+        self.n = basis.n
+        self.center = np.ascontiguousarray(basis.center, dtype=np.float64)
+        self.nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)
+        self.exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
+        self.coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
+        self.w = np.zeros_like(self.exps)
+        rc = lib().oracle_normalize(self.n, _i(self.nprim), _d(self.exps), _d(self.coefs), _d(self.w))
+        if rc != 0:
+            raise ValueError("oracle_normalize failed")
+        self._Q = None
+
+    def _b(self):
+        return (self.n, _d(self.center), _i(self.nprim), _d(self.exps), _d(self.w))
+
+    def eri(self, p, q, r, s):
+        return lib().oracle_eri(*self._b(), p, q, r, s)
+
+    def eri_tensor(self):
+        out = np.zeros((self.n,) * 4)
+        lib().oracle_eri_tensor(*self._b(), _d(out))
+        return out
+
+    @property
+    def Q(self):
+        if self._Q is None:
+            Q = np.zeros((self.n, self.n))
+            lib().oracle_schwarz(*self._b(), _d(Q))
+            self._Q = Q
+        return self._Q
+
+    def jk_brute(self, eri, D, tol):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        m = D.shape[0]
+        J = np.zeros_like(D)
+        K = np.zeros_like(D)
+        eri = np.ascontiguousarray(eri)
+        lib().oracle_jk_brute(self.n, _d(eri), _d(self.Q), tol, m, _d(D), _d(J), _d(K))
+        return J, K
+
+    def jk_unique(self, D, tol, pair_range=None, eri_list=None):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        m = D.shape[0]
+        J = np.zeros_like(D)
+        K = np.zeros_like(D)
+        npair = self.n * (self.n + 1) // 2
+        b, e = pair_range if pair_range is not None else (0, npair)
+        el = None
+        if eri_list is not None:
+            eri_list = np.ascontiguousarray(eri_list, dtype=np.float64)
+            el = _d(eri_list)
+        nk = lib().oracle_jk_unique(*self._b(), _d(self.Q), tol, m, _d(D), _d(J), _d(K),
+                                     b, e, el)
+        return J, K, int(nk)
+
+    def unique_list(self, tol, pair_range, cap):
+        out = np.zeros(cap)
+        cnt = lib().oracle_unique_list(*self._b(), _d(self.Q), tol, pair_range[0],
+                                       pair_range[1], _d(out), cap)
+        return out[:min(cnt, cap)], int(cnt)
+
+    def count_kept(self, tol):
+        return int(lib().oracle_count_kept(self.n, _d(self.Q), tol))
+
+    def jk_elements(self, D, tol, jidx, kidx):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        m = D.shape[0]
+        jidx = np.ascontiguousarray(np.asarray(jidx, dtype=np.int32).reshape(-1, 2))
+        kidx = np.ascontiguousarray(np.asarray(kidx, dtype=np.int32).reshape(-1, 2))
+        Jo = np.zeros((m, jidx.shape[0]))
+        Ko = np.zeros((m, kidx.shape[0]))
+        lib().oracle_jk_elements(*self._b(), _d(self.Q), tol, m, _d(D),
+                                 jidx.shape[0], _i(jidx), _d(Jo), kidx.shape[0], _i(kidx), _d(Ko))
+        return Jo, Ko
+
+    @staticmethod
+    def fock_traces(D, J, K):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        m, n, _ = D.shape
+        F = np.zeros_like(D)
+        t = np.zeros(m)
+        lib().oracle_fock_traces(n, m, _d(D), _d(np.ascontiguousarray(J)),
+                                 _d(np.ascontiguousarray(K)), _d(F), _d(t))
+        return F, t
+
+
+def boys0(T):
+    return lib().oracle_boys0(float(T))

@@ -1,0 +1,249 @@
+"""Seeded synthetic inputs for the grouped J/K build.
+
+This module is shared by the CUDA path, the FP64 oracle, the tests and the
+benchmark.  It holds no integral, screening or contraction arithmetic: it only
+draws geometries, primitive exponents, unnormalised contraction coefficients
+and the generalized density matrices D_k that the Fock-like builds consume.
+
+The paper's own workloads are cc-pVDZ molecules whose integrals come from an
+external package (Sec. III.A); those basis sets are not available here, so
+contracted s-type Gaussians on random or lattice geometries stand in for them.
+
+Density recipes follow the notation table (Table I) and the list of nine
+Fock-like densities in Sec. II.C:
+  Theta^T Theta, Theta^T sigma Gamma, A, R^T Theta, R^T sigma Gamma,
+  Theta^T mu Gamma, Theta^T sigma Phi, Theta^T mu sigma^T Theta, B.
+V (orbitals in rows) is the transpose of a seeded Q factor, Theta / Gamma are
+its first N_o / last N_v rows, W = M^T V with M random antisymmetric gives
+R / Phi.  Matrix B is dimensionally inconsistent as printed in Table I; it is
+read here as Phi^T sigma^T sigma Gamma - R^T sigma sigma^T Theta.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 2002003220
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+@dataclass
+class Basis:
+    """Contracted s-type Gaussian basis (host arrays, bohr units).
+
+    center: (N, 3) float64; nprim: (N,) int32; exps, coefs: (sum nprim,) float64.
+    coefs are unnormalised contraction coefficients d_k.
+    """
+
+    center: np.ndarray
+    nprim: np.ndarray
+    exps: np.ndarray
+    coefs: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.center.shape[0])
+
+    def subset(self, idx) -> "Basis":
+        idx = np.asarray(idx, dtype=np.int64)
+        off = np.concatenate([[0], np.cumsum(self.nprim)])
+        sel = np.concatenate([np.arange(off[i], off[i + 1]) for i in idx])
+        return Basis(self.center[idx].copy(), self.nprim[idx].copy(),
+                     self.exps[sel].copy(), self.coefs[sel].copy())
+
+
+@dataclass
+class Workload:
+    name: str
+    basis: Basis
+    D: np.ndarray                 # (m, N, N) float64, row-major
+    tol: float
+    nocc: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def m(self) -> int:
+        return int(self.D.shape[0])
+
+
+# ---------------------------------------------------------------- geometry
+def cube_centers(rng, n, edge, min_dist=0.0, max_tries=200000):
+    """Uniform points in [0, edge]^3, rejecting any closer than min_dist."""
+    pts = []
+    tries = 0
+    while len(pts) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place centers with the requested spacing")
+        x = rng.uniform(0.0, edge, size=3)
+        if min_dist > 0 and pts:
+            d = np.linalg.norm(np.asarray(pts) - x, axis=1)
+            if d.min() < min_dist:
+                continue
+        pts.append(x)
+    return np.asarray(pts, dtype=np.float64)
+
+
+def ribbon_centers(width, length, spacing):
+    """Square lattice width x length in the xy plane (a 2D ribbon)."""
+    ii, jj = np.meshgrid(np.arange(length), np.arange(width), indexing="ij")
+    pts = np.stack([ii.ravel() * spacing, jj.ravel() * spacing,
+                    np.zeros(ii.size)], axis=1)
+    return pts.astype(np.float64)
+
+
+def s_basis(rng, centers, per_center=2, nprim=3, lo=0.1, hi=10.0) -> Basis:
+    """per_center contracted s functions per center; exponents log-uniform
+    in [lo, hi] bohr^-2, coefficients uniform in (0.1, 1]."""
+    ncen = centers.shape[0]
+    n = ncen * per_center
+    center = np.repeat(centers, per_center, axis=0)
+    npr = np.full(n, nprim, dtype=np.int32)
+    exps = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n * nprim))
+    coefs = 1.0 - rng.uniform(0.0, 0.9, size=n * nprim)   # (0.1, 1]
+    return Basis(center.astype(np.float64), npr, exps.astype(np.float64),
+                 coefs.astype(np.float64))
+
+
+# ---------------------------------------------------------------- densities
+def orbitals(rng, n):
+    """Rows are orthonormal orbitals (V = U^T C with U = I, C a Q factor)."""
+    g = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(g)
+    q = q * np.sign(np.diag(r))[None, :]
+    return np.ascontiguousarray(q.T)
+
+
+def _unit(rng, shape):
+    x = rng.standard_normal(shape)
+    return x / np.linalg.norm(x)
+
+
+def esmf_densities(rng, n, nocc, m, first=None):
+    """m generalized densities: the nine ESMF Fock-like densities (Sec. II.C),
+    then extra transition densities Theta^T sigma_k Gamma with fresh sigma_k.
+    For m < 9 the first m of the nine are used.  `first` may prepend the
+    closed-/open-shell pair used by the tiny configuration."""
+    nv = n - nocc
+    V = orbitals(rng, n)
+    Th, Ga = V[:nocc], V[nocc:]
+    sig = _unit(rng, (nocc, nv))
+    mu = _unit(rng, (nocc, nv))
+    M = rng.standard_normal((n, n)) / np.sqrt(n)
+    M = M - M.T
+    W = M.T @ V
+    R, Phi = W[:nocc], W[nocc:]
+    A = Ga.T @ sig.T @ sig @ Ga - Th.T @ sig @ sig.T @ Th
+    B = Phi.T @ sig.T @ sig @ Ga - R.T @ sig @ sig.T @ Th
+    nine = [Th.T @ Th, Th.T @ sig @ Ga, A, R.T @ Th, R.T @ sig @ Ga,
+            Th.T @ mu @ Ga, Th.T @ sig @ Phi, Th.T @ mu @ sig.T @ Th, B]
+    out = []
+    if first == "closed_open_transition":
+        P = Th.T @ Th
+        h, l = V[nocc - 1], V[nocc]
+        out = [P, P - np.outer(h, h) + np.outer(l, l)]
+        while len(out) < m:
+            s = _unit(rng, (nocc, nv))
+            out.append(Th.T @ s @ Ga)
+    else:
+        out = nine[:m]
+        while len(out) < m:
+            s = _unit(rng, (nocc, nv))
+            out.append(Th.T @ s @ Ga)
+    return np.ascontiguousarray(np.stack(out[:m]).astype(np.float64))
+
+
+# ---------------------------------------------------------------- configs
+def tiny(seed_offset=0) -> Workload:
+    """24 contracted s functions (3 primitives) on 12 random centers in an
+    8 bohr cube, m = 4 (closed, open, two transition), N_occ = 6, tol 0."""
+    rng = rng_for(BASE_SEED + 0 + seed_offset)
+    cen = cube_centers(rng, 12, 8.0)
+    b = s_basis(rng, cen, 2, 3)
+    D = esmf_densities(rng, b.n, 6, 4, first="closed_open_transition")
+    return Workload("tiny_n24_m4", b, D, 0.0, 6)
+
+
+def stored(seed_offset=0, m=16) -> Workload:
+    """200 s functions (2 per center) on 100 centers in a random 3D cluster
+    (10 bohr cube, 1.4 bohr minimum spacing), m = 16, N_occ = 40, tol 1e-10."""
+    rng = rng_for(BASE_SEED + 1 + seed_offset)
+    cen = cube_centers(rng, 100, 10.0, 1.4)
+    b = s_basis(rng, cen, 2, 3)
+    D = esmf_densities(rng, b.n, 40, m)
+    return Workload("stored_n200_m16", b, D, 1e-10, 40)
+
+
+def direct(seed_offset=0, length=250, m=32) -> Workload:
+    """2000 s functions on a 4 x 250 ribbon of centers at 1.4 bohr spacing,
+    m = 32, N_occ = 400, tol 1e-10 (integral-direct)."""
+    rng = rng_for(BASE_SEED + 2 + seed_offset)
+    cen = ribbon_centers(4, length, 1.4)
+    b = s_basis(rng, cen, 2, 3)
+    nocc = max(1, b.n // 5)
+    D = esmf_densities(rng, b.n, nocc, m)
+    return Workload(f"direct_n{b.n}_m{m}", b, D, 1e-10, nocc)
+
+
+def precision(seed_offset=0, m=64) -> Workload:
+    """400 s functions on 200 random centers (12.6 bohr cube, 1.4 bohr
+    spacing), m = 64, N_occ = 80, tol 1e-10."""
+    rng = rng_for(BASE_SEED + 3 + seed_offset)
+    cen = cube_centers(rng, 200, 12.6, 1.4)
+    b = s_basis(rng, cen, 2, 3)
+    D = esmf_densities(rng, b.n, 80, m)
+    return Workload("precision_n400_m64", b, D, 1e-10, 80)
+
+
+def random_molecule(rng, n, m, tol=1e-10) -> Workload:
+    """C2-like cube scaled to n/2 centers at the same density."""
+    ncen = n // 2
+    edge = 10.0 * (ncen / 100.0) ** (1.0 / 3.0)
+    cen = cube_centers(rng, ncen, edge, 1.4)
+    b = s_basis(rng, cen, 2, 3)
+    nocc = max(1, int(round(0.2 * b.n)))
+    D = esmf_densities(rng, b.n, nocc, m)
+    return Workload(f"mol_n{b.n}_m{m}", b, D, tol, nocc)
+
+
+def small_random(n, m, seed, tol=0.0, edge=None, min_dist=0.0) -> Workload:
+    """Small random case for parity tests (n even, 2 functions per center)."""
+    rng = rng_for(BASE_SEED + 100 + seed)
+    ncen = max(1, n // 2)
+    if edge is None:
+        edge = 6.0 * (ncen / 12.0) ** (1.0 / 3.0)
+    cen = cube_centers(rng, ncen, edge, min_dist)
+    b = s_basis(rng, cen, 2, 3)
+    if b.n > n:
+        b = b.subset(np.arange(n))
+    nocc = max(1, b.n // 5)
+    D = esmf_densities(rng, b.n, nocc, m)
+    return Workload(f"random_n{b.n}_m{m}_s{seed}", b, D, tol, nocc)
+
+
+def serving_requests(n_requests=256, pool=32, seed_offset=0,
+                     nmin=50, nmax=600, mmin=4, mmax=32):
+    """Request stream for the serving configuration: a pool of `pool` random
+    molecules (basis size uniform in [nmin, nmax], even), each request picks a
+    pool molecule and m uniform in [mmin, mmax].  Returns (pool_bases,
+    requests) where each request is (pool_index, m, seed)."""
+    rng = rng_for(BASE_SEED + 4 + seed_offset)
+    sizes = 2 * rng.integers(nmin // 2, nmax // 2 + 1, size=pool)
+    mols = []
+    for i, n in enumerate(sizes):
+        mols.append(random_molecule(rng_for(BASE_SEED + 1000 + i + seed_offset),
+                                    int(n), 1))
+    reqs = []
+    for r in range(n_requests):
+        reqs.append((int(rng.integers(0, pool)), int(rng.integers(mmin, mmax + 1)),
+                     int(rng.integers(0, 2**31 - 1))))
+    return mols, reqs
+
+
+def request_densities(mol: Workload, m, seed):
+    rng = rng_for(seed)
+    return esmf_densities(rng, mol.basis.n, mol.nocc, m)
