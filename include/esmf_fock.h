@@ -1,0 +1,181 @@
+/*
+ * esmf_fock.h -- C ABI of the GB300 grouped generalized-Fock-build library.
+ *
+ * The library builds, for a batch of m generalized density matrices D_k
+ * (closed-shell, open-shell or non-symmetric transition-like), the
+ * generalized Coulomb and exchange matrices of Eq. (J_and_K), Sec. II.B.1:
+ *
+ *     J[D]_pq = sum_rs D_rs (rs|pq)
+ *     K[D]_pq = sum_rs D_rs (pr|qs)
+ *     F[D]_pq = 2 J[D]_pq - K[D]_pq
+ *
+ * with the two-electron integrals (pq|rs) in chemists' (1122) order over a
+ * basis of contracted s-type Gaussians, all m matrices in ONE pass over the
+ * integrals ("grouping Fock builds", Sec. II.C), with Schwarz screening of
+ * integral quartets (kept iff Q_pq * Q_rs >= tol, Q_pq = sqrt((pq|pq)); the
+ * bound-based form of the shell-pair screening of Sec. II.C).  It also forms
+ * the inner products t_k = D_k . F_k = sum_pq D_k,pq F_k,pq (Table I).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major N x N float64; a batch of m matrices is one
+ *     contiguous array of m * N * N doubles, matrix k at offset k*N*N.
+ *   - Pointers documented as "device" must be CUDA device (or managed)
+ *     memory on the handle's device; "host" pointers are ordinary host
+ *     memory (page-locked memory makes the host-buffer entry faster).
+ *   - The caller owns every buffer it passes; the handle owns the integral,
+ *     pair, Schwarz and work memory it allocates and frees it on destroy.
+ *   - Functions return 0 (ESMF_OK) or a negative ESMF_ERR_* code; nothing
+ *     throws.  esmf_strerror() names a code, esmf_last_error() gives the
+ *     calling thread's most recent detailed message.
+ *   - A handle may be used from one host thread at a time.
+ */
+#ifndef ESMF_FOCK_H
+#define ESMF_FOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESMF_OK                 0
+#define ESMF_ERR_INVALID_ARG   -1   /* bad size, pointer, exponent, NaN ...   */
+#define ESMF_ERR_OOM           -2   /* device or host allocation failed       */
+#define ESMF_ERR_CUDA          -3   /* a CUDA runtime call failed             */
+#define ESMF_ERR_TIMEOUT       -4   /* a bounded wait expired                 */
+#define ESMF_ERR_UNSUPPORTED   -5   /* mode/precision not available for input */
+
+/* integral handling */
+#define ESMF_MODE_STORED  0   /* screened unique integrals stored at create   */
+#define ESMF_MODE_DIRECT  1   /* integrals recomputed inside every build      */
+#define ESMF_MODE_AUTO    2   /* stored if it fits the device budget          */
+
+/* arithmetic of the integral x density products (accumulation is FP64) */
+#define ESMF_PREC_FP64    0   /* FP64 integrals, FP64 products                */
+#define ESMF_PREC_FP32    1   /* FP32 integrals and products, FP64 flushes    */
+#define ESMF_PREC_FP16X2  2   /* integrals as scaled FP16 hi+lo pairs, tensor */
+                              /* cores with FP32 accumulation (stored only)   */
+#define ESMF_PREC_BF16X2  3   /* as FP16X2 with BF16 halves (ablation)        */
+
+/*
+ * Basis of N contracted s-type Gaussians.  All pointers are HOST memory,
+ * read during esmf_fock_create only.
+ *   n_basis  N > 0
+ *   center   N x 3 Cartesian centers in bohr
+ *   n_prim   N primitive counts, each in [1, ESMF_MAX_PRIM]
+ *   exps     sum(n_prim) exponents in bohr^-2, finite and > 0, function by
+ *            function in order
+ *   coefs    sum(n_prim) unnormalised contraction coefficients (finite); the
+ *            library normalises each primitive and each contraction to one.
+ */
+#define ESMF_MAX_PRIM 4
+typedef struct {
+    int32_t        n_basis;
+    const double  *center;
+    const int32_t *n_prim;
+    const double  *exps;
+    const double  *coefs;
+} esmf_basis_t;
+
+typedef struct esmf_fock esmf_fock_t;
+
+typedef struct {
+    int64_t n_basis;            /* N                                           */
+    int64_t n_pairs;            /* N(N+1)/2                                    */
+    int64_t n_quartets_unique;  /* P(P+1)/2, P = n_pairs                       */
+    int64_t n_quartets_kept;    /* unique quartets with Q_pq Q_rs >= tol       */
+    int64_t n_bricks;           /* kept 8x8x8x8 function-block quartets        */
+    int64_t n_stored;           /* integrals held in the store (stored mode)   */
+    int64_t store_bytes;        /* bytes of the integral store                 */
+    int64_t device_bytes;       /* all device memory held by the handle        */
+    int32_t mode;               /* ESMF_MODE_STORED or ESMF_MODE_DIRECT        */
+    int32_t precision;          /* ESMF_PREC_*                                 */
+    double  schwarz_tol;
+    double  create_ms;          /* wall time of esmf_fock_create               */
+} esmf_stats_t;
+
+/*
+ * esmf_fock_create -- Sec. II.C screening set-up, run once per basis
+ * ("at the beginning of an ESMF optimization"): normalises the basis,
+ * builds primitive-pair data, the Schwarz table Q_pq = sqrt((pq|pq)) in
+ * FP64, the list of kept 8x8x8x8 function-block quartets, and in stored
+ * mode evaluates and stores every kept unique integral.
+ *   basis        host description (above)
+ *   schwarz_tol  >= 0; quartets with Q_pq Q_rs < tol are dropped, 0 keeps all
+ *   mode         ESMF_MODE_*;   precision  ESMF_PREC_*
+ *   device       CUDA device ordinal the handle lives on
+ *   budget_bytes device-memory budget for AUTO mode (0 = no limit)
+ *   out          receives the handle (NULL on failure)
+ * Runs on the device's legacy default stream and returns after it has
+ * finished.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED (FP16X2/BF16X2
+ * requested in direct mode, or stored mode beyond budget_bytes).
+ */
+int esmf_fock_create(const esmf_basis_t *basis, double schwarz_tol, int mode,
+                     int precision, int device, int64_t budget_bytes,
+                     esmf_fock_t **out);
+
+/*
+ * esmf_fock_build -- one grouped pass over the (stored or recomputed)
+ * integrals building J_k and K_k for all k < m (Eq. J_and_K), then
+ * optionally F_k = 2 J_k - K_k and t_k = D_k . F_k (Table I).
+ *   h        handle from esmf_fock_create
+ *   m        number of densities, 1 <= m <= ESMF_MAX_DENSITIES
+ *   D        device, m x N x N, read only, any (non-symmetric) values
+ *   J, K     device, m x N x N, overwritten (not accumulated)
+ *   F        device, m x N x N or NULL
+ *   traces   device, m doubles or NULL
+ *   stream   cudaStream_t to run on (NULL = legacy default stream)
+ * Asynchronous: returns once the work is queued; the results are ready
+ * when the stream reaches that point.  The handle's work memory is reused
+ * by the next build, so builds on one handle must not overlap on the GPU
+ * (issue them on one stream, or synchronise in between).
+ * Errors: INVALID_ARG, OOM (growing the work memory), CUDA.
+ */
+#define ESMF_MAX_DENSITIES 1024
+int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J,
+                    double *K, double *F, double *traces, void *stream);
+
+/*
+ * esmf_fock_build_host -- the same build with HOST buffers: copies D to the
+ * device, builds, copies J, K (and F, traces when non-NULL) back, and waits
+ * for completion with a bounded wait of timeout_ms milliseconds (<= 0 means
+ * 600000).  Host buffers: m x N x N doubles (traces: m doubles).
+ * Errors: as esmf_fock_build, plus TIMEOUT if the wait expires (the work may
+ * still be running; the handle must not be reused until it finishes).
+ */
+int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host,
+                         double *J_host, double *K_host, double *F_host,
+                         double *traces_host, void *stream, int timeout_ms);
+
+/*
+ * Kernel timing (measurement aid).  With timing enabled, each build records a
+ * pair of CUDA events on its stream around its grouped contraction kernel
+ * (the dominant kernel).  esmf_fock_kernel_time waits for the recorded
+ * events, returns the summed milliseconds and the number of timed launches,
+ * and clears the record when reset != 0.  At most 65536 launches are kept
+ * between resets; later ones are not timed.  Errors: INVALID_ARG, CUDA.
+ */
+int esmf_fock_set_timing(esmf_fock_t *h, int enable);
+int esmf_fock_kernel_time(esmf_fock_t *h, double *ms, int64_t *launches, int reset);
+
+/* Statistics of a handle (host struct filled in).  Errors: INVALID_ARG. */
+int esmf_fock_stats(const esmf_fock_t *h, esmf_stats_t *out);
+
+/* Schwarz table: copies the N x N FP64 matrix Q_pq = sqrt((pq|pq)) into the
+ * host array Q_host.  Errors: INVALID_ARG, CUDA. */
+int esmf_fock_schwarz(const esmf_fock_t *h, double *Q_host);
+
+/* Frees every device and host resource of the handle (NULL is a no-op).
+ * Waits for the handle's outstanding work first. */
+void esmf_fock_destroy(esmf_fock_t *h);
+
+/* Static string naming a status code. */
+const char *esmf_strerror(int status);
+
+/* Most recent detailed error message of the calling host thread. */
+const char *esmf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESMF_FOCK_H */

@@ -152,15 +152,16 @@ int oracle_eri_tensor(int n, const double *center, const int32_t *nprim,
     return 0;
 }
 
-/* Q[p N + q] = sqrt((pq|pq)) */
+/* Q[p N + q] = Q[q N + p] = sqrt((pq|pq)), evaluated once for p >= q */
 int oracle_schwarz(int n, const double *center, const int32_t *nprim,
                    const double *exps, const double *w, double *Q)
 {
     obasis b = mk_basis(n, center, nprim, exps, w);
     for (int p = 0; p < n; ++p)
-        for (int q = 0; q < n; ++q) {
+        for (int q = 0; q <= p; ++q) {
             double v = eri_c(&b, p, q, p, q);
             Q[(int64_t)p * n + q] = sqrt(v > 0.0 ? v : 0.0);
+            Q[(int64_t)q * n + p] = Q[(int64_t)p * n + q];
         }
     free(b.off);
     return 0;

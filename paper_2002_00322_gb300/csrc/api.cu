@@ -1,0 +1,518 @@
+// C ABI of the grouped generalized-Fock-build library (declared in
+// include/esmf_fock.h).  Host-side orchestration only: argument checks,
+// device memory ownership, the kept-brick list, and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "esmf_internal.cuh"
+
+namespace esmf {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int launch_jk_cuda_split(const JKArgs &a, const float *scales, cudaStream_t s);
+
+}  // namespace esmf
+
+using namespace esmf;
+
+struct esmf_fock {
+    int device = 0;
+    int n = 0, np = 0, nb = 0;
+    double tol = 0.0;
+    int mode = ESMF_MODE_STORED, prec = ESMF_PREC_FP64;
+    // basis (device)
+    double *center = nullptr, *exps = nullptr, *w = nullptr, *coefs = nullptr;
+    int *nprim = nullptr, *poff = nullptr;
+    double *Q = nullptr;
+    // bricks and store (device)
+    BrickDesc *bricks = nullptr;
+    int64_t nbricks = 0;
+    int64_t *offsets = nullptr;
+    void *store = nullptr;
+    float *scales = nullptr;
+    int64_t n_stored = 0, store_bytes = 0, n_kept_unique = 0;
+    // work (device)
+    double *Jacc = nullptr, *Kacc = nullptr;
+    int work_m = 0;
+    // staging for the host-buffer entry (device)
+    double *sD = nullptr, *sJ = nullptr, *sK = nullptr, *sF = nullptr, *st = nullptr;
+    int stage_m = 0;
+    cudaEvent_t done = nullptr;
+    // optional kernel timing
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    size_t ev_used = 0;
+    int64_t device_bytes = 0;
+    double create_ms = 0.0;
+
+    DevBasis dev() const {
+        DevBasis b;
+        b.n = n; b.np = np; b.nb = nb;
+        b.center = center; b.nprim = nprim; b.poff = poff; b.exps = exps; b.w = w;
+        return b;
+    }
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define CKR(call)                                                                  \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));                    \
+            return e_ == cudaErrorMemoryAllocation ? ESMF_ERR_OOM : ESMF_ERR_CUDA; \
+        }                                                                          \
+    } while (0)
+
+#define RET(x)                                                                     \
+    do {                                                                           \
+        int r_ = (x);                                                              \
+        if (r_ != ESMF_OK) return r_;                                              \
+    } while (0)
+
+template <typename T>
+int dalloc(esmf_fock *h, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? ESMF_ERR_OOM : ESMF_ERR_CUDA;
+    }
+    h->device_bytes += (int64_t)(count * sizeof(T));
+    return ESMF_OK;
+}
+
+template <typename T>
+void dfree(esmf_fock *h, T **p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        h->device_bytes -= (int64_t)((count ? count : 1) * sizeof(T));
+    }
+    *p = nullptr;
+}
+
+void release(esmf_fock *h) {
+    if (!h) return;
+    cudaFree(h->center); cudaFree(h->exps); cudaFree(h->w); cudaFree(h->coefs);
+    cudaFree(h->nprim); cudaFree(h->poff); cudaFree(h->Q);
+    cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->scales);
+    cudaFree(h->Jacc); cudaFree(h->Kacc);
+    cudaFree(h->sD); cudaFree(h->sJ); cudaFree(h->sK); cudaFree(h->sF); cudaFree(h->st);
+    if (h->done) cudaEventDestroy(h->done);
+    for (auto &e : h->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    delete h;
+}
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+int elem_bytes(int prec) {
+    switch (prec) {
+        case ESMF_PREC_FP64: return 8;
+        case ESMF_PREC_FP32: return 4;
+        default: return 4;   // hi+lo 16-bit pair
+    }
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure_work(esmf_fock *h, int m) {
+    if (m <= h->work_m) return ESMF_OK;
+    const size_t cnt = (size_t)m * h->np * h->np;
+    dfree(h, &h->Jacc, (size_t)h->work_m * h->np * h->np);
+    dfree(h, &h->Kacc, (size_t)h->work_m * h->np * h->np);
+    h->work_m = 0;
+    RET(dalloc(h, &h->Jacc, cnt));
+    RET(dalloc(h, &h->Kacc, cnt));
+    h->work_m = m;
+    return ESMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *esmf_strerror(int status) {
+    switch (status) {
+        case ESMF_OK: return "ok";
+        case ESMF_ERR_INVALID_ARG: return "invalid argument";
+        case ESMF_ERR_OOM: return "out of memory";
+        case ESMF_ERR_CUDA: return "CUDA error";
+        case ESMF_ERR_TIMEOUT: return "timed out";
+        case ESMF_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *esmf_last_error(void) { return g_err; }
+
+int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precision, int device,
+                     int64_t budget_bytes, esmf_fock_t **out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) { set_error("out is NULL"); return ESMF_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!basis || basis->n_basis <= 0 || !basis->center || !basis->n_prim || !basis->exps ||
+        !basis->coefs) {
+        set_error("basis missing or empty");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    if (!(tol >= 0.0) || !is_finite(tol)) { set_error("schwarz_tol must be finite and >= 0"); return ESMF_ERR_INVALID_ARG; }
+    if (mode < ESMF_MODE_STORED || mode > ESMF_MODE_AUTO) { set_error("bad mode %d", mode); return ESMF_ERR_INVALID_ARG; }
+    if (precision < ESMF_PREC_FP64 || precision > ESMF_PREC_BF16X2) { set_error("bad precision %d", precision); return ESMF_ERR_INVALID_ARG; }
+    if (budget_bytes < 0) { set_error("budget_bytes < 0"); return ESMF_ERR_INVALID_ARG; }
+    const int n = basis->n_basis;
+    if (n > 8 * 32767) { set_error("n_basis %d too large", n); return ESMF_ERR_INVALID_ARG; }
+    int64_t nprim_tot = 0;
+    for (int i = 0; i < n; ++i) {
+        const int k = basis->n_prim[i];
+        if (k < 1 || k > ESMF_MAX_PRIM) { set_error("n_prim[%d] = %d outside [1, %d]", i, k, ESMF_MAX_PRIM); return ESMF_ERR_INVALID_ARG; }
+        for (int x = 0; x < 3; ++x)
+            if (!is_finite(basis->center[3 * i + x])) { set_error("center[%d] not finite", i); return ESMF_ERR_INVALID_ARG; }
+        nprim_tot += k;
+    }
+    for (int64_t j = 0; j < nprim_tot; ++j) {
+        if (!(basis->exps[j] > 0.0) || !is_finite(basis->exps[j])) { set_error("exps[%lld] must be finite and > 0", (long long)j); return ESMF_ERR_INVALID_ARG; }
+        if (!is_finite(basis->coefs[j])) { set_error("coefs[%lld] not finite", (long long)j); return ESMF_ERR_INVALID_ARG; }
+    }
+    // every contraction must have a positive norm
+    {
+        int64_t o = 0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < basis->n_prim[i]; ++k)
+                for (int l = 0; l < basis->n_prim[i]; ++l) {
+                    const double ak = basis->exps[o + k], al = basis->exps[o + l];
+                    s += basis->coefs[o + k] * basis->coefs[o + l] * std::pow(2.0 * std::sqrt(ak * al) / (ak + al), 1.5);
+                }
+            if (!(s > 0.0)) { set_error("contraction %d has zero norm", i); return ESMF_ERR_INVALID_ARG; }
+            o += basis->n_prim[i];
+        }
+    }
+    if (mode == ESMF_MODE_DIRECT && precision >= ESMF_PREC_FP16X2) {
+        set_error("split 16-bit precisions need stored integrals");
+        return ESMF_ERR_UNSUPPORTED;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("device %d not available (%d devices)", device, ndev);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    if (!g.ok) { set_error("cudaSetDevice(%d) failed", device); return ESMF_ERR_CUDA; }
+
+    esmf_fock *h = new (std::nothrow) esmf_fock();
+    if (!h) { set_error("host allocation failed"); return ESMF_ERR_OOM; }
+    h->device = device; h->n = n; h->tol = tol; h->prec = precision;
+    h->nb = (n + BLK - 1) / BLK;
+    h->np = h->nb * BLK;
+    const int np = h->np;
+    auto fail = [&](int code) { cudaDeviceSynchronize(); cudaGetLastError(); release(h); return code; };
+    int rc;
+
+    // padded host copies
+    std::vector<double> hc((size_t)np * 3, 0.0);
+    std::vector<int> hn(np, 0), ho(np, 0);
+    std::memcpy(hc.data(), basis->center, sizeof(double) * 3 * n);
+    int64_t o = 0;
+    for (int i = 0; i < np; ++i) {
+        ho[i] = (int)o;
+        if (i < n) { hn[i] = basis->n_prim[i]; o += hn[i]; }
+    }
+    if ((rc = dalloc(h, &h->center, (size_t)np * 3)) || (rc = dalloc(h, &h->nprim, np)) ||
+        (rc = dalloc(h, &h->poff, np)) || (rc = dalloc(h, &h->exps, nprim_tot)) ||
+        (rc = dalloc(h, &h->coefs, nprim_tot)) || (rc = dalloc(h, &h->w, nprim_tot)) ||
+        (rc = dalloc(h, &h->Q, (size_t)np * np)))
+        return fail(rc);
+    cudaStream_t s = 0;
+    auto ck = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess) { set_error("%s: %s", what, cudaGetErrorString(e)); return false; }
+        return true;
+    };
+    if (!ck(cudaMemcpy(h->center, hc.data(), sizeof(double) * np * 3, cudaMemcpyHostToDevice), "copy centers") ||
+        !ck(cudaMemcpy(h->nprim, hn.data(), sizeof(int) * np, cudaMemcpyHostToDevice), "copy nprim") ||
+        !ck(cudaMemcpy(h->poff, ho.data(), sizeof(int) * np, cudaMemcpyHostToDevice), "copy poff") ||
+        !ck(cudaMemcpy(h->exps, basis->exps, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice), "copy exps") ||
+        !ck(cudaMemcpy(h->coefs, basis->coefs, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice), "copy coefs"))
+        return fail(ESMF_ERR_CUDA);
+    const DevBasis db = h->dev();
+    if ((rc = launch_normalize(db, h->coefs, h->w, s)) || (rc = launch_schwarz(db, h->Q, s))) return fail(rc);
+    std::vector<double> hQ((size_t)np * np);
+    if (!ck(cudaMemcpy(hQ.data(), h->Q, sizeof(double) * np * np, cudaMemcpyDeviceToHost), "copy Q"))
+        return fail(ESMF_ERR_CUDA);
+
+    // block-level screening: Qblk = max over the 8x8 block; brick kept iff
+    // Qblk(PQ) * Qblk(RS) >= tol (element-level screening inside the brick)
+    const int nb = h->nb;
+    std::vector<double> qblk((size_t)nb * nb, 0.0);
+    for (int p = 0; p < np; ++p)
+        for (int q = 0; q < np; ++q) {
+            double &m_ = qblk[(size_t)(p / BLK) * nb + q / BLK];
+            m_ = std::max(m_, hQ[(size_t)p * np + q]);
+        }
+    std::vector<std::pair<int, int>> bp;
+    std::vector<double> bq;
+    for (int P = 0; P < nb; ++P)
+        for (int Q = 0; Q <= P; ++Q) { bp.push_back({P, Q}); bq.push_back(qblk[(size_t)P * nb + Q]); }
+    std::vector<BrickDesc> cand;
+    for (size_t i = 0; i < bp.size(); ++i)
+        for (size_t j = 0; j <= i; ++j)
+            if (bq[i] * bq[j] >= tol) {
+                BrickDesc d;
+                d.P = (int16_t)bp[i].first; d.Q = (int16_t)bp[i].second;
+                d.R = (int16_t)bp[j].first; d.S = (int16_t)bp[j].second;
+                d.nkept = 0; d.pad = 0;
+                cand.push_back(d);
+            }
+    int64_t ncand = (int64_t)cand.size();
+    std::vector<int32_t> counts;
+    if (ncand > 0) {
+        BrickDesc *dc = nullptr;
+        int32_t *dcount = nullptr;
+        if ((rc = dalloc(h, &dc, ncand)) || (rc = dalloc(h, &dcount, 2 * ncand))) {
+            dfree(h, &dc, ncand);
+            return fail(rc);
+        }
+        counts.resize(2 * ncand);
+        bool ok = ck(cudaMemcpy(dc, cand.data(), sizeof(BrickDesc) * ncand, cudaMemcpyHostToDevice), "copy bricks");
+        if (ok) ok = (rc = launch_brick_count(db, h->Q, tol, dc, ncand, dcount, s)) == ESMF_OK;
+        if (ok) ok = ck(cudaMemcpy(counts.data(), dcount, sizeof(int32_t) * 2 * ncand, cudaMemcpyDeviceToHost), "copy counts");
+        dfree(h, &dc, ncand);
+        dfree(h, &dcount, 2 * ncand);
+        if (!ok) return fail(rc ? rc : ESMF_ERR_CUDA);
+    }
+    std::vector<BrickDesc> kept;
+    std::vector<int64_t> offs;
+    const int eb = elem_bytes(precision);
+    const int align_elems = 16 / eb;     // every brick's packed run starts on 16 bytes
+    int64_t off = 0, unique = 0;
+    for (int64_t i = 0; i < ncand; ++i) {
+        if (counts[i] == 0) continue;
+        BrickDesc d = cand[i];
+        d.nkept = counts[i];
+        kept.push_back(d);
+        offs.push_back(off);
+        off += (counts[i] + align_elems - 1) / align_elems * align_elems;
+        unique += counts[ncand + i];
+    }
+    offs.push_back(off);
+    h->nbricks = (int64_t)kept.size();
+    h->n_kept_unique = unique;
+    h->n_stored = 0;
+    for (auto &d : kept) h->n_stored += d.nkept;
+    h->store_bytes = off * eb;
+
+    int use_mode = mode;
+    if (mode == ESMF_MODE_AUTO) {
+        use_mode = (budget_bytes == 0 || h->device_bytes + h->store_bytes <= budget_bytes) ? ESMF_MODE_STORED
+                                                                                          : ESMF_MODE_DIRECT;
+        if (use_mode == ESMF_MODE_DIRECT && precision >= ESMF_PREC_FP16X2) h->prec = ESMF_PREC_FP32;
+    } else if (mode == ESMF_MODE_STORED && budget_bytes > 0 && h->device_bytes + h->store_bytes > budget_bytes) {
+        set_error("stored integrals need %lld bytes, budget %lld", (long long)h->store_bytes, (long long)budget_bytes);
+        return fail(ESMF_ERR_UNSUPPORTED);
+    }
+    h->mode = use_mode;
+    if (use_mode != ESMF_MODE_STORED) h->store_bytes = 0;
+
+    if (h->nbricks > 0) {
+        if ((rc = dalloc(h, &h->bricks, h->nbricks))) return fail(rc);
+        if (!ck(cudaMemcpy(h->bricks, kept.data(), sizeof(BrickDesc) * h->nbricks, cudaMemcpyHostToDevice), "copy kept bricks"))
+            return fail(ESMF_ERR_CUDA);
+        if (use_mode == ESMF_MODE_STORED) {
+            if ((rc = dalloc(h, &h->offsets, h->nbricks + 1))) return fail(rc);
+            if ((rc = dalloc(h, (unsigned char **)&h->store, (size_t)h->store_bytes))) return fail(rc);
+            if (h->prec >= ESMF_PREC_FP16X2 && (rc = dalloc(h, &h->scales, h->nbricks))) return fail(rc);
+            if (!ck(cudaMemcpy(h->offsets, offs.data(), sizeof(int64_t) * (h->nbricks + 1), cudaMemcpyHostToDevice), "copy offsets"))
+                return fail(ESMF_ERR_CUDA);
+            if (!ck(cudaMemset(h->store, 0, (size_t)h->store_bytes), "clear store")) return fail(ESMF_ERR_CUDA);
+            if ((rc = launch_brick_generate(db, h->Q, tol, h->bricks, h->nbricks, h->offsets, h->prec,
+                                            h->store, h->scales, s)))
+                return fail(rc);
+        }
+    }
+    if (!ck(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming), "event")) return fail(ESMF_ERR_CUDA);
+    if (!ck(cudaDeviceSynchronize(), "create kernels")) return fail(ESMF_ERR_CUDA);
+    h->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return ESMF_OK;
+}
+
+int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K, double *F,
+                    double *traces, void *stream) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    if (m < 1 || m > ESMF_MAX_DENSITIES) { set_error("m = %d outside [1, %d]", m, ESMF_MAX_DENSITIES); return ESMF_ERR_INVALID_ARG; }
+    if (!D || !J || !K) { set_error("D, J and K are required"); return ESMF_ERR_INVALID_ARG; }
+    DeviceGuard g(h->device);
+    if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
+    if (!is_device_ptr(D) || !is_device_ptr(J) || !is_device_ptr(K) || (F && !is_device_ptr(F)) ||
+        (traces && !is_device_ptr(traces))) {
+        set_error("D, J, K, F and traces must be device memory");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    RET(ensure_work(h, m));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t acc = sizeof(double) * (size_t)m * h->np * h->np;
+    CKR(cudaMemsetAsync(h->Jacc, 0, acc, s));
+    CKR(cudaMemsetAsync(h->Kacc, 0, acc, s));
+    if (traces) CKR(cudaMemsetAsync(traces, 0, sizeof(double) * m, s));
+    if (h->nbricks > 0) {
+        JKArgs a;
+        a.b = h->dev(); a.Q = h->Q; a.tol = h->tol; a.bricks = h->bricks; a.nbricks = h->nbricks;
+        a.offsets = h->offsets; a.store = h->store; a.precision = h->prec; a.mode = h->mode;
+        a.m = m; a.D = D; a.Jacc = h->Jacc; a.Kacc = h->Kacc;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->timing && h->ev_used < 65536) {
+            if (h->ev_used == h->ev_pool.size()) {
+                cudaEvent_t x, y;
+                CKR(cudaEventCreate(&x));
+                CKR(cudaEventCreate(&y));
+                h->ev_pool.push_back({x, y});
+            }
+            e0 = h->ev_pool[h->ev_used].first;
+            e1 = h->ev_pool[h->ev_used].second;
+            ++h->ev_used;
+            CKR(cudaEventRecord(e0, s));
+        }
+        if (h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2) RET(launch_jk_cuda_split(a, h->scales, s));
+        else RET(launch_jk_cuda(a, s));
+        if (e1) CKR(cudaEventRecord(e1, s));
+    }
+    RET(launch_finalize(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s));
+    return ESMF_OK;
+}
+
+int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host, double *J_host, double *K_host,
+                         double *F_host, double *traces_host, void *stream, int timeout_ms) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    if (m < 1 || m > ESMF_MAX_DENSITIES) { set_error("m = %d outside [1, %d]", m, ESMF_MAX_DENSITIES); return ESMF_ERR_INVALID_ARG; }
+    if (!D_host || !J_host || !K_host) { set_error("D, J and K are required"); return ESMF_ERR_INVALID_ARG; }
+    DeviceGuard g(h->device);
+    if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
+    const size_t mat = (size_t)h->n * h->n;
+    if (m > h->stage_m) {
+        dfree(h, &h->sD, (size_t)h->stage_m * mat); dfree(h, &h->sJ, (size_t)h->stage_m * mat);
+        dfree(h, &h->sK, (size_t)h->stage_m * mat); dfree(h, &h->sF, (size_t)h->stage_m * mat);
+        dfree(h, &h->st, (size_t)h->stage_m);
+        h->stage_m = 0;
+        RET(dalloc(h, &h->sD, m * mat)); RET(dalloc(h, &h->sJ, m * mat)); RET(dalloc(h, &h->sK, m * mat));
+        RET(dalloc(h, &h->sF, m * mat)); RET(dalloc(h, &h->st, (size_t)m));
+        h->stage_m = m;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * m * mat;
+    CKR(cudaMemcpyAsync(h->sD, D_host, bytes, cudaMemcpyHostToDevice, s));
+    RET(esmf_fock_build(h, m, h->sD, h->sJ, h->sK, F_host ? h->sF : nullptr, traces_host ? h->st : nullptr, s));
+    CKR(cudaMemcpyAsync(J_host, h->sJ, bytes, cudaMemcpyDeviceToHost, s));
+    CKR(cudaMemcpyAsync(K_host, h->sK, bytes, cudaMemcpyDeviceToHost, s));
+    if (F_host) CKR(cudaMemcpyAsync(F_host, h->sF, bytes, cudaMemcpyDeviceToHost, s));
+    if (traces_host) CKR(cudaMemcpyAsync(traces_host, h->st, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->done, s));
+    // bounded wait: poll the event, give up after timeout_ms
+    const int limit = timeout_ms > 0 ? timeout_ms : 600000;
+    const auto t0 = std::chrono::steady_clock::now();
+    int spin = 0;
+    for (;;) {
+        cudaError_t q = cudaEventQuery(h->done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) { set_error("build: %s", cudaGetErrorString(q)); return ESMF_ERR_CUDA; }
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > limit) { set_error("build did not finish within %d ms", limit); return ESMF_ERR_TIMEOUT; }
+        if (++spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    return ESMF_OK;
+}
+
+int esmf_fock_set_timing(esmf_fock_t *h, int enable) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    h->timing = enable != 0;
+    return ESMF_OK;
+}
+
+int esmf_fock_kernel_time(esmf_fock_t *h, double *ms, int64_t *launches, int reset) {
+    if (!h || !ms || !launches) { set_error("NULL argument"); return ESMF_ERR_INVALID_ARG; }
+    DeviceGuard g(h->device);
+    double tot = 0.0;
+    for (size_t i = 0; i < h->ev_used; ++i) {
+        CKR(cudaEventSynchronize(h->ev_pool[i].second));
+        float x = 0.f;
+        CKR(cudaEventElapsedTime(&x, h->ev_pool[i].first, h->ev_pool[i].second));
+        tot += x;
+    }
+    *ms = tot;
+    *launches = (int64_t)h->ev_used;
+    if (reset) h->ev_used = 0;
+    return ESMF_OK;
+}
+
+int esmf_fock_stats(const esmf_fock_t *h, esmf_stats_t *out) {
+    if (!h || !out) { set_error("NULL argument"); return ESMF_ERR_INVALID_ARG; }
+    const int64_t P = (int64_t)h->n * (h->n + 1) / 2;
+    out->n_basis = h->n;
+    out->n_pairs = P;
+    out->n_quartets_unique = P * (P + 1) / 2;
+    out->n_quartets_kept = h->n_kept_unique;
+    out->n_bricks = h->nbricks;
+    out->n_stored = h->mode == ESMF_MODE_STORED ? h->n_stored : 0;
+    out->store_bytes = h->store_bytes;
+    out->device_bytes = h->device_bytes;
+    out->mode = h->mode;
+    out->precision = h->prec;
+    out->schwarz_tol = h->tol;
+    out->create_ms = h->create_ms;
+    return ESMF_OK;
+}
+
+int esmf_fock_schwarz(const esmf_fock_t *h, double *Q_host) {
+    if (!h || !Q_host) { set_error("NULL argument"); return ESMF_ERR_INVALID_ARG; }
+    DeviceGuard g(h->device);
+    CKR(cudaMemcpy2D(Q_host, sizeof(double) * h->n, h->Q, sizeof(double) * h->np, sizeof(double) * h->n,
+                     h->n, cudaMemcpyDeviceToHost));
+    return ESMF_OK;
+}
+
+void esmf_fock_destroy(esmf_fock_t *h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    release(h);
+}
+
+}  // extern "C"

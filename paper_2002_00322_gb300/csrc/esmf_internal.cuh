@@ -1,0 +1,75 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "esmf_fock.h"
+
+namespace esmf {
+
+// Function blocks of 8: a "brick" is the 8x8x8x8 block of integrals
+// (P Q | R S) between four function blocks.  Bricks are kept in canonical
+// form P >= Q, R >= S, pair(P,Q) >= pair(R,S); a brick stores every element
+// (p q | r s) with p in P, q in Q, r in R, s in S at local index
+// ((p*8 + q)*8 + r)*8 + s, of which only the Schwarz-kept ones are stored
+// (packed, in local-index order).
+constexpr int BLK = 8;
+constexpr int BRICK = BLK * BLK * BLK * BLK;   // 4096
+constexpr int MAXP = ESMF_MAX_PRIM;
+constexpr int MAXPP = MAXP * MAXP;
+
+struct BrickDesc {          // 16 bytes
+    int16_t P, Q, R, S;     // function-block indices
+    int32_t nkept;          // kept elements
+    int32_t pad;
+};
+
+// device view of the basis: functions padded to a multiple of BLK; padded
+// functions have nprim = 0 and Q = 0 and are never kept
+struct DevBasis {
+    int n;          // real functions
+    int np;         // padded
+    int nb;         // blocks
+    const double *center;  // np x 3
+    const int *nprim;      // np
+    const int *poff;       // np
+    const double *exps;    // primitives
+    const double *w;       // normalised raw-Gaussian weights
+};
+
+void set_error(const char *fmt, ...);
+
+// ---- setup.cu
+int launch_normalize(const DevBasis &b, const double *coefs, double *w, cudaStream_t s);
+int launch_schwarz(const DevBasis &b, double *Q, cudaStream_t s);
+int launch_brick_count(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
+                       int64_t nbricks, int32_t *counts, cudaStream_t s);
+int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
+                          int64_t nbricks, const int64_t *offsets, int precision, void *store,
+                          float *scales, cudaStream_t s);
+
+// ---- jk_cuda.cu (CUDA-core contraction)
+struct JKArgs {
+    DevBasis b;
+    const double *Q;
+    double tol;
+    const BrickDesc *bricks;
+    int64_t nbricks;
+    const int64_t *offsets;   // packed-store element offsets (stored mode)
+    const void *store;
+    int precision;
+    int mode;
+    int m;
+    const double *D;          // m x n x n (caller layout)
+    double *Jacc, *Kacc;      // m x np x np accumulators (zeroed by caller)
+};
+int launch_jk_cuda(const JKArgs &a, cudaStream_t s);
+int launch_finalize(const DevBasis &b, int m, const double *D, const double *Jacc,
+                    const double *Kacc, double *J, double *K, double *F, double *tsum,
+                    cudaStream_t s);
+
+}  // namespace esmf

@@ -1,0 +1,122 @@
+// Device-side s-type integral arithmetic.
+//
+// Raw Gaussian primitives exp(-a |r - A|^2) with normalised weights w
+// (contracted function = sum_k w_k exp(-a_k |r - A|^2)); the two-electron
+// integral over four raw primitives is the textbook closed form (Boys 1950;
+// Szabo & Ostlund App. A, which the paper cites for its integral theory):
+//   p = a + b, P = (a A + b B)/p, q = c + d, Q = (c C + d D)/q,
+//   [ab|cd] = 2 pi^{5/2} / (p q sqrt(p + q)) * exp(-ab/p |AB|^2)
+//             * exp(-cd/q |CD|^2) * F0(pq/(p+q) |PQ|^2),
+// F0(T) = int_0^1 exp(-T u^2) du = (1/2) sqrt(pi/T) erf(sqrt(T)).
+// The pair factors (p, P, w_a w_b exp(-ab/p |AB|^2)) are formed once per
+// primitive pair; the quartet loop only needs T, one erf and a reciprocal
+// square root per primitive quartet.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace esmf {
+
+constexpr double kTwoPi52 = 34.986836655249725;    // 2 pi^{5/2}
+constexpr double kHalfSqrtPi = 0.88622692545275801; // sqrt(pi)/2
+
+// F0 in double: Taylor series sum_k (-T)^k/(k!(2k+1)) below 1e-6 (four terms,
+// truncation < 1e-25), erf form above; for T > 40 erf(sqrt T) = 1 to double.
+__device__ __forceinline__ double boys0_d(double T) {
+    if (T < 1e-6) return 1.0 - T * (1.0 / 3.0) + T * T * 0.1 - T * T * T * (1.0 / 42.0);
+    double x = sqrt(T);
+    if (T > 40.0) return kHalfSqrtPi / x;
+    return kHalfSqrtPi * erf(x) / x;
+}
+
+// F0 in float: series below 1e-3 (truncation < 1e-14), erf form above; for
+// T > 16 erff(sqrt T) rounds to 1.
+__device__ __forceinline__ float boys0_f(float T) {
+    if (T < 1e-3f) return 1.0f - T * (1.0f / 3.0f) + T * T * 0.1f - T * T * T * (1.0f / 42.0f);
+    float r = rsqrtf(T);
+    if (T > 16.0f) return (float)kHalfSqrtPi * r;
+    return (float)kHalfSqrtPi * erff(T * r) * r;
+}
+
+template <typename T> struct Boys;
+template <> struct Boys<double> {
+    static __device__ __forceinline__ double f0(double t) { return boys0_d(t); }
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+};
+template <> struct Boys<float> {
+    static __device__ __forceinline__ float f0(float t) { return boys0_f(t); }
+    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+};
+
+// Primitive-pair data of one function pair, structure of arrays in shared
+// memory: exponent sum p, product center P (relative to a local origin),
+// and weight K = w_a w_b exp(-ab/p |AB|^2).
+template <typename T, int NPAIR, int MAXPP_>
+struct PairSmem {
+    T pe[NPAIR][MAXPP_];
+    T px[NPAIR][MAXPP_];
+    T py[NPAIR][MAXPP_];
+    T pz[NPAIR][MAXPP_];
+    T kw[NPAIR][MAXPP_];
+    int npp[NPAIR];
+};
+
+// contracted (bra pair ib | ket pair ik) from shared pair data
+template <typename T, int NPAIR, int MAXPP_>
+__device__ __forceinline__ T contracted_eri(const PairSmem<T, NPAIR, MAXPP_> &bra, int ib,
+                                            const PairSmem<T, NPAIR, MAXPP_> &ket, int ik) {
+    T acc = T(0);
+    const int nb = bra.npp[ib], nk = ket.npp[ik];
+    for (int i = 0; i < nb; ++i) {
+        const T p = bra.pe[ib][i], Px = bra.px[ib][i], Py = bra.py[ib][i], Pz = bra.pz[ib][i];
+        const T kb = bra.kw[ib][i];
+        T part = T(0);
+        for (int k = 0; k < nk; ++k) {
+            const T q = ket.pe[ik][k];
+            const T dx = Px - ket.px[ik][k], dy = Py - ket.py[ik][k], dz = Pz - ket.pz[ik][k];
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const T pq = p * q, s = p + q;
+            const T rho = pq / s;
+            // 2 pi^{5/2} / (p q sqrt(p+q)) = 2 pi^{5/2} * rsqrt(s) / pq
+            const T pref = T(kTwoPi52) * Boys<T>::rsq(s) / pq;
+            part += ket.kw[ik][k] * pref * Boys<T>::f0(rho * r2);
+        }
+        acc += kb * part;
+    }
+    return acc;
+}
+
+// Fill pair data for the 64 ordered pairs (p, q) of function blocks (PB, QB)
+// with local origin (ox, oy, oz).  Called by all threads of a block.
+template <typename T, int MAXPP_>
+__device__ __forceinline__ void fill_pairs(PairSmem<T, 128, MAXPP_> &ps, int base, int PB, int QB,
+                                           const double *center, const int *nprim, const int *poff,
+                                           const double *exps, const double *w, int np,
+                                           double ox, double oy, double oz) {
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+        const int p = PB * 8 + (t >> 3), q = QB * 8 + (t & 7);
+        const int slot = base + t;
+        int cnt = 0;
+        if (p < np && q < np) {
+            const int np_ = nprim[p], nq_ = nprim[q];
+            const double ax = center[3 * p], ay = center[3 * p + 1], az = center[3 * p + 2];
+            const double bx = center[3 * q], by = center[3 * q + 1], bz = center[3 * q + 2];
+            const double ab2 = (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
+            for (int i = 0; i < np_; ++i)
+                for (int j = 0; j < nq_; ++j) {
+                    const double a = exps[poff[p] + i], b = exps[poff[q] + j];
+                    const double pe = a + b;
+                    const double kw = w[poff[p] + i] * w[poff[q] + j] * exp(-a * b / pe * ab2);
+                    ps.pe[slot][cnt] = (T)pe;
+                    ps.px[slot][cnt] = (T)((a * ax + b * bx) / pe - ox);
+                    ps.py[slot][cnt] = (T)((a * ay + b * by) / pe - oy);
+                    ps.pz[slot][cnt] = (T)((a * az + b * bz) / pe - oz);
+                    ps.kw[slot][cnt] = (T)kw;
+                    ++cnt;
+                }
+        }
+        ps.npp[slot] = cnt;
+    }
+}
+
+}  // namespace esmf

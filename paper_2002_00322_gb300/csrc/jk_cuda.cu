@@ -1,0 +1,300 @@
+// Grouped J/K contraction on CUDA cores (Eq. J_and_K, all m densities in one
+// pass over the integrals, Sec. II.C).
+//
+// One CTA processes one brick (P Q | R S) at a time.  The brick's kept
+// integrals are expanded into a dense 8^4 tile in shared memory (from the
+// packed store, or evaluated in place in direct mode), and every DISTINCT
+// ordered block tuple of its permutation orbit
+//   (P Q R S) (Q P R S) (P Q S R) (Q P S R) (R S P Q) (S R P Q) (R S Q P) (S R Q P)
+// contributes, for every density k,
+//   K[a][c] += sum_{b,d} (ab|cd) D_k[b][d]      (tuple (A,B,C,E), a in A ...)
+//   J[a][b] += sum_{c,d} (ab|cd) D_k[c][d]      (only tuples with A >= B)
+// which is the ordered-tuple form of Eq. J_and_K.  Each output element is a
+// 64-term dot product accumulated in registers (TA) and flushed to the FP64
+// accumulators with one atomic add per brick.  J is accumulated only on the
+// lower block triangle and mirrored by the finalisation kernel.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
+#include "esmf_internal.cuh"
+#include "integrals.cuh"
+
+namespace esmf {
+
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));                    \
+            return ESMF_ERR_CUDA;                                                  \
+        }                                                                          \
+    } while (0)
+
+__constant__ int c_tuple[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
+                                  {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
+__constant__ int c_stride[4] = {512, 64, 8, 1};
+
+__device__ __forceinline__ bool kept_e(const double *qb, const double *qk, int e, double tol, int n,
+                                       int P, int Q, int R, int S) {
+    const int p = e >> 9, q = (e >> 6) & 7, r = (e >> 3) & 7, s = e & 7;
+    if (P * 8 + p >= n || Q * 8 + q >= n || R * 8 + r >= n || S * 8 + s >= n) return false;
+    return qb[p * 8 + q] * qk[r * 8 + s] >= tol;
+}
+
+__device__ __forceinline__ int scan256(int v, int *wsum) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = (lane < 8) ? wsum[lane] : 0;
+        for (int o = 1; o < 8; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < 8) wsum[8 + lane] = w;
+    }
+    __syncthreads();
+    return ((wid > 0) ? wsum[8 + wid - 1] : 0) + x - v;
+}
+
+template <typename TA, int MC, bool DIRECT>
+struct JKSmem {
+    TA V[BRICK];
+    TA Ds[16][64][MC];
+    double qb[64], qk[64];
+    int wsum[16];
+    int active[12];
+    int blk[4];
+};
+template <typename TA, int MC>
+struct JKSmemDirect : JKSmem<TA, MC, true> {
+    PairSmem<TA, 128, MAXPP> pairs;
+};
+
+// SRC: 0 fp64 store, 1 fp32 store, 2 fp16 hi+lo, 3 bf16 hi+lo, 4 direct (evaluated in TA)
+template <typename TA, int MC, int SRC>
+__global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a, const float *scales) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    using SM = typename std::conditional<SRC == 4, JKSmemDirect<TA, MC>, JKSmem<TA, MC, false>>::type;
+    SM &sm = *reinterpret_cast<SM *>(smraw);
+    const int n = a.b.n, np = a.b.np;
+    const int64_t nn = (int64_t)n * n, npnp = (int64_t)np * np;
+
+    for (int64_t bi = blockIdx.x; bi < a.nbricks; bi += gridDim.x) {
+        const BrickDesc d = a.bricks[bi];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            sm.blk[0] = d.P; sm.blk[1] = d.Q; sm.blk[2] = d.R; sm.blk[3] = d.S;
+            const int bl[4] = {d.P, d.Q, d.R, d.S};
+            for (int t = 0; t < 8; ++t) {
+                int act = 1;
+                for (int u = 0; u < t; ++u) {
+                    bool same = true;
+                    for (int x = 0; x < 4; ++x) same &= bl[c_tuple[t][x]] == bl[c_tuple[u][x]];
+                    if (same) { act = 0; break; }
+                }
+                sm.active[t] = act;
+            }
+            sm.active[8] = sm.active[0];
+            sm.active[9] = sm.active[2];
+            sm.active[10] = sm.active[4];
+            sm.active[11] = sm.active[6];
+        }
+        if (threadIdx.x < 64) {
+            const int t = threadIdx.x;
+            sm.qb[t] = a.Q[(int64_t)(d.P * 8 + (t >> 3)) * np + d.Q * 8 + (t & 7)];
+            sm.qk[t] = a.Q[(int64_t)(d.R * 8 + (t >> 3)) * np + d.S * 8 + (t & 7)];
+        }
+        if constexpr (SRC == 4) {
+            const int o = d.P * 8;
+            const double ox = a.b.center[3 * o], oy = a.b.center[3 * o + 1], oz = a.b.center[3 * o + 2];
+            fill_pairs<TA, MAXPP>(sm.pairs, 0, d.P, d.Q, a.b.center, a.b.nprim, a.b.poff, a.b.exps,
+                                  a.b.w, np, ox, oy, oz);
+            fill_pairs<TA, MAXPP>(sm.pairs, 64, d.R, d.S, a.b.center, a.b.nprim, a.b.poff, a.b.exps,
+                                  a.b.w, np, ox, oy, oz);
+        }
+        __syncthreads();
+        // ---- dense brick tile
+        {
+            const int e0 = threadIdx.x * 16;
+            unsigned mask = 0;
+            for (int j = 0; j < 16; ++j)
+                if (kept_e(sm.qb, sm.qk, e0 + j, a.tol, n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
+            if constexpr (SRC == 4) {
+                for (int j = 0; j < 16; ++j) {
+                    const int e = e0 + j;
+                    TA v = TA(0);
+                    if (mask & (1u << j))
+                        v = contracted_eri<TA, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
+                    sm.V[e] = v;
+                }
+            } else {
+                int pos = scan256(__popc(mask), sm.wsum);
+                const int64_t base = a.offsets[bi];
+                const float inv = (SRC >= 2) ? 1.0f / scales[bi] : 1.0f;
+                for (int j = 0; j < 16; ++j) {
+                    TA v = TA(0);
+                    if (mask & (1u << j)) {
+                        const int64_t i = base + pos++;
+                        if (SRC == 0) v = (TA)reinterpret_cast<const double *>(a.store)[i];
+                        else if (SRC == 1) v = (TA)reinterpret_cast<const float *>(a.store)[i];
+                        else {
+                            const uint32_t u = reinterpret_cast<const uint32_t *>(a.store)[i];
+                            float hi, lo;
+                            if (SRC == 2) {
+                                hi = __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
+                                lo = __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+                            } else {
+                                hi = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u & 0xffffu)));
+                                lo = __bfloat162float(__ushort_as_bfloat16((unsigned short)(u >> 16)));
+                            }
+                            v = (TA)((hi + lo) * inv);
+                        }
+                    }
+                    sm.V[e0 + j] = v;
+                }
+            }
+        }
+        // ---- densities in chunks of MC
+        for (int d0 = 0; d0 < a.m; d0 += MC) {
+            __syncthreads();
+            for (int t = threadIdx.x; t < 16 * 64 * MC; t += blockDim.x) {
+                const int dd = t % MC, ij = (t / MC) & 63, ab = t / (MC * 64);
+                const int ra = sm.blk[ab >> 2] * 8 + (ij >> 3), cb = sm.blk[ab & 3] * 8 + (ij & 7);
+                TA v = TA(0);
+                if (d0 + dd < a.m && ra < n && cb < n) v = (TA)a.D[(int64_t)(d0 + dd) * nn + (int64_t)ra * n + cb];
+                sm.Ds[ab][ij][dd] = v;
+            }
+            __syncthreads();
+            for (int task = threadIdx.x; task < 12 * 64; task += blockDim.x) {
+                const int slot = task >> 6, e = task & 63;
+                if (!sm.active[slot]) continue;
+                const bool isJ = slot >= 8;
+                const int tu = isJ ? (slot - 8) * 2 : slot;
+                const int A = c_tuple[tu][0], B = c_tuple[tu][1], C = c_tuple[tu][2], E = c_tuple[tu][3];
+                int base, s1, s2, dab, orow, ocol;
+                if (!isJ) {   // output (a in A, c in C), terms (b in B, d in E)
+                    const int ia = e >> 3, ic = e & 7;
+                    base = ia * c_stride[A] + ic * c_stride[C];
+                    s1 = c_stride[B]; s2 = c_stride[E];
+                    dab = B * 4 + E;
+                    orow = sm.blk[A] * 8 + ia; ocol = sm.blk[C] * 8 + ic;
+                } else {      // output (a in A, b in B), terms (c in C, d in E)
+                    const int ia = e >> 3, ib = e & 7;
+                    base = ia * c_stride[A] + ib * c_stride[B];
+                    s1 = c_stride[C]; s2 = c_stride[E];
+                    dab = C * 4 + E;
+                    orow = sm.blk[A] * 8 + ia; ocol = sm.blk[B] * 8 + ib;
+                }
+                TA acc[MC];
+#pragma unroll
+                for (int dd = 0; dd < MC; ++dd) acc[dd] = TA(0);
+                for (int x = 0; x < 8; ++x)
+                    for (int y = 0; y < 8; ++y) {
+                        const TA v = sm.V[base + x * s1 + y * s2];
+                        const TA *dp = sm.Ds[dab][x * 8 + y];
+#pragma unroll
+                        for (int dd = 0; dd < MC; ++dd) acc[dd] += v * dp[dd];
+                    }
+                double *out = isJ ? a.Jacc : a.Kacc;
+#pragma unroll
+                for (int dd = 0; dd < MC; ++dd)
+                    if (d0 + dd < a.m) atomicAdd(out + (int64_t)(d0 + dd) * npnp + (int64_t)orow * np + ocol, (double)acc[dd]);
+            }
+        }
+    }
+}
+
+template <typename TA, int MC, int SRC>
+static int jk_launch(const JKArgs &a, const float *scales, cudaStream_t s) {
+    using SM = typename std::conditional<SRC == 4, JKSmemDirect<TA, MC>, JKSmem<TA, MC, false>>::type;
+    const size_t smem = sizeof(SM);
+    CK(cudaFuncSetAttribute(k_jk_cuda<TA, MC, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jk_cuda<TA, MC, SRC>, 256, smem));
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+    if (grid > a.nbricks) grid = a.nbricks;
+    if (grid < 1) return ESMF_OK;
+    k_jk_cuda<TA, MC, SRC><<<(int)grid, 256, smem, s>>>(a, scales);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
+int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
+    const float *scales = nullptr;
+    if (a.mode == ESMF_MODE_DIRECT) {
+        if (a.precision == ESMF_PREC_FP64) return jk_launch<double, 8, 4>(a, scales, s);
+        return jk_launch<float, 16, 4>(a, scales, s);
+    }
+    switch (a.precision) {
+        case ESMF_PREC_FP64: return jk_launch<double, 8, 0>(a, scales, s);
+        case ESMF_PREC_FP32: return jk_launch<float, 16, 1>(a, scales, s);
+        default: break;
+    }
+    set_error("launch_jk_cuda: precision %d needs the split-precision path", a.precision);
+    return ESMF_ERR_UNSUPPORTED;
+}
+
+// split-precision stores on CUDA cores (reference path for the tensor kernel)
+int launch_jk_cuda_split(const JKArgs &a, const float *scales, cudaStream_t s) {
+    if (a.precision == ESMF_PREC_FP16X2) return jk_launch<float, 16, 2>(a, scales, s);
+    if (a.precision == ESMF_PREC_BF16X2) return jk_launch<float, 16, 3>(a, scales, s);
+    set_error("launch_jk_cuda_split: bad precision %d", a.precision);
+    return ESMF_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------- finalise
+// J from the lower block triangle, F = 2J - K, t_k = sum_pq D_k[pq] F_k[pq].
+__global__ void k_finalize(int n, int np, int m, const double *D, const double *Jacc,
+                           const double *Kacc, double *J, double *K, double *F, double *tsum) {
+    const int k = blockIdx.y;
+    const int64_t nn = (int64_t)n * n, npnp = (int64_t)np * np;
+    double part = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(e / n), q = (int)(e % n);
+        const double jv = ((p >> 3) >= (q >> 3)) ? Jacc[k * npnp + (int64_t)p * np + q]
+                                                 : Jacc[k * npnp + (int64_t)q * np + p];
+        const double kv = Kacc[k * npnp + (int64_t)p * np + q];
+        const double fv = 2.0 * jv - kv;
+        J[k * nn + e] = jv;
+        K[k * nn + e] = kv;
+        if (F) F[k * nn + e] = fv;
+        part += D[k * nn + e] * fv;
+    }
+    if (tsum) {
+        __shared__ double red[8];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            atomicAdd(tsum + k, s);
+        }
+    }
+}
+
+int launch_finalize(const DevBasis &b, int m, const double *D, const double *Jacc,
+                    const double *Kacc, double *J, double *K, double *F, double *tsum,
+                    cudaStream_t s) {
+    const int64_t nn = (int64_t)b.n * b.n;
+    int gx = (int)((nn + 255) / 256);
+    if (gx > 512) gx = 512;
+    dim3 grid(gx, m);
+    k_finalize<<<grid, 256, 0, s>>>(b.n, b.np, m, D, Jacc, Kacc, J, K, F, tsum);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
+}  // namespace esmf

@@ -1,0 +1,330 @@
+// Screening set-up kernels run once per basis (Sec. II.C: the screening
+// data are formed "at the beginning of an ESMF optimization"):
+//   normalisation of the contracted s functions, the Schwarz table
+//   Q_pq = sqrt((pq|pq)) in FP64, per-brick kept-element counts, and the
+//   evaluation of every kept integral into the packed brick store.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "esmf_internal.cuh"
+#include "integrals.cuh"
+
+namespace esmf {
+
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            set_error("%s: %s", #call, cudaGetErrorString(e_));                    \
+            return ESMF_ERR_CUDA;                                                  \
+        }                                                                          \
+    } while (0)
+
+static inline int grid_for(int64_t work, int per_block, int cap = 152 * 32) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------- normalise
+// <g_k|g_l> for normalised primitives on one center is
+// (2 sqrt(a_k a_l)/(a_k + a_l))^{3/2}; phi = c sum_k d_k g_k, <phi|phi> = 1;
+// w_k = c d_k (2 a_k / pi)^{3/4} multiplies the raw exp(-a_k r^2).
+__global__ void k_normalize(int n, const int *nprim, const int *poff, const double *exps,
+                            const double *coefs, double *w) {
+    int mu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mu >= n) return;
+    const int o = poff[mu], np_ = nprim[mu];
+    double s = 0.0;
+    for (int k = 0; k < np_; ++k)
+        for (int l = 0; l < np_; ++l) {
+            const double ak = exps[o + k], al = exps[o + l];
+            const double r = 2.0 * sqrt(ak * al) / (ak + al);
+            s += coefs[o + k] * coefs[o + l] * r * sqrt(r);
+        }
+    const double c = rsqrt(s);
+    for (int k = 0; k < np_; ++k) {
+        const double t = 2.0 * exps[o + k] / 3.14159265358979323846;
+        w[o + k] = c * coefs[o + k] * sqrt(t * sqrt(t));   // t^{3/4}
+    }
+}
+
+int launch_normalize(const DevBasis &b, const double *coefs, double *w, cudaStream_t s) {
+    k_normalize<<<grid_for(b.n, 128), 128, 0, s>>>(b.n, b.nprim, b.poff, b.exps, coefs, w);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
+// ---------------------------------------------------------------- Schwarz
+// One thread per pair p >= q: (pq|pq) over all primitive quartets in FP64,
+// Q_pq = Q_qp = sqrt((pq|pq)).  Padded functions get Q = 0.
+__global__ void k_schwarz(DevBasis b, double *Q) {
+    const int64_t npair = (int64_t)b.np * (b.np + 1) / 2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npair;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int p = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((int64_t)p * (p + 1) / 2 > t) --p;
+        while ((int64_t)(p + 1) * (p + 2) / 2 <= t) ++p;
+        const int q = (int)(t - (int64_t)p * (p + 1) / 2);
+        double v = 0.0;
+        if (p < b.n && q < b.n) {
+            double pe[MAXPP], px[MAXPP], py[MAXPP], pz[MAXPP], kw[MAXPP];
+            const double ax = b.center[3 * p], ay = b.center[3 * p + 1], az = b.center[3 * p + 2];
+            const double bx = b.center[3 * q], by = b.center[3 * q + 1], bz = b.center[3 * q + 2];
+            const double ab2 = (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
+            int c = 0;
+            for (int i = 0; i < b.nprim[p]; ++i)
+                for (int j = 0; j < b.nprim[q]; ++j) {
+                    const double a = b.exps[b.poff[p] + i], bb = b.exps[b.poff[q] + j];
+                    const double e = a + bb;
+                    pe[c] = e;
+                    px[c] = (a * ax + bb * bx) / e - ax;
+                    py[c] = (a * ay + bb * by) / e - ay;
+                    pz[c] = (a * az + bb * bz) / e - az;
+                    kw[c] = b.w[b.poff[p] + i] * b.w[b.poff[q] + j] * exp(-a * bb / e * ab2);
+                    ++c;
+                }
+            for (int i = 0; i < c; ++i) {
+                double part = 0.0;
+                for (int k = 0; k < c; ++k) {
+                    const double dx = px[i] - px[k], dy = py[i] - py[k], dz = pz[i] - pz[k];
+                    const double pq = pe[i] * pe[k], sum = pe[i] + pe[k];
+                    part += kw[k] * kTwoPi52 * rsqrt(sum) / pq *
+                            boys0_d(pq / sum * (dx * dx + dy * dy + dz * dz));
+                }
+                v += kw[i] * part;
+            }
+        }
+        const double qv = sqrt(v > 0.0 ? v : 0.0);
+        Q[(int64_t)p * b.np + q] = qv;
+        Q[(int64_t)q * b.np + p] = qv;
+    }
+}
+
+int launch_schwarz(const DevBasis &b, double *Q, cudaStream_t s) {
+    const int64_t npair = (int64_t)b.np * (b.np + 1) / 2;
+    k_schwarz<<<grid_for(npair, 128), 128, 0, s>>>(b, Q);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
+// ---------------------------------------------------------------- masks
+// Element (p q | r s) of a brick is kept iff all four functions are real and
+// Q_pq * Q_rs >= tol (the same FP64 product the oracle forms).
+__device__ __forceinline__ bool elem_kept(const double *qb, const double *qk, int e, double tol,
+                                          int n, int P, int Qb, int R, int S) {
+    const int p = e >> 9, q = (e >> 6) & 7, r = (e >> 3) & 7, s = e & 7;
+    if (P * 8 + p >= n || Qb * 8 + q >= n || R * 8 + r >= n || S * 8 + s >= n) return false;
+    return qb[p * 8 + q] * qk[r * 8 + s] >= tol;
+}
+
+// An element counts once per unique quartet: among the members of its
+// 8-fold permutation orbit that lie inside this brick, the one with the
+// smallest local index is the representative.
+__device__ __forceinline__ bool elem_canonical(int e, int P, int Qb, int R, int S) {
+    const int g[4] = {P * 8 + (e >> 9), Qb * 8 + ((e >> 6) & 7), R * 8 + ((e >> 3) & 7), S * 8 + (e & 7)};
+    const int perm[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
+                            {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
+    const int blk[4] = {P, Qb, R, S};
+    for (int t = 1; t < 8; ++t) {
+        int a[4];
+        bool inside = true;
+        for (int x = 0; x < 4; ++x) {
+            a[x] = g[perm[t][x]];
+            inside &= (a[x] >> 3) == blk[x];
+        }
+        if (!inside) continue;
+        const int le = ((a[0] & 7) << 9) | ((a[1] & 7) << 6) | ((a[2] & 7) << 3) | (a[3] & 7);
+        if (le < e) return false;
+    }
+    return true;
+}
+
+__global__ void k_brick_count(DevBasis b, const double *Q, double tol, const BrickDesc *bricks,
+                              int64_t nbricks, int32_t *counts, int32_t *canon) {
+    __shared__ double qb[64], qk[64];
+    __shared__ int red[2][4];
+    for (int64_t bi = blockIdx.x; bi < nbricks; bi += gridDim.x) {
+        const BrickDesc d = bricks[bi];
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int t = threadIdx.x;
+            qb[t] = Q[(int64_t)(d.P * 8 + (t >> 3)) * b.np + d.Q * 8 + (t & 7)];
+            qk[t] = Q[(int64_t)(d.R * 8 + (t >> 3)) * b.np + d.S * 8 + (t & 7)];
+        }
+        __syncthreads();
+        int c = 0, cc = 0;
+        for (int e = threadIdx.x; e < BRICK; e += blockDim.x) {
+            if (elem_kept(qb, qk, e, tol, b.n, d.P, d.Q, d.R, d.S)) {
+                ++c;
+                cc += elem_canonical(e, d.P, d.Q, d.R, d.S);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            cc += __shfl_xor_sync(0xffffffffu, cc, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = c;
+            red[1][threadIdx.x >> 5] = cc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            counts[bi] = red[0][0] + red[0][1] + red[0][2] + red[0][3];
+            canon[bi] = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+        }
+    }
+}
+
+int launch_brick_count(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
+                       int64_t nbricks, int32_t *counts, cudaStream_t s) {
+    // counts holds 2*nbricks: kept elements, then canonical kept elements
+    k_brick_count<<<grid_for(nbricks, 1, 152 * 16), 128, 0, s>>>(b, Q, tol, bricks, nbricks, counts,
+                                                                  counts + nbricks);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
+// ---------------------------------------------------------------- generation
+// 256 threads; thread t owns the 16 consecutive local indices [16t, 16t+16).
+// A block-wide exclusive scan of the kept counts gives packed positions.
+__device__ __forceinline__ int block_excl_scan256(int v, int *wsum, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = (lane < 8) ? wsum[lane] : 0;
+        for (int o = 1; o < 8; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < 8) wsum[8 + lane] = w;   // inclusive warp prefix
+    }
+    __syncthreads();
+    const int before = (wid > 0) ? wsum[8 + wid - 1] : 0;
+    total = wsum[15];
+    return before + x - v;
+}
+
+template <typename T>
+struct GenSmem {
+    PairSmem<T, 128, MAXPP> pairs;
+    double qb[64], qk[64];
+    int wsum[16];
+    float wmax[8];
+};
+
+// precision: 0 FP64 store (T = double), 1 FP32 store, 2 FP16 hi+lo, 3 BF16 hi+lo
+template <typename T, int PREC>
+__global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double *Q, double tol,
+                                                        const BrickDesc *bricks, int64_t nbricks,
+                                                        const int64_t *offsets, void *store,
+                                                        float *scales) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    GenSmem<T> &sm = *reinterpret_cast<GenSmem<T> *>(smraw);
+    for (int64_t bi = blockIdx.x; bi < nbricks; bi += gridDim.x) {
+        const BrickDesc d = bricks[bi];
+        __syncthreads();
+        // local origin: center of the first function of block P (keeps FP32
+        // coordinate differences small)
+        const int o = d.P * 8;
+        const double ox = b.center[3 * o], oy = b.center[3 * o + 1], oz = b.center[3 * o + 2];
+        fill_pairs<T, MAXPP>(sm.pairs, 0, d.P, d.Q, b.center, b.nprim, b.poff, b.exps, b.w, b.np,
+                             ox, oy, oz);
+        fill_pairs<T, MAXPP>(sm.pairs, 64, d.R, d.S, b.center, b.nprim, b.poff, b.exps, b.w, b.np,
+                             ox, oy, oz);
+        if (threadIdx.x < 64) {
+            const int t = threadIdx.x;
+            sm.qb[t] = Q[(int64_t)(d.P * 8 + (t >> 3)) * b.np + d.Q * 8 + (t & 7)];
+            sm.qk[t] = Q[(int64_t)(d.R * 8 + (t >> 3)) * b.np + d.S * 8 + (t & 7)];
+        }
+        __syncthreads();
+        const int e0 = threadIdx.x * 16;
+        unsigned mask = 0;
+        for (int j = 0; j < 16; ++j)
+            if (elem_kept(sm.qb, sm.qk, e0 + j, tol, b.n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
+        int total;
+        int pos = block_excl_scan256(__popc(mask), sm.wsum, total);
+        T vals[16];
+        float amax = 0.f;
+        for (int j = 0; j < 16; ++j) {
+            T v = T(0);
+            if (mask & (1u << j)) {
+                const int e = e0 + j;
+                v = contracted_eri<T, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
+            }
+            vals[j] = v;
+            amax = fmaxf(amax, fabsf((float)v));
+        }
+        const int64_t base = offsets[bi];
+        if (PREC == 0 || PREC == 1) {
+            T *out = reinterpret_cast<T *>(store) + base;
+            for (int j = 0; j < 16; ++j)
+                if (mask & (1u << j)) out[pos++] = vals[j];
+        } else {
+            // per-brick power-of-two scale: largest |x| * scale in [2^14, 2^15)
+            for (int off = 16; off > 0; off >>= 1)
+                amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+            if ((threadIdx.x & 31) == 0) sm.wmax[threadIdx.x >> 5] = amax;
+            __syncthreads();
+            float bm = 0.f;
+            for (int w = 0; w < 8; ++w) bm = fmaxf(bm, sm.wmax[w]);
+            int ex = 0;
+            if (bm > 0.f) { frexpf(bm, &ex); }   // bm in [2^(ex-1), 2^ex)
+            const float scale = (bm > 0.f) ? ldexpf(1.0f, 15 - ex) : 1.0f;
+            if (threadIdx.x == 0) scales[bi] = scale;
+            uint32_t *out = reinterpret_cast<uint32_t *>(store) + base;
+            for (int j = 0; j < 16; ++j)
+                if (mask & (1u << j)) {
+                    const double xs = (double)vals[j] * (double)scale;
+                    uint16_t hb, lb;
+                    if (PREC == 2) {
+                        __half h = __double2half(xs);
+                        __half l = __double2half(xs - (double)__half2float(h));
+                        hb = __half_as_ushort(h);
+                        lb = __half_as_ushort(l);
+                    } else {
+                        __nv_bfloat16 h = __double2bfloat16(xs);
+                        __nv_bfloat16 l = __double2bfloat16(xs - (double)__bfloat162float(h));
+                        hb = __bfloat16_as_ushort(h);
+                        lb = __bfloat16_as_ushort(l);
+                    }
+                    out[pos++] = (uint32_t)hb | ((uint32_t)lb << 16);
+                }
+        }
+    }
+}
+
+template <typename T, int PREC>
+static int gen_launch(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
+                      int64_t nbricks, const int64_t *offsets, void *store, float *scales,
+                      cudaStream_t s) {
+    const size_t smem = sizeof(GenSmem<T>);
+    CK(cudaFuncSetAttribute(k_brick_generate<T, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+    k_brick_generate<T, PREC><<<grid_for(nbricks, 1, 152 * 4), 256, smem, s>>>(
+        b, Q, tol, bricks, nbricks, offsets, store, scales);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
+int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
+                          int64_t nbricks, const int64_t *offsets, int precision, void *store,
+                          float *scales, cudaStream_t s) {
+    switch (precision) {
+        case ESMF_PREC_FP64: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
+        case ESMF_PREC_FP32: return gen_launch<float, 1>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
+        case ESMF_PREC_FP16X2: return gen_launch<float, 2>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
+        case ESMF_PREC_BF16X2: return gen_launch<float, 3>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
+    }
+    set_error("unknown precision %d", precision);
+    return ESMF_ERR_INVALID_ARG;
+}
+
+}  // namespace esmf

@@ -1,0 +1,246 @@
+"""Python binding of the C ABI in include/esmf_fock.h (ctypes).
+
+Argument marshalling only: every step of the build runs in the CUDA library.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if the
+compiled library is missing or a CUDA device is absent, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libesmf_fock.so")
+
+ESMF_OK = 0
+ESMF_ERR_INVALID_ARG = -1
+ESMF_ERR_OOM = -2
+ESMF_ERR_CUDA = -3
+ESMF_ERR_TIMEOUT = -4
+ESMF_ERR_UNSUPPORTED = -5
+
+MODES = {"stored": 0, "direct": 1, "auto": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16x2": 2, "bf16x2": 3}
+MAX_PRIM = 4
+
+# every symbol include/esmf_fock.h declares
+EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_fock_stats",
+           "esmf_fock_schwarz", "esmf_fock_destroy", "esmf_strerror", "esmf_last_error",
+           "esmf_fock_set_timing", "esmf_fock_kernel_time"]
+
+
+class EsmfError(RuntimeError):
+    def __init__(self, code, where, detail):
+        super().__init__(f"{where}: status {code} ({detail})")
+        self.code = code
+
+
+class esmf_basis_t(C.Structure):
+    _fields_ = [("n_basis", C.c_int32), ("center", C.POINTER(C.c_double)),
+                ("n_prim", C.POINTER(C.c_int32)), ("exps", C.POINTER(C.c_double)),
+                ("coefs", C.POINTER(C.c_double))]
+
+
+class esmf_stats_t(C.Structure):
+    _fields_ = [("n_basis", C.c_int64), ("n_pairs", C.c_int64), ("n_quartets_unique", C.c_int64),
+                ("n_quartets_kept", C.c_int64), ("n_bricks", C.c_int64), ("n_stored", C.c_int64),
+                ("store_bytes", C.c_int64), ("device_bytes", C.c_int64), ("mode", C.c_int32),
+                ("precision", C.c_int32), ("schwarz_tol", C.c_double), ("create_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path=None):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+        L = C.CDLL(p)
+        vp = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        L.esmf_fock_create.argtypes = [C.POINTER(esmf_basis_t), C.c_double, C.c_int, C.c_int, C.c_int,
+                                       C.c_int64, C.POINTER(vp)]
+        L.esmf_fock_create.restype = C.c_int
+        L.esmf_fock_build.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
+        L.esmf_fock_build.restype = C.c_int
+        L.esmf_fock_build_host.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, C.c_int]
+        L.esmf_fock_build_host.restype = C.c_int
+        L.esmf_fock_stats.argtypes = [vp, C.POINTER(esmf_stats_t)]
+        L.esmf_fock_stats.restype = C.c_int
+        L.esmf_fock_schwarz.argtypes = [vp, dp]
+        L.esmf_fock_schwarz.restype = C.c_int
+        L.esmf_fock_set_timing.argtypes = [vp, C.c_int]
+        L.esmf_fock_set_timing.restype = C.c_int
+        L.esmf_fock_kernel_time.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int]
+        L.esmf_fock_kernel_time.restype = C.c_int
+        L.esmf_fock_destroy.argtypes = [vp]
+        L.esmf_fock_destroy.restype = None
+        L.esmf_strerror.argtypes = [C.c_int]
+        L.esmf_strerror.restype = C.c_char_p
+        L.esmf_last_error.argtypes = []
+        L.esmf_last_error.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def _check(rc, where):
+    if rc != ESMF_OK:
+        L = load()
+        raise EsmfError(rc, where, L.esmf_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------- C-ABI names
+def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0):
+    """Returns an opaque handle (c_void_p); see include/esmf_fock.h."""
+    L = load()
+    center = np.ascontiguousarray(basis.center, dtype=np.float64)
+    nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)
+    exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
+    coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
+    b = esmf_basis_t(int(center.shape[0]), center.ctypes.data_as(C.POINTER(C.c_double)),
+                     nprim.ctypes.data_as(C.POINTER(C.c_int32)),
+                     exps.ctypes.data_as(C.POINTER(C.c_double)),
+                     coefs.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = L.esmf_fock_create(C.byref(b), float(schwarz_tol), m, p, int(device), int(budget_bytes), C.byref(h))
+    _check(rc, "esmf_fock_create")
+    return h
+
+
+def esmf_fock_build(h, m, D, J, K, F=None, traces=None, stream=None):
+    rc = load().esmf_fock_build(h, int(m), _ptr(D), _ptr(J), _ptr(K), _ptr(F), _ptr(traces),
+                                _stream_ptr(stream))
+    _check(rc, "esmf_fock_build")
+
+
+def esmf_fock_build_host(h, m, D, J, K, F=None, traces=None, stream=None, timeout_ms=0):
+    """Host buffers: numpy arrays or (pinned) CPU torch tensors."""
+    def hp(x):
+        if x is None:
+            return None
+        if isinstance(x, np.ndarray):
+            return C.c_void_p(x.ctypes.data)
+        return C.c_void_p(x.data_ptr())
+    rc = load().esmf_fock_build_host(h, int(m), hp(D), hp(J), hp(K), hp(F), hp(traces),
+                                     _stream_ptr(stream), int(timeout_ms))
+    _check(rc, "esmf_fock_build_host")
+
+
+def esmf_fock_stats(h):
+    st = esmf_stats_t()
+    _check(load().esmf_fock_stats(h, C.byref(st)), "esmf_fock_stats")
+    return st.as_dict()
+
+
+def esmf_fock_schwarz(h, n):
+    Q = np.zeros((n, n))
+    _check(load().esmf_fock_schwarz(h, Q.ctypes.data_as(C.POINTER(C.c_double))), "esmf_fock_schwarz")
+    return Q
+
+
+def esmf_fock_set_timing(h, enable):
+    _check(load().esmf_fock_set_timing(h, int(bool(enable))), "esmf_fock_set_timing")
+
+
+def esmf_fock_kernel_time(h, reset=True):
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(load().esmf_fock_kernel_time(h, C.byref(ms), C.byref(n), int(bool(reset))),
+           "esmf_fock_kernel_time")
+    return ms.value, n.value
+
+
+def esmf_fock_destroy(h):
+    if h:
+        load().esmf_fock_destroy(h)
+
+
+def esmf_strerror(code):
+    return load().esmf_strerror(int(code)).decode()
+
+
+def esmf_last_error():
+    return load().esmf_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------- convenience
+class FockBuilder:
+    """Owns one handle; D, J, K are torch float64 CUDA tensors (m, N, N)."""
+
+    def __init__(self, basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("FockBuilder needs a CUDA device")
+        self.n = int(basis.center.shape[0])
+        self.device = int(device)
+        self.h = esmf_fock_create(basis, schwarz_tol, mode, precision, device, budget_bytes)
+
+    def stats(self):
+        return esmf_fock_stats(self.h)
+
+    def schwarz(self):
+        return esmf_fock_schwarz(self.h, self.n)
+
+    def build(self, D, J=None, K=None, F=None, traces=None, want_F=False, want_traces=True, stream=None):
+        import torch
+        if D.dtype != torch.float64 or not D.is_cuda or D.dim() != 3 or D.shape[1:] != (self.n, self.n):
+            raise ValueError("D must be a CUDA float64 tensor of shape (m, N, N)")
+        D = D.contiguous()
+        m = D.shape[0]
+        J = torch.empty_like(D) if J is None else J
+        K = torch.empty_like(D) if K is None else K
+        if want_F and F is None:
+            F = torch.empty_like(D)
+        if want_traces and traces is None:
+            traces = torch.empty(m, dtype=torch.float64, device=D.device)
+        esmf_fock_build(self.h, m, D, J, K, F, traces, stream)
+        return J, K, F, traces
+
+    def build_host(self, D, J=None, K=None, traces=None, stream=None, timeout_ms=0):
+        m = D.shape[0]
+        J = np.empty_like(D) if J is None else J
+        K = np.empty_like(D) if K is None else K
+        esmf_fock_build_host(self.h, m, D, J, K, None, traces, stream, timeout_ms)
+        return J, K, traces
+
+    def close(self):
+        if getattr(self, "h", None):
+            esmf_fock_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

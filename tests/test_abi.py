@@ -1,0 +1,93 @@
+"""C-ABI checks that need no GPU: the library builds, loads, and exports
+every entry point include/*.h declares; argument errors that are caught on
+the host before any CUDA call come back as status codes."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        txt = open(os.path.join(inc, f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(esmf_\w+)\s*\(", txt, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_00322_gb300 import build as b
+    from paper_2002_00322_gb300 import fock
+    b.build()
+    return fock.load()
+
+
+def test_header_lists_the_entry_points():
+    names = declared_functions()
+    from paper_2002_00322_gb300 import fock
+    assert set(fock.EXPORTS) <= set(names)
+    assert "esmf_fock_create" in names and "esmf_fock_build" in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_strerror_and_host_side_argument_errors(lib):
+    from paper_2002_00322_gb300 import fock
+    assert fock.esmf_strerror(0) == "ok"
+    assert fock.esmf_strerror(fock.ESMF_ERR_TIMEOUT) == "timed out"
+    h = C.c_void_p()
+    # NULL basis / NULL out are rejected before touching CUDA
+    assert lib.esmf_fock_create(None, 0.0, 0, 0, 0, 0, C.byref(h)) == fock.ESMF_ERR_INVALID_ARG
+    b = fock.esmf_basis_t(0, None, None, None, None)
+    assert lib.esmf_fock_create(C.byref(b), 0.0, 0, 0, 0, 0, None) == fock.ESMF_ERR_INVALID_ARG
+    assert lib.esmf_fock_build(None, 1, None, None, None, None, None, None) == fock.ESMF_ERR_INVALID_ARG
+    st = fock.esmf_stats_t()
+    assert lib.esmf_fock_stats(None, C.byref(st)) == fock.ESMF_ERR_INVALID_ARG
+    lib.esmf_fock_destroy(None)
+
+
+@pytest.mark.parametrize("bad", ["exp", "nprim", "coef", "tol", "mode", "prec", "direct16"])
+def test_invalid_basis_rejected(lib, bad):
+    from paper_2002_00322_gb300 import fock
+    from paper_2002_00322_gb300 import workloads as W
+    w = W.small_random(6, 1, 1)
+    b = w.basis
+    exps, nprim, coefs = b.exps.copy(), b.nprim.copy(), b.coefs.copy()
+    tol, mode, prec = 0.0, 0, 0
+    if bad == "exp":
+        exps[2] = -1.0
+    elif bad == "nprim":
+        nprim[1] = fock.MAX_PRIM + 1
+    elif bad == "coef":
+        coefs[0] = np.nan
+    elif bad == "tol":
+        tol = -1.0
+    elif bad == "mode":
+        mode = 7
+    elif bad == "prec":
+        prec = 9
+    elif bad == "direct16":
+        mode, prec = 1, 2
+    center = np.ascontiguousarray(b.center)
+    cb = fock.esmf_basis_t(b.n, center.ctypes.data_as(C.POINTER(C.c_double)),
+                           nprim.ctypes.data_as(C.POINTER(C.c_int32)),
+                           exps.ctypes.data_as(C.POINTER(C.c_double)),
+                           coefs.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    rc = lib.esmf_fock_create(C.byref(cb), tol, mode, prec, 0, 0, C.byref(h))
+    expect = fock.ESMF_ERR_UNSUPPORTED if bad == "direct16" else fock.ESMF_ERR_INVALID_ARG
+    assert rc == expect, (bad, rc, fock.esmf_last_error())
+    assert not h.value

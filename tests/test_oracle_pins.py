@@ -128,7 +128,10 @@ def test_cauchy_schwarz_bound(tiny):
     Q = o.Q
     bound = Q[:, :, None, None] * Q[None, None, :, :]
     assert np.all(np.abs(E) <= bound * (1 + 1e-12) + 1e-300)
-    assert np.allclose(Q, Q.T, rtol=1e-14, atol=0)
+    assert np.array_equal(Q, Q.T)
+    assert np.allclose(np.diag(Q) ** 2, np.einsum('pppp->p', E), rtol=1e-13)
+    i, j = 3, 17
+    assert abs(Q[i, j] ** 2 - E[i, j, i, j]) <= 1e-13 * E[i, j, i, j]
 
 
 # ------------------------------------------------------------- J / K
