@@ -158,6 +158,32 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host,
 int esmf_fock_set_timing(esmf_fock_t *h, int enable);
 int esmf_fock_kernel_time(esmf_fock_t *h, double *ms, int64_t *launches, int reset);
 
+/*
+ * esmf_fock_build_noalloc -- the build of esmf_fock_build for callers that
+ * must not allocate device memory while they build: the host application
+ * owns every device allocation through its own pool or fixed memory plan, or
+ * the caller sits on a latency-critical path where cudaMalloc / cudaFree would
+ * synchronise the device and stall unrelated streams.  The paper has no
+ * counterpart; it is a property of this library's memory handling only.
+ *
+ * Same arguments, results and asynchrony as esmf_fock_build.  The FP64 J/K
+ * accumulators are taken from one static device array of
+ * ESMF_NOALLOC_MAX_SCRATCH_DOUBLES doubles (32 MiB) that the library holds on
+ * every device it is loaded on until the process exits; nothing is allocated
+ * by this call.  It needs 2 * m * Np^2 doubles, Np = N rounded up to a
+ * multiple of 8; larger requests are rejected with ESMF_ERR_INVALID_ARG.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  Every call clears and reuses the one array, so
+ * calls through this entry point must not overlap on the GPU (one stream, or
+ * synchronise in between); overlapping calls race and give wrong sums.
+ * The handle itself comes from esmf_fock_create as usual.
+ * Errors: INVALID_ARG (including the size limit), CUDA.
+ */
+#define ESMF_NOALLOC_MAX_SCRATCH_DOUBLES 4194304
+int esmf_fock_build_noalloc(esmf_fock_t *h, int m, const double *D, double *J,
+                            double *K, double *F, double *traces, void *stream);
+
 /* Statistics of a handle (host struct filled in).  Errors: INVALID_ARG. */
 int esmf_fock_stats(const esmf_fock_t *h, esmf_stats_t *out);
 

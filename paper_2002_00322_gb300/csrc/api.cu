@@ -26,8 +26,6 @@ void set_error(const char *fmt, ...) {
     va_end(ap);
 }
 
-int launch_jk_cuda_split(const JKArgs &a, const float *scales, cudaStream_t s);
-
 }  // namespace esmf
 
 using namespace esmf;
@@ -516,3 +514,20 @@ void esmf_fock_destroy(esmf_fock_t *h) {
 }
 
 }  // extern "C"
+
+namespace esmf {
+
+// Fills the contraction arguments of handle h for m densities D without
+// touching its work memory (the caller supplies the accumulators).
+int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, int *device,
+                           const float **scales, bool *split) {
+    a->b = h->dev(); a->Q = h->Q; a->tol = h->tol; a->bricks = h->bricks; a->nbricks = h->nbricks;
+    a->offsets = h->offsets; a->store = h->store; a->precision = h->prec; a->mode = h->mode;
+    a->m = m; a->D = D; a->Jacc = nullptr; a->Kacc = nullptr;
+    *device = h->device;
+    *scales = h->scales;
+    *split = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
+    return ESMF_OK;
+}
+
+}  // namespace esmf

@@ -68,6 +68,7 @@ struct JKArgs {
     double *Jacc, *Kacc;      // m x np x np accumulators (zeroed by caller)
 };
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s);
+int launch_jk_cuda_split(const JKArgs &a, const float *scales, cudaStream_t s);
 int launch_finalize(const DevBasis &b, int m, const double *D, const double *Jacc,
                     const double *Kacc, double *J, double *K, double *F, double *tsum,
                     cudaStream_t s);

@@ -29,7 +29,8 @@ MAX_PRIM = 4
 # every symbol include/esmf_fock.h declares
 EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_fock_stats",
            "esmf_fock_schwarz", "esmf_fock_destroy", "esmf_strerror", "esmf_last_error",
-           "esmf_fock_set_timing", "esmf_fock_kernel_time"]
+           "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc"]
+NOALLOC_MAX_SCRATCH_DOUBLES = 4194304
 
 
 class EsmfError(RuntimeError):
@@ -75,6 +76,8 @@ def load(path=None):
         L.esmf_fock_create.restype = C.c_int
         L.esmf_fock_build.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         L.esmf_fock_build.restype = C.c_int
+        L.esmf_fock_build_noalloc.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
+        L.esmf_fock_build_noalloc.restype = C.c_int
         L.esmf_fock_build_host.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, C.c_int]
         L.esmf_fock_build_host.restype = C.c_int
         L.esmf_fock_stats.argtypes = [vp, C.POINTER(esmf_stats_t)]
@@ -136,6 +139,14 @@ def esmf_fock_build(h, m, D, J, K, F=None, traces=None, stream=None):
     rc = load().esmf_fock_build(h, int(m), _ptr(D), _ptr(J), _ptr(K), _ptr(F), _ptr(traces),
                                 _stream_ptr(stream))
     _check(rc, "esmf_fock_build")
+
+
+def esmf_fock_build_noalloc(h, m, D, J, K, F=None, traces=None, stream=None):
+    """The build for callers that cannot allocate device memory: accumulators
+    come from the library's static device array (see include/esmf_fock.h)."""
+    rc = load().esmf_fock_build_noalloc(h, int(m), _ptr(D), _ptr(J), _ptr(K), _ptr(F), _ptr(traces),
+                                        _stream_ptr(stream))
+    _check(rc, "esmf_fock_build_noalloc")
 
 
 def esmf_fock_build_host(h, m, D, J, K, F=None, traces=None, stream=None, timeout_ms=0):
