@@ -148,6 +148,25 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host,
                          double *traces_host, void *stream, int timeout_ms);
 
 /*
+ * Contraction kernel choice for split 16-bit stores (FP16X2 / BF16X2):
+ * ESMF_PATH_AUTO uses the tensor-core kernel, ESMF_PATH_CUDA_CORE the
+ * CUDA-core kernel (same results within rounding; kept as a cross-check).
+ * Other precisions always use the CUDA-core kernels.  Errors: INVALID_ARG.
+ */
+#define ESMF_PATH_AUTO       0
+#define ESMF_PATH_CUDA_CORE  1
+int esmf_fock_set_path(esmf_fock_t *h, int path);
+
+/*
+ * Device-side error flag of the handle: non-zero when a bounded wait inside
+ * the tensor-core kernel expired (its results are then incomplete).  Read it
+ * after the build has completed (stream synchronised); reset != 0 clears it.
+ * esmf_fock_build_host checks it itself and returns ESMF_ERR_TIMEOUT.
+ * Returns the flag (>= 0) or INVALID_ARG.
+ */
+int esmf_fock_device_error(esmf_fock_t *h, int reset);
+
+/*
  * Kernel timing (measurement aid).  With timing enabled, each build records a
  * pair of CUDA events on its stream around its grouped contraction kernel
  * (the dominant kernel).  esmf_fock_kernel_time waits for the recorded

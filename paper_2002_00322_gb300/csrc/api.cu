@@ -44,7 +44,13 @@ struct esmf_fock {
     int64_t nbricks = 0;
     int64_t *offsets = nullptr;
     void *store = nullptr;
-    float *scales = nullptr;
+    float vscale = 1.0f;           // power-of-two scale of split 16-bit stores
+    int path = ESMF_PATH_AUTO;
+    int num_sms = 0;
+    // tensor-core path work memory
+    uint16_t *kbank = nullptr, *jbank = nullptr;
+    unsigned int *dmax = nullptr;
+    int *err_host = nullptr, *err_dev = nullptr;   // mapped page-locked flag
     int64_t n_stored = 0, store_bytes = 0, n_kept_unique = 0;
     // work (device)
     double *Jacc = nullptr, *Kacc = nullptr;
@@ -125,7 +131,9 @@ void release(esmf_fock *h) {
     if (!h) return;
     cudaFree(h->center); cudaFree(h->exps); cudaFree(h->w); cudaFree(h->coefs);
     cudaFree(h->nprim); cudaFree(h->poff); cudaFree(h->Q);
-    cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->scales);
+    cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store);
+    cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
+    if (h->err_host) cudaFreeHost(h->err_host);
     cudaFree(h->Jacc); cudaFree(h->Kacc);
     cudaFree(h->sD); cudaFree(h->sJ); cudaFree(h->sK); cudaFree(h->sF); cudaFree(h->st);
     if (h->done) cudaEventDestroy(h->done);
@@ -153,6 +161,11 @@ bool is_device_ptr(const void *p) {
 }
 
 int ensure_work(esmf_fock *h, int m) {
+    if (h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2 && !h->kbank) {
+        RET(dalloc(h, (unsigned char **)&h->kbank, umma_kbank_bytes(h->nb)));
+        RET(dalloc(h, (unsigned char **)&h->jbank, umma_jbank_bytes(h->nb)));
+        RET(dalloc(h, &h->dmax, 1));
+    }
     if (m <= h->work_m) return ESMF_OK;
     const size_t cnt = (size_t)m * h->np * h->np;
     dfree(h, &h->Jacc, (size_t)h->work_m * h->np * h->np);
@@ -320,7 +333,9 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     std::vector<BrickDesc> kept;
     std::vector<int64_t> offs;
     const int eb = elem_bytes(precision);
-    const int align_elems = 16 / eb;     // every brick's packed run starts on 16 bytes
+    const int align_elems = 16 / eb;     // every brick's record starts on 16 bytes
+    const bool split16 = precision >= ESMF_PREC_FP16X2;
+    const int head = split16 ? MASK_WORDS : 0;   // keep mask ahead of the values
     int64_t off = 0, unique = 0;
     for (int64_t i = 0; i < ncand; ++i) {
         if (counts[i] == 0) continue;
@@ -328,10 +343,31 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
         d.nkept = counts[i];
         kept.push_back(d);
         offs.push_back(off);
-        off += (counts[i] + align_elems - 1) / align_elems * align_elems;
+        off += (head + counts[i] + align_elems - 1) / align_elems * align_elems;
         unique += counts[ncand + i];
     }
     offs.push_back(off);
+    // runs of bricks sharing (P, Q, R); the brick (P Q | P Q) is a run of its own
+    {
+        auto diag = [&](size_t i) { return kept[i].R == kept[i].P && kept[i].S == kept[i].Q; };
+        auto same = [&](size_t i, size_t j) {
+            return kept[i].P == kept[j].P && kept[i].Q == kept[j].Q && kept[i].R == kept[j].R;
+        };
+        for (size_t i = 0; i < kept.size(); ++i) {
+            const bool first = i == 0 || !same(i, i - 1) || diag(i) || diag(i - 1);
+            const bool last = i + 1 == kept.size() || !same(i, i + 1) || diag(i) || diag(i + 1);
+            kept[i].pad = (first ? 1 : 0) | (last ? 2 : 0);
+        }
+    }
+    // split 16-bit stores: one power-of-two scale with |value * scale| < 2^14
+    // (Cauchy-Schwarz: |(pq|rs)| <= Q_pq Q_rs <= max Q^2)
+    if (split16) {
+        double qmax = 0.0;
+        for (double x : hQ) qmax = std::max(qmax, x);
+        int e = 0;
+        if (qmax > 0.0) std::frexp(qmax * qmax, &e);
+        h->vscale = qmax > 0.0 ? (float)std::ldexp(1.0, 14 - e) : 1.0f;
+    }
     h->nbricks = (int64_t)kept.size();
     h->n_kept_unique = unique;
     h->n_stored = 0;
@@ -357,16 +393,21 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
         if (use_mode == ESMF_MODE_STORED) {
             if ((rc = dalloc(h, &h->offsets, h->nbricks + 1))) return fail(rc);
             if ((rc = dalloc(h, (unsigned char **)&h->store, (size_t)h->store_bytes))) return fail(rc);
-            if (h->prec >= ESMF_PREC_FP16X2 && (rc = dalloc(h, &h->scales, h->nbricks))) return fail(rc);
             if (!ck(cudaMemcpy(h->offsets, offs.data(), sizeof(int64_t) * (h->nbricks + 1), cudaMemcpyHostToDevice), "copy offsets"))
                 return fail(ESMF_ERR_CUDA);
             if (!ck(cudaMemset(h->store, 0, (size_t)h->store_bytes), "clear store")) return fail(ESMF_ERR_CUDA);
             if ((rc = launch_brick_generate(db, h->Q, tol, h->bricks, h->nbricks, h->offsets, h->prec,
-                                            h->store, h->scales, s)))
+                                            h->store, h->vscale, s)))
                 return fail(rc);
         }
     }
     if (!ck(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming), "event")) return fail(ESMF_ERR_CUDA);
+    if (!ck(cudaHostAlloc((void **)&h->err_host, sizeof(int), cudaHostAllocMapped), "error flag") ||
+        !ck(cudaHostGetDevicePointer((void **)&h->err_dev, h->err_host, 0), "error flag address"))
+        return fail(ESMF_ERR_CUDA);
+    *h->err_host = 0;
+    if (!ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count"))
+        return fail(ESMF_ERR_CUDA);
     if (!ck(cudaDeviceSynchronize(), "create kernels")) return fail(ESMF_ERR_CUDA);
     h->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h;
@@ -409,8 +450,21 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
             ++h->ev_used;
             CKR(cudaEventRecord(e0, s));
         }
-        if (h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2) RET(launch_jk_cuda_split(a, h->scales, s));
-        else RET(launch_jk_cuda(a, s));
+        a.vscale = h->vscale;
+        const bool split16 = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
+        if (split16 && h->path != ESMF_PATH_CUDA_CORE) {
+            UmmaLaunch L;
+            L.bricks = h->bricks; L.nbricks = h->nbricks; L.offsets = h->offsets;
+            L.store = (const uint32_t *)h->store; L.kbank = h->kbank; L.jbank = h->jbank;
+            L.dmax_bits = h->dmax; L.D = D; L.n = h->n; L.np = h->np; L.nb = h->nb; L.m = m;
+            L.bf16 = h->prec == ESMF_PREC_BF16X2; L.num_sms = h->num_sms; L.vscale = h->vscale;
+            L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev;
+            RET(launch_jk_umma(L, s));
+        } else if (split16) {
+            RET(launch_jk_cuda_split(a, s));
+        } else {
+            RET(launch_jk_cuda(a, s));
+        }
         if (e1) CKR(cudaEventRecord(e1, s));
     }
     RET(launch_finalize(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s));
@@ -455,7 +509,24 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host, double *J_
         if (ms > limit) { set_error("build did not finish within %d ms", limit); return ESMF_ERR_TIMEOUT; }
         if (++spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    if (*(volatile int *)h->err_host) {
+        set_error("a bounded wait inside the contraction kernel expired (code %d)", *(volatile int *)h->err_host);
+        return ESMF_ERR_TIMEOUT;
+    }
     return ESMF_OK;
+}
+
+int esmf_fock_set_path(esmf_fock_t *h, int path) {
+    if (!h || path < ESMF_PATH_AUTO || path > ESMF_PATH_CUDA_CORE) { set_error("bad handle or path"); return ESMF_ERR_INVALID_ARG; }
+    h->path = path;
+    return ESMF_OK;
+}
+
+int esmf_fock_device_error(esmf_fock_t *h, int reset) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    const int v = *(volatile int *)h->err_host;
+    if (reset) *(volatile int *)h->err_host = 0;
+    return v;
 }
 
 int esmf_fock_set_timing(esmf_fock_t *h, int enable) {
@@ -520,12 +591,12 @@ namespace esmf {
 // Fills the contraction arguments of handle h for m densities D without
 // touching its work memory (the caller supplies the accumulators).
 int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, int *device,
-                           const float **scales, bool *split) {
+                           bool *split) {
     a->b = h->dev(); a->Q = h->Q; a->tol = h->tol; a->bricks = h->bricks; a->nbricks = h->nbricks;
     a->offsets = h->offsets; a->store = h->store; a->precision = h->prec; a->mode = h->mode;
     a->m = m; a->D = D; a->Jacc = nullptr; a->Kacc = nullptr;
+    a->vscale = h->vscale;
     *device = h->device;
-    *scales = h->scales;
     *split = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
     return ESMF_OK;
 }

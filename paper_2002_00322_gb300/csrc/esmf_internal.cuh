@@ -25,8 +25,14 @@ constexpr int MAXPP = MAXP * MAXP;
 struct BrickDesc {          // 16 bytes
     int16_t P, Q, R, S;     // function-block indices
     int32_t nkept;          // kept elements
-    int32_t pad;
+    int32_t pad;            // bit 0: first brick of a (P,Q,R) run, bit 1: last brick of it
 };
+
+// Split 16-bit stores (FP16X2 / BF16X2) hold one record per brick: a 512-byte
+// keep mask (byte v = p*64 + q*8 + r, bit s) followed by the kept values as
+// 32-bit words (hi half in the low 16 bits, lo half in the high 16 bits),
+// all scaled by one power of two (the handle's vscale).
+constexpr int MASK_WORDS = 128;
 
 // device view of the basis: functions padded to a multiple of BLK; padded
 // functions have nprim = 0 and Q = 0 and are never kept
@@ -50,7 +56,7 @@ int launch_brick_count(const DevBasis &b, const double *Q, double tol, const Bri
                        int64_t nbricks, int32_t *counts, cudaStream_t s);
 int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                           int64_t nbricks, const int64_t *offsets, int precision, void *store,
-                          float *scales, cudaStream_t s);
+                          float vscale, cudaStream_t s);
 
 // ---- jk_cuda.cu (CUDA-core contraction)
 struct JKArgs {
@@ -66,9 +72,29 @@ struct JKArgs {
     int m;
     const double *D;          // m x n x n (caller layout)
     double *Jacc, *Kacc;      // m x np x np accumulators (zeroed by caller)
+    float vscale;             // store scale of the split 16-bit precisions
 };
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s);
-int launch_jk_cuda_split(const JKArgs &a, const float *scales, cudaStream_t s);
+int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s);
+
+// ---- jk_umma.cu (tensor-core contraction for split 16-bit stores)
+struct UmmaLaunch {
+    const BrickDesc *bricks;
+    int64_t nbricks;
+    const int64_t *offsets;
+    const uint32_t *store;
+    uint16_t *kbank, *jbank;     // density operand tiles (work memory)
+    unsigned int *dmax_bits;     // work scalar
+    const double *D;
+    int n, np, nb, m, bf16, num_sms;
+    float vscale;
+    double *Jacc, *Kacc;
+    int *error;                  // device flag, 0 = ok
+};
+int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s);
+int umma_smem_bytes();
+size_t umma_kbank_bytes(int nb);
+size_t umma_jbank_bytes(int nb);
 int launch_finalize(const DevBasis &b, int m, const double *D, const double *Jacc,
                     const double *Kacc, double *J, double *K, double *F, double *tsum,
                     cudaStream_t s);

@@ -80,7 +80,7 @@ struct JKSmemDirect : JKSmem<TA, MC, true> {
 
 // SRC: 0 fp64 store, 1 fp32 store, 2 fp16 hi+lo, 3 bf16 hi+lo, 4 direct (evaluated in TA)
 template <typename TA, int MC, int SRC>
-__global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a, const float *scales) {
+__global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     using SM = typename std::conditional<SRC == 4, JKSmemDirect<TA, MC>, JKSmem<TA, MC, false>>::type;
     SM &sm = *reinterpret_cast<SM *>(smraw);
@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a, const float *scales) 
                 }
             } else {
                 int pos = scan256(__popc(mask), sm.wsum);
-                const int64_t base = a.offsets[bi];
-                const float inv = (SRC >= 2) ? 1.0f / scales[bi] : 1.0f;
+                const int64_t base = a.offsets[bi] + (SRC >= 2 ? MASK_WORDS : 0);
+                const float inv = (SRC >= 2) ? 1.0f / a.vscale : 1.0f;
                 for (int j = 0; j < 16; ++j) {
                     TA v = TA(0);
                     if (mask & (1u << j)) {
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a, const float *scales) 
 }
 
 template <typename TA, int MC, int SRC>
-static int jk_launch(const JKArgs &a, const float *scales, cudaStream_t s) {
+static int jk_launch(const JKArgs &a, cudaStream_t s) {
     using SM = typename std::conditional<SRC == 4, JKSmemDirect<TA, MC>, JKSmem<TA, MC, false>>::type;
     const size_t smem = sizeof(SM);
     CK(cudaFuncSetAttribute(k_jk_cuda<TA, MC, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -225,20 +225,19 @@ static int jk_launch(const JKArgs &a, const float *scales, cudaStream_t s) {
     int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (grid > a.nbricks) grid = a.nbricks;
     if (grid < 1) return ESMF_OK;
-    k_jk_cuda<TA, MC, SRC><<<(int)grid, 256, smem, s>>>(a, scales);
+    k_jk_cuda<TA, MC, SRC><<<(int)grid, 256, smem, s>>>(a);
     CK(cudaGetLastError());
     return ESMF_OK;
 }
 
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
-    const float *scales = nullptr;
     if (a.mode == ESMF_MODE_DIRECT) {
-        if (a.precision == ESMF_PREC_FP64) return jk_launch<double, 8, 4>(a, scales, s);
-        return jk_launch<float, 16, 4>(a, scales, s);
+        if (a.precision == ESMF_PREC_FP64) return jk_launch<double, 8, 4>(a, s);
+        return jk_launch<float, 16, 4>(a, s);
     }
     switch (a.precision) {
-        case ESMF_PREC_FP64: return jk_launch<double, 8, 0>(a, scales, s);
-        case ESMF_PREC_FP32: return jk_launch<float, 16, 1>(a, scales, s);
+        case ESMF_PREC_FP64: return jk_launch<double, 8, 0>(a, s);
+        case ESMF_PREC_FP32: return jk_launch<float, 16, 1>(a, s);
         default: break;
     }
     set_error("launch_jk_cuda: precision %d needs the split-precision path", a.precision);
@@ -246,9 +245,9 @@ int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
 }
 
 // split-precision stores on CUDA cores (reference path for the tensor kernel)
-int launch_jk_cuda_split(const JKArgs &a, const float *scales, cudaStream_t s) {
-    if (a.precision == ESMF_PREC_FP16X2) return jk_launch<float, 16, 2>(a, scales, s);
-    if (a.precision == ESMF_PREC_BF16X2) return jk_launch<float, 16, 3>(a, scales, s);
+int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s) {
+    if (a.precision == ESMF_PREC_FP16X2) return jk_launch<float, 16, 2>(a, s);
+    if (a.precision == ESMF_PREC_BF16X2) return jk_launch<float, 16, 3>(a, s);
     set_error("launch_jk_cuda_split: bad precision %d", a.precision);
     return ESMF_ERR_INVALID_ARG;
 }

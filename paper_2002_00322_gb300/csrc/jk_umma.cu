@@ -1,0 +1,471 @@
+// Grouped J/K contraction on the sm_103a tensor cores (tcgen05), for integral
+// stores held as scaled 16-bit hi+lo pairs (FP16 or BF16 halves).
+//
+// Every kept brick (P Q | R S) of 8x8x8x8 integrals feeds, for all m densities,
+// the ordered-tuple updates of Eq. (J_and_K) (see jk_cuda.cu).  Grouped by
+// output block they are six small GEMMs with M = 64 output rows, K = 64:
+//   exchange  V1 (pr|qs): K[P,R] += V D[Q,S],  K[R,P]^T += V D[S,Q]^T
+//             V2 (qr|ps): K[Q,R] += V D[P,S],  K[R,Q]^T += V D[S,P]^T
+//             V3 (ps|qr): K[P,S] += V D[Q,R],  K[S,P]^T += V D[R,Q]^T
+//             V4 (qs|pr): K[Q,S] += V D[P,R],  K[S,Q]^T += V D[R,P]^T
+//   Coulomb   J1 (pq|rs): J[P,Q] += V Dj[R,S],  J2 (rs|pq): J[R,S] += V^T Dj[P,Q]
+// with Dj[X,Y] = D[X,Y] + [X != Y] D[Y,X]^T.  The brick tile V[p][q][r][s]
+// (fp16, s fastest) is a canonical no-swizzle operand for all four exchange
+// views (two K-major, two MN-major descriptors over the same bytes); the
+// Coulomb views read a second copy W[p][r][q][s].  Products are formed as
+//   V_hi D_hi + V_hi D_lo + V_lo D_hi   (FP32 accumulation in tensor memory),
+// i.e. one MMA with N = [D_hi | D^T_hi | D_lo | D^T_lo] and one with the
+// first half of those columns.
+//
+// Bricks are ordered so that runs share (P, Q, R): V1, V2 and J1 keep their
+// outputs across a run in tensor memory; V3, V4 and J2 are flushed per brick
+// (double-buffered).  Flushes add into FP64 accumulators with atomics.
+//
+// Warp roles (320 threads): warp 0 producer (bulk copies of the packed brick
+// record and the six density tiles), warp 1 tensor-memory owner and MMA
+// issuer, warps 2-5 expand packed records into the operand tiles, warps 6-9
+// read accumulators and flush them.  Every mbarrier wait is bounded; on
+// timeout the kernel records an error and all roles leave.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "esmf_internal.cuh"
+#include "umma.cuh"
+
+namespace esmf {
+
+using namespace umma;
+
+namespace {
+
+constexpr int NTHREADS = 320;
+constexpr int MPMAX = 16;                         // densities per pass
+constexpr int KB_BYTES_MAX = 512 * MPMAX;         // 4 mp rows x 64 k x 2 B
+constexpr int JB_BYTES_MAX = 256 * MPMAX;         // 2 mp rows x 64 k x 2 B
+constexpr int IN_BYTES = 512 + 4 * BRICK;         // mask + packed values
+// per-stage layout
+constexpr int OFF_VH = 0, OFF_VL = 8192, OFF_WH = 16384, OFF_WL = 24576;
+constexpr int OFF_B1 = 32768;                     // four exchange tiles
+constexpr int OFF_B5 = OFF_B1 + 4 * KB_BYTES_MAX; // two Coulomb tiles
+constexpr int OFF_IN = OFF_B5 + 2 * JB_BYTES_MAX;
+constexpr int STAGE_BYTES = ((OFF_IN + IN_BYTES + 1023) / 1024) * 1024;
+constexpr int CTRL_BYTES = 4096;
+constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES;
+
+struct Ctrl {
+    uint64_t full[2], conv[2], mmad[2], acce[2], fixe;
+    uint32_t tmem_base;
+    int abort_flag;
+    int scan[8];
+    int vpos[512];
+};
+static_assert(sizeof(Ctrl) <= CTRL_BYTES, "control block");
+
+__constant__ int c_tup[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
+                                {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
+
+__device__ __forceinline__ unsigned tuple_activity(int P, int Q, int R, int S) {
+    const int bl[4] = {P, Q, R, S};
+    unsigned act = 0;
+    for (int t = 0; t < 8; ++t) {
+        bool dup = false;
+        for (int u = 0; u < t && !dup; ++u) {
+            bool same = true;
+            for (int x = 0; x < 4; ++x) same &= bl[c_tup[t][x]] == bl[c_tup[u][x]];
+            dup = same;
+        }
+        if (!dup) act |= 1u << t;
+    }
+    return act;
+}
+
+__device__ __forceinline__ float density_scale(const unsigned int *dmax_bits) {
+    const float dm = __uint_as_float(*dmax_bits);
+    if (!(dm > 0.f)) return 1.0f;
+    int e;
+    frexpf(2.0f * dm, &e);            // 2 max|D| in [2^(e-1), 2^e)
+    return ldexpf(1.0f, 14 - e);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- density tiles
+__global__ void k_dmax(const double *D, int64_t count, unsigned int *out) {
+    float mx = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, __double2float_ru(fabs(D[i])));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+__device__ __forceinline__ uint16_t split16(float x, int part_lo, int bf16) {
+    if (bf16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        if (!part_lo) return __bfloat16_as_ushort(h);
+        return __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    }
+    __half h = __float2half_rn(x);
+    if (!part_lo) return __half_as_ushort(h);
+    return __half_as_ushort(__float2half_rn(x - __half2float(h)));
+}
+
+// canonical K-major operand tile: row n (density column of the MMA), k = b*8 + d
+__device__ __forceinline__ int tile_off(int row, int k) {
+    return (row & 7) * 16 + (k & 7) * 2 + (k >> 3) * 128 + (row >> 3) * 1024;
+}
+
+__global__ void k_dbank(const double *D, int n, int nb, int m, int d0, int mp, const unsigned int *dmax_bits,
+                        int bf16, uint16_t *kbank, uint16_t *jbank) {
+    const float sD = density_scale(dmax_bits);
+    const int64_t nn = (int64_t)n * n;
+    const int F = 4 * mp, G = 2 * mp;
+    const int64_t kcount = (int64_t)nb * nb * F * 64;
+    const int64_t jcount = (int64_t)nb * (nb + 1) / 2 * G * 64;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kcount + jcount;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < kcount) {
+            const int kidx = (int)(e & 63);
+            const int row = (int)((e >> 6) % F);
+            const int64_t t = (e >> 6) / F;
+            const int X = (int)(t / nb), Y = (int)(t % nb);
+            const int kk = row % mp, part = row / mp;           // 0 D_hi, 1 D^T_hi, 2 D_lo, 3 D^T_lo
+            const int b = kidx >> 3, dd = kidx & 7;
+            const int k = d0 + kk;
+            double v = 0.0;
+            int r0, c0;
+            if (part & 1) { r0 = Y * 8 + dd; c0 = X * 8 + b; }
+            else { r0 = X * 8 + b; c0 = Y * 8 + dd; }
+            if (kk < m && r0 < n && c0 < n) v = D[(int64_t)k * nn + (int64_t)r0 * n + c0];
+            const float x = (float)(v * (double)sD);
+            kbank[t * (F * 64) + (tile_off(row, kidx) >> 1)] = split16(x, part >= 2, bf16);
+        } else {
+            const int64_t f = e - kcount;
+            const int kidx = (int)(f & 63);
+            const int row = (int)((f >> 6) % G);
+            const int64_t t = (f >> 6) / G;
+            int X = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+            while ((int64_t)X * (X + 1) / 2 > t) --X;
+            while ((int64_t)(X + 1) * (X + 2) / 2 <= t) ++X;
+            const int Y = (int)(t - (int64_t)X * (X + 1) / 2);
+            const int kk = row % mp, part = row / mp;           // 0 Dj_hi, 1 Dj_lo
+            const int b = kidx >> 3, dd = kidx & 7;
+            const int k = d0 + kk;
+            double v = 0.0;
+            const int r0 = X * 8 + b, c0 = Y * 8 + dd;
+            if (kk < m && r0 < n && c0 < n) {
+                v = D[(int64_t)k * nn + (int64_t)r0 * n + c0];
+                if (X != Y) v += D[(int64_t)k * nn + (int64_t)c0 * n + r0];
+            }
+            const float x = (float)(v * (double)sD);
+            jbank[t * (G * 64) + (tile_off(row, kidx) >> 1)] = split16(x, part, bf16);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- main kernel
+struct UmmaParams {
+    const BrickDesc *bricks;
+    int64_t nbricks;
+    const int64_t *offsets;        // record start, in 32-bit words
+    const uint32_t *store;
+    const uint16_t *kbank, *jbank;
+    int nb, np, mp, m, d0, bf16;
+    float vscale;
+    const unsigned int *dmax_bits;
+    double *Jacc, *Kacc;
+    int *error;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    Ctrl &c = *reinterpret_cast<Ctrl *>(sm + 2 * STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t beg = a.nbricks * blockIdx.x / gridDim.x;
+    const int64_t end = a.nbricks * (blockIdx.x + 1) / gridDim.x;
+    const int nloc = (int)(end - beg);
+    const int mp = a.mp, F = 4 * mp, G = 2 * mp;
+    const uint32_t kbytes = 512u * mp, jbytes = 256u * mp;
+    volatile int *abort_flag = &c.abort_flag;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&c.full[s], 1);
+            mbar_init(&c.conv[s], 4);
+            mbar_init(&c.mmad[s], 1);
+            mbar_init(&c.acce[s], 4);
+        }
+        mbar_init(&c.fixe, 4);
+        c.abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tmem_alloc(&c.tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = c.tmem_base;
+    auto fail = [&](int code) {
+        *abort_flag = 1;
+        atomicExch(a.error, code);
+    };
+
+    if (nloc > 0 && warp == 0 && lane == 0) {
+        // ------------------------------------------------ producer
+        int issued = 0;
+        for (int i = 0; i < nloc; ++i) {
+            const int s = i & 1;
+            if (i >= 2 && !mbar_wait(&c.mmad[s], ((i - 2) >> 1) & 1, abort_flag)) { fail(2); break; }
+            const BrickDesc d = a.bricks[beg + i];
+            unsigned char *st = sm + s * STAGE_BYTES;
+            const uint32_t rec = ((512u + 4u * (uint32_t)d.nkept) + 15u) & ~15u;
+            const uint16_t *kb = a.kbank, *jb = a.jbank;
+            const size_t kw = kbytes / 2, jw = jbytes / 2;
+            mbar_arrive_expect_tx(&c.full[s], rec + 4 * kbytes + 2 * jbytes);
+            bulk_g2s(st + OFF_IN, a.store + a.offsets[beg + i], rec, &c.full[s]);
+            bulk_g2s(st + OFF_B1 + 0 * KB_BYTES_MAX, kb + ((size_t)d.Q * a.nb + d.S) * kw, kbytes, &c.full[s]);
+            bulk_g2s(st + OFF_B1 + 1 * KB_BYTES_MAX, kb + ((size_t)d.P * a.nb + d.S) * kw, kbytes, &c.full[s]);
+            bulk_g2s(st + OFF_B1 + 2 * KB_BYTES_MAX, kb + ((size_t)d.Q * a.nb + d.R) * kw, kbytes, &c.full[s]);
+            bulk_g2s(st + OFF_B1 + 3 * KB_BYTES_MAX, kb + ((size_t)d.P * a.nb + d.R) * kw, kbytes, &c.full[s]);
+            bulk_g2s(st + OFF_B5, jb + ((size_t)d.R * (d.R + 1) / 2 + d.S) * jw, jbytes, &c.full[s]);
+            bulk_g2s(st + OFF_B5 + JB_BYTES_MAX, jb + ((size_t)d.P * (d.P + 1) / 2 + d.Q) * jw, jbytes, &c.full[s]);
+            issued = i + 1;
+        }
+        // no copy may still be landing when the CTA leaves
+        for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
+            mbar_wait(&c.full[i & 1], (i >> 1) & 1, abort_flag);
+    } else if (nloc > 0 && warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        int run = 0, committed = 0;
+        const uint32_t id_full = idesc_f16(64, F, 0, a.bf16), id_half = idesc_f16(64, G, 0, a.bf16);
+        const uint32_t idm_full = idesc_f16(64, F, 1, a.bf16), idm_half = idesc_f16(64, G, 1, a.bf16);
+        const uint32_t id_jf = idesc_f16(64, G, 0, a.bf16), id_jh = idesc_f16(64, mp, 0, a.bf16);
+        const uint32_t idm_jf = idesc_f16(64, G, 1, a.bf16), idm_jh = idesc_f16(64, mp, 1, a.bf16);
+        const uint32_t colV1 = 0, colV2 = F, colJ1 = 2 * F;
+        for (int i = 0; i < nloc; ++i) {
+            const int s = i & 1, b = i & 1;
+            const BrickDesc d = a.bricks[beg + i];
+            const bool first = (i == 0) || (d.pad & 1);
+            const bool last = (i == nloc - 1) || (d.pad & 2);
+            if (!mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag)) { fail(3); break; }
+            if (i >= 2 && !mbar_wait(&c.acce[b], ((i - 2) >> 1) & 1, abort_flag)) { fail(4); break; }
+            if (first && run >= 1 && !mbar_wait(&c.fixe, (run - 1) & 1, abort_flag)) { fail(5); break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(sm + s * STAGE_BYTES);
+            const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
+            const uint32_t B1 = st + OFF_B1, B2 = B1 + KB_BYTES_MAX, B3 = B2 + KB_BYTES_MAX,
+                           B4 = B3 + KB_BYTES_MAX, B5 = st + OFF_B5, B6 = B5 + JB_BYTES_MAX;
+            const uint32_t var = 2 * F + G + (uint32_t)b * (2 * F + G);
+            const uint32_t colV3 = var, colV4 = var + F, colJ2 = var + 2 * F;
+            // exchange views: K-major (V1, V2) and MN-major (V3, V4) over the same tile
+            struct View { uint32_t col, kstep, lbo, sbo, idf, idh, B; bool fresh; };
+            const View views[4] = {
+                {colV1, 256, 128, 1024, id_full, id_half, B1, first},
+                {colV2, 2048, 1024, 128, id_full, id_half, B2, first},
+                {colV3, 256, 128, 1024, idm_full, idm_half, B3, true},
+                {colV4, 2048, 1024, 128, idm_full, idm_half, B4, true}};
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const View &w = views[v];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_f16(tmem + w.col, sdesc(VH + j * w.kstep, w.lbo, w.sbo), sdesc(w.B + j * 256, 128, 1024), w.idf,
+                            (j > 0 || !w.fresh) ? 1u : 0u);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_f16(tmem + w.col, sdesc(VL + j * w.kstep, w.lbo, w.sbo), sdesc(w.B + j * 256, 128, 1024), w.idh, 1u);
+            }
+            // Coulomb views over the q<->r swapped copy
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                mma_f16(tmem + colJ1, sdesc(WH + j * 256, 128, 1024), sdesc(B5 + j * 256, 128, 1024), id_jf,
+                        (j > 0 || !first) ? 1u : 0u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                mma_f16(tmem + colJ1, sdesc(WL + j * 256, 128, 1024), sdesc(B5 + j * 256, 128, 1024), id_jh, 1u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                mma_f16(tmem + colJ2, sdesc(WH + j * 2048, 1024, 128), sdesc(B6 + j * 256, 128, 1024), idm_jf,
+                        j > 0 ? 1u : 0u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                mma_f16(tmem + colJ2, sdesc(WL + j * 2048, 1024, 128), sdesc(B6 + j * 256, 128, 1024), idm_jh, 1u);
+            mma_commit(&c.mmad[s]);
+            committed = i + 1;
+            if (last) ++run;
+        }
+        if (committed > 0) {
+            const int i = committed - 1;
+            mbar_wait(&c.mmad[i & 1], (i >> 1) & 1, abort_flag);
+        }
+    } else if (nloc > 0 && warp >= 2 && warp < 6) {
+        // ------------------------------------------------ converters
+        const int ct = threadIdx.x - 64;
+        for (int i = 0; i < nloc; ++i) {
+            const int s = i & 1;
+            if (!mbar_wait(&c.full[s], (i >> 1) & 1, abort_flag)) { fail(6); break; }
+            unsigned char *st = sm + s * STAGE_BYTES;
+            const unsigned char *mask = st + OFF_IN;
+            const uint32_t *vals = reinterpret_cast<const uint32_t *>(st + OFF_IN + 512);
+            // packed positions: exclusive scan of per-vector counts in local order
+            int cnt[4], tot = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { cnt[j] = __popc(mask[4 * ct + j]); tot += cnt[j]; }
+            int incl = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) c.scan[ct >> 5] = incl;
+            named_bar_sync(1, 128);
+            int base = incl - tot;
+            for (int w = 0; w < (ct >> 5); ++w) base += c.scan[w];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { c.vpos[4 * ct + j] = base; base += cnt[j]; }
+            named_bar_sync(1, 128);
+            // expand: 4 s-vectors per thread, mapped so that both the V and the
+            // W tile stores of 8 neighbouring threads hit distinct bank groups
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int u = k * 128 + ct;
+                const int jj = u & 7, cc = (u >> 3) & 7, p = u >> 6;
+                const int q = jj, r = (jj + cc) & 7;
+                const int v = p * 64 + q * 8 + r;
+                const unsigned m8 = mask[v];
+                int pos = c.vpos[v];
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    uint32_t x0 = 0, x1 = 0;
+                    if (m8 & (1u << (2 * h))) x0 = vals[pos++];
+                    if (m8 & (1u << (2 * h + 1))) x1 = vals[pos++];
+                    hi[h] = (x0 & 0xffffu) | (x1 << 16);
+                    lo[h] = (x0 >> 16) | (x1 & 0xffff0000u);
+                }
+                const uint4 H = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                const uint4 L = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                *reinterpret_cast<uint4 *>(st + OFF_VH + v * 16) = H;
+                *reinterpret_cast<uint4 *>(st + OFF_VL + v * 16) = L;
+                const int vw = p * 64 + r * 8 + q;
+                *reinterpret_cast<uint4 *>(st + OFF_WH + vw * 16) = H;
+                *reinterpret_cast<uint4 *>(st + OFF_WL + vw * 16) = L;
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&c.conv[s]);
+            named_bar_sync(1, 128);   // vpos / scan reused by the next brick
+        }
+    } else if (nloc > 0 && warp >= 6) {
+        // ------------------------------------------------ epilogue
+        const int slice = warp & 3;
+        const int row = slice * 16 + (lane & 15);       // accumulator row of this thread (lane < 16)
+        const bool live = lane < 16;
+        const uint32_t tl = tmem + ((uint32_t)(slice * 32) << 16);
+        const float inv = 1.0f / (a.vscale * density_scale(a.dmax_bits));
+        const int np = a.np;
+        const int64_t npnp = (int64_t)np * np;
+        const int m = a.m, d0 = a.d0;
+        int run = 0;
+        float acc[64];
+        auto load_cols = [&](uint32_t col, int ncols) {
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 16)
+                if (c0 < ncols) tmem_ld16(tl + col + c0, acc + c0);
+            tmem_wait_ld();
+        };
+        // exchange view flush: rows (x in X, y in Y) -> K[X x][Y y] (D part) and K[Y y][X x] (D^T part)
+        auto flush_k = [&](int X, int Y, bool actD, bool actT) {
+            if (!live) return;
+            const int x = row >> 3, y = row & 7;
+            const int64_t rc = (int64_t)(X * 8 + x) * np + (Y * 8 + y);
+            const int64_t cr = (int64_t)(Y * 8 + y) * np + (X * 8 + x);
+            for (int k = 0; k < m; ++k) {
+                if (actD) atomicAdd(a.Kacc + (int64_t)(d0 + k) * npnp + rc, (double)((acc[k] + acc[2 * mp + k]) * inv));
+                if (actT) atomicAdd(a.Kacc + (int64_t)(d0 + k) * npnp + cr, (double)((acc[mp + k] + acc[3 * mp + k]) * inv));
+            }
+        };
+        auto flush_j = [&](int X, int Y) {
+            if (!live) return;
+            const int x = row >> 3, y = row & 7;
+            const int64_t rc = (int64_t)(X * 8 + x) * np + (Y * 8 + y);
+            for (int k = 0; k < m; ++k)
+                atomicAdd(a.Jacc + (int64_t)(d0 + k) * npnp + rc, (double)((acc[k] + acc[mp + k]) * inv));
+        };
+        for (int i = 0; i < nloc; ++i) {
+            const int s = i & 1, b = i & 1;
+            const BrickDesc d = a.bricks[beg + i];
+            const bool last = (i == nloc - 1) || (d.pad & 2);
+            if (!mbar_wait(&c.mmad[s], (i >> 1) & 1, abort_flag)) { fail(7); break; }
+            tc_fence_after();
+            const unsigned act = tuple_activity(d.P, d.Q, d.R, d.S);
+            const uint32_t var = 2 * F + G + (uint32_t)b * (2 * F + G);
+            // per-brick accumulators: V3, V4, J2
+            load_cols(var, F);
+            flush_k(d.P, d.S, act & (1u << 2), act & (1u << 5));
+            load_cols(var + F, F);
+            flush_k(d.Q, d.S, act & (1u << 3), act & (1u << 7));
+            load_cols(var + 2 * F, G);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&c.acce[b]);
+            if (act & (1u << 4)) flush_j(d.R, d.S);
+            if (last) {
+                load_cols(0, F);
+                flush_k(d.P, d.R, true, act & (1u << 4));
+                load_cols(F, F);
+                flush_k(d.Q, d.R, act & (1u << 1), act & (1u << 6));
+                load_cols(2 * F, G);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&c.fixe);
+                flush_j(d.P, d.Q);
+                ++run;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+int umma_smem_bytes() { return SMEM_TOTAL; }
+size_t umma_kbank_bytes(int nb) { return (size_t)nb * nb * KB_BYTES_MAX; }
+size_t umma_jbank_bytes(int nb) { return (size_t)nb * (nb + 1) / 2 * JB_BYTES_MAX; }
+
+int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
+    // density tiles for chunks of at most 16 densities; one contraction pass per chunk
+    const int64_t nn = (int64_t)L.n * L.n;
+    cudaError_t e = cudaMemsetAsync(L.dmax_bits, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) { set_error("memset dmax: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+    k_dmax<<<256, 256, 0, s>>>(L.D, (int64_t)L.m * nn, L.dmax_bits);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("k_dmax: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+    e = cudaFuncSetAttribute(k_jk_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    if (e != cudaSuccess) { set_error("smem attribute: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+    for (int d0 = 0; d0 < L.m; d0 += MPMAX) {
+        const int mc = (L.m - d0) < MPMAX ? (L.m - d0) : MPMAX;
+        const int mp = mc <= 8 ? 8 : 16;
+        const int64_t work = (int64_t)L.nb * L.nb * 4 * mp * 64 + (int64_t)L.nb * (L.nb + 1) / 2 * 2 * mp * 64;
+        int g = (int)((work + 255) / 256);
+        if (g > 4096) g = 4096;
+        k_dbank<<<g, 256, 0, s>>>(L.D, L.n, L.nb, mc, d0, mp, L.dmax_bits, L.bf16, L.kbank, L.jbank);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error("k_dbank: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+        if (L.nbricks == 0) continue;
+        UmmaParams p;
+        p.bricks = L.bricks; p.nbricks = L.nbricks; p.offsets = L.offsets; p.store = L.store;
+        p.kbank = L.kbank; p.jbank = L.jbank; p.nb = L.nb; p.np = L.np; p.mp = mp; p.m = mc; p.d0 = d0;
+        p.bf16 = L.bf16; p.vscale = L.vscale; p.dmax_bits = L.dmax_bits; p.Jacc = L.Jacc; p.Kacc = L.Kacc;
+        p.error = L.error;
+        int grid = L.num_sms;
+        if (grid > L.nbricks) grid = (int)L.nbricks;
+        k_jk_umma<<<grid, NTHREADS, SMEM_TOTAL, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error("k_jk_umma: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+    }
+    return ESMF_OK;
+}
+
+}  // namespace esmf

@@ -20,7 +20,7 @@
 
 namespace esmf {
 int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, int *device,
-                           const float **scales, bool *split);
+                           bool *split);
 }  // namespace esmf
 
 using namespace esmf;
@@ -74,9 +74,8 @@ extern "C" int esmf_fock_build_noalloc(esmf_fock_t *h, int m, const double *D, d
     if (!D || !J || !K) { set_error("D, J and K are required"); return ESMF_ERR_INVALID_ARG; }
     JKArgs a;
     int device = 0;
-    const float *scales = nullptr;
     bool split = false;
-    int rc = handle_prepare_noalloc(h, m, D, &a, &device, &scales, &split);
+    int rc = handle_prepare_noalloc(h, m, D, &a, &device, &split);
     if (rc != ESMF_OK) return rc;
     const int64_t per = (int64_t)m * a.b.np * a.b.np;
     if (2 * per > (int64_t)ESMF_NOALLOC_MAX_SCRATCH_DOUBLES) {
@@ -110,7 +109,7 @@ extern "C" int esmf_fock_build_noalloc(esmf_fock_t *h, int m, const double *D, d
     a.Jacc = scratch;
     a.Kacc = scratch + per;
     if (a.nbricks > 0) {
-        rc = split ? launch_jk_cuda_split(a, scales, s) : launch_jk_cuda(a, s);
+        rc = split ? launch_jk_cuda_split(a, s) : launch_jk_cuda(a, s);
         if (rc != ESMF_OK) return rc;
     }
     return launch_finalize(a.b, m, D, a.Jacc, a.Kacc, J, K, F, traces, s);

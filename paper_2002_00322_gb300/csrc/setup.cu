@@ -217,7 +217,6 @@ struct GenSmem {
     PairSmem<T, 128, MAXPP> pairs;
     double qb[64], qk[64];
     int wsum[16];
-    float wmax[8];
 };
 
 // precision: 0 FP64 store (T = double), 1 FP32 store, 2 FP16 hi+lo, 3 BF16 hi+lo
@@ -225,7 +224,7 @@ template <typename T, int PREC>
 __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double *Q, double tol,
                                                         const BrickDesc *bricks, int64_t nbricks,
                                                         const int64_t *offsets, void *store,
-                                                        float *scales) {
+                                                        float vscale) {
     extern __shared__ __align__(16) unsigned char smraw[];
     GenSmem<T> &sm = *reinterpret_cast<GenSmem<T> *>(smraw);
     for (int64_t bi = blockIdx.x; bi < nbricks; bi += gridDim.x) {
@@ -252,7 +251,6 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
         int total;
         int pos = block_excl_scan256(__popc(mask), sm.wsum, total);
         T vals[16];
-        float amax = 0.f;
         for (int j = 0; j < 16; ++j) {
             T v = T(0);
             if (mask & (1u << j)) {
@@ -260,7 +258,6 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
                 v = contracted_eri<T, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
             }
             vals[j] = v;
-            amax = fmaxf(amax, fabsf((float)v));
         }
         const int64_t base = offsets[bi];
         if (PREC == 0 || PREC == 1) {
@@ -268,21 +265,16 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
             for (int j = 0; j < 16; ++j)
                 if (mask & (1u << j)) out[pos++] = vals[j];
         } else {
-            // per-brick power-of-two scale: largest |x| * scale in [2^14, 2^15)
-            for (int off = 16; off > 0; off >>= 1)
-                amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-            if ((threadIdx.x & 31) == 0) sm.wmax[threadIdx.x >> 5] = amax;
-            __syncthreads();
-            float bm = 0.f;
-            for (int w = 0; w < 8; ++w) bm = fmaxf(bm, sm.wmax[w]);
-            int ex = 0;
-            if (bm > 0.f) { frexpf(bm, &ex); }   // bm in [2^(ex-1), 2^ex)
-            const float scale = (bm > 0.f) ? ldexpf(1.0f, 15 - ex) : 1.0f;
-            if (threadIdx.x == 0) scales[bi] = scale;
-            uint32_t *out = reinterpret_cast<uint32_t *>(store) + base;
+            // record: 512-byte keep mask, then the kept values as (hi | lo << 16)
+            // words of the value times the store's power-of-two scale
+            uint32_t *rec = reinterpret_cast<uint32_t *>(store) + base;
+            unsigned char *mk = reinterpret_cast<unsigned char *>(rec);
+            mk[2 * threadIdx.x] = (unsigned char)(mask & 0xffu);
+            mk[2 * threadIdx.x + 1] = (unsigned char)(mask >> 8);
+            uint32_t *out = rec + MASK_WORDS;
             for (int j = 0; j < 16; ++j)
                 if (mask & (1u << j)) {
-                    const double xs = (double)vals[j] * (double)scale;
+                    const double xs = (double)vals[j] * (double)vscale;
                     uint16_t hb, lb;
                     if (PREC == 2) {
                         __half h = __double2half(xs);
@@ -303,25 +295,25 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
 
 template <typename T, int PREC>
 static int gen_launch(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
-                      int64_t nbricks, const int64_t *offsets, void *store, float *scales,
+                      int64_t nbricks, const int64_t *offsets, void *store, float vscale,
                       cudaStream_t s) {
     const size_t smem = sizeof(GenSmem<T>);
     CK(cudaFuncSetAttribute(k_brick_generate<T, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem));
     k_brick_generate<T, PREC><<<grid_for(nbricks, 1, 152 * 4), 256, smem, s>>>(
-        b, Q, tol, bricks, nbricks, offsets, store, scales);
+        b, Q, tol, bricks, nbricks, offsets, store, vscale);
     CK(cudaGetLastError());
     return ESMF_OK;
 }
 
 int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                           int64_t nbricks, const int64_t *offsets, int precision, void *store,
-                          float *scales, cudaStream_t s) {
+                          float vscale, cudaStream_t s) {
     switch (precision) {
-        case ESMF_PREC_FP64: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
-        case ESMF_PREC_FP32: return gen_launch<float, 1>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
-        case ESMF_PREC_FP16X2: return gen_launch<float, 2>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
-        case ESMF_PREC_BF16X2: return gen_launch<float, 3>(b, Q, tol, bricks, nbricks, offsets, store, scales, s);
+        case ESMF_PREC_FP64: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
+        case ESMF_PREC_FP32: return gen_launch<float, 1>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
+        case ESMF_PREC_FP16X2: return gen_launch<float, 2>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
+        case ESMF_PREC_BF16X2: return gen_launch<float, 3>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
     }
     set_error("unknown precision %d", precision);
     return ESMF_ERR_INVALID_ARG;

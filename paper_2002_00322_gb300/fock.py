@@ -29,7 +29,9 @@ MAX_PRIM = 4
 # every symbol include/esmf_fock.h declares
 EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_fock_stats",
            "esmf_fock_schwarz", "esmf_fock_destroy", "esmf_strerror", "esmf_last_error",
-           "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc"]
+           "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
+           "esmf_fock_set_path", "esmf_fock_device_error"]
+PATHS = {"auto": 0, "cuda_core": 1}
 NOALLOC_MAX_SCRATCH_DOUBLES = 4194304
 
 
@@ -84,6 +86,10 @@ def load(path=None):
         L.esmf_fock_stats.restype = C.c_int
         L.esmf_fock_schwarz.argtypes = [vp, dp]
         L.esmf_fock_schwarz.restype = C.c_int
+        L.esmf_fock_set_path.argtypes = [vp, C.c_int]
+        L.esmf_fock_set_path.restype = C.c_int
+        L.esmf_fock_device_error.argtypes = [vp, C.c_int]
+        L.esmf_fock_device_error.restype = C.c_int
         L.esmf_fock_set_timing.argtypes = [vp, C.c_int]
         L.esmf_fock_set_timing.restype = C.c_int
         L.esmf_fock_kernel_time.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int]
@@ -174,6 +180,18 @@ def esmf_fock_schwarz(h, n):
     return Q
 
 
+def esmf_fock_set_path(h, path):
+    p = PATHS[path] if isinstance(path, str) else int(path)
+    _check(load().esmf_fock_set_path(h, p), "esmf_fock_set_path")
+
+
+def esmf_fock_device_error(h, reset=False):
+    rc = load().esmf_fock_device_error(h, int(bool(reset)))
+    if rc < 0:
+        _check(rc, "esmf_fock_device_error")
+    return rc
+
+
 def esmf_fock_set_timing(h, enable):
     _check(load().esmf_fock_set_timing(h, int(bool(enable))), "esmf_fock_set_timing")
 
@@ -213,6 +231,12 @@ class FockBuilder:
 
     def stats(self):
         return esmf_fock_stats(self.h)
+
+    def set_path(self, path):
+        esmf_fock_set_path(self.h, path)
+
+    def device_error(self, reset=False):
+        return esmf_fock_device_error(self.h, reset)
 
     def schwarz(self):
         return esmf_fock_schwarz(self.h, self.n)

@@ -197,3 +197,29 @@ def test_direct_small_ribbon_full(esmf):
     J, K, F, t, st = gpu_build(esmf, w, "direct", "fp32")
     check(J, K, F, t, Jr, Kr, w.D, TOL["fp32"], "direct ribbon")
     assert st["n_quartets_kept"] == nk
+
+
+# ------------------------------------------------------------- tensor cores
+@pytest.mark.parametrize("prec", ["fp16x2", "bf16x2"])
+@pytest.mark.parametrize("case", ["ragged", "stored"])
+def test_tensor_path_matches_cuda_core_path(esmf, prec, case):
+    """The tcgen05 kernel and the CUDA-core kernel read the same split store;
+    they must agree to the split precision, and the tensor kernel must report
+    no expired wait."""
+    import torch
+    if case == "ragged":
+        w = W.small_random(37, 5, 5, tol=1e-10, edge=13.25)
+    else:
+        w = W.stored()
+    D = torch.from_numpy(np.ascontiguousarray(w.D)).cuda()
+    with esmf.FockBuilder(w.basis, w.tol, "stored", prec) as fb:
+        J1, K1, _, t1 = fb.build(D)
+        torch.cuda.synchronize()
+        assert fb.device_error() == 0
+        fb.set_path("cuda_core")
+        J2, K2, _, t2 = fb.build(D)
+        torch.cuda.synchronize()
+    tol = TOL[prec]
+    for k in range(w.m):
+        assert relerr(J1[k].cpu().numpy(), J2[k].cpu().numpy()) <= tol
+        assert relerr(K1[k].cpu().numpy(), K2[k].cpu().numpy()) <= tol
