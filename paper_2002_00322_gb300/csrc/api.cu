@@ -448,7 +448,6 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
             e0 = h->ev_pool[h->ev_used].first;
             e1 = h->ev_pool[h->ev_used].second;
             ++h->ev_used;
-            CKR(cudaEventRecord(e0, s));
         }
         a.vscale = h->vscale;
         const bool split16 = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
@@ -459,12 +458,13 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
             L.dmax_bits = h->dmax; L.D = D; L.n = h->n; L.np = h->np; L.nb = h->nb; L.m = m;
             L.bf16 = h->prec == ESMF_PREC_BF16X2; L.num_sms = h->num_sms; L.vscale = h->vscale;
             L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev;
+            L.ev_start = e0; L.ev_stop = e1;
             RET(launch_jk_umma(L, s));
-        } else if (split16) {
-            RET(launch_jk_cuda_split(a, s));
-        } else {
-            RET(launch_jk_cuda(a, s));
+            return launch_finalize_blocked(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s);
         }
+        if (e0) CKR(cudaEventRecord(e0, s));
+        if (split16) RET(launch_jk_cuda_split(a, s));
+        else RET(launch_jk_cuda(a, s));
         if (e1) CKR(cudaEventRecord(e1, s));
     }
     RET(launch_finalize(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s));

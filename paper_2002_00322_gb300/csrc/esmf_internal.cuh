@@ -88,10 +88,13 @@ struct UmmaLaunch {
     const double *D;
     int n, np, nb, m, bf16, num_sms;
     float vscale;
-    double *Jacc, *Kacc;
+    double *Jacc, *Kacc;         // block-major accumulators [X][Y][k][x][y]
     int *error;                  // device flag, 0 = ok
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional timing
 };
 int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s);
+int launch_finalize_blocked(const DevBasis &b, int m, const double *D, const double *Jb, const double *Kb,
+                            double *J, double *K, double *F, double *tsum, cudaStream_t s);
 int umma_smem_bytes();
 size_t umma_kbank_bytes(int nb);
 size_t umma_jbank_bytes(int nb);

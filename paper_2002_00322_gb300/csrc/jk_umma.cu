@@ -50,12 +50,17 @@ constexpr int OFF_B5 = OFF_B1 + 4 * KB_BYTES_MAX; // two Coulomb tiles
 constexpr int OFF_IN = OFF_B5 + 2 * JB_BYTES_MAX;
 constexpr int STAGE_BYTES = ((OFF_IN + IN_BYTES + 1023) / 1024) * 1024;
 constexpr int CTRL_BYTES = 4096;
-constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES;
+// epilogue staging of flushed output blocks: two exchange views (D and D^T
+// parts, 2 x 16 x 64 floats each) and one Coulomb view (16 x 64 floats)
+constexpr int STAGE_K_FLOATS = 2 * MPMAX * 64;
+constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + MPMAX * 64) * 4;
+constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES + EPI_BYTES;
 
 struct Ctrl {
     uint64_t full[2], conv[2], mmad[2], acce[2], fixe;
     uint32_t tmem_base;
     int abort_flag;
+    int cdecide, edecide;   // group-uniform copies of abort_flag (converters, epilogue)
     int scan[8];
     int vpos[512];
 };
@@ -169,12 +174,59 @@ struct UmmaParams {
     const int64_t *offsets;        // record start, in 32-bit words
     const uint32_t *store;
     const uint16_t *kbank, *jbank;
-    int nb, np, mp, m, d0, bf16;
+    int nb, np, mp, m, d0, mtot, bf16;
     float vscale;
     const unsigned int *dmax_bits;
-    double *Jacc, *Kacc;
+    double *Jacc, *Kacc;   // block-major: [X][Y][k][x][y], k < mtot
     int *error;
 };
+
+namespace {
+
+// Load one accumulator view (this thread's TMEM lane) and write it, scaled,
+// to the staging area in block order: D part at [k][x][y], D^T part at
+// [k][y][x] (row = x*8 + y of the view's output block).
+template <int MP, bool KVIEW>
+__device__ __forceinline__ void stage_view(uint32_t taddr, bool live, int row, int m, float inv, float *st) {
+    constexpr int NC = KVIEW ? 4 * MP : 2 * MP;
+    float v[NC];
+#pragma unroll
+    for (int c0 = 0; c0 < NC; c0 += 16) tmem_ld16(taddr + c0, v + c0);
+    tmem_wait_ld();
+    if (!live) return;
+    const int x = row >> 3, y = row & 7;
+#pragma unroll
+    for (int k = 0; k < MP; ++k) {
+        if (k < m) {
+            if (KVIEW) {
+                st[k * 64 + x * 8 + y] = (v[k] + v[2 * MP + k]) * inv;
+                st[MPMAX * 64 + k * 64 + y * 8 + x] = (v[MP + k] + v[3 * MP + k]) * inv;
+            } else {
+                st[k * 64 + x * 8 + y] = (v[k] + v[MP + k]) * inv;
+            }
+        }
+    }
+}
+
+// Coalesced reduction of one staged block (m x 64 values, m <= 16) into the
+// block-major accumulator at dst (contiguous m*64 doubles): all shared loads
+// of a thread are issued before its reductions so their latencies overlap.
+__device__ __forceinline__ void flush_block(const float *st, double *dst, int m, int et) {
+    const int cnt = m * 64;
+    float v[MPMAX / 2];
+#pragma unroll
+    for (int j = 0; j < MPMAX / 2; ++j) {
+        const int i = et + 128 * j;
+        v[j] = (i < cnt) ? st[i] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < MPMAX / 2; ++j) {
+        const int i = et + 128 * j;
+        if (i < cnt) atomicAdd(dst + i, (double)v[j]);
+    }
+}
+
+}  // namespace
 
 __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -240,9 +292,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         const uint32_t id_jf = idesc_f16(64, G, 0, a.bf16), id_jh = idesc_f16(64, mp, 0, a.bf16);
         const uint32_t idm_jf = idesc_f16(64, G, 1, a.bf16), idm_jh = idesc_f16(64, mp, 1, a.bf16);
         const uint32_t colV1 = 0, colV2 = F, colJ1 = 2 * F;
+        BrickDesc dnext = a.bricks[beg];
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1, b = i & 1;
-            const BrickDesc d = a.bricks[beg + i];
+            const BrickDesc d = dnext;
+            if (i + 1 < nloc) dnext = a.bricks[beg + i + 1];
             const bool first = (i == 0) || (d.pad & 1);
             const bool last = (i == nloc - 1) || (d.pad & 2);
             if (!mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag)) { fail(3); break; }
@@ -301,7 +355,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         const int ct = threadIdx.x - 64;
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1;
-            if (!mbar_wait(&c.full[s], (i >> 1) & 1, abort_flag)) { fail(6); break; }
+            if (!mbar_wait(&c.full[s], (i >> 1) & 1, abort_flag)) fail(6);
+            // leave together: every converter thread must reach the same named barriers
+            named_bar_sync(1, 128);
+            if (ct == 0) c.cdecide = *abort_flag;
+            named_bar_sync(1, 128);
+            if (c.cdecide) break;
             unsigned char *st = sm + s * STAGE_BYTES;
             const unsigned char *mask = st + OFF_IN;
             const uint32_t *vals = reinterpret_cast<const uint32_t *>(st + OFF_IN + 512);
@@ -359,66 +418,62 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         const int slice = warp & 3;
         const int row = slice * 16 + (lane & 15);       // accumulator row of this thread (lane < 16)
         const bool live = lane < 16;
+        const int et = threadIdx.x - 192;               // 0..127
         const uint32_t tl = tmem + ((uint32_t)(slice * 32) << 16);
         const float inv = 1.0f / (a.vscale * density_scale(a.dmax_bits));
-        const int np = a.np;
-        const int64_t npnp = (int64_t)np * np;
-        const int m = a.m, d0 = a.d0;
-        int run = 0;
-        float acc[64];
-        auto load_cols = [&](uint32_t col, int ncols) {
-#pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 16)
-                if (c0 < ncols) tmem_ld16(tl + col + c0, acc + c0);
-            tmem_wait_ld();
-        };
-        // exchange view flush: rows (x in X, y in Y) -> K[X x][Y y] (D part) and K[Y y][X x] (D^T part)
-        auto flush_k = [&](int X, int Y, bool actD, bool actT) {
-            if (!live) return;
-            const int x = row >> 3, y = row & 7;
-            const int64_t rc = (int64_t)(X * 8 + x) * np + (Y * 8 + y);
-            const int64_t cr = (int64_t)(Y * 8 + y) * np + (X * 8 + x);
-            for (int k = 0; k < m; ++k) {
-                if (actD) atomicAdd(a.Kacc + (int64_t)(d0 + k) * npnp + rc, (double)((acc[k] + acc[2 * mp + k]) * inv));
-                if (actT) atomicAdd(a.Kacc + (int64_t)(d0 + k) * npnp + cr, (double)((acc[mp + k] + acc[3 * mp + k]) * inv));
+        const int m = a.m, nb = a.nb, mtot = a.mtot;
+        float *stA = reinterpret_cast<float *>(sm + 2 * STAGE_BYTES + CTRL_BYTES);
+        float *stB = stA + STAGE_K_FLOATS;
+        float *stJ = stB + STAGE_K_FLOATS;
+        auto blk = [&](double *base, int X, int Y) { return base + ((int64_t)(X * nb + Y) * mtot + a.d0) * 64; };
+        auto stage3 = [&](uint32_t c1, uint32_t c2, uint32_t c3) {
+            if (mp == 16) {
+                stage_view<16, true>(tl + c1, live, row, m, inv, stA);
+                stage_view<16, true>(tl + c2, live, row, m, inv, stB);
+                stage_view<16, false>(tl + c3, live, row, m, inv, stJ);
+            } else {
+                stage_view<8, true>(tl + c1, live, row, m, inv, stA);
+                stage_view<8, true>(tl + c2, live, row, m, inv, stB);
+                stage_view<8, false>(tl + c3, live, row, m, inv, stJ);
             }
-        };
-        auto flush_j = [&](int X, int Y) {
-            if (!live) return;
-            const int x = row >> 3, y = row & 7;
-            const int64_t rc = (int64_t)(X * 8 + x) * np + (Y * 8 + y);
-            for (int k = 0; k < m; ++k)
-                atomicAdd(a.Jacc + (int64_t)(d0 + k) * npnp + rc, (double)((acc[k] + acc[mp + k]) * inv));
         };
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1, b = i & 1;
             const BrickDesc d = a.bricks[beg + i];
             const bool last = (i == nloc - 1) || (d.pad & 2);
-            if (!mbar_wait(&c.mmad[s], (i >> 1) & 1, abort_flag)) { fail(7); break; }
+            if (!mbar_wait(&c.mmad[s], (i >> 1) & 1, abort_flag)) fail(7);
+            // leave together: every epilogue thread must reach the same named barriers
+            named_bar_sync(2, 128);
+            if (et == 0) c.edecide = *abort_flag;
+            named_bar_sync(2, 128);
+            if (c.edecide) break;
             tc_fence_after();
             const unsigned act = tuple_activity(d.P, d.Q, d.R, d.S);
             const uint32_t var = 2 * F + G + (uint32_t)b * (2 * F + G);
-            // per-brick accumulators: V3, V4, J2
-            load_cols(var, F);
-            flush_k(d.P, d.S, act & (1u << 2), act & (1u << 5));
-            load_cols(var + F, F);
-            flush_k(d.Q, d.S, act & (1u << 3), act & (1u << 7));
-            load_cols(var + 2 * F, G);
+            // per-brick accumulators V3, V4, J2 -> staging, then release them
+            stage3(var, var + F, var + 2 * F);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&c.acce[b]);
-            if (act & (1u << 4)) flush_j(d.R, d.S);
+            named_bar_sync(2, 128);
+            if (act & (1u << 2)) flush_block(stA, blk(a.Kacc, d.P, d.S), m, et);
+            if (act & (1u << 5)) flush_block(stA + MPMAX * 64, blk(a.Kacc, d.S, d.P), m, et);
+            if (act & (1u << 3)) flush_block(stB, blk(a.Kacc, d.Q, d.S), m, et);
+            if (act & (1u << 7)) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.S, d.Q), m, et);
+            if (act & (1u << 4)) flush_block(stJ, blk(a.Jacc, d.R, d.S), m, et);
+            named_bar_sync(2, 128);
             if (last) {
-                load_cols(0, F);
-                flush_k(d.P, d.R, true, act & (1u << 4));
-                load_cols(F, F);
-                flush_k(d.Q, d.R, act & (1u << 1), act & (1u << 6));
-                load_cols(2 * F, G);
+                stage3(0, F, 2 * F);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&c.fixe);
-                flush_j(d.P, d.Q);
-                ++run;
+                named_bar_sync(2, 128);
+                flush_block(stA, blk(a.Kacc, d.P, d.R), m, et);
+                if (act & (1u << 4)) flush_block(stA + MPMAX * 64, blk(a.Kacc, d.R, d.P), m, et);
+                if (act & (1u << 1)) flush_block(stB, blk(a.Kacc, d.Q, d.R), m, et);
+                if (act & (1u << 6)) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.R, d.Q), m, et);
+                flush_block(stJ, blk(a.Jacc, d.P, d.Q), m, et);
+                named_bar_sync(2, 128);
             }
         }
     }
@@ -457,14 +512,60 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
         UmmaParams p;
         p.bricks = L.bricks; p.nbricks = L.nbricks; p.offsets = L.offsets; p.store = L.store;
         p.kbank = L.kbank; p.jbank = L.jbank; p.nb = L.nb; p.np = L.np; p.mp = mp; p.m = mc; p.d0 = d0;
+        p.mtot = L.m;
         p.bf16 = L.bf16; p.vscale = L.vscale; p.dmax_bits = L.dmax_bits; p.Jacc = L.Jacc; p.Kacc = L.Kacc;
         p.error = L.error;
         int grid = L.num_sms;
         if (grid > L.nbricks) grid = (int)L.nbricks;
+        if (L.ev_start && d0 == 0) cudaEventRecord(L.ev_start, s);
         k_jk_umma<<<grid, NTHREADS, SMEM_TOTAL, s>>>(p);
+        if (L.ev_stop && d0 + MPMAX >= L.m) cudaEventRecord(L.ev_stop, s);
         e = cudaGetLastError();
         if (e != cudaSuccess) { set_error("k_jk_umma: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
     }
+    return ESMF_OK;
+}
+
+// J from the lower block triangle of the block-major accumulators, F = 2J - K,
+// t_k = sum_pq D_k[pq] F_k[pq]; outputs in the caller's [k][p][q] layout.
+__global__ void k_finalize_blocked(int n, int nb, int m, const double *D, const double *Jb,
+                                   const double *Kb, double *J, double *K, double *F, double *tsum) {
+    const int k = blockIdx.y;
+    const int64_t nn = (int64_t)n * n;
+    double part = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(e / n), q = (int)(e % n);
+        const int X = p >> 3, Y = q >> 3, x = p & 7, y = q & 7;
+        const double jv = (X >= Y) ? Jb[(((int64_t)X * nb + Y) * m + k) * 64 + x * 8 + y]
+                                   : Jb[(((int64_t)Y * nb + X) * m + k) * 64 + y * 8 + x];
+        const double kv = Kb[(((int64_t)X * nb + Y) * m + k) * 64 + x * 8 + y];
+        const double fv = 2.0 * jv - kv;
+        J[k * nn + e] = jv;
+        K[k * nn + e] = kv;
+        if (F) F[k * nn + e] = fv;
+        part += D[k * nn + e] * fv;
+    }
+    if (tsum) {
+        __shared__ double red[8];
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+            atomicAdd(tsum + k, sum);
+        }
+    }
+}
+
+int launch_finalize_blocked(const DevBasis &b, int m, const double *D, const double *Jb, const double *Kb,
+                            double *J, double *K, double *F, double *tsum, cudaStream_t s) {
+    const int64_t nn = (int64_t)b.n * b.n;
+    int gx = (int)((nn + 255) / 256);
+    if (gx > 512) gx = 512;
+    k_finalize_blocked<<<dim3(gx, m), 256, 0, s>>>(b.n, b.nb, m, D, Jb, Kb, J, K, F, tsum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("k_finalize_blocked: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
     return ESMF_OK;
 }
 

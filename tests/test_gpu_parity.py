@@ -178,7 +178,7 @@ def sampled_check(esmf, w, mode, prec, n_j=6, n_k=10, seed=0, tol=None):
     return J, K, st
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16x2"])
 def test_stored_full_size_sampled(esmf, prec):
     w = W.stored()
     J, K, st = sampled_check(esmf, w, "stored", prec)
