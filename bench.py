@@ -97,6 +97,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def ncu_traffic(kernel, precision):
+    """DRAM traffic per launch from the committed ncu capture, or None when the
+    kernel's source has changed since that capture (or no capture exists)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel)
+    if not rec or precision not in rec.get("workload", ""):
+        return None
+    h = hashlib.sha1()
+    for f in rec["files"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return rec["traffic_bytes_per_launch"] if h.hexdigest() == rec["source_sha1"] else None
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -181,9 +197,10 @@ def run_ours(args):
     kern_avg_s = (kern_ms / max(kern_n, 1)) / 1e3
     hbm, src, _ = peaks()
     achieved = alg_bytes / kern_avg_s / 1e9
+    kname = "k_jk_umma" if args.precision in ("fp16x2", "bf16x2") else "k_jk_cuda"
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-            "kernel": "k_jk_umma" if args.precision in ("fp16x2", "bf16x2") else "k_jk_cuda",
+            "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(kname, args.precision),
+            "peak_source": src, "kernel": kname,
             "kernel_ms": round(kern_avg_s * 1e3, 4),
             "stored_bytes": st["store_bytes"], "algorithmic_bytes": alg_bytes}
 
