@@ -294,6 +294,68 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ serving
+def run_serving(args):
+    """Serving workload: 256 requests over a pool of 32 random molecules
+    (N uniform in [50, 600], m uniform in [4, 32]) on one build server with a
+    60 GB device budget.  Closed loop first (all requests queued at once:
+    builds/s), then Poisson arrivals at 0.8x that rate (p50/p99 latency)."""
+    import numpy as np
+    from paper_2002_00322_gb300 import workloads as W
+    from paper_2002_00322_gb300.server import Server
+    rank, world, local = env_rank()
+    if rank != 0:
+        return
+    mols, reqs = W.serving_requests(args.serve_requests, pool=args.serve_pool,
+                                    nmax=args.serve_nmax)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    dens = [W.request_densities(mols[i], m, seed) for (i, m, seed) in reqs]
+    out = {"metric": "served grouped J+K builds: builds/s and p50/p99 latency", "unit": "builds/s",
+           "n_gpus": 1, "higher_is_better": True, "dtype": "f16x2+f32acc", "data": "synthetic",
+           "config": {"workload": f"serving_{len(reqs)}req_pool{len(mols)}_n50-{args.serve_nmax}_m4-32",
+                      "budget_gb": args.serve_budget_gb, "max_inflight": args.serve_inflight,
+                      "precision": "fp16x2", "graphs": True}}
+    with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True,
+                device=local) as srv:
+        ids = [srv.register(w.basis, w.tol) for w in mols]
+        # closed loop
+        t0 = time.perf_counter()
+        tickets = [srv.submit(ids[i], D) for (i, _, _), D in zip(reqs, dens)]
+        for t in tickets:
+            srv.wait(t)
+        closed_s = time.perf_counter() - t0
+        st_closed = srv.stats()
+        rate = 0.8 * len(reqs) / closed_s
+        srv.reset_stats()
+        # open loop, Poisson arrivals
+        rng = np.random.default_rng(7)
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for g, ((i, _, _), D) in zip(gaps, zip(reqs, dens)):
+            due += g
+            while time.perf_counter() < due:
+                time.sleep(min(0.0005, max(0.0, due - time.perf_counter())))
+            tickets.append(srv.submit(ids[i], D))
+        for t in tickets:
+            srv.wait(t)
+        open_s = time.perf_counter() - t0
+        st_open = srv.stats()
+    out["value"] = round(len(reqs) / closed_s, 3)
+    out["closed_loop"] = {"seconds": round(closed_s, 3), "creates": st_closed["creates"],
+                          "evictions": st_closed["evictions"], "graph_launches": st_closed["graph_launches"],
+                          "peak_inflight": st_closed["peak_inflight"], "p50_ms": round(st_closed["p50_ms"], 2),
+                          "p99_ms": round(st_closed["p99_ms"], 2)}
+    out["open_loop"] = {"arrival_rate_per_s": round(rate, 3), "seconds": round(open_s, 3),
+                        "builds_per_s": round(len(reqs) / open_s, 3), "p50_ms": round(st_open["p50_ms"], 2),
+                        "p99_ms": round(st_open["p99_ms"], 2), "mean_ms": round(st_open["mean_ms"], 2),
+                        "creates": st_open["creates"], "evictions": st_open["evictions"],
+                        "peak_inflight": st_open["peak_inflight"], "failed": st_open["failed"]}
+    out["density_builds"] = int(sum(m for (_, m, _) in reqs))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,8 +365,16 @@ def main():
     ap.add_argument("--precision", default="fp16x2", choices=["fp64", "fp32", "fp16x2", "bf16x2"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-pool", type=int, default=32)
+    ap.add_argument("--serve-nmax", type=int, default=600)
+    ap.add_argument("--serve-budget-gb", type=float, default=60.0)
+    ap.add_argument("--serve-inflight", type=int, default=4)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.serving:
+        run_serving(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -1,0 +1,87 @@
+/*
+ * esmf_server.h -- C ABI of the build server: many concurrent ESMF
+ * optimisations (different molecules, different numbers of densities) asking
+ * for grouped J/K builds (Eq. J_and_K; one grouped pass per request as in
+ * Sec. II.C) on one GPU.
+ *
+ * The server keeps each registered molecule's screening data and integral
+ * store resident (a handle from esmf_fock_create) while they fit a device-
+ * memory budget, evicting idle molecules least-recently-used first and
+ * re-creating them on their next request.  A worker thread admits queued
+ * requests whenever an execution slot, the molecule and enough memory are
+ * free, so requests that arrive while others run start as soon as resources
+ * allow and their work overlaps on the device (one non-blocking CUDA stream
+ * per slot).  Builds of one molecule are serialised; different molecules run
+ * concurrently.  Each build can be replayed from a captured CUDA graph.
+ *
+ * Conventions as in esmf_fock.h: 0 or a negative ESMF_ERR_* code; buffers are
+ * row-major float64; the caller owns them.
+ */
+#ifndef ESMF_SERVER_H
+#define ESMF_SERVER_H
+
+#include <stdint.h>
+
+#include "esmf_fock.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct esmf_server esmf_server_t;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t creates;            /* handles built (first use or after eviction)   */
+    int64_t evictions;          /* idle handles released to fit the budget       */
+    int64_t graph_launches;     /* builds replayed from a captured CUDA graph    */
+    int64_t resident_bytes;     /* device bytes held by resident handles         */
+    int64_t peak_inflight;      /* most requests on the device at once           */
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* submit-to-ready latency          */
+    double span_s;              /* first submit to last completion               */
+} esmf_server_stats_t;
+
+/*
+ * esmf_server_create -- start a server on `device`.
+ *   budget_bytes  device memory the resident handles may hold (> 0)
+ *   max_inflight  concurrent requests on the device, 1..64
+ *   precision     ESMF_PREC_* used for every molecule's integral store
+ *   use_graphs    non-zero: capture each (molecule, m, slot) build into a
+ *                 CUDA graph once and replay it
+ * Errors: INVALID_ARG, CUDA, OOM.
+ */
+int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int precision,
+                       int use_graphs, esmf_server_t **out);
+
+/* Register a molecule (the basis is copied); returns its id in *basis_id.
+ * The handle is created on the molecule's first request.  Errors: INVALID_ARG. */
+int esmf_server_register(esmf_server_t *s, const esmf_basis_t *basis, double schwarz_tol,
+                         int *basis_id);
+
+/*
+ * Queue one grouped build for molecule basis_id with m densities.
+ *   D       host, m x N x N, read when the request is admitted
+ *   J, K    host, m x N x N, written before the request completes
+ *   traces  host, m doubles, or NULL
+ * The buffers must stay valid until esmf_server_wait reports completion.
+ * Errors: INVALID_ARG (unknown id, m out of range, NULL buffers).
+ */
+int esmf_server_submit(esmf_server_t *s, int basis_id, int m, const double *D, double *J,
+                       double *K, double *traces, int64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a ticket.  Returns 0 when its
+ * results are in the caller's buffers, ESMF_ERR_TIMEOUT if it has not
+ * finished yet, or the error the build failed with. */
+int esmf_server_wait(esmf_server_t *s, int64_t ticket, int timeout_ms);
+
+/* Statistics since creation or the last reset. */
+int esmf_server_stats(esmf_server_t *s, esmf_server_stats_t *out);
+int esmf_server_reset_stats(esmf_server_t *s);
+
+/* Stop the worker after the queued requests finish, free everything. */
+void esmf_server_destroy(esmf_server_t *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESMF_SERVER_H */

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libesmf_fock.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "setup.cu", "jk_cuda.cu", "jk_umma.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "setup.cu", "jk_cuda.cu", "jk_umma.cu", "noalloc.cu", "server.cu"]
 
 
 def nvcc():
@@ -41,7 +41,7 @@ def _stale(obj, deps):
 def build(verbose=False, extra=None, force=False):
     os.makedirs(OUT, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "esmf_fock.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     cc = nvcc()
     flags = _flags() + (extra or [])
     jobs = []

@@ -256,7 +256,20 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     h->nb = (n + BLK - 1) / BLK;
     h->np = h->nb * BLK;
     const int np = h->np;
-    auto fail = [&](int code) { cudaDeviceSynchronize(); cudaGetLastError(); release(h); return code; };
+    // create runs on a private non-blocking stream so that it does not wait for
+    // (or stall) builds of other handles running on other streams
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_error("cudaStreamCreate failed");
+        return ESMF_ERR_CUDA;
+    }
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } cs_guard{cs};
+    auto fail = [&](int code) { cudaStreamSynchronize(cs); cudaGetLastError(); release(h); return code; };
     int rc;
 
     // padded host copies
@@ -273,21 +286,21 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
         (rc = dalloc(h, &h->coefs, nprim_tot)) || (rc = dalloc(h, &h->w, nprim_tot)) ||
         (rc = dalloc(h, &h->Q, (size_t)np * np)))
         return fail(rc);
-    cudaStream_t s = 0;
+    cudaStream_t s = cs;
     auto ck = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess) { set_error("%s: %s", what, cudaGetErrorString(e)); return false; }
         return true;
     };
-    if (!ck(cudaMemcpy(h->center, hc.data(), sizeof(double) * np * 3, cudaMemcpyHostToDevice), "copy centers") ||
-        !ck(cudaMemcpy(h->nprim, hn.data(), sizeof(int) * np, cudaMemcpyHostToDevice), "copy nprim") ||
-        !ck(cudaMemcpy(h->poff, ho.data(), sizeof(int) * np, cudaMemcpyHostToDevice), "copy poff") ||
-        !ck(cudaMemcpy(h->exps, basis->exps, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice), "copy exps") ||
-        !ck(cudaMemcpy(h->coefs, basis->coefs, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice), "copy coefs"))
+    if (!ck(cudaMemcpyAsync(h->center, hc.data(), sizeof(double) * np * 3, cudaMemcpyHostToDevice, cs), "copy centers") ||
+        !ck(cudaMemcpyAsync(h->nprim, hn.data(), sizeof(int) * np, cudaMemcpyHostToDevice, cs), "copy nprim") ||
+        !ck(cudaMemcpyAsync(h->poff, ho.data(), sizeof(int) * np, cudaMemcpyHostToDevice, cs), "copy poff") ||
+        !ck(cudaMemcpyAsync(h->exps, basis->exps, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs), "copy exps") ||
+        !ck(cudaMemcpyAsync(h->coefs, basis->coefs, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs), "copy coefs"))
         return fail(ESMF_ERR_CUDA);
     const DevBasis db = h->dev();
     if ((rc = launch_normalize(db, h->coefs, h->w, s)) || (rc = launch_schwarz(db, h->Q, s))) return fail(rc);
     std::vector<double> hQ((size_t)np * np);
-    if (!ck(cudaMemcpy(hQ.data(), h->Q, sizeof(double) * np * np, cudaMemcpyDeviceToHost), "copy Q"))
+    if (!ck(cudaMemcpyAsync(hQ.data(), h->Q, sizeof(double) * np * np, cudaMemcpyDeviceToHost, cs), "copy Q"))
         return fail(ESMF_ERR_CUDA);
 
     // block-level screening: Qblk = max over the 8x8 block; brick kept iff
@@ -323,9 +336,9 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
             return fail(rc);
         }
         counts.resize(2 * ncand);
-        bool ok = ck(cudaMemcpy(dc, cand.data(), sizeof(BrickDesc) * ncand, cudaMemcpyHostToDevice), "copy bricks");
+        bool ok = ck(cudaMemcpyAsync(dc, cand.data(), sizeof(BrickDesc) * ncand, cudaMemcpyHostToDevice, cs), "copy bricks");
         if (ok) ok = (rc = launch_brick_count(db, h->Q, tol, dc, ncand, dcount, s)) == ESMF_OK;
-        if (ok) ok = ck(cudaMemcpy(counts.data(), dcount, sizeof(int32_t) * 2 * ncand, cudaMemcpyDeviceToHost), "copy counts");
+        if (ok) ok = ck(cudaMemcpyAsync(counts.data(), dcount, sizeof(int32_t) * 2 * ncand, cudaMemcpyDeviceToHost, cs), "copy counts");
         dfree(h, &dc, ncand);
         dfree(h, &dcount, 2 * ncand);
         if (!ok) return fail(rc ? rc : ESMF_ERR_CUDA);
@@ -388,14 +401,14 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
 
     if (h->nbricks > 0) {
         if ((rc = dalloc(h, &h->bricks, h->nbricks))) return fail(rc);
-        if (!ck(cudaMemcpy(h->bricks, kept.data(), sizeof(BrickDesc) * h->nbricks, cudaMemcpyHostToDevice), "copy kept bricks"))
+        if (!ck(cudaMemcpyAsync(h->bricks, kept.data(), sizeof(BrickDesc) * h->nbricks, cudaMemcpyHostToDevice, cs), "copy kept bricks"))
             return fail(ESMF_ERR_CUDA);
         if (use_mode == ESMF_MODE_STORED) {
             if ((rc = dalloc(h, &h->offsets, h->nbricks + 1))) return fail(rc);
             if ((rc = dalloc(h, (unsigned char **)&h->store, (size_t)h->store_bytes))) return fail(rc);
-            if (!ck(cudaMemcpy(h->offsets, offs.data(), sizeof(int64_t) * (h->nbricks + 1), cudaMemcpyHostToDevice), "copy offsets"))
+            if (!ck(cudaMemcpyAsync(h->offsets, offs.data(), sizeof(int64_t) * (h->nbricks + 1), cudaMemcpyHostToDevice, cs), "copy offsets"))
                 return fail(ESMF_ERR_CUDA);
-            if (!ck(cudaMemset(h->store, 0, (size_t)h->store_bytes), "clear store")) return fail(ESMF_ERR_CUDA);
+            if (!ck(cudaMemsetAsync(h->store, 0, (size_t)h->store_bytes, cs), "clear store")) return fail(ESMF_ERR_CUDA);
             if ((rc = launch_brick_generate(db, h->Q, tol, h->bricks, h->nbricks, h->offsets, h->prec,
                                             h->store, h->vscale, s)))
                 return fail(rc);
@@ -408,7 +421,7 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     *h->err_host = 0;
     if (!ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count"))
         return fail(ESMF_ERR_CUDA);
-    if (!ck(cudaDeviceSynchronize(), "create kernels")) return fail(ESMF_ERR_CUDA);
+    if (!ck(cudaStreamSynchronize(cs), "create kernels")) return fail(ESMF_ERR_CUDA);
     h->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h;
     return ESMF_OK;
@@ -599,6 +612,19 @@ int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, in
     *device = h->device;
     *split = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
     return ESMF_OK;
+}
+
+}  // namespace esmf
+
+namespace esmf {
+
+// Grow the handle's work memory for builds with m densities now (so that a
+// later build, e.g. one being captured into a CUDA graph, allocates nothing).
+int handle_reserve(esmf_fock_t *h, int m) {
+    if (!h || m < 1 || m > ESMF_MAX_DENSITIES) { set_error("bad reserve arguments"); return ESMF_ERR_INVALID_ARG; }
+    DeviceGuard g(h->device);
+    if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
+    return ensure_work(h, m);
 }
 
 }  // namespace esmf

@@ -32,6 +32,10 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
            "esmf_fock_set_path", "esmf_fock_device_error"]
 PATHS = {"auto": 0, "cuda_core": 1}
+# declared in include/esmf_server.h, bound in server.py
+SERVER_EXPORTS = ["esmf_server_create", "esmf_server_register", "esmf_server_submit",
+                  "esmf_server_wait", "esmf_server_stats", "esmf_server_reset_stats",
+                  "esmf_server_destroy"]
 NOALLOC_MAX_SCRATCH_DOUBLES = 4194304
 
 

@@ -1,0 +1,66 @@
+"""Build server: continuous batching of requests from several molecules.
+Every result must equal the same build run alone (same kernels, different
+atomic order: within the precision's tolerance) and the FP64 oracle; the
+memory budget must force evictions without changing results."""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_2002_00322_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp16x2": 2e-6}
+
+
+def relerr(x, r):
+    return np.linalg.norm(x - r) / max(np.linalg.norm(r), 1e-300)
+
+
+def molecules():
+    return [W.small_random(n, 1, 40 + i, tol=1e-10, edge=4.0 + n / 5) for i, n in enumerate((24, 37, 52))]
+
+
+@pytest.mark.parametrize("prec,graphs,budget,inflight", [("fp16x2", True, 1 << 34, 4), ("fp64", False, 1 << 34, 4),
+                                                         ("fp16x2", True, 0, 1)])
+def test_mixed_requests_equal_standalone(esmf, prec, graphs, budget, inflight):
+    import torch
+    from paper_2002_00322_gb300.server import Server
+    mols = molecules()
+    if budget == 0:
+        # room for the largest molecule's handle alone: every switch must evict
+        sizes = []
+        for w in mols:
+            with esmf.FockBuilder(w.basis, w.tol, "stored", prec) as fb:
+                fb.build(torch.zeros((19, w.basis.n, w.basis.n), dtype=torch.float64, device="cuda"))
+                torch.cuda.synchronize()
+                sizes.append(fb.stats()["device_bytes"])
+        budget = max(sizes) + (256 << 10)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for r in range(12):
+        i = int(rng.integers(0, len(mols)))
+        m = int(rng.integers(1, 20))
+        D = rng.standard_normal((m, mols[i].basis.n, mols[i].basis.n))
+        reqs.append((i, D))
+    with Server(budget, max_inflight=inflight, precision=prec, use_graphs=graphs) as srv:
+        ids = [srv.register(w.basis, w.tol) for w in mols]
+        tickets = [srv.submit(ids[i], D) for i, D in reqs]
+        outs = [srv.wait(t, 600000) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    if budget < (1 << 30):
+        assert st["evictions"] > 0
+    for (i, D), (J, K, tr) in zip(reqs, outs):
+        with esmf.FockBuilder(mols[i].basis, mols[i].tol, "stored", prec) as fb:
+            Ja, Ka, _, ta = fb.build(torch.from_numpy(D).cuda())
+            Ja, Ka = Ja.cpu().numpy(), Ka.cpu().numpy()
+        for k in range(D.shape[0]):
+            assert relerr(J[k], Ja[k]) <= TOL[prec] and relerr(K[k], Ka[k]) <= TOL[prec]
+    # and one request against the oracle
+    i, D = reqs[0]
+    Jr, Kr, _ = Oracle(mols[i].basis).jk_unique(D, mols[i].tol)
+    J, K, _ = outs[0]
+    for k in range(D.shape[0]):
+        assert relerr(J[k], Jr[k]) <= TOL[prec] and relerr(K[k], Kr[k]) <= TOL[prec]
