@@ -50,7 +50,7 @@ template <> struct Boys<float> {
 
 // Primitive-pair data of one function pair, structure of arrays in shared
 // memory: exponent sum p, product center P (relative to a local origin),
-// and weight K = w_a w_b exp(-ab/p |AB|^2).
+// and weight K/p with K = w_a w_b exp(-ab/p |AB|^2).
 template <typename T, int NPAIR, int MAXPP_>
 struct PairSmem {
     T pe[NPAIR][MAXPP_];
@@ -61,25 +61,27 @@ struct PairSmem {
     int npp[NPAIR];
 };
 
-// contracted (bra pair ib | ket pair ik) from shared pair data
+// contracted (bra pair ib | ket pair ik) from shared pair data.  Per primitive
+// quartet one reciprocal square root r = (p+q)^{-1/2} gives both
+// rho = p q r^2 and the prefactor 2 pi^{5/2} r / (p q) (the 1/p, 1/q factors
+// are folded into the stored pair weights), so no division is needed.
 template <typename T, int NPAIR, int MAXPP_>
 __device__ __forceinline__ T contracted_eri(const PairSmem<T, NPAIR, MAXPP_> &bra, int ib,
                                             const PairSmem<T, NPAIR, MAXPP_> &ket, int ik) {
     T acc = T(0);
     const int nb = bra.npp[ib], nk = ket.npp[ik];
     for (int i = 0; i < nb; ++i) {
-        const T p = bra.pe[ib][i], Px = bra.px[ib][i], Py = bra.py[ib][i], Pz = bra.pz[ib][i];
-        const T kb = bra.kw[ib][i];
+        const T p = bra.pe[ib][i];
+        const T Px = bra.px[ib][i], Py = bra.py[ib][i], Pz = bra.pz[ib][i];
+        const T kb = bra.kw[ib][i] * T(kTwoPi52);
         T part = T(0);
         for (int k = 0; k < nk; ++k) {
             const T q = ket.pe[ik][k];
             const T dx = Px - ket.px[ik][k], dy = Py - ket.py[ik][k], dz = Pz - ket.pz[ik][k];
             const T r2 = dx * dx + dy * dy + dz * dz;
-            const T pq = p * q, s = p + q;
-            const T rho = pq / s;
-            // 2 pi^{5/2} / (p q sqrt(p+q)) = 2 pi^{5/2} * rsqrt(s) / pq
-            const T pref = T(kTwoPi52) * Boys<T>::rsq(s) / pq;
-            part += ket.kw[ik][k] * pref * Boys<T>::f0(rho * r2);
+            const T r = Boys<T>::rsq(p + q);
+            const T rho = p * q * r * r;
+            part += ket.kw[ik][k] * r * Boys<T>::f0(rho * r2);
         }
         acc += kb * part;
     }
@@ -111,7 +113,7 @@ __device__ __forceinline__ void fill_pairs(PairSmem<T, 128, MAXPP_> &ps, int bas
                     ps.px[slot][cnt] = (T)((a * ax + b * bx) / pe - ox);
                     ps.py[slot][cnt] = (T)((a * ay + b * by) / pe - oy);
                     ps.pz[slot][cnt] = (T)((a * az + b * bz) / pe - oz);
-                    ps.kw[slot][cnt] = (T)kw;
+                    ps.kw[slot][cnt] = (T)(kw / pe);
                     ++cnt;
                 }
         }

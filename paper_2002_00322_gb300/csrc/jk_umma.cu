@@ -17,9 +17,11 @@
 // i.e. one MMA with N = [D_hi | D^T_hi | D_lo | D^T_lo] and one with the
 // first half of those columns.
 //
-// Bricks are ordered so that runs share (P, Q, R): V1, V2 and J1 keep their
-// outputs across a run in tensor memory; V3, V4 and J2 are flushed per brick
-// (double-buffered).  Flushes add into FP64 accumulators with atomics.
+// Bricks are ordered so that runs share (P, Q, R): V1 and V2 keep their
+// outputs across a run in tensor memory; V3, V4, J2 and J1 are flushed per
+// brick (double-buffered; the Coulomb views are flushed per brick because
+// their FP32 sums over a run lose accuracy when transition densities cancel).
+// Flushes add into FP64 accumulators with reductions.
 //
 // Warp roles (320 threads): warp 0 producer (bulk copies of the packed brick
 // record and the six density tiles), warp 1 tensor-memory owner and MMA
@@ -53,7 +55,7 @@ constexpr int CTRL_BYTES = 4096;
 // epilogue staging of flushed output blocks: two exchange views (D and D^T
 // parts, 2 x 16 x 64 floats each) and one Coulomb view (16 x 64 floats)
 constexpr int STAGE_K_FLOATS = 2 * MPMAX * 64;
-constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + MPMAX * 64) * 4;
+constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + 2 * MPMAX * 64) * 4;
 constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES + EPI_BYTES;
 
 struct Ctrl {
@@ -291,7 +293,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         const uint32_t idm_full = idesc_f16(64, F, 1, a.bf16), idm_half = idesc_f16(64, G, 1, a.bf16);
         const uint32_t id_jf = idesc_f16(64, G, 0, a.bf16), id_jh = idesc_f16(64, mp, 0, a.bf16);
         const uint32_t idm_jf = idesc_f16(64, G, 1, a.bf16), idm_jh = idesc_f16(64, mp, 1, a.bf16);
-        const uint32_t colV1 = 0, colV2 = F, colJ1 = 2 * F;
+        // tensor memory: V1, V2 resident for a run (2F columns); per brick,
+        // double-buffered: V3, V4, J2, J1 (2F + 2G columns each); 6F + 4G <= 512
+        const uint32_t colV1 = 0, colV2 = F;
         BrickDesc dnext = a.bricks[beg];
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1, b = i & 1;
@@ -307,8 +311,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
             const uint32_t B1 = st + OFF_B1, B2 = B1 + KB_BYTES_MAX, B3 = B2 + KB_BYTES_MAX,
                            B4 = B3 + KB_BYTES_MAX, B5 = st + OFF_B5, B6 = B5 + JB_BYTES_MAX;
-            const uint32_t var = 2 * F + G + (uint32_t)b * (2 * F + G);
-            const uint32_t colV3 = var, colV4 = var + F, colJ2 = var + 2 * F;
+            const uint32_t var = 2 * F + (uint32_t)b * (2 * F + 2 * G);
+            const uint32_t colV3 = var, colV4 = var + F, colJ2 = var + 2 * F, colJ1 = var + 2 * F + G;
             // exchange views: K-major (V1, V2) and MN-major (V3, V4) over the same tile
             struct View { uint32_t col, kstep, lbo, sbo, idf, idh, B; bool fresh; };
             const View views[4] = {
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 mma_f16(tmem + colJ1, sdesc(WH + j * 256, 128, 1024), sdesc(B5 + j * 256, 128, 1024), id_jf,
-                        (j > 0 || !first) ? 1u : 0u);
+                        j > 0 ? 1u : 0u);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 mma_f16(tmem + colJ1, sdesc(WL + j * 256, 128, 1024), sdesc(B5 + j * 256, 128, 1024), id_jh, 1u);
@@ -425,16 +429,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         float *stA = reinterpret_cast<float *>(sm + 2 * STAGE_BYTES + CTRL_BYTES);
         float *stB = stA + STAGE_K_FLOATS;
         float *stJ = stB + STAGE_K_FLOATS;
+        float *stJ1 = stJ + MPMAX * 64;
         auto blk = [&](double *base, int X, int Y) { return base + ((int64_t)(X * nb + Y) * mtot + a.d0) * 64; };
-        auto stage3 = [&](uint32_t c1, uint32_t c2, uint32_t c3) {
+        // exchange views c1, c2 and (when c3 >= 0) Coulomb views c3 -> stJ, c4 -> stJ1
+        auto stage4 = [&](uint32_t c1, uint32_t c2, int c3, int c4) {
             if (mp == 16) {
                 stage_view<16, true>(tl + c1, live, row, m, inv, stA);
                 stage_view<16, true>(tl + c2, live, row, m, inv, stB);
-                stage_view<16, false>(tl + c3, live, row, m, inv, stJ);
+                if (c3 >= 0) stage_view<16, false>(tl + c3, live, row, m, inv, stJ);
+                if (c4 >= 0) stage_view<16, false>(tl + c4, live, row, m, inv, stJ1);
             } else {
                 stage_view<8, true>(tl + c1, live, row, m, inv, stA);
                 stage_view<8, true>(tl + c2, live, row, m, inv, stB);
-                stage_view<8, false>(tl + c3, live, row, m, inv, stJ);
+                if (c3 >= 0) stage_view<8, false>(tl + c3, live, row, m, inv, stJ);
+                if (c4 >= 0) stage_view<8, false>(tl + c4, live, row, m, inv, stJ1);
             }
         };
         for (int i = 0; i < nloc; ++i) {
@@ -449,9 +457,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             if (c.edecide) break;
             tc_fence_after();
             const unsigned act = tuple_activity(d.P, d.Q, d.R, d.S);
-            const uint32_t var = 2 * F + G + (uint32_t)b * (2 * F + G);
-            // per-brick accumulators V3, V4, J2 -> staging, then release them
-            stage3(var, var + F, var + 2 * F);
+            const uint32_t var = 2 * F + (uint32_t)b * (2 * F + 2 * G);
+            // per-brick accumulators V3, V4, J2, J1 -> staging, then release them
+            stage4(var, var + F, (int)(var + 2 * F), (int)(var + 2 * F + G));
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&c.acce[b]);
@@ -461,9 +469,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             if (act & (1u << 3)) flush_block(stB, blk(a.Kacc, d.Q, d.S), m, et);
             if (act & (1u << 7)) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.S, d.Q), m, et);
             if (act & (1u << 4)) flush_block(stJ, blk(a.Jacc, d.R, d.S), m, et);
+            flush_block(stJ1, blk(a.Jacc, d.P, d.Q), m, et);
             named_bar_sync(2, 128);
             if (last) {
-                stage3(0, F, 2 * F);
+                stage4(0, F, -1, -1);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&c.fixe);
@@ -472,7 +481,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
                 if (act & (1u << 4)) flush_block(stA + MPMAX * 64, blk(a.Kacc, d.R, d.P), m, et);
                 if (act & (1u << 1)) flush_block(stB, blk(a.Kacc, d.Q, d.R), m, et);
                 if (act & (1u << 6)) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.R, d.Q), m, et);
-                flush_block(stJ, blk(a.Jacc, d.P, d.Q), m, et);
                 named_bar_sync(2, 128);
             }
         }

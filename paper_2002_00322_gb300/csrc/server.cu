@@ -38,6 +38,7 @@ struct Molecule {
     int64_t bytes = 0;        // device bytes of the handle
     uint64_t last_use = 0;
     bool busy = false;
+    int queued = 0;           // requests waiting for this molecule
 };
 
 struct Request {
@@ -131,8 +132,9 @@ void evict(esmf_server *s, int idx) {
     ++s->evictions;
 }
 
-// free device memory for a handle of molecule idx: evict idle handles,
-// least recently used first, until the upper bound of its store fits
+// free device memory for a handle of molecule idx: evict idle handles until
+// the upper bound of its store fits, taking molecules with no queued requests
+// first and, among equals, the least recently used
 void make_room(esmf_server *s, int idx) {
     const Molecule &mol = s->mols[idx];
     const int64_t np = (mol.n + 7) / 8 * 8;
@@ -145,7 +147,10 @@ void make_room(esmf_server *s, int idx) {
         for (size_t i = 0; i < s->mols.size(); ++i) {
             const Molecule &c = s->mols[i];
             if ((int)i == idx || !c.h || c.busy) continue;
-            if (victim < 0 || c.last_use < s->mols[victim].last_use) victim = (int)i;
+            if (victim < 0) { victim = (int)i; continue; }
+            const Molecule &v = s->mols[victim];
+            const bool cq = c.queued > 0, vq = v.queued > 0;
+            if ((cq != vq && !cq) || (cq == vq && c.last_use < v.last_use)) victim = (int)i;
         }
         if (victim < 0) return;
         evict(s, victim);
@@ -308,12 +313,23 @@ void worker_main(esmf_server *s) {
                 finish(s, sl, ESMF_ERR_CUDA);
             }
         }
-        // admissions, in arrival order; a request whose molecule is busy waits
-        // without blocking the requests behind it
-        for (auto it = s->pending.begin(); it != s->pending.end();) {
-            if (s->inflight >= s->max_inflight) break;
-            if (try_admit(s, *it)) it = s->pending.erase(it);
-            else ++it;
+        // admissions: first, in arrival order, requests whose molecule is
+        // resident (no integral evaluation needed); then the others, which
+        // may create handles and evict idle molecules.  A request whose
+        // molecule is busy waits without blocking the requests behind it.
+        for (int pass = 0; pass < 2; ++pass) {
+            for (auto it = s->pending.begin(); it != s->pending.end();) {
+                if (s->inflight >= s->max_inflight) break;
+                Molecule &mol = s->mols[(*it)->mol];
+                if (pass == 0 && !mol.h) { ++it; continue; }
+                --mol.queued;
+                if (try_admit(s, *it)) {
+                    it = s->pending.erase(it);
+                } else {
+                    ++mol.queued;
+                    ++it;
+                }
+            }
         }
         if (s->inflight > 0) {
             lk.unlock();
@@ -407,6 +423,7 @@ int esmf_server_submit(esmf_server_t *s, int basis_id, int m, const double *D, d
         r->ticket = s->next_ticket++;
         s->tickets[r->ticket] = r;
         s->pending.push_back(r);
+        ++s->mols[basis_id].queued;
         ++s->submitted;
         if (!s->have_first) { s->first_submit = r->t_submit; s->have_first = true; }
         *ticket = r->ticket;
