@@ -139,6 +139,8 @@ def run_ours(args):
     def step():
         fock.esmf_fock_build(fb.h, m, D, J, K, F, t, stream)
 
+    # the autotuner picks densities per pass for this m (untimed, like warm-up)
+    chunk = fock.esmf_fock_autotune(fb.h, m, D, J, K, 3, stream) if not args.no_autotune else 0
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -215,6 +217,7 @@ def run_ours(args):
                       "l2": "integral store larger than L2 streams every step",
                       "store_bytes": st["store_bytes"], "quartets_kept": st["n_quartets_kept"],
                       "bricks": st["n_bricks"], "setup_ms": round(st["create_ms"], 1),
+                      "densities_per_pass": chunk,
                       "parallelism": f"replicas x{world}"},
            "quartets_per_s": round(world * st["n_quartets_kept"] / (ms_step / 1e3), 1),
            "density_builds_per_s": round(world * m * 1e3 / ms_step, 1),
@@ -365,6 +368,7 @@ def main():
     ap.add_argument("--precision", default="fp16x2", choices=["fp64", "fp32", "fp16x2", "bf16x2"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=32)

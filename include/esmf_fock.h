@@ -136,6 +136,17 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J,
                     double *K, double *F, double *traces, void *stream);
 
 /*
+ * esmf_fock_build_shard -- the part of esmf_fock_build contributed by shard
+ * `shard` of `nshards` equal contiguous slices of the handle's kept brick
+ * list.  J, K, F and the traces are linear in the integrals, so the element-
+ * wise sum of the outputs of all shards (e.g. one all-reduce across GPUs, each
+ * holding a handle for the same basis) equals the full build.  Same buffers,
+ * asynchrony and errors as esmf_fock_build; INVALID_ARG for a bad shard.
+ */
+int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const double *D,
+                          double *J, double *K, double *F, double *traces, void *stream);
+
+/*
  * esmf_fock_build_host -- the same build with HOST buffers: copies D to the
  * device, builds, copies J, K (and F, traces when non-NULL) back, and waits
  * for completion with a bounded wait of timeout_ms milliseconds (<= 0 means
@@ -156,6 +167,18 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host,
 #define ESMF_PATH_AUTO       0
 #define ESMF_PATH_CUDA_CORE  1
 int esmf_fock_set_path(esmf_fock_t *h, int path);
+
+/*
+ * esmf_fock_autotune -- pick the number of densities contracted per pass
+ * over each brick tile for builds with m densities on this handle: times each
+ * candidate (16 or 8 per tensor-core pass; 16/8/4 per CUDA-core pass for
+ * FP32, 8/4 for FP64) as the median of `reps` builds (after one warm-up) on
+ * the caller's device buffers D (read), J and K (overwritten), and records
+ * the fastest; later builds with the same m use it.  *chosen (optional)
+ * receives it.  Synchronises the stream.  Errors: as esmf_fock_build.
+ */
+int esmf_fock_autotune(esmf_fock_t *h, int m, const double *D, double *J, double *K, int reps,
+                       void *stream, int *chosen);
 
 /*
  * Device-side error flag of the handle: non-zero when a bounded wait inside

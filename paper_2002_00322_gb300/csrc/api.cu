@@ -46,6 +46,8 @@ struct esmf_fock {
     void *store = nullptr;
     float vscale = 1.0f;           // power-of-two scale of split 16-bit stores
     int path = ESMF_PATH_AUTO;
+    std::vector<std::pair<int, int>> tuned;   // (m, densities per pass) picked by esmf_fock_autotune
+    int force_chunk = 0;                      // set while the autotuner times a candidate
     int num_sms = 0;
     // tensor-core path work memory
     uint16_t *kbank = nullptr, *jbank = nullptr;
@@ -427,8 +429,15 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     return ESMF_OK;
 }
 
-int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K, double *F,
-                    double *traces, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// the build over kept bricks [b0, b1) of the handle's list; J, K, F and the
+// traces are linear in the integrals, so builds over a partition of the list
+// sum to the full build
+int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, double *J, double *K,
+                double *F, double *traces, void *stream) {
     if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
     if (m < 1 || m > ESMF_MAX_DENSITIES) { set_error("m = %d outside [1, %d]", m, ESMF_MAX_DENSITIES); return ESMF_ERR_INVALID_ARG; }
     if (!D || !J || !K) { set_error("D, J and K are required"); return ESMF_ERR_INVALID_ARG; }
@@ -445,10 +454,11 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
     CKR(cudaMemsetAsync(h->Jacc, 0, acc, s));
     CKR(cudaMemsetAsync(h->Kacc, 0, acc, s));
     if (traces) CKR(cudaMemsetAsync(traces, 0, sizeof(double) * m, s));
-    if (h->nbricks > 0) {
+    if (b1 > b0) {
         JKArgs a;
-        a.b = h->dev(); a.Q = h->Q; a.tol = h->tol; a.bricks = h->bricks; a.nbricks = h->nbricks;
-        a.offsets = h->offsets; a.store = h->store; a.precision = h->prec; a.mode = h->mode;
+        a.b = h->dev(); a.Q = h->Q; a.tol = h->tol; a.bricks = h->bricks + b0; a.nbricks = b1 - b0;
+        a.offsets = h->offsets ? h->offsets + b0 : nullptr; a.store = h->store; a.precision = h->prec;
+        a.mode = h->mode;
         a.m = m; a.D = D; a.Jacc = h->Jacc; a.Kacc = h->Kacc;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->timing && h->ev_used < 65536) {
@@ -463,15 +473,21 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
             ++h->ev_used;
         }
         a.vscale = h->vscale;
+        int chunk = h->force_chunk;
+        if (!chunk)
+            for (auto &t : h->tuned)
+                if (t.first == m) chunk = t.second;
+        a.mc = chunk;
         const bool split16 = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
         if (split16 && h->path != ESMF_PATH_CUDA_CORE) {
             UmmaLaunch L;
-            L.bricks = h->bricks; L.nbricks = h->nbricks; L.offsets = h->offsets;
+            L.bricks = h->bricks + b0; L.nbricks = b1 - b0; L.offsets = h->offsets + b0;
             L.store = (const uint32_t *)h->store; L.kbank = h->kbank; L.jbank = h->jbank;
             L.dmax_bits = h->dmax; L.D = D; L.n = h->n; L.np = h->np; L.nb = h->nb; L.m = m;
             L.bf16 = h->prec == ESMF_PREC_BF16X2; L.num_sms = h->num_sms; L.vscale = h->vscale;
             L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev;
             L.ev_start = e0; L.ev_stop = e1;
+            L.chunk = chunk ? chunk : 16;
             RET(launch_jk_umma(L, s));
             return launch_finalize_blocked(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s);
         }
@@ -482,6 +498,27 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
     }
     RET(launch_finalize(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s));
     return ESMF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K, double *F,
+                    double *traces, void *stream) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    return build_range(h, 0, h->nbricks, m, D, J, K, F, traces, stream);
+}
+
+int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const double *D, double *J,
+                          double *K, double *F, double *traces, void *stream) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    if (nshards < 1 || shard < 0 || shard >= nshards) {
+        set_error("shard %d of %d", shard, nshards);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    const int64_t b0 = h->nbricks * shard / nshards, b1 = h->nbricks * (shard + 1) / nshards;
+    return build_range(h, b0, b1, m, D, J, K, F, traces, stream);
 }
 
 int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host, double *J_host, double *K_host,
@@ -532,6 +569,54 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host, double *J_
 int esmf_fock_set_path(esmf_fock_t *h, int path) {
     if (!h || path < ESMF_PATH_AUTO || path > ESMF_PATH_CUDA_CORE) { set_error("bad handle or path"); return ESMF_ERR_INVALID_ARG; }
     h->path = path;
+    return ESMF_OK;
+}
+
+int esmf_fock_autotune(esmf_fock_t *h, int m, const double *D, double *J, double *K, int reps,
+                       void *stream, int *chosen) {
+    if (!h || m < 1 || m > ESMF_MAX_DENSITIES || !D || !J || !K) { set_error("bad autotune arguments"); return ESMF_ERR_INVALID_ARG; }
+    DeviceGuard g(h->device);
+    if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
+    const bool tensor = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2 && h->path != ESMF_PATH_CUDA_CORE;
+    std::vector<int> cand;
+    if (tensor) { cand.push_back(16); if (m > 8) cand.push_back(8); }
+    else if (h->prec == ESMF_PREC_FP64) { cand.push_back(8); cand.push_back(4); }
+    else { cand.push_back(16); cand.push_back(8); cand.push_back(4); }
+    if (reps < 1) reps = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CKR(cudaEventCreate(&e0));
+    CKR(cudaEventCreate(&e1));
+    int best = cand[0];
+    float best_ms = 0.f;
+    int rc = ESMF_OK;
+    for (int c : cand) {
+        h->force_chunk = c;
+        if ((rc = esmf_fock_build(h, m, D, J, K, nullptr, nullptr, s)) != ESMF_OK) break;   // warm-up
+        std::vector<float> t;
+        for (int r = 0; r < reps && rc == ESMF_OK; ++r) {
+            cudaEventRecord(e0, s);
+            rc = esmf_fock_build(h, m, D, J, K, nullptr, nullptr, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = ESMF_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t.push_back(ms);
+        }
+        if (rc != ESMF_OK) break;
+        std::sort(t.begin(), t.end());
+        const float med = t[t.size() / 2];
+        if (c == cand[0] || med < best_ms) { best = c; best_ms = med; }
+    }
+    h->force_chunk = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ESMF_OK) return rc;
+    bool found = false;
+    for (auto &t : h->tuned)
+        if (t.first == m) { t.second = best; found = true; }
+    if (!found) h->tuned.push_back({m, best});
+    if (chosen) *chosen = best;
     return ESMF_OK;
 }
 

@@ -73,6 +73,7 @@ struct JKArgs {
     const double *D;          // m x n x n (caller layout)
     double *Jacc, *Kacc;      // m x np x np accumulators (zeroed by caller)
     float vscale;             // store scale of the split 16-bit precisions
+    int mc = 0;               // densities per pass (0: default for the precision)
 };
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s);
 int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s);
@@ -91,6 +92,7 @@ struct UmmaLaunch {
     double *Jacc, *Kacc;         // block-major accumulators [X][Y][k][x][y]
     int *error;                  // device flag, 0 = ok
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional timing
+    int chunk = 16;              // densities per tensor-core pass (8 or 16)
 };
 int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s);
 int launch_finalize_blocked(const DevBasis &b, int m, const double *D, const double *Jb, const double *Kb,

@@ -230,14 +230,27 @@ static int jk_launch(const JKArgs &a, cudaStream_t s) {
     return ESMF_OK;
 }
 
+// MC (densities per pass over a brick's shared-memory tile) is a tuning
+// parameter: 4/8/16 for float arithmetic, 4/8 for double (0 = default).
+template <typename TA, int SRC>
+static int jk_launch_mc(const JKArgs &a, cudaStream_t s) {
+    if (sizeof(TA) == 8) {
+        if (a.mc == 4) return jk_launch<TA, 4, SRC>(a, s);
+        return jk_launch<TA, 8, SRC>(a, s);
+    }
+    if (a.mc == 4) return jk_launch<TA, 4, SRC>(a, s);
+    if (a.mc == 8) return jk_launch<TA, 8, SRC>(a, s);
+    return jk_launch<TA, 16, SRC>(a, s);
+}
+
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
     if (a.mode == ESMF_MODE_DIRECT) {
-        if (a.precision == ESMF_PREC_FP64) return jk_launch<double, 8, 4>(a, s);
-        return jk_launch<float, 16, 4>(a, s);
+        if (a.precision == ESMF_PREC_FP64) return jk_launch_mc<double, 4>(a, s);
+        return jk_launch_mc<float, 4>(a, s);
     }
     switch (a.precision) {
-        case ESMF_PREC_FP64: return jk_launch<double, 8, 0>(a, s);
-        case ESMF_PREC_FP32: return jk_launch<float, 16, 1>(a, s);
+        case ESMF_PREC_FP64: return jk_launch_mc<double, 0>(a, s);
+        case ESMF_PREC_FP32: return jk_launch_mc<float, 1>(a, s);
         default: break;
     }
     set_error("launch_jk_cuda: precision %d needs the split-precision path", a.precision);
@@ -246,8 +259,8 @@ int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
 
 // split-precision stores on CUDA cores (reference path for the tensor kernel)
 int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s) {
-    if (a.precision == ESMF_PREC_FP16X2) return jk_launch<float, 16, 2>(a, s);
-    if (a.precision == ESMF_PREC_BF16X2) return jk_launch<float, 16, 3>(a, s);
+    if (a.precision == ESMF_PREC_FP16X2) return jk_launch_mc<float, 2>(a, s);
+    if (a.precision == ESMF_PREC_BF16X2) return jk_launch_mc<float, 3>(a, s);
     set_error("launch_jk_cuda_split: bad precision %d", a.precision);
     return ESMF_ERR_INVALID_ARG;
 }

@@ -507,8 +507,9 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
     if (e != cudaSuccess) { set_error("k_dmax: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
     e = cudaFuncSetAttribute(k_jk_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
     if (e != cudaSuccess) { set_error("smem attribute: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
-    for (int d0 = 0; d0 < L.m; d0 += MPMAX) {
-        const int mc = (L.m - d0) < MPMAX ? (L.m - d0) : MPMAX;
+    const int chunk = (L.chunk == 8) ? 8 : MPMAX;
+    for (int d0 = 0; d0 < L.m; d0 += chunk) {
+        const int mc = (L.m - d0) < chunk ? (L.m - d0) : chunk;
         const int mp = mc <= 8 ? 8 : 16;
         const int64_t work = (int64_t)L.nb * L.nb * 4 * mp * 64 + (int64_t)L.nb * (L.nb + 1) / 2 * 2 * mp * 64;
         int g = (int)((work + 255) / 256);
@@ -527,7 +528,7 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
         if (grid > L.nbricks) grid = (int)L.nbricks;
         if (L.ev_start && d0 == 0) cudaEventRecord(L.ev_start, s);
         k_jk_umma<<<grid, NTHREADS, SMEM_TOTAL, s>>>(p);
-        if (L.ev_stop && d0 + MPMAX >= L.m) cudaEventRecord(L.ev_stop, s);
+        if (L.ev_stop && d0 + chunk >= L.m) cudaEventRecord(L.ev_stop, s);
         e = cudaGetLastError();
         if (e != cudaSuccess) { set_error("k_jk_umma: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
     }

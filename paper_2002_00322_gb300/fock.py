@@ -30,7 +30,8 @@ MAX_PRIM = 4
 EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_fock_stats",
            "esmf_fock_schwarz", "esmf_fock_destroy", "esmf_strerror", "esmf_last_error",
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
-           "esmf_fock_set_path", "esmf_fock_device_error"]
+           "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
+           "esmf_fock_autotune"]
 PATHS = {"auto": 0, "cuda_core": 1}
 # declared in include/esmf_server.h, bound in server.py
 SERVER_EXPORTS = ["esmf_server_create", "esmf_server_register", "esmf_server_submit",
@@ -84,6 +85,10 @@ def load(path=None):
         L.esmf_fock_build.restype = C.c_int
         L.esmf_fock_build_noalloc.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         L.esmf_fock_build_noalloc.restype = C.c_int
+        L.esmf_fock_autotune.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, vp, C.POINTER(C.c_int)]
+        L.esmf_fock_autotune.restype = C.c_int
+        L.esmf_fock_build_shard.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+        L.esmf_fock_build_shard.restype = C.c_int
         L.esmf_fock_build_host.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, C.c_int]
         L.esmf_fock_build_host.restype = C.c_int
         L.esmf_fock_stats.argtypes = [vp, C.POINTER(esmf_stats_t)]
@@ -157,6 +162,21 @@ def esmf_fock_build_noalloc(h, m, D, J, K, F=None, traces=None, stream=None):
     rc = load().esmf_fock_build_noalloc(h, int(m), _ptr(D), _ptr(J), _ptr(K), _ptr(F), _ptr(traces),
                                         _stream_ptr(stream))
     _check(rc, "esmf_fock_build_noalloc")
+
+
+def esmf_fock_autotune(h, m, D, J, K, reps=3, stream=None):
+    """Returns the chosen number of densities per pass."""
+    ch = C.c_int()
+    rc = load().esmf_fock_autotune(h, int(m), _ptr(D), _ptr(J), _ptr(K), int(reps), _stream_ptr(stream),
+                                   C.byref(ch))
+    _check(rc, "esmf_fock_autotune")
+    return ch.value
+
+
+def esmf_fock_build_shard(h, shard, nshards, m, D, J, K, F=None, traces=None, stream=None):
+    rc = load().esmf_fock_build_shard(h, int(shard), int(nshards), int(m), _ptr(D), _ptr(J), _ptr(K),
+                                      _ptr(F), _ptr(traces), _stream_ptr(stream))
+    _check(rc, "esmf_fock_build_shard")
 
 
 def esmf_fock_build_host(h, m, D, J, K, F=None, traces=None, stream=None, timeout_ms=0):
@@ -235,6 +255,12 @@ class FockBuilder:
 
     def stats(self):
         return esmf_fock_stats(self.h)
+
+    def autotune(self, D, reps=3):
+        import torch
+        J = torch.empty_like(D)
+        K = torch.empty_like(D)
+        return esmf_fock_autotune(self.h, D.shape[0], D, J, K, reps)
 
     def set_path(self, path):
         esmf_fock_set_path(self.h, path)

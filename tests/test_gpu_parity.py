@@ -258,3 +258,21 @@ def test_direct_full_ribbon_sampled(esmf, mode, prec):
         ej = np.max(np.abs(J[k][jidx[:, 0], jidx[:, 1]] - Je[k])) / np.max(np.abs(J[k]))
         ek = np.max(np.abs(K[k][kidx[:, 0], kidx[:, 1]] - Ke[k])) / np.max(np.abs(K[k]))
         assert ej <= 2e-6 and ek <= 2e-6, (k, ej, ek)
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "fp32", "fp64"])
+def test_autotune_keeps_results(esmf, prec):
+    """The autotuner may change how many densities each pass contracts; the
+    results must not change beyond the precision's tolerance."""
+    import torch
+    w = W.small_random(37, 12, 5, tol=1e-10, edge=13.25)
+    D = torch.from_numpy(w.D).cuda()
+    with esmf.FockBuilder(w.basis, w.tol, "stored", prec) as fb:
+        J0, K0, _, _ = fb.build(D)
+        chosen = fb.autotune(D, reps=2)
+        J1, K1, _, _ = fb.build(D)
+        torch.cuda.synchronize()
+    assert chosen in (4, 8, 16)
+    for k in range(w.m):
+        assert relerr(J1[k].cpu().numpy(), J0[k].cpu().numpy()) <= TOL[prec]
+        assert relerr(K1[k].cpu().numpy(), K0[k].cpu().numpy()) <= TOL[prec]
