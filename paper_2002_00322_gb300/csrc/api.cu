@@ -351,27 +351,48 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     const int align_elems = 16 / eb;     // every brick's record starts on 16 bytes
     const bool split16 = precision >= ESMF_PREC_FP16X2;
     const int head = split16 ? MASK_WORDS : 0;   // keep mask ahead of the values
-    int64_t off = 0, unique = 0;
+    int64_t unique = 0;
+    std::vector<int64_t> order;
     for (int64_t i = 0; i < ncand; ++i) {
         if (counts[i] == 0) continue;
+        order.push_back(i);
+        unique += counts[ncand + i];
+    }
+    // bricks of one bra pair are consecutive in candidate order (R, S ascending);
+    // reorder them by (S window, R, S)
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const BrickDesc &x = cand[a], &y = cand[b];
+        if (x.P != y.P) return x.P < y.P;
+        if (x.Q != y.Q) return x.Q < y.Q;
+        if (x.S / SWIN != y.S / SWIN) return x.S / SWIN < y.S / SWIN;
+        if (x.R != y.R) return x.R < y.R;
+        return x.S < y.S;
+    });
+    int64_t off = 0;
+    for (int64_t i : order) {
         BrickDesc d = cand[i];
         d.nkept = counts[i];
         kept.push_back(d);
         offs.push_back(off);
         off += (head + counts[i] + align_elems - 1) / align_elems * align_elems;
-        unique += counts[ncand + i];
     }
     offs.push_back(off);
-    // runs of bricks sharing (P, Q, R); the brick (P Q | P Q) is a run of its own
+    // runs share (P, Q, R) inside an item; items share (P, Q, S window); the
+    // brick (P Q | P Q) is a run and an item of its own
     {
         auto diag = [&](size_t i) { return kept[i].R == kept[i].P && kept[i].S == kept[i].Q; };
-        auto same = [&](size_t i, size_t j) {
-            return kept[i].P == kept[j].P && kept[i].Q == kept[j].Q && kept[i].R == kept[j].R;
+        auto same_item = [&](size_t i, size_t j) {
+            return kept[i].P == kept[j].P && kept[i].Q == kept[j].Q && kept[i].S / SWIN == kept[j].S / SWIN &&
+                   !diag(i) && !diag(j);
         };
+        auto same_run = [&](size_t i, size_t j) { return same_item(i, j) && kept[i].R == kept[j].R; };
         for (size_t i = 0; i < kept.size(); ++i) {
-            const bool first = i == 0 || !same(i, i - 1) || diag(i) || diag(i - 1);
-            const bool last = i + 1 == kept.size() || !same(i, i + 1) || diag(i) || diag(i + 1);
-            kept[i].pad = (first ? 1 : 0) | (last ? 2 : 0);
+            const bool fr = i == 0 || !same_run(i, i - 1);
+            const bool lr = i + 1 == kept.size() || !same_run(i, i + 1);
+            const bool fi = i == 0 || !same_item(i, i - 1);
+            const bool li = i + 1 == kept.size() || !same_item(i, i + 1);
+            kept[i].pad = (fr ? BRICK_RUN_FIRST : 0) | (lr ? BRICK_RUN_LAST : 0) | (fi ? BRICK_ITEM_FIRST : 0) |
+                          (li ? BRICK_ITEM_LAST : 0);
         }
     }
     // split 16-bit stores: one power-of-two scale with |value * scale| < 2^14

@@ -25,8 +25,14 @@ constexpr int MAXPP = MAXP * MAXP;
 struct BrickDesc {          // 16 bytes
     int16_t P, Q, R, S;     // function-block indices
     int32_t nkept;          // kept elements
-    int32_t pad;            // bit 0: first brick of a (P,Q,R) run, bit 1: last brick of it
+    int32_t pad;            // bits 0/1: first/last brick of a run, bits 2/3: first/last of an item
 };
+
+// Brick order of a store: by bra block pair (P,Q), then by window of SWIN
+// consecutive S blocks (an "item"), then R (a "run": fixed P, Q, R), then S.
+// The brick (P Q | P Q) forms an item of its own.
+constexpr int SWIN = 5;
+enum : int { BRICK_RUN_FIRST = 1, BRICK_RUN_LAST = 2, BRICK_ITEM_FIRST = 4, BRICK_ITEM_LAST = 8 };
 
 // Split 16-bit stores (FP16X2 / BF16X2) hold one record per brick: a 512-byte
 // keep mask (byte v = p*64 + q*8 + r, bit s) followed by the kept values as

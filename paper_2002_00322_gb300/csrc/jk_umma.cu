@@ -14,14 +14,15 @@
 // views (two K-major, two MN-major descriptors over the same bytes); the
 // Coulomb views read a second copy W[p][r][q][s].  Products are formed as
 //   V_hi D_hi + V_hi D_lo + V_lo D_hi   (FP32 accumulation in tensor memory),
-// i.e. one MMA with N = [D_hi | D^T_hi | D_lo | D^T_lo] and one with the
-// first half of those columns.
+// three MMAs into the same columns ([D | D^T] for exchange, N = 2m).
 //
-// Bricks are ordered so that runs share (P, Q, R): V1 and V2 keep their
-// outputs across a run in tensor memory; V3, V4, J2 and J1 are flushed per
-// brick (double-buffered; the Coulomb views are flushed per brick because
-// their FP32 sums over a run lose accuracy when transition densities cancel).
-// Flushes add into FP64 accumulators with reductions.
+// Bricks come in items: a bra pair (P,Q) with a window of SWIN S blocks, all
+// R; within an item, runs share R.  V3 and V4 accumulate K{P,S} and K{Q,S}
+// for every S of the window over the whole item, V1 and V2 accumulate K{P,R}
+// and K{Q,R} over a run (double-buffered by run), and the Coulomb views are
+// flushed per brick (double-buffered; their FP32 sums over longer spans lose
+// accuracy when transition densities cancel).  Flushes add into FP64
+// accumulators with reductions.
 //
 // Warp roles (320 threads): warp 0 producer (bulk copies of the packed brick
 // record and the six density tiles), warp 1 tensor-memory owner and MMA
@@ -59,7 +60,7 @@ constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + 2 * MPMAX * 64) * 4;
 constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES + EPI_BYTES;
 
 struct Ctrl {
-    uint64_t full[2], conv[2], mmad[2], acce[2], fixe;
+    uint64_t full[2], conv[2], mmad[2], acce[2], runfree[2], itemfree;
     uint32_t tmem_base;
     int abort_flag;
     int cdecide, edecide;   // group-uniform copies of abort_flag (converters, epilogue)
@@ -185,27 +186,26 @@ struct UmmaParams {
 
 namespace {
 
-// Load one accumulator view (this thread's TMEM lane) and write it, scaled,
-// to the staging area in block order: D part at [k][x][y], D^T part at
-// [k][y][x] (row = x*8 + y of the view's output block).
+// Load one accumulator region (this thread's TMEM lane) and write it, scaled,
+// to the staging area in block order.  Exchange regions hold [D part | D^T
+// part] (2 MP columns): the D part goes to [k][x][y] and the D^T part to
+// [k][y][x] (row = x*8 + y of the view's output block); Coulomb regions hold
+// MP columns.
 template <int MP, bool KVIEW>
 __device__ __forceinline__ void stage_view(uint32_t taddr, bool live, int row, int m, float inv, float *st) {
-    constexpr int NC = KVIEW ? 4 * MP : 2 * MP;
-    float v[NC];
+    constexpr int NC = KVIEW ? 2 * MP : MP;
+    float v[NC < 16 ? 16 : NC];
 #pragma unroll
     for (int c0 = 0; c0 < NC; c0 += 16) tmem_ld16(taddr + c0, v + c0);
+    if (NC < 16) tmem_ld8(taddr, v);
     tmem_wait_ld();
     if (!live) return;
     const int x = row >> 3, y = row & 7;
 #pragma unroll
     for (int k = 0; k < MP; ++k) {
         if (k < m) {
-            if (KVIEW) {
-                st[k * 64 + x * 8 + y] = (v[k] + v[2 * MP + k]) * inv;
-                st[MPMAX * 64 + k * 64 + y * 8 + x] = (v[MP + k] + v[3 * MP + k]) * inv;
-            } else {
-                st[k * 64 + x * 8 + y] = (v[k] + v[MP + k]) * inv;
-            }
+            st[k * 64 + x * 8 + y] = v[k] * inv;
+            if (KVIEW) st[MPMAX * 64 + k * 64 + y * 8 + x] = v[MP + k] * inv;
         }
     }
 }
@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             mbar_init(&c.mmad[s], 1);
             mbar_init(&c.acce[s], 4);
         }
-        mbar_init(&c.fixe, 4);
+        mbar_init(&c.runfree[0], 4);
+        mbar_init(&c.runfree[1], 4);
+        mbar_init(&c.itemfree, 4);
         c.abort_flag = 0;
         mbar_fence_init();
     }
@@ -288,67 +290,70 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             mbar_wait(&c.full[i & 1], (i >> 1) & 1, abort_flag);
     } else if (nloc > 0 && warp == 1 && lane == 0) {
         // ------------------------------------------------ MMA issuer
-        int run = 0, committed = 0;
-        const uint32_t id_full = idesc_f16(64, F, 0, a.bf16), id_half = idesc_f16(64, G, 0, a.bf16);
-        const uint32_t idm_full = idesc_f16(64, F, 1, a.bf16), idm_half = idesc_f16(64, G, 1, a.bf16);
-        const uint32_t id_jf = idesc_f16(64, G, 0, a.bf16), id_jh = idesc_f16(64, mp, 0, a.bf16);
-        const uint32_t idm_jf = idesc_f16(64, G, 1, a.bf16), idm_jh = idesc_f16(64, mp, 1, a.bf16);
-        // tensor memory: V1, V2 resident for a run (2F columns); per brick,
-        // double-buffered: V3, V4, J2, J1 (2F + 2G columns each); 6F + 4G <= 512
-        const uint32_t colV1 = 0, colV2 = F;
+        // tensor memory: window regions V3[w] at RW*w and V4[w] at RW*(SWIN+w);
+        // run regions V1, V2 at WV + rb*2RW (+RW); per-brick J2, J1 at
+        // WJ + b*2mp (+mp).  At mp = 16: 320 + 128 + 64 = 512 columns.
+        const uint32_t RW = 2 * mp, WV = 2 * SWIN * RW, WJ = WV + 4 * RW;
+        const uint32_t id_k = idesc_f16(64, RW, 0, a.bf16), idm_k = idesc_f16(64, RW, 1, a.bf16);
+        const uint32_t id_j = idesc_f16(64, mp, 0, a.bf16), idm_j = idesc_f16(64, mp, 1, a.bf16);
+        const uint32_t klo = 256u * mp, jlo = 128u * mp;     // byte offset of the lo rows in B tiles
+        int run = 0, item = 0, committed = 0;
+        unsigned touched3 = 0, touched4 = 0;
         BrickDesc dnext = a.bricks[beg];
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1, b = i & 1;
             const BrickDesc d = dnext;
             if (i + 1 < nloc) dnext = a.bricks[beg + i + 1];
-            const bool first = (i == 0) || (d.pad & 1);
-            const bool last = (i == nloc - 1) || (d.pad & 2);
+            const bool frun = (i == 0) || (d.pad & BRICK_RUN_FIRST);
+            const bool lrun = (i == nloc - 1) || (d.pad & BRICK_RUN_LAST);
+            const bool fitem = (i == 0) || (d.pad & BRICK_ITEM_FIRST);
+            const bool litem = (i == nloc - 1) || (d.pad & BRICK_ITEM_LAST);
+            const int rb = run & 1;
             if (!mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag)) { fail(3); break; }
             if (i >= 2 && !mbar_wait(&c.acce[b], ((i - 2) >> 1) & 1, abort_flag)) { fail(4); break; }
-            if (first && run >= 1 && !mbar_wait(&c.fixe, (run - 1) & 1, abort_flag)) { fail(5); break; }
+            if (frun && run >= 2 && !mbar_wait(&c.runfree[rb], ((run - 2) >> 1) & 1, abort_flag)) { fail(5); break; }
+            if (fitem && item >= 1 && !mbar_wait(&c.itemfree, (item - 1) & 1, abort_flag)) { fail(10); break; }
+            if (fitem) { touched3 = 0; touched4 = 0; }
             tc_fence_after();
             const uint32_t st = smem_u32(sm + s * STAGE_BYTES);
             const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
             const uint32_t B1 = st + OFF_B1, B2 = B1 + KB_BYTES_MAX, B3 = B2 + KB_BYTES_MAX,
                            B4 = B3 + KB_BYTES_MAX, B5 = st + OFF_B5, B6 = B5 + JB_BYTES_MAX;
-            const uint32_t var = 2 * F + (uint32_t)b * (2 * F + 2 * G);
-            const uint32_t colV3 = var, colV4 = var + F, colJ2 = var + 2 * F, colJ1 = var + 2 * F + G;
-            // exchange views: K-major (V1, V2) and MN-major (V3, V4) over the same tile
-            struct View { uint32_t col, kstep, lbo, sbo, idf, idh, B; bool fresh; };
-            const View views[4] = {
-                {colV1, 256, 128, 1024, id_full, id_half, B1, first},
-                {colV2, 2048, 1024, 128, id_full, id_half, B2, first},
-                {colV3, 256, 128, 1024, idm_full, idm_half, B3, true},
-                {colV4, 2048, 1024, 128, idm_full, idm_half, B4, true}};
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const View &w = views[v];
+            const bool pq_diff = d.P != d.Q, rs_diff = d.R != d.S;
+            const int w = d.S % SWIN;
+            // three passes into the same columns: hi x [D|D^T]_hi, hi x [D|D^T]_lo, lo x [D|D^T]_hi
+            auto view = [&](uint32_t col, uint32_t AH, uint32_t AL, uint32_t kstep, uint32_t lbo, uint32_t sbo,
+                            uint32_t id, uint32_t B, uint32_t blo, bool fresh) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    mma_f16(tmem + w.col, sdesc(VH + j * w.kstep, w.lbo, w.sbo), sdesc(w.B + j * 256, 128, 1024), w.idf,
-                            (j > 0 || !w.fresh) ? 1u : 0u);
+                    mma_f16(tmem + col, sdesc(AH + j * kstep, lbo, sbo), sdesc(B + j * 256, 128, 1024), id,
+                            (j > 0 || !fresh) ? 1u : 0u);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    mma_f16(tmem + w.col, sdesc(VL + j * w.kstep, w.lbo, w.sbo), sdesc(w.B + j * 256, 128, 1024), w.idh, 1u);
+                    mma_f16(tmem + col, sdesc(AH + j * kstep, lbo, sbo), sdesc(B + blo + j * 256, 128, 1024), id, 1u);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_f16(tmem + col, sdesc(AL + j * kstep, lbo, sbo), sdesc(B + j * 256, 128, 1024), id, 1u);
+            };
+            // exchange: V1, V2 over the run; V3, V4 over the item (nothing when R == S,
+            // V2 and V4 nothing when P == Q: those permutations repeat others)
+            view(WV + rb * 2 * RW, VH, VL, 256, 128, 1024, id_k, B1, klo, frun);
+            if (pq_diff) view(WV + rb * 2 * RW + RW, VH, VL, 2048, 1024, 128, id_k, B2, klo, frun);
+            if (rs_diff) {
+                view(RW * w, VH, VL, 256, 128, 1024, idm_k, B3, klo, !(touched3 & (1u << w)));
+                touched3 |= 1u << w;
             }
-            // Coulomb views over the q<->r swapped copy
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                mma_f16(tmem + colJ1, sdesc(WH + j * 256, 128, 1024), sdesc(B5 + j * 256, 128, 1024), id_jf,
-                        j > 0 ? 1u : 0u);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                mma_f16(tmem + colJ1, sdesc(WL + j * 256, 128, 1024), sdesc(B5 + j * 256, 128, 1024), id_jh, 1u);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                mma_f16(tmem + colJ2, sdesc(WH + j * 2048, 1024, 128), sdesc(B6 + j * 256, 128, 1024), idm_jf,
-                        j > 0 ? 1u : 0u);
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                mma_f16(tmem + colJ2, sdesc(WL + j * 2048, 1024, 128), sdesc(B6 + j * 256, 128, 1024), idm_jh, 1u);
+            if (rs_diff && pq_diff) {
+                view(RW * (SWIN + w), VH, VL, 2048, 1024, 128, idm_k, B4, klo, !(touched4 & (1u << w)));
+                touched4 |= 1u << w;
+            }
+            // Coulomb views, per brick: J1 (K-major over W) and J2 (MN-major over W)
+            view(WJ + b * 2 * mp + mp, WH, WL, 256, 128, 1024, id_j, B5, jlo, true);
+            view(WJ + b * 2 * mp, WH, WL, 2048, 1024, 128, idm_j, B6, jlo, true);
             mma_commit(&c.mmad[s]);
             committed = i + 1;
-            if (last) ++run;
+            if (lrun) ++run;
+            if (litem) ++item;
         }
         if (committed > 0) {
             const int i = committed - 1;
@@ -426,29 +431,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         const uint32_t tl = tmem + ((uint32_t)(slice * 32) << 16);
         const float inv = 1.0f / (a.vscale * density_scale(a.dmax_bits));
         const int m = a.m, nb = a.nb, mtot = a.mtot;
+        const uint32_t RW = 2 * mp, WV = 2 * SWIN * RW, WJ = WV + 4 * RW;
         float *stA = reinterpret_cast<float *>(sm + 2 * STAGE_BYTES + CTRL_BYTES);
         float *stB = stA + STAGE_K_FLOATS;
         float *stJ = stB + STAGE_K_FLOATS;
         float *stJ1 = stJ + MPMAX * 64;
         auto blk = [&](double *base, int X, int Y) { return base + ((int64_t)(X * nb + Y) * mtot + a.d0) * 64; };
-        // exchange views c1, c2 and (when c3 >= 0) Coulomb views c3 -> stJ, c4 -> stJ1
-        auto stage4 = [&](uint32_t c1, uint32_t c2, int c3, int c4) {
+        auto stage = [&](uint32_t col, bool kview, float *dst) {
             if (mp == 16) {
-                stage_view<16, true>(tl + c1, live, row, m, inv, stA);
-                stage_view<16, true>(tl + c2, live, row, m, inv, stB);
-                if (c3 >= 0) stage_view<16, false>(tl + c3, live, row, m, inv, stJ);
-                if (c4 >= 0) stage_view<16, false>(tl + c4, live, row, m, inv, stJ1);
+                if (kview) stage_view<16, true>(tl + col, live, row, m, inv, dst);
+                else stage_view<16, false>(tl + col, live, row, m, inv, dst);
             } else {
-                stage_view<8, true>(tl + c1, live, row, m, inv, stA);
-                stage_view<8, true>(tl + c2, live, row, m, inv, stB);
-                if (c3 >= 0) stage_view<8, false>(tl + c3, live, row, m, inv, stJ);
-                if (c4 >= 0) stage_view<8, false>(tl + c4, live, row, m, inv, stJ1);
+                if (kview) stage_view<8, true>(tl + col, live, row, m, inv, dst);
+                else stage_view<8, false>(tl + col, live, row, m, inv, dst);
             }
         };
+        auto release = [&](uint64_t *bar) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar);
+        };
+        int run = 0;
+        unsigned touched3 = 0, touched4 = 0;
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1, b = i & 1;
             const BrickDesc d = a.bricks[beg + i];
-            const bool last = (i == nloc - 1) || (d.pad & 2);
+            const bool lrun = (i == nloc - 1) || (d.pad & BRICK_RUN_LAST);
+            const bool fitem = (i == 0) || (d.pad & BRICK_ITEM_FIRST);
+            const bool litem = (i == nloc - 1) || (d.pad & BRICK_ITEM_LAST);
+            const bool pq_diff = d.P != d.Q, rs_diff = d.R != d.S;
+            const bool diag = d.R == d.P && d.S == d.Q;
+            if (fitem) { touched3 = 0; touched4 = 0; }
+            if (rs_diff) touched3 |= 1u << (d.S % SWIN);
+            if (rs_diff && pq_diff) touched4 |= 1u << (d.S % SWIN);
             if (!mbar_wait(&c.mmad[s], (i >> 1) & 1, abort_flag)) fail(7);
             // leave together: every epilogue thread must reach the same named barriers
             named_bar_sync(2, 128);
@@ -456,32 +471,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             named_bar_sync(2, 128);
             if (c.edecide) break;
             tc_fence_after();
-            const unsigned act = tuple_activity(d.P, d.Q, d.R, d.S);
-            const uint32_t var = 2 * F + (uint32_t)b * (2 * F + 2 * G);
-            // per-brick accumulators V3, V4, J2, J1 -> staging, then release them
-            stage4(var, var + F, (int)(var + 2 * F), (int)(var + 2 * F + G));
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&c.acce[b]);
+            // per brick: Coulomb views J2 -> J[R,S] (not for the (PQ|PQ) brick) and J1 -> J[P,Q]
+            stage(WJ + b * 2 * mp, false, stJ);
+            stage(WJ + b * 2 * mp + mp, false, stJ1);
+            release(&c.acce[b]);
             named_bar_sync(2, 128);
-            if (act & (1u << 2)) flush_block(stA, blk(a.Kacc, d.P, d.S), m, et);
-            if (act & (1u << 5)) flush_block(stA + MPMAX * 64, blk(a.Kacc, d.S, d.P), m, et);
-            if (act & (1u << 3)) flush_block(stB, blk(a.Kacc, d.Q, d.S), m, et);
-            if (act & (1u << 7)) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.S, d.Q), m, et);
-            if (act & (1u << 4)) flush_block(stJ, blk(a.Jacc, d.R, d.S), m, et);
+            if (!diag) flush_block(stJ, blk(a.Jacc, d.R, d.S), m, et);
             flush_block(stJ1, blk(a.Jacc, d.P, d.Q), m, et);
             named_bar_sync(2, 128);
-            if (last) {
-                stage4(0, F, -1, -1);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&c.fixe);
+            if (lrun) {
+                // V1 -> K[P,R] (and K[R,P] unless (PQ|PQ)), V2 -> K[Q,R], K[R,Q] (P != Q)
+                const int rb = run & 1;
+                stage(WV + rb * 2 * RW, true, stA);
+                if (pq_diff) stage(WV + rb * 2 * RW + RW, true, stB);
+                release(&c.runfree[rb]);
                 named_bar_sync(2, 128);
                 flush_block(stA, blk(a.Kacc, d.P, d.R), m, et);
-                if (act & (1u << 4)) flush_block(stA + MPMAX * 64, blk(a.Kacc, d.R, d.P), m, et);
-                if (act & (1u << 1)) flush_block(stB, blk(a.Kacc, d.Q, d.R), m, et);
-                if (act & (1u << 6)) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.R, d.Q), m, et);
+                if (!diag) flush_block(stA + MPMAX * 64, blk(a.Kacc, d.R, d.P), m, et);
+                if (pq_diff) {
+                    flush_block(stB, blk(a.Kacc, d.Q, d.R), m, et);
+                    if (!diag) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.R, d.Q), m, et);
+                }
                 named_bar_sync(2, 128);
+                ++run;
+            }
+            if (litem) {
+                // window regions: V3 -> K[P,S], K[S,P]; V4 -> K[Q,S], K[S,Q] (D^T parts
+                // not for the (PQ|PQ) item)
+                const int S0 = d.S - d.S % SWIN;
+                for (int w = 0; w < SWIN; ++w) {
+                    const bool h3 = touched3 & (1u << w), h4 = touched4 & (1u << w);
+                    if (!h3 && !h4) continue;
+                    if (h3) stage(RW * w, true, stA);
+                    if (h4) stage(RW * (SWIN + w), true, stB);
+                    named_bar_sync(2, 128);
+                    const int S = S0 + w;
+                    if (h3) {
+                        flush_block(stA, blk(a.Kacc, d.P, S), m, et);
+                        if (!diag) flush_block(stA + MPMAX * 64, blk(a.Kacc, S, d.P), m, et);
+                    }
+                    if (h4) {
+                        flush_block(stB, blk(a.Kacc, d.Q, S), m, et);
+                        if (!diag) flush_block(stB + MPMAX * 64, blk(a.Kacc, S, d.Q), m, et);
+                    }
+                    named_bar_sync(2, 128);
+                }
+                release(&c.itemfree);
             }
         }
     }
