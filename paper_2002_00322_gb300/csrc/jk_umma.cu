@@ -60,7 +60,11 @@ constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + 2 * MPMAX * 64) * 4;
 constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES + EPI_BYTES;
 
 struct Ctrl {
-    uint64_t full[2], conv[2], mmad[2], acce[2], runfree[2], itemfree;
+    uint64_t full[2], conv[2], mmad[2], acce[2], runfree[2];
+    // window region w has been staged at the end of wstaged[w] / 4 items (each
+    // epilogue warp adds one); monotonic, so a waiter can be any number of
+    // items behind (an mbarrier phase parity could alias two completions)
+    unsigned wstaged[SWIN];
     uint32_t tmem_base;
     int abort_flag;
     int cdecide, edecide;   // group-uniform copies of abort_flag (converters, epilogue)
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         }
         mbar_init(&c.runfree[0], 4);
         mbar_init(&c.runfree[1], 4);
-        mbar_init(&c.itemfree, 4);
+        for (int w = 0; w < SWIN; ++w) c.wstaged[w] = 0;
         c.abort_flag = 0;
         mbar_fence_init();
     }
@@ -312,8 +316,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             if (!mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag)) { fail(3); break; }
             if (i >= 2 && !mbar_wait(&c.acce[b], ((i - 2) >> 1) & 1, abort_flag)) { fail(4); break; }
             if (frun && run >= 2 && !mbar_wait(&c.runfree[rb], ((run - 2) >> 1) & 1, abort_flag)) { fail(5); break; }
-            if (fitem && item >= 1 && !mbar_wait(&c.itemfree, (item - 1) & 1, abort_flag)) { fail(10); break; }
             if (fitem) { touched3 = 0; touched4 = 0; }
+            // window region w (V3[w] and V4[w]) is free once the epilogue has
+            // staged it at the end of the previous item
+            const int wreg = d.S % SWIN;
+            if (d.R != d.S && item >= 1 && !((touched3 | touched4) & (1u << wreg)) &&
+                !counter_wait(&c.wstaged[wreg], 4u * (unsigned)item, abort_flag)) { fail(10); break; }
             tc_fence_after();
             const uint32_t st = smem_u32(sm + s * STAGE_BYTES);
             const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
@@ -501,9 +509,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
                 const int S0 = d.S - d.S % SWIN;
                 for (int w = 0; w < SWIN; ++w) {
                     const bool h3 = touched3 & (1u << w), h4 = touched4 & (1u << w);
-                    if (!h3 && !h4) continue;
                     if (h3) stage(RW * w, true, stA);
                     if (h4) stage(RW * (SWIN + w), true, stB);
+                    tc_fence_before();                  // every region, once per item
+                    __syncwarp();
+                    if (lane == 0) counter_release_add(&c.wstaged[w]);
+                    if (!h3 && !h4) continue;
                     named_bar_sync(2, 128);
                     const int S = S0 + w;
                     if (h3) {
@@ -516,7 +527,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
                     }
                     named_bar_sync(2, 128);
                 }
-                release(&c.itemfree);
             }
         }
     }

@@ -45,6 +45,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const 
     return false;
 }
 
+// ---- monotonic shared-memory counters (release add / bounded acquire spin)
+__device__ __forceinline__ void counter_release_add(unsigned *ctr) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], 1;" ::"r"(smem_u32(ctr)) : "memory");
+}
+__device__ __forceinline__ unsigned counter_acquire(const unsigned *ctr) {
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(ctr)) : "memory");
+    return v;
+}
+// waits until *ctr >= target; gives up after `limit` polls or on *abort
+__device__ __forceinline__ bool counter_wait(const unsigned *ctr, unsigned target, const volatile int *abort,
+                                             uint32_t limit = (1u << 26)) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        if (counter_acquire(ctr) >= target) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort) return false;
+            __nanosleep(64);
+        }
+    }
+    return false;
+}
+
 // ---- bulk copy global -> shared, completion counted on an mbarrier (bytes)
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
