@@ -54,9 +54,10 @@ constexpr int OFF_IN = OFF_B5 + 2 * JB_BYTES_MAX;
 constexpr int STAGE_BYTES = ((OFF_IN + IN_BYTES + 1023) / 1024) * 1024;
 constexpr int CTRL_BYTES = 4096;
 // epilogue staging of flushed output blocks: two exchange views (D and D^T
-// parts, 2 x 16 x 64 floats each) and one Coulomb view (16 x 64 floats)
+// parts, 2 x 16 x 64 floats each), the J2 view and the hi and lo words of the
+// compensated J1 sum (16 x 64 floats each)
 constexpr int STAGE_K_FLOATS = 2 * MPMAX * 64;
-constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + 2 * MPMAX * 64) * 4;
+constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + 3 * MPMAX * 64) * 4;
 constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES + EPI_BYTES;
 
 struct Ctrl {
@@ -214,6 +215,31 @@ __device__ __forceinline__ void stage_view(uint32_t taddr, bool live, int row, i
     }
 }
 
+// Error-free sum (Knuth's TwoSum) of the running value hi and the term t:
+// hi <- fl(hi + t), lo collects the rounding error, so hi + lo carries the
+// sum of all terms to about twice single precision.  Written with explicit
+// round-to-nearest intrinsics so that no step is contracted or reassociated.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float t) {
+    const float s = __fadd_rn(hi, t);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+// Add one Coulomb accumulator row (this thread's TMEM lane, MP columns),
+// scaled, into the thread's compensated running sums.
+template <int MP>
+__device__ __forceinline__ void accumulate_row(uint32_t taddr, bool live, float inv, float *hi, float *lo) {
+    float v[16];
+    if (MP == 16) tmem_ld16(taddr, v);
+    else tmem_ld8(taddr, v);
+    tmem_wait_ld();
+    if (!live) return;
+#pragma unroll
+    for (int k = 0; k < MP; ++k) two_sum_acc(hi[k], lo[k], __fmul_rn(v[k], inv));
+}
+
 // Coalesced reduction of one staged block (m x 64 values, m <= 16) into the
 // block-major accumulator at dst (contiguous m*64 doubles): all shared loads
 // of a thread are issued before its reductions so their latencies overlap.
@@ -232,6 +258,22 @@ __device__ __forceinline__ void flush_block(const float *st, double *dst, int m,
     }
 }
 
+// As flush_block for a block staged as hi and lo words: adds hi + lo in FP64.
+__device__ __forceinline__ void flush_block2(const float *hi, const float *lo, double *dst, int m, int et) {
+    const int cnt = m * 64;
+    double v[MPMAX / 2];
+#pragma unroll
+    for (int j = 0; j < MPMAX / 2; ++j) {
+        const int i = et + 128 * j;
+        v[j] = (i < cnt) ? (double)hi[i] + (double)lo[i] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < MPMAX / 2; ++j) {
+        const int i = et + 128 * j;
+        if (i < cnt) atomicAdd(dst + i, v[j]);
+    }
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
@@ -241,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
     const int64_t beg = a.nbricks * blockIdx.x / gridDim.x;
     const int64_t end = a.nbricks * (blockIdx.x + 1) / gridDim.x;
     const int nloc = (int)(end - beg);
-    const int mp = a.mp, F = 4 * mp, G = 2 * mp;
+    const int mp = a.mp;
     const uint32_t kbytes = 512u * mp, jbytes = 256u * mp;
     volatile int *abort_flag = &c.abort_flag;
 
@@ -292,8 +334,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         // no copy may still be landing when the CTA leaves
         for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
             mbar_wait(&c.full[i & 1], (i >> 1) & 1, abort_flag);
-    } else if (nloc > 0 && warp == 1 && lane == 0) {
+    } else if (nloc > 0 && warp == 1) {
         // ------------------------------------------------ MMA issuer
+        // The whole warp runs the loop and takes every wait (decisions made
+        // warp-uniform); one elected lane issues the MMAs and the commit.
+        // Descriptors are formed once per view and advanced by adding the
+        // byte offset / 16 to the start-address field (shared addresses stay
+        // below 256 KB, so the 14-bit field never carries).
         // tensor memory: window regions V3[w] at RW*w and V4[w] at RW*(SWIN+w);
         // run regions V1, V2 at WV + rb*2RW (+RW); per-brick J2, J1 at
         // WJ + b*2mp (+mp).  At mp = 16: 320 + 128 + 64 = 512 columns.
@@ -313,52 +360,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             const bool fitem = (i == 0) || (d.pad & BRICK_ITEM_FIRST);
             const bool litem = (i == nloc - 1) || (d.pad & BRICK_ITEM_LAST);
             const int rb = run & 1;
-            if (!mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag)) { fail(3); break; }
-            if (i >= 2 && !mbar_wait(&c.acce[b], ((i - 2) >> 1) & 1, abort_flag)) { fail(4); break; }
-            if (frun && run >= 2 && !mbar_wait(&c.runfree[rb], ((run - 2) >> 1) & 1, abort_flag)) { fail(5); break; }
+            if (!__all_sync(~0u, mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag))) { fail(3); break; }
+            if (i >= 2 && !__all_sync(~0u, mbar_wait(&c.acce[b], ((i - 2) >> 1) & 1, abort_flag))) { fail(4); break; }
+            if (frun && run >= 2 && !__all_sync(~0u, mbar_wait(&c.runfree[rb], ((run - 2) >> 1) & 1, abort_flag))) { fail(5); break; }
             if (fitem) { touched3 = 0; touched4 = 0; }
             // window region w (V3[w] and V4[w]) is free once the epilogue has
             // staged it at the end of the previous item
             const int wreg = d.S % SWIN;
             if (d.R != d.S && item >= 1 && !((touched3 | touched4) & (1u << wreg)) &&
-                !counter_wait(&c.wstaged[wreg], 4u * (unsigned)item, abort_flag)) { fail(10); break; }
+                !__all_sync(~0u, counter_wait(&c.wstaged[wreg], 4u * (unsigned)item, abort_flag))) { fail(10); break; }
             tc_fence_after();
-            const uint32_t st = smem_u32(sm + s * STAGE_BYTES);
-            const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
-            const uint32_t B1 = st + OFF_B1, B2 = B1 + KB_BYTES_MAX, B3 = B2 + KB_BYTES_MAX,
-                           B4 = B3 + KB_BYTES_MAX, B5 = st + OFF_B5, B6 = B5 + JB_BYTES_MAX;
             const bool pq_diff = d.P != d.Q, rs_diff = d.R != d.S;
             const int w = d.S % SWIN;
-            // three passes into the same columns: hi x [D|D^T]_hi, hi x [D|D^T]_lo, lo x [D|D^T]_hi
-            auto view = [&](uint32_t col, uint32_t AH, uint32_t AL, uint32_t kstep, uint32_t lbo, uint32_t sbo,
-                            uint32_t id, uint32_t B, uint32_t blo, bool fresh) {
+            const bool fresh3 = !(touched3 & (1u << w)), fresh4 = !(touched4 & (1u << w));
+            if (rs_diff) touched3 |= 1u << w;
+            if (rs_diff && pq_diff) touched4 |= 1u << w;
+            if (elect_one()) {
+                const uint32_t st = smem_u32(sm + s * STAGE_BYTES);
+                const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
+                const uint32_t B1 = st + OFF_B1, B2 = B1 + KB_BYTES_MAX, B3 = B2 + KB_BYTES_MAX,
+                               B4 = B3 + KB_BYTES_MAX, B5 = st + OFF_B5, B6 = B5 + JB_BYTES_MAX;
+                // three passes into the same columns: hi x [D|D^T]_hi, hi x [D|D^T]_lo, lo x [D|D^T]_hi
+                auto view = [&](uint32_t col, uint32_t AH, uint32_t AL, uint32_t kstep, uint32_t lbo, uint32_t sbo,
+                                uint32_t id, uint32_t B, uint32_t blo, bool fresh) {
+                    const uint64_t ah = sdesc(AH, lbo, sbo), al = ah + ((AL - AH) >> 4);
+                    const uint64_t bh = sdesc(B, 128, 1024), bl = bh + (blo >> 4);
+                    const uint32_t ks = kstep >> 4;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_f16(tmem + col, sdesc(AH + j * kstep, lbo, sbo), sdesc(B + j * 256, 128, 1024), id,
-                            (j > 0 || !fresh) ? 1u : 0u);
+                    for (int j = 0; j < 4; ++j)
+                        mma_f16(tmem + col, ah + j * ks, bh + 16 * j, id, (j > 0 || !fresh) ? 1u : 0u);
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_f16(tmem + col, sdesc(AH + j * kstep, lbo, sbo), sdesc(B + blo + j * 256, 128, 1024), id, 1u);
+                    for (int j = 0; j < 4; ++j)
+                        mma_f16(tmem + col, ah + j * ks, bl + 16 * j, id, 1u);
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_f16(tmem + col, sdesc(AL + j * kstep, lbo, sbo), sdesc(B + j * 256, 128, 1024), id, 1u);
-            };
-            // exchange: V1, V2 over the run; V3, V4 over the item (nothing when R == S,
-            // V2 and V4 nothing when P == Q: those permutations repeat others)
-            view(WV + rb * 2 * RW, VH, VL, 256, 128, 1024, id_k, B1, klo, frun);
-            if (pq_diff) view(WV + rb * 2 * RW + RW, VH, VL, 2048, 1024, 128, id_k, B2, klo, frun);
-            if (rs_diff) {
-                view(RW * w, VH, VL, 256, 128, 1024, idm_k, B3, klo, !(touched3 & (1u << w)));
-                touched3 |= 1u << w;
+                    for (int j = 0; j < 4; ++j)
+                        mma_f16(tmem + col, al + j * ks, bh + 16 * j, id, 1u);
+                };
+                // exchange: V1, V2 over the run; V3, V4 over the item (nothing when R == S,
+                // V2 and V4 nothing when P == Q: those permutations repeat others)
+                view(WV + rb * 2 * RW, VH, VL, 256, 128, 1024, id_k, B1, klo, frun);
+                if (pq_diff) view(WV + rb * 2 * RW + RW, VH, VL, 2048, 1024, 128, id_k, B2, klo, frun);
+                if (rs_diff) view(RW * w, VH, VL, 256, 128, 1024, idm_k, B3, klo, fresh3);
+                if (rs_diff && pq_diff) view(RW * (SWIN + w), VH, VL, 2048, 1024, 128, idm_k, B4, klo, fresh4);
+                // Coulomb views, per brick: J1 (K-major over W) and J2 (MN-major over W)
+                view(WJ + b * 2 * mp + mp, WH, WL, 256, 128, 1024, id_j, B5, jlo, true);
+                view(WJ + b * 2 * mp, WH, WL, 2048, 1024, 128, idm_j, B6, jlo, true);
+                mma_commit(&c.mmad[s]);
             }
-            if (rs_diff && pq_diff) {
-                view(RW * (SWIN + w), VH, VL, 2048, 1024, 128, idm_k, B4, klo, !(touched4 & (1u << w)));
-                touched4 |= 1u << w;
-            }
-            // Coulomb views, per brick: J1 (K-major over W) and J2 (MN-major over W)
-            view(WJ + b * 2 * mp + mp, WH, WL, 256, 128, 1024, id_j, B5, jlo, true);
-            view(WJ + b * 2 * mp, WH, WL, 2048, 1024, 128, idm_j, B6, jlo, true);
-            mma_commit(&c.mmad[s]);
+            __syncwarp();
             committed = i + 1;
             if (lrun) ++run;
             if (litem) ++item;
@@ -443,7 +492,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         float *stA = reinterpret_cast<float *>(sm + 2 * STAGE_BYTES + CTRL_BYTES);
         float *stB = stA + STAGE_K_FLOATS;
         float *stJ = stB + STAGE_K_FLOATS;
-        float *stJ1 = stJ + MPMAX * 64;
+        float *stJ1 = stJ + MPMAX * 64, *stJ1lo = stJ1 + MPMAX * 64;
+        // compensated running sum of J1 -> J[P,Q] over the item (P, Q fixed)
+        float j1h[MPMAX], j1l[MPMAX];
+#pragma unroll
+        for (int k = 0; k < MPMAX; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
         auto blk = [&](double *base, int X, int Y) { return base + ((int64_t)(X * nb + Y) * mtot + a.d0) * 64; };
         auto stage = [&](uint32_t col, bool kview, float *dst) {
             if (mp == 16) {
@@ -479,13 +532,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
             named_bar_sync(2, 128);
             if (c.edecide) break;
             tc_fence_after();
-            // per brick: Coulomb views J2 -> J[R,S] (not for the (PQ|PQ) brick) and J1 -> J[P,Q]
+            // per brick: Coulomb view J2 -> J[R,S] (not for the (PQ|PQ) brick) is
+            // flushed; J1 -> J[P,Q] joins the item's compensated sum
             stage(WJ + b * 2 * mp, false, stJ);
-            stage(WJ + b * 2 * mp + mp, false, stJ1);
+            if (mp == 16) accumulate_row<16>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
+            else accumulate_row<8>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
             release(&c.acce[b]);
-            named_bar_sync(2, 128);
-            if (!diag) flush_block(stJ, blk(a.Jacc, d.R, d.S), m, et);
-            flush_block(stJ1, blk(a.Jacc, d.P, d.Q), m, et);
+            if (!diag) {
+                named_bar_sync(2, 128);
+                flush_block(stJ, blk(a.Jacc, d.R, d.S), m, et);
+            }
             named_bar_sync(2, 128);
             if (lrun) {
                 // V1 -> K[P,R] (and K[R,P] unless (PQ|PQ)), V2 -> K[Q,R], K[R,Q] (P != Q)
@@ -504,6 +560,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
                 ++run;
             }
             if (litem) {
+                if (live) {
+#pragma unroll
+                    for (int k = 0; k < MPMAX; ++k)
+                        if (k < m) { stJ1[k * 64 + row] = j1h[k]; stJ1lo[k * 64 + row] = j1l[k]; }
+                }
+#pragma unroll
+                for (int k = 0; k < MPMAX; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
+                named_bar_sync(2, 128);
+                flush_block2(stJ1, stJ1lo, blk(a.Jacc, d.P, d.Q), m, et);
+                named_bar_sync(2, 128);
                 // window regions: V3 -> K[P,S], K[S,P]; V4 -> K[Q,S], K[S,Q] (D^T parts
                 // not for the (PQ|PQ) item)
                 const int S0 = d.S - d.S % SWIN;
