@@ -49,6 +49,10 @@ struct esmf_fock {
     std::vector<std::pair<int, int>> tuned;   // (m, densities per pass) picked by esmf_fock_autotune
     int force_chunk = 0;                      // set while the autotuner times a candidate
     int num_sms = 0;
+    // cost-balanced split of the whole brick list over the tensor kernel's
+    // CTAs: CTA g takes bricks [parts[g], parts[g+1]) (device, nparts + 1)
+    int64_t *parts = nullptr;
+    int nparts = 0;
     // tensor-core path work memory
     uint16_t *kbank = nullptr, *jbank = nullptr;
     unsigned int *dmax = nullptr;
@@ -129,11 +133,52 @@ void dfree(esmf_fock *h, T **p, size_t count) {
     *p = nullptr;
 }
 
+// Relative cost of each brick in the tensor-core contraction, for splitting
+// the list over CTAs: a base cost, one unit per issued exchange/Coulomb view
+// and one per output block whose flush the brick triggers (its Coulomb J2
+// block; at a run end the run's V1/V2 blocks; at an item end the J1 block and
+// the window's V3/V4 blocks).  The coefficients are per-CTA cycle counts
+// fitted on GB300 (the flush of a 16 x 64 block dominates).
+constexpr double kCostBrick = 300.0, kCostView = 250.0, kCostBlock = 700.0;
+
+std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
+    const int64_t n = (int64_t)kept.size();
+    if (G > n) G = (int)n;
+    std::vector<int64_t> parts;
+    if (G < 1) return parts;
+    std::vector<double> pre(n + 1, 0.0);
+    unsigned t3 = 0, t4 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const BrickDesc &d = kept[i];
+        const bool pq = d.P != d.Q, rs = d.R != d.S, diag = d.R == d.P && d.S == d.Q;
+        const int two = diag ? 1 : 2;
+        if (d.pad & BRICK_ITEM_FIRST) t3 = t4 = 0;
+        if (rs) t3 |= 1u << (d.S % SWIN);
+        if (rs && pq) t4 |= 1u << (d.S % SWIN);
+        double blocks = diag ? 0 : 1;
+        if (d.pad & BRICK_RUN_LAST) blocks += two + (pq ? two : 0);
+        if (d.pad & BRICK_ITEM_LAST) blocks += 1 + two * (__builtin_popcount(t3) + __builtin_popcount(t4));
+        const int views = 2 + (pq ? 1 : 0) + (rs ? 1 : 0) + (pq && rs ? 1 : 0);
+        pre[i + 1] = pre[i] + kCostBrick + kCostView * views + kCostBlock * blocks;
+    }
+    parts.resize(G + 1);
+    parts[0] = 0;
+    int64_t j = 0;
+    for (int g = 1; g < G; ++g) {
+        const double target = pre[n] * g / G;
+        while (j < n && pre[j] < target) ++j;
+        parts[g] = std::max(j, parts[g - 1] + 1);      // every CTA gets a brick
+    }
+    parts[G] = n;
+    for (int g = G - 1; g >= 1; --g) parts[g] = std::min(parts[g], parts[g + 1] - 1);
+    return parts;
+}
+
 void release(esmf_fock *h) {
     if (!h) return;
     cudaFree(h->center); cudaFree(h->exps); cudaFree(h->w); cudaFree(h->coefs);
     cudaFree(h->nprim); cudaFree(h->poff); cudaFree(h->Q);
-    cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store);
+    cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts);
     cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
     if (h->err_host) cudaFreeHost(h->err_host);
     cudaFree(h->Jacc); cudaFree(h->Kacc);
@@ -404,6 +449,9 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
         if (qmax > 0.0) std::frexp(qmax * qmax, &e);
         h->vscale = qmax > 0.0 ? (float)std::ldexp(1.0, 14 - e) : 1.0f;
     }
+    if (!ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count"))
+        return fail(ESMF_ERR_CUDA);
+    const std::vector<int64_t> parts = balance_parts(kept, h->num_sms);
     h->nbricks = (int64_t)kept.size();
     h->n_kept_unique = unique;
     h->n_stored = 0;
@@ -426,6 +474,12 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
         if ((rc = dalloc(h, &h->bricks, h->nbricks))) return fail(rc);
         if (!ck(cudaMemcpyAsync(h->bricks, kept.data(), sizeof(BrickDesc) * h->nbricks, cudaMemcpyHostToDevice, cs), "copy kept bricks"))
             return fail(ESMF_ERR_CUDA);
+        if (!parts.empty()) {
+            if ((rc = dalloc(h, &h->parts, parts.size()))) return fail(rc);
+            if (!ck(cudaMemcpyAsync(h->parts, parts.data(), sizeof(int64_t) * parts.size(), cudaMemcpyHostToDevice, cs), "copy parts"))
+                return fail(ESMF_ERR_CUDA);
+            h->nparts = (int)parts.size() - 1;
+        }
         if (use_mode == ESMF_MODE_STORED) {
             if ((rc = dalloc(h, &h->offsets, h->nbricks + 1))) return fail(rc);
             if ((rc = dalloc(h, (unsigned char **)&h->store, (size_t)h->store_bytes))) return fail(rc);
@@ -442,8 +496,6 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
         !ck(cudaHostGetDevicePointer((void **)&h->err_dev, h->err_host, 0), "error flag address"))
         return fail(ESMF_ERR_CUDA);
     *h->err_host = 0;
-    if (!ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count"))
-        return fail(ESMF_ERR_CUDA);
     if (!ck(cudaStreamSynchronize(cs), "create kernels")) return fail(ESMF_ERR_CUDA);
     h->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     *out = h;
@@ -509,6 +561,7 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
             L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev;
             L.ev_start = e0; L.ev_stop = e1;
             L.chunk = chunk ? chunk : 16;
+            if (b0 == 0 && b1 == h->nbricks && h->parts) { L.part = h->parts; L.nparts = h->nparts; }
             RET(launch_jk_umma(L, s));
             return launch_finalize_blocked(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s);
         }

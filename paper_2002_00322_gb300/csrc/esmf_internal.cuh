@@ -99,6 +99,8 @@ struct UmmaLaunch {
     int *error;                  // device flag, 0 = ok
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional timing
     int chunk = 16;              // densities per tensor-core pass (8 or 16)
+    const int64_t *part = nullptr;   // optional per-CTA brick ranges (nparts + 1 entries)
+    int nparts = 0;
 };
 int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s);
 int launch_finalize_blocked(const DevBasis &b, int m, const double *D, const double *Jb, const double *Kb,

@@ -187,6 +187,7 @@ struct UmmaParams {
     const unsigned int *dmax_bits;
     double *Jacc, *Kacc;   // block-major: [X][Y][k][x][y], k < mtot
     int *error;
+    const int64_t *part;   // per-CTA brick ranges, or null for an even split by count
 };
 
 namespace {
@@ -280,8 +281,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     Ctrl &c = *reinterpret_cast<Ctrl *>(sm + 2 * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t beg = a.nbricks * blockIdx.x / gridDim.x;
-    const int64_t end = a.nbricks * (blockIdx.x + 1) / gridDim.x;
+    const int64_t beg = a.part ? a.part[blockIdx.x] : a.nbricks * blockIdx.x / gridDim.x;
+    const int64_t end = a.part ? a.part[blockIdx.x + 1] : a.nbricks * (blockIdx.x + 1) / gridDim.x;
     const int nloc = (int)(end - beg);
     const int mp = a.mp;
     const uint32_t kbytes = 512u * mp, jbytes = 256u * mp;
@@ -313,16 +314,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
     if (nloc > 0 && warp == 0 && lane == 0) {
         // ------------------------------------------------ producer
         int issued = 0;
+        // the next brick's descriptor and record offset are loaded one
+        // iteration ahead, so their latency overlaps the wait for a free stage
+        BrickDesc dnext = a.bricks[beg];
+        int64_t onext = a.offsets[beg];
         for (int i = 0; i < nloc; ++i) {
             const int s = i & 1;
+            const BrickDesc d = dnext;
+            const int64_t off = onext;
+            if (i + 1 < nloc) {
+                dnext = a.bricks[beg + i + 1];
+                onext = a.offsets[beg + i + 1];
+            }
             if (i >= 2 && !mbar_wait(&c.mmad[s], ((i - 2) >> 1) & 1, abort_flag)) { fail(2); break; }
-            const BrickDesc d = a.bricks[beg + i];
             unsigned char *st = sm + s * STAGE_BYTES;
             const uint32_t rec = ((512u + 4u * (uint32_t)d.nkept) + 15u) & ~15u;
             const uint16_t *kb = a.kbank, *jb = a.jbank;
             const size_t kw = kbytes / 2, jw = jbytes / 2;
             mbar_arrive_expect_tx(&c.full[s], rec + 4 * kbytes + 2 * jbytes);
-            bulk_g2s(st + OFF_IN, a.store + a.offsets[beg + i], rec, &c.full[s]);
+            bulk_g2s(st + OFF_IN, a.store + off, rec, &c.full[s]);
             bulk_g2s(st + OFF_B1 + 0 * KB_BYTES_MAX, kb + ((size_t)d.Q * a.nb + d.S) * kw, kbytes, &c.full[s]);
             bulk_g2s(st + OFF_B1 + 1 * KB_BYTES_MAX, kb + ((size_t)d.P * a.nb + d.S) * kw, kbytes, &c.full[s]);
             bulk_g2s(st + OFF_B1 + 2 * KB_BYTES_MAX, kb + ((size_t)d.Q * a.nb + d.R) * kw, kbytes, &c.full[s]);
@@ -635,8 +645,10 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
         p.mtot = L.m;
         p.bf16 = L.bf16; p.vscale = L.vscale; p.dmax_bits = L.dmax_bits; p.Jacc = L.Jacc; p.Kacc = L.Kacc;
         p.error = L.error;
+        p.part = L.part;
         int grid = L.num_sms;
         if (grid > L.nbricks) grid = (int)L.nbricks;
+        if (L.part) grid = L.nparts;
         if (L.ev_start && d0 == 0) cudaEventRecord(L.ev_start, s);
         k_jk_umma<<<grid, NTHREADS, SMEM_TOTAL, s>>>(p);
         if (L.ev_stop && d0 + chunk >= L.m) cudaEventRecord(L.ev_stop, s);
