@@ -137,9 +137,10 @@ void dfree(esmf_fock *h, T **p, size_t count) {
 // the list over CTAs: a base cost, one unit per issued exchange/Coulomb view
 // and one per output block whose flush the brick triggers (its Coulomb J2
 // block; at a run end the run's V1/V2 blocks; at an item end the J1 block and
-// the window's V3/V4 blocks).  The coefficients are per-CTA cycle counts
-// fitted on GB300 (the flush of a 16 x 64 block dominates).
-constexpr double kCostBrick = 300.0, kCostView = 250.0, kCostBlock = 700.0;
+// the window's V3/V4 blocks).  The coefficients are a least-squares fit of
+// per-CTA cycle counts on GB300 (stored_n200_m16, 152 CTAs): about 1.9K cycles
+// per brick plus 0.84K per flushed 16 x 64 block.
+constexpr double kCostBrick = 1900.0, kCostView = 100.0, kCostBlock = 840.0;
 
 std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
     const int64_t n = (int64_t)kept.size();
