@@ -157,6 +157,44 @@ def esmf_densities(rng, n, nocc, m, first=None):
     return np.ascontiguousarray(np.stack(out[:m]).astype(np.float64))
 
 
+# ---------------------------------------------------------------- ESMF state
+@dataclass
+class EsmfState:
+    """Inputs of the ESMF energy and gradient (Sec. II.B.2, Table I).
+
+    G: (N, N) symmetric one-electron AO matrix; V: (N, N) orbitals in rows
+    (Theta = V[:nocc], Gamma = V[nocc:]); sigma: (nocc, N - nocc) singles
+    coefficients; c0: reference-determinant coefficient.
+    """
+
+    G: np.ndarray
+    V: np.ndarray
+    sigma: np.ndarray
+    c0: float
+    nocc: int
+
+
+def esmf_state(rng, basis: Basis, nocc, sigma_norm=0.3) -> EsmfState:
+    """Seeded ESMF wave-function state for a basis.
+
+    The paper takes the one-electron integrals from an external package; G
+    here is a synthetic symmetric stand-in with the shape of a core
+    Hamiltonian: negative diagonal in [-3, -1] hartree and couplings that
+    decay as a Gaussian of the distance between function centers.  V has
+    orthonormal rows, sigma is a Gaussian matrix of Frobenius norm
+    sigma_norm and c0 is uniform in [0.8, 1]."""
+    n = basis.n
+    V = orbitals(rng, n)
+    sig = _unit(rng, (nocc, n - nocc)) * sigma_norm
+    c0 = float(rng.uniform(0.8, 1.0))
+    c = basis.center
+    d2 = np.sum((c[:, None, :] - c[None, :, :]) ** 2, axis=2)
+    X = -rng.uniform(0.2, 1.0, size=(n, n)) * np.exp(-0.25 * d2)
+    G = 0.5 * (X + X.T)
+    G[np.diag_indices(n)] = -rng.uniform(1.0, 3.0, size=n)
+    return EsmfState(np.ascontiguousarray(G), V, np.ascontiguousarray(sig), c0, int(nocc))
+
+
 # ---------------------------------------------------------------- configs
 def tiny(seed_offset=0) -> Workload:
     """24 contracted s functions (3 primitives) on 12 random centers in an
