@@ -13,6 +13,7 @@
 #include <thread>
 #include <vector>
 
+#include "esmf_energy.h"
 #include "esmf_internal.cuh"
 
 namespace esmf {
@@ -60,6 +61,8 @@ struct esmf_fock {
     int64_t n_stored = 0, store_bytes = 0, n_kept_unique = 0;
     // work (device)
     double *Jacc = nullptr, *Kacc = nullptr;
+    double *ework = nullptr;       // ESMF energy / gradient work memory
+    size_t ework_n = 0;
     int work_m = 0;
     // staging for the host-buffer entry (device)
     double *sD = nullptr, *sJ = nullptr, *sK = nullptr, *sF = nullptr, *st = nullptr;
@@ -182,7 +185,7 @@ void release(esmf_fock *h) {
     cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts);
     cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
     if (h->err_host) cudaFreeHost(h->err_host);
-    cudaFree(h->Jacc); cudaFree(h->Kacc);
+    cudaFree(h->Jacc); cudaFree(h->Kacc); cudaFree(h->ework);
     cudaFree(h->sD); cudaFree(h->sJ); cudaFree(h->sK); cudaFree(h->sF); cudaFree(h->st);
     if (h->done) cudaEventDestroy(h->done);
     for (auto &e : h->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -583,6 +586,44 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
                     double *traces, void *stream) {
     if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
     return build_range(h, 0, h->nbricks, m, D, J, K, F, traces, stream);
+}
+
+int esmf_energy_gradient(esmf_fock_t *h, int n_occ, double c0, const double *G, const double *V,
+                         const double *sigma, double *scalars, double *dE_dsigma, double *dE_dV,
+                         void *stream) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    const int n = h->n;
+    if (n_occ < 1 || n_occ >= n) {
+        set_error("n_occ = %d outside [1, %d)", n_occ, n);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    if (!is_finite(c0)) { set_error("c0 is not finite"); return ESMF_ERR_INVALID_ARG; }
+    if (!G || !V || !sigma || !scalars) { set_error("G, V, sigma and scalars are required"); return ESMF_ERR_INVALID_ARG; }
+    if ((dE_dsigma == nullptr) != (dE_dV == nullptr)) {
+        set_error("dE_dsigma and dE_dV must both be given or both be NULL");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
+    if (!is_device_ptr(G) || !is_device_ptr(V) || !is_device_ptr(sigma) || !is_device_ptr(scalars) ||
+        (dE_dsigma && (!is_device_ptr(dE_dsigma) || !is_device_ptr(dE_dV)))) {
+        set_error("G, V, sigma, scalars and the gradient outputs must be device memory");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    const size_t need = energy_work_doubles(n, n_occ);
+    if (need > h->ework_n) {
+        dfree(h, &h->ework, h->ework_n);
+        h->ework_n = 0;
+        RET(dalloc(h, &h->ework, need));
+        h->ework_n = need;
+    }
+    const EnergyWork w = energy_work_layout(h->ework, n, n_occ);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool grad = dE_dsigma != nullptr;
+    RET(launch_energy_densities(n, n_occ, V, sigma, w, s));
+    // one grouped build: F[P], F[T] (energy) and F[A] (gradient)
+    RET(build_range(h, 0, h->nbricks, grad ? 3 : 2, w.D, w.J, w.K, w.F, nullptr, stream));
+    return launch_energy_finish(n, n_occ, c0, G, V, sigma, w, scalars, dE_dsigma, dE_dV, s);
 }
 
 int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const double *D, double *J,

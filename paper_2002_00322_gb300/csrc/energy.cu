@@ -1,0 +1,355 @@
+// Kernels of the ESMF energy and gradient (Sec. II.B.2, Eqs. esmf_energy_1b,
+// esmf_energy_2b and the appendix derivatives): an FP64 GEMM for the O(N^3)
+// matrix products, the elementwise assembly of the derivative matrices and a
+// deterministic reduction of the scalar inner products.  The Fock-like
+// builds themselves are the library's grouped contraction.
+//
+// Notation: Theta = first N_o rows of V, Gamma = last N_v rows; P = Theta^T
+// Theta, T = Theta^T sigma Gamma, A = Gamma^T sigma^T sigma Gamma -
+// Theta^T sigma sigma^T Theta; F_X = F[X] = 2 J[X] - K[X]; Fk = G + F_P (the
+// closed-shell Fock matrix of the rotated reference); N2 = c0^2 + 2 |sigma|^2.
+// With E_HF = (G + Fk) . P, the energy is
+//   E = (N2 E_HF + 4 c0 Fk . T + 2 Fk . A + 2 F_T . T) / N2
+// (E1 + E2 of the paper, its last E2 term read as 2 F[T] . T).
+#include <cuda_runtime.h>
+
+#include "esmf_internal.cuh"
+
+#define RET_IF(x)                  \
+    do {                           \
+        int r_ = (x);              \
+        if (r_ != ESMF_OK) return r_; \
+    } while (0)
+
+namespace esmf {
+
+namespace {
+
+constexpr int GK = 16;             // K step of the GEMM tiles
+
+// One problem of a grouped FP64 GEMM: C (M x N) = alpha op(A) op(B) + beta C,
+// row-major; op(A) is M x K (A stored K x M when ta), op(B) is K x N (B stored
+// N x K when tb).
+struct GemmProblem {
+    int M, N, K, lda, ldb, ldc, ta, tb;
+    double alpha, beta;
+    const double *A, *B;
+    double *C;
+};
+constexpr int MAX_GROUP = 8;
+struct GemmGroup {
+    GemmProblem p[MAX_GROUP];
+    int tiles[MAX_GROUP + 1];          // prefix sums of the problems' tile counts
+    int count;
+};
+
+// Independent GEMMs in one launch (GB300's FP64 rate per SM is low, so the
+// small O(N^3) products must spread over all SMs).  Tile T x T outputs with
+// (T/4)^2 threads, each owning a 4 x 4 strided patch (rows ty + T/4 i,
+// columns tx + T/4 j).
+template <int T>
+__global__ void __launch_bounds__((T / 4) * (T / 4)) k_gemm_group(const __grid_constant__ GemmGroup g) {
+    constexpr int NT = (T / 4) * (T / 4), S = T / 4;
+    __shared__ double As[GK][T + 1];
+    __shared__ double Bs[GK][T + 1];
+    int q = 0;
+    while (q + 1 < g.count && (int)blockIdx.x >= g.tiles[q + 1]) ++q;
+    const GemmProblem &P = g.p[q];
+    const int tile = blockIdx.x - g.tiles[q];
+    const int tn = (P.N + T - 1) / T;
+    const int m0 = (tile / tn) * T, n0 = (tile % tn) * T;
+    const int t = threadIdx.x, tx = t % S, ty = t / S;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < P.K; k0 += GK) {
+        for (int e = t; e < T * GK; e += NT) {
+            int mm, kk;
+            if (P.ta) { mm = e % T; kk = e / T; }     // contiguous along m in memory
+            else { mm = e / GK; kk = e % GK; }        // contiguous along k
+            const int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < P.M && gk < P.K) v = P.ta ? P.A[(size_t)gk * P.lda + gm] : P.A[(size_t)gm * P.lda + gk];
+            As[kk][mm] = v;
+            int nn, kb;
+            if (P.tb) { nn = e / GK; kb = e % GK; }   // contiguous along k
+            else { nn = e % T; kb = e / T; }          // contiguous along n
+            const int gn = n0 + nn, gkb = k0 + kb;
+            double w = 0.0;
+            if (gn < P.N && gkb < P.K) w = P.tb ? P.B[(size_t)gn * P.ldb + gkb] : P.B[(size_t)gkb * P.ldb + gn];
+            Bs[kb][nn] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + S * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + S * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty + S * i;
+        if (gm >= P.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx + S * j;
+            if (gn >= P.N) continue;
+            double *c = P.C + (size_t)gm * P.ldc + gn;
+            *c = P.beta == 0.0 ? P.alpha * acc[i][j] : fma(P.alpha, acc[i][j], P.beta * *c);
+        }
+    }
+}
+
+GemmProblem gp(bool ta, bool tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,
+               int ldb, double beta, double *C, int ldc) {
+    GemmProblem p;
+    p.M = M; p.N = N; p.K = K; p.lda = lda; p.ldb = ldb; p.ldc = ldc; p.ta = ta; p.tb = tb;
+    p.alpha = alpha; p.beta = beta; p.A = A; p.B = B; p.C = C;
+    return p;
+}
+
+int tiles_of(const GemmProblem &p, int T) { return ((p.M + T - 1) / T) * ((p.N + T - 1) / T); }
+
+// Fk = G + F_P and M1 = 4 c0 (F_T + F_T^T) + 2 (F_A + F_A^T) (the Theta-derivative
+// contributions of F[P] . T and F[P] . A through F[P]).
+__global__ void k_energy_fock(int n, double c0, const double *__restrict__ G, const double *__restrict__ F,
+                              double *__restrict__ Fk, double *__restrict__ M1, int with_grad) {
+    const size_t nn = (size_t)n * n;
+    const double *FP = F, *FT = F + nn, *FA = F + 2 * nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        Fk[e] = G[e] + FP[e];
+        if (with_grad) {
+            const size_t p = e / n, q = e % n, tr = q * n + p;
+            M1[e] = 4.0 * c0 * (FT[e] + FT[tr]) + 2.0 * (FA[e] + FA[tr]);
+        }
+    }
+}
+
+// Per-block partial sums of the five scalars the energy needs:
+// (G + Fk) . P, Fk . T, Fk . A, F_T . T and |sigma|^2.
+constexpr int DOT_BLOCKS = 256;
+__global__ void __launch_bounds__(256) k_energy_dots(int n, int nsig, const double *__restrict__ G,
+                                                     const double *__restrict__ Fk, const double *__restrict__ F,
+                                                     const double *__restrict__ D, const double *__restrict__ sigma,
+                                                     double *__restrict__ partial) {
+    const size_t nn = (size_t)n * n;
+    const double *P = D, *T = D + nn, *A = D + 2 * nn, *FT = F + nn;
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const double fk = Fk[e];
+        s[0] += (G[e] + fk) * P[e];
+        s[1] += fk * T[e];
+        s[2] += fk * A[e];
+        s[3] += FT[e] * T[e];
+    }
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)nsig; e += (size_t)gridDim.x * blockDim.x)
+        s[4] += sigma[e] * sigma[e];
+    __shared__ double red[8][5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+        partial[blockIdx.x * 5 + threadIdx.x] = v;
+    }
+}
+
+// Sums the partials in a fixed order and forms E and dE/dc0 (Eq. eng_der_c0):
+// out = {E, dE/dc0}; sc = {E_HF, E, N2}.
+__global__ void k_energy_scalars(double c0, const double *__restrict__ partial, double *__restrict__ out,
+                                 double *__restrict__ sc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < DOT_BLOCKS; ++b)
+        for (int k = 0; k < 5; ++k) s[k] += partial[b * 5 + k];
+    const double N2 = c0 * c0 + 2.0 * s[4];
+    const double ehf = s[0];
+    const double E = (N2 * ehf + 4.0 * c0 * s[1] + 2.0 * s[2] + 2.0 * s[3]) / N2;
+    out[0] = E;
+    out[1] = (2.0 * c0 * ehf + 4.0 * s[1]) / N2 - 2.0 * c0 * E / N2;
+    sc[0] = ehf;
+    sc[1] = E;
+    sc[2] = N2;
+}
+
+// Final assembly with the device scalars sc = {E_HF, E, N2}:
+//   dE/dsigma = (4 c0 Z1a + 4 Z1b + 4 Z1c - 4 Z3 + 4 (E_HF - E) sigma) / N2   (Eq. eng_der_sigma_jb)
+//   dE/dTheta = 4 X1 + (R1 + 4 R2 - 4 R3 + 4 c0 X2) / N2                       (dE/dTheta, from E)
+//   dE/dGamma = (4 c0 X4 + 4 Rg1 + 4 Rg2) / N2                                 (Eq. eng_der_ucp)
+// with X1 = Theta Fk, X2 = sigma Gamma Fk, X3 = Theta F_T, X4 = sigma^T Theta Fk,
+// Z1a,b,c = X1,2,3 Gamma^T, Z3 = X1 Theta^T sigma, R1 = Theta M1,
+// R2 = sigma Gamma F_T^T, R3 = sigma X4, Rg1 = sigma^T X2, Rg2 = sigma^T Theta F_T.
+// dV holds Theta's rows then Gamma's.
+__global__ void k_energy_finish(int n, int no, int nv, double c0, EnergyWork w, const double *__restrict__ sigma,
+                                double *__restrict__ dsig, double *__restrict__ dV) {
+    const double ehf = w.sc[0], E = w.sc[1], inv = 1.0 / w.sc[2];
+    const size_t ns = (size_t)no * nv, nt = (size_t)no * n, ng = (size_t)nv * n;
+    const size_t tot = ns + nt + ng;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < ns) {
+            dsig[e] = (4.0 * c0 * w.Z1a[e] + 4.0 * w.Z1b[e] + 4.0 * w.Z1c[e] - 4.0 * w.Z3[e] +
+                       4.0 * (ehf - E) * sigma[e]) * inv;
+        } else if (e < ns + nt) {
+            const size_t i = e - ns;
+            dV[i] = 4.0 * w.X1[i] + (w.R1[i] + 4.0 * w.R2[i] - 4.0 * w.R3[i] + 4.0 * c0 * w.X2[i]) * inv;
+        } else {
+            const size_t i = e - ns - nt;
+            dV[nt + i] = (4.0 * c0 * w.X4[i] + 4.0 * w.Rg1[i] + 4.0 * w.Rg2[i]) * inv;
+        }
+    }
+}
+
+int grid_for(size_t len) {
+    size_t g = (len + 255) / 256;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+int check(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s: %s", what, cudaGetErrorString(e));
+        return ESMF_ERR_CUDA;
+    }
+    return ESMF_OK;
+}
+
+// Launches up to MAX_GROUP independent GEMMs together, with the largest tile
+// that still gives about two blocks per SM (GB300: 152 SMs).
+int launch_group(const GemmProblem *ps, int count, cudaStream_t s) {
+    GemmGroup g;
+    g.count = 0;
+    for (int i = 0; i < count; ++i)
+        if (ps[i].M > 0 && ps[i].N > 0) g.p[g.count++] = ps[i];
+    if (g.count == 0) return ESMF_OK;
+    int T = 16;
+    for (int cand : {64, 32}) {
+        int tot = 0;
+        for (int i = 0; i < g.count; ++i) tot += tiles_of(g.p[i], cand);
+        if (tot >= 304) { T = cand; break; }
+    }
+    g.tiles[0] = 0;
+    for (int i = 0; i < g.count; ++i) g.tiles[i + 1] = g.tiles[i] + tiles_of(g.p[i], T);
+    const int blocks = g.tiles[g.count];
+    if (T == 64) k_gemm_group<64><<<blocks, 256, 0, s>>>(g);
+    else if (T == 32) k_gemm_group<32><<<blocks, 64, 0, s>>>(g);
+    else k_gemm_group<16><<<blocks, 16, 0, s>>>(g);
+    return check("k_gemm_group");
+}
+
+}  // namespace
+
+size_t energy_work_doubles(int n, int no) {
+    const size_t nn = (size_t)n * n, nv = (size_t)(n - no);
+    // D, J, K, F (3 each), Fk, M1, Wc, Wm; X1, X2, X3, R1, R2, R3 (no x n);
+    // X4, Rg1, Rg2 (nv x n); Z1a, Z1b, Z1c, Z3 (no x nv); Z2 (no x no); partials, scalars
+    return 16 * nn + 6 * (size_t)no * n + 3 * nv * n + 4 * (size_t)no * nv + (size_t)no * no +
+           5 * DOT_BLOCKS + 8;
+}
+
+EnergyWork energy_work_layout(double *base, int n, int no) {
+    const size_t nn = (size_t)n * n, nv = (size_t)(n - no), non = (size_t)no * n, nvn = nv * n;
+    EnergyWork w;
+    double *p = base;
+    w.D = p; p += 3 * nn;
+    w.J = p; p += 3 * nn;
+    w.K = p; p += 3 * nn;
+    w.F = p; p += 3 * nn;
+    w.Fk = p; p += nn;
+    w.M1 = p; p += nn;
+    w.Wc = p; p += nn;
+    w.Wm = p; p += nn;
+    w.X1 = p; p += non;
+    w.X2 = p; p += non;
+    w.X3 = p; p += non;
+    w.R1 = p; p += non;
+    w.R2 = p; p += non;
+    w.R3 = p; p += non;
+    w.X4 = p; p += nvn;
+    w.Rg1 = p; p += nvn;
+    w.Rg2 = p; p += nvn;
+    w.Z1a = p; p += (size_t)no * nv;
+    w.Z1b = p; p += (size_t)no * nv;
+    w.Z1c = p; p += (size_t)no * nv;
+    w.Z3 = p; p += (size_t)no * nv;
+    w.Z2 = p; p += (size_t)no * no;
+    w.partial = p; p += 5 * DOT_BLOCKS;
+    w.sc = p;
+    return w;
+}
+
+// Densities of the grouped build: P, T and (for the energy's Fk . A) A, from
+//   Wc = [sigma Gamma; sigma^T Theta] and Wm = [sigma Gamma; -sigma^T Theta]
+// (W1 = sigma Gamma, W2 = sigma^T Theta):
+//   P = Theta^T Theta, T = Theta^T W1, A = Wc^T Wm = W1^T W1 - W2^T W2.
+int launch_energy_densities(int n, int no, const double *V, const double *sigma, const EnergyWork &w,
+                            cudaStream_t s) {
+    const int nv = n - no;
+    const double *Th = V, *Ga = V + (size_t)no * n;
+    const size_t nn = (size_t)n * n, non = (size_t)no * n;
+    const GemmProblem g1[4] = {
+        gp(false, false, no, n, nv, 1.0, sigma, nv, Ga, n, 0.0, w.Wc, n),
+        gp(true, false, nv, n, no, 1.0, sigma, nv, Th, n, 0.0, w.Wc + non, n),
+        gp(false, false, no, n, nv, 1.0, sigma, nv, Ga, n, 0.0, w.Wm, n),
+        gp(true, false, nv, n, no, -1.0, sigma, nv, Th, n, 0.0, w.Wm + non, n)};
+    RET_IF(launch_group(g1, 4, s));
+    const GemmProblem g2[3] = {
+        gp(true, false, n, n, no, 1.0, Th, n, Th, n, 0.0, w.D, n),
+        gp(true, false, n, n, no, 1.0, Th, n, w.Wc, n, 0.0, w.D + nn, n),
+        gp(true, false, n, n, n, 1.0, w.Wc, n, w.Wm, n, 0.0, w.D + 2 * nn, n)};
+    return launch_group(g2, 3, s);
+}
+
+// Everything after the grouped build (F = [F_P, F_T, F_A] in w.F).
+int launch_energy_finish(int n, int no, double c0, const double *G, const double *V, const double *sigma,
+                         const EnergyWork &w, double *scalars, double *dsig, double *dV, cudaStream_t s) {
+    const int nv = n - no;
+    const size_t nn = (size_t)n * n, non = (size_t)no * n;
+    const double *Th = V, *Ga = V + non, *FT = w.F + nn;
+    const double *W1 = w.Wc, *W2 = w.Wc + non;
+    const bool grad = dsig != nullptr;
+    k_energy_fock<<<grid_for(nn), 256, 0, s>>>(n, c0, G, w.F, w.Fk, w.M1, grad ? 1 : 0);
+    RET_IF(check("k_energy_fock"));
+    k_energy_dots<<<DOT_BLOCKS, 256, 0, s>>>(n, no * nv, G, w.Fk, w.F, w.D, sigma, w.partial);
+    RET_IF(check("k_energy_dots"));
+    k_energy_scalars<<<1, 32, 0, s>>>(c0, w.partial, scalars, w.sc);
+    RET_IF(check("k_energy_scalars"));
+    if (!grad) return ESMF_OK;
+    const GemmProblem g3[7] = {
+        gp(false, false, no, n, n, 1.0, Th, n, w.Fk, n, 0.0, w.X1, n),
+        gp(false, false, no, n, n, 1.0, W1, n, w.Fk, n, 0.0, w.X2, n),
+        gp(false, false, no, n, n, 1.0, Th, n, FT, n, 0.0, w.X3, n),
+        gp(false, false, nv, n, n, 1.0, W2, n, w.Fk, n, 0.0, w.X4, n),
+        gp(false, false, no, n, n, 1.0, Th, n, w.M1, n, 0.0, w.R1, n),
+        gp(false, true, no, n, n, 1.0, W1, n, FT, n, 0.0, w.R2, n),
+        gp(false, false, nv, n, n, 1.0, W2, n, FT, n, 0.0, w.Rg2, n)};
+    RET_IF(launch_group(g3, 7, s));
+    const GemmProblem g4[6] = {
+        gp(false, true, no, nv, n, 1.0, w.X1, n, Ga, n, 0.0, w.Z1a, nv),
+        gp(false, true, no, nv, n, 1.0, w.X2, n, Ga, n, 0.0, w.Z1b, nv),
+        gp(false, true, no, nv, n, 1.0, w.X3, n, Ga, n, 0.0, w.Z1c, nv),
+        gp(false, true, no, no, n, 1.0, w.X1, n, Th, n, 0.0, w.Z2, no),
+        gp(false, false, no, n, nv, 1.0, sigma, nv, w.X4, n, 0.0, w.R3, n),
+        gp(true, false, nv, n, no, 1.0, sigma, nv, w.X2, n, 0.0, w.Rg1, n)};
+    RET_IF(launch_group(g4, 6, s));
+    const GemmProblem g5[1] = {gp(false, false, no, nv, no, 1.0, w.Z2, no, sigma, nv, 0.0, w.Z3, nv)};
+    RET_IF(launch_group(g5, 1, s));
+    const size_t tot = (size_t)no * nv + non + (size_t)nv * n;
+    k_energy_finish<<<grid_for(tot), 256, 0, s>>>(n, no, nv, c0, w, sigma, dsig, dV);
+    return check("k_energy_finish");
+}
+
+}  // namespace esmf

@@ -112,4 +112,20 @@ int launch_finalize(const DevBasis &b, int m, const double *D, const double *Jac
                     const double *Kacc, double *J, double *K, double *F, double *tsum,
                     cudaStream_t s);
 
+// ---- energy.cu (ESMF energy and gradient around the grouped build)
+struct EnergyWork {
+    double *D, *J, *K, *F;               // 3 x N x N each: P, T, A and their J, K, F
+    double *Fk, *M1, *Wc, *Wm;           // N x N
+    double *X1, *X2, *X3, *R1, *R2, *R3; // N_o x N
+    double *X4, *Rg1, *Rg2;              // N_v x N
+    double *Z1a, *Z1b, *Z1c, *Z3, *Z2;   // N_o x N_v (four), N_o x N_o
+    double *partial, *sc;                // reduction partials; {E_HF, E, N2}
+};
+size_t energy_work_doubles(int n, int no);
+EnergyWork energy_work_layout(double *base, int n, int no);
+int launch_energy_densities(int n, int no, const double *V, const double *sigma, const EnergyWork &w,
+                            cudaStream_t s);
+int launch_energy_finish(int n, int no, double c0, const double *G, const double *V, const double *sigma,
+                         const EnergyWork &w, double *scalars, double *dsig, double *dV, cudaStream_t s);
+
 }  // namespace esmf

@@ -33,6 +33,8 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
            "esmf_fock_autotune"]
 PATHS = {"auto": 0, "cuda_core": 1}
+# declared in include/esmf_energy.h
+ENERGY_EXPORTS = ["esmf_energy_gradient"]
 # declared in include/esmf_server.h, bound in server.py
 SERVER_EXPORTS = ["esmf_server_create", "esmf_server_register", "esmf_server_submit",
                   "esmf_server_wait", "esmf_server_stats", "esmf_server_reset_stats",
@@ -103,6 +105,8 @@ def load(path=None):
         L.esmf_fock_set_timing.restype = C.c_int
         L.esmf_fock_kernel_time.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int]
         L.esmf_fock_kernel_time.restype = C.c_int
+        L.esmf_energy_gradient.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, vp, vp, vp]
+        L.esmf_energy_gradient.restype = C.c_int
         L.esmf_fock_destroy.argtypes = [vp]
         L.esmf_fock_destroy.restype = None
         L.esmf_strerror.argtypes = [C.c_int]
@@ -154,6 +158,12 @@ def esmf_fock_build(h, m, D, J, K, F=None, traces=None, stream=None):
     rc = load().esmf_fock_build(h, int(m), _ptr(D), _ptr(J), _ptr(K), _ptr(F), _ptr(traces),
                                 _stream_ptr(stream))
     _check(rc, "esmf_fock_build")
+
+
+def esmf_energy_gradient(h, n_occ, c0, G, V, sigma, scalars, dE_dsigma=None, dE_dV=None, stream=None):
+    rc = load().esmf_energy_gradient(h, int(n_occ), float(c0), _ptr(G), _ptr(V), _ptr(sigma), _ptr(scalars),
+                                     _ptr(dE_dsigma), _ptr(dE_dV), _stream_ptr(stream))
+    _check(rc, "esmf_energy_gradient")
 
 
 def esmf_fock_build_noalloc(h, m, D, J, K, F=None, traces=None, stream=None):
@@ -285,6 +295,23 @@ class FockBuilder:
             traces = torch.empty(m, dtype=torch.float64, device=D.device)
         esmf_fock_build(self.h, m, D, J, K, F, traces, stream)
         return J, K, F, traces
+
+    def energy_gradient(self, G, V, sigma, c0, n_occ, gradient=True, stream=None):
+        """ESMF energy (and gradient) for CUDA float64 tensors G, V (N x N) and
+        sigma (n_occ x (N - n_occ)).  Returns (scalars, dE_dsigma, dE_dV) as
+        device tensors, scalars = [E, dE/dc0]; the gradients are None when
+        gradient is False."""
+        import torch
+        n = self.n
+        for name, t, shape in (("G", G, (n, n)), ("V", V, (n, n)), ("sigma", sigma, (n_occ, n - n_occ))):
+            if t.dtype != torch.float64 or not t.is_cuda or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be a CUDA float64 tensor of shape {shape}")
+        G, V, sigma = G.contiguous(), V.contiguous(), sigma.contiguous()
+        scalars = torch.empty(2, dtype=torch.float64, device=G.device)
+        ds = torch.empty_like(sigma) if gradient else None
+        dV = torch.empty_like(V) if gradient else None
+        esmf_energy_gradient(self.h, n_occ, c0, G, V, sigma, scalars, ds, dV, stream)
+        return scalars, ds, dV
 
     def build_host(self, D, J=None, K=None, traces=None, stream=None, timeout_ms=0):
         m = D.shape[0]

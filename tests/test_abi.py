@@ -35,7 +35,7 @@ def lib():
 def test_header_lists_the_entry_points():
     names = declared_functions()
     from paper_2002_00322_gb300 import fock
-    assert set(fock.EXPORTS) | set(fock.SERVER_EXPORTS) == set(names)
+    assert set(fock.EXPORTS) | set(fock.SERVER_EXPORTS) | set(fock.ENERGY_EXPORTS) == set(names)
     assert "esmf_fock_create" in names and "esmf_fock_build" in names
 
 
@@ -54,6 +54,8 @@ def test_strerror_and_host_side_argument_errors(lib):
     b = fock.esmf_basis_t(0, None, None, None, None)
     assert lib.esmf_fock_create(C.byref(b), 0.0, 0, 0, 0, 0, None) == fock.ESMF_ERR_INVALID_ARG
     assert lib.esmf_fock_build(None, 1, None, None, None, None, None, None) == fock.ESMF_ERR_INVALID_ARG
+    assert lib.esmf_energy_gradient(None, 1, 1.0, None, None, None, None, None, None, None) == \
+        fock.ESMF_ERR_INVALID_ARG
     st = fock.esmf_stats_t()
     assert lib.esmf_fock_stats(None, C.byref(st)) == fock.ESMF_ERR_INVALID_ARG
     lib.esmf_fock_destroy(None)

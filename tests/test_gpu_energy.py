@@ -1,0 +1,158 @@
+"""ESMF energy and gradient on the GPU (esmf_energy_gradient) against the FP64
+oracle (oracle/esmf_energy.py).
+
+Small molecules: every output against the oracle's energy and derivatives
+computed with the oracle's own J/K.  Full bench size (200 functions): the
+oracle's Fock builds take minutes there, so the checks are properties that
+hold at any size and the oracle's assembly on top of the library's FP64 J/K
+(whose parity is tested elsewhere), plus finite differences of the GPU energy.
+
+Tolerances: FP64 builds 1e-10 relative; FP32 and split-FP16 builds 2e-6 on E
+(the J/K bound, since E is a sum of F . D inner products with little
+cancellation) and 1e-5 relative Frobenius on the gradients, whose terms cancel
+(dE/dsigma is a difference of O(1) matrices that nearly vanishes near a
+stationary point).
+"""
+import numpy as np
+import pytest
+
+from oracle import esmf_energy as EE
+from oracle.oracle import Oracle
+from paper_2002_00322_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(x, r):
+    return float(np.linalg.norm(np.asarray(x) - np.asarray(r)) / max(np.linalg.norm(r), 1e-300))
+
+
+def gpu_energy(esmf, fb, st, gradient=True):
+    import torch
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sc, ds, dV = fb.energy_gradient(t(st.G), t(st.V), t(st.sigma), st.c0, st.nocc, gradient=gradient)
+    torch.cuda.synchronize()
+    sc = sc.cpu().numpy()
+    if not gradient:
+        return float(sc[0]), float(sc[1]), None, None
+    return float(sc[0]), float(sc[1]), ds.cpu().numpy(), dV.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = W.small_random(48, 1, 21, tol=1e-10, edge=7.0, min_dist=1.2)
+    st = W.esmf_state(W.rng_for(W.BASE_SEED + 700), w.basis, 10, sigma_norm=0.4)
+    o = Oracle(w.basis)
+    jk = lambda D: o.jk_unique(D, w.tol)[:2]
+    ref = EE.energy_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc)
+    return w, st, ref
+
+
+@pytest.mark.parametrize("mode,prec,tol_e,tol_g", [
+    ("stored", "fp64", 1e-10, 1e-10), ("direct", "fp64", 1e-10, 1e-10),
+    ("stored", "fp32", 2e-6, 1e-5), ("stored", "fp16x2", 2e-6, 1e-5),
+])
+def test_energy_gradient_matches_oracle(esmf, small, mode, prec, tol_e, tol_g):
+    w, st, (E, dc0, ds, dV) = small
+    with esmf.FockBuilder(w.basis, w.tol, mode, prec) as fb:
+        Eg, dc0g, dsg, dVg = gpu_energy(esmf, fb, st)
+        Eo, dc0o, _, _ = gpu_energy(esmf, fb, st, gradient=False)
+    errs = (abs(Eg - E) / abs(E), abs(dc0g - dc0) / max(abs(dc0), 1e-12), rel(dsg, ds), rel(dVg, dV))
+    print(f"\nENERGY {w.name} {mode}/{prec}: E {errs[0]:.2e} dE/dc0 {errs[1]:.2e} "
+          f"dE/dsigma {errs[2]:.2e} dE/dV {errs[3]:.2e}")
+    assert errs[0] <= tol_e
+    assert errs[1] <= tol_g and errs[2] <= tol_g and errs[3] <= tol_g
+    # the energy-only call builds two densities instead of three (FP64
+    # reductions may then add in another order)
+    assert abs(Eo - Eg) <= max(tol_e, 1e-13) * abs(Eg)
+
+
+def test_hf_special_case_on_gpu(esmf, small):
+    """sigma = 0, c0 = 1: the GPU energy is the oracle's HF energy and dE/dc0 = 0."""
+    w, st, _ = small
+    st0 = W.EsmfState(st.G, st.V, np.zeros_like(st.sigma), 1.0, st.nocc)
+    o = Oracle(w.basis)
+    jk = lambda D: o.jk_unique(D, w.tol)[:2]
+    E = EE.energy(jk, st0.G, st0.V, st0.sigma, 1.0, st0.nocc)
+    with esmf.FockBuilder(w.basis, w.tol, "stored", "fp64") as fb:
+        Eg, dc0g, _, _ = gpu_energy(esmf, fb, st0)
+    assert Eg == pytest.approx(E, rel=1e-11)
+    assert abs(dc0g) < 1e-10 * abs(E)
+
+
+@pytest.fixture(scope="module")
+def full():
+    w = W.stored()
+    st = W.esmf_state(W.rng_for(W.BASE_SEED + 701), w.basis, w.nocc, sigma_norm=0.3)
+    return w, st
+
+
+def test_full_size_against_oracle_assembly(esmf, full):
+    """200 functions: GPU energy and gradient (FP64 and split-FP16 builds)
+    against the oracle's assembly over the library's FP64 J/K."""
+    import torch
+    w, st = full
+    with esmf.FockBuilder(w.basis, w.tol, "stored", "fp64") as fb:
+        def jk(D):
+            J, K, _, _ = fb.build(torch.from_numpy(np.ascontiguousarray(D)).cuda(), want_traces=False)
+            return J.cpu().numpy(), K.cpu().numpy()
+        E, dc0, ds, dV = EE.energy_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc)
+        Eg, dc0g, dsg, dVg = gpu_energy(esmf, fb, st)
+    assert abs(Eg - E) <= 1e-10 * abs(E)
+    assert abs(dc0g - dc0) <= 1e-10 * max(abs(dc0), 1.0)
+    assert rel(dsg, ds) <= 1e-10 and rel(dVg, dV) <= 1e-10
+    with esmf.FockBuilder(w.basis, w.tol, "stored", "fp16x2") as fb:
+        Eh, dc0h, dsh, dVh = gpu_energy(esmf, fb, st)
+    errs = (abs(Eh - E) / abs(E), abs(dc0h - dc0) / max(abs(dc0), 1e-12), rel(dsh, ds), rel(dVh, dV))
+    print(f"\nENERGY stored_n200 stored/fp16x2 vs FP64: E {errs[0]:.2e} dE/dc0 {errs[1]:.2e} "
+          f"dE/dsigma {errs[2]:.2e} dE/dV {errs[3]:.2e}")
+    assert errs[0] <= 2e-6 and max(errs[1:]) <= 1e-5
+
+
+def test_full_size_properties(esmf, full):
+    """Scale invariance (c0 dE/dc0 + sigma . dE/dsigma = 0) and directional
+    derivatives of the GPU energy along random unit directions in sigma and V
+    (central differences at steps h and h/2, Richardson-extrapolated: error
+    O(h^4))."""
+    w, st = full
+    rng = np.random.default_rng(3)
+    with esmf.FockBuilder(w.basis, w.tol, "stored", "fp64") as fb:
+        E, dc0, ds, dV = gpu_energy(esmf, fb, st)
+        assert abs(st.c0 * dc0 + np.sum(st.sigma * ds)) <= 1e-10 * max(1.0, abs(E))
+        h = 2e-3
+        Es = lambda s=st.sigma, V=st.V: gpu_energy(esmf, fb, W.EsmfState(st.G, V, s, st.c0, st.nocc), False)[0]
+
+        def deriv(f):
+            c = lambda t: (f(t) - f(-t)) / (2 * t)
+            return (4.0 * c(h / 2) - c(h)) / 3.0
+
+        for _ in range(2):
+            d = rng.standard_normal(st.sigma.shape)
+            d /= np.linalg.norm(d)
+            fd = deriv(lambda t: Es(s=st.sigma + t * d))
+            assert fd == pytest.approx(np.sum(ds * d), rel=1e-7, abs=1e-8)
+            d = rng.standard_normal(st.V.shape)
+            d /= np.linalg.norm(d)
+            fd = deriv(lambda t: Es(V=st.V + t * d))
+            assert fd == pytest.approx(np.sum(dV * d), rel=1e-7, abs=1e-8)
+
+
+def test_invalid_arguments(esmf, small):
+    import torch
+    w, st, _ = small
+    n = w.basis.n
+    with esmf.FockBuilder(w.basis, w.tol, "stored", "fp64") as fb:
+        G = torch.zeros(n, n, dtype=torch.float64, device="cuda")
+        V = torch.zeros(n, n, dtype=torch.float64, device="cuda")
+        s = torch.zeros(st.nocc, n - st.nocc, dtype=torch.float64, device="cuda")
+        sc = torch.zeros(2, dtype=torch.float64, device="cuda")
+        for nocc in (0, n):
+            with pytest.raises(esmf.EsmfError):
+                esmf.esmf_energy_gradient(fb.h, nocc, 1.0, G, V, s, sc)
+        with pytest.raises(esmf.EsmfError):
+            esmf.esmf_energy_gradient(fb.h, st.nocc, float("nan"), G, V, s, sc)
+        with pytest.raises(esmf.EsmfError):      # host memory where device memory is required
+            esmf.esmf_energy_gradient(fb.h, st.nocc, 1.0, G.cpu(), V, s, sc)
+        with pytest.raises(esmf.EsmfError):      # only one of the two gradient outputs
+            esmf.esmf_energy_gradient(fb.h, st.nocc, 1.0, G, V, s, sc, s.clone(), None)
