@@ -192,6 +192,27 @@ def run_ours(args):
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         e2e_s = float(x.item())
 
+    # ESMF energy and gradient on the same handle (one grouped build of three
+    # densities plus the O(N^3) FP64 algebra), timed on the device
+    es = W.esmf_state(W.rng_for(W.BASE_SEED + 701), w.basis, w.nocc, sigma_norm=0.3)
+    Gd, Vd, Sd = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (es.G, es.V, es.sigma))
+    for _ in range(2):
+        fb.energy_gradient(Gd, Vd, Sd, es.c0, es.nocc, stream=stream)
+    e_reps = max(5, args.steps // 2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e_reps):
+        fb.energy_gradient(Gd, Vd, Sd, es.c0, es.nocc, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1) / e_reps
+    energy = {"ms_per_eval": round(e_ms, 4), "evals_per_s": round(world * 1e3 / e_ms, 2),
+              "n_occ": es.nocc, "fock_builds_grouped": 3,
+              "what": "E, dE/dc0, dE/dsigma, dE/dV (esmf_energy_gradient)",
+              # k_gemm_group x5, k_dmax, k_dbank, k_jk_umma, k_finalize_blocked,
+              # k_energy_fock, k_energy_dots, k_energy_scalars, k_energy_finish
+              "gpu_launches_per_eval": 13 if args.precision in ("fp16x2", "bf16x2") else 11}
+
     # roofline of the dominant (contraction) kernel: algorithmic bytes =
     # kept unique integrals x bytes + D in + J, K out (FP64)
     eb = {"fp64": 8, "fp32": 4, "fp16x2": 4, "bf16x2": 4}[args.precision]
@@ -228,7 +249,8 @@ def run_ours(args):
            # our kernels per step: tensor path k_dmax, k_dbank, k_jk_umma, k_finalize_blocked;
            # CUDA-core path k_jk_cuda, k_finalize
            "gpu_launches": int((4 if args.precision in ("fp16x2", "bf16x2") else 2) * args.steps),
-           "clocks": clk.summary()}
+           "clocks": clk.summary(),
+           "esmf_energy_gradient": energy}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_seconds)
     if rank == 0:

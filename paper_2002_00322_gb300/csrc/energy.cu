@@ -25,7 +25,7 @@ namespace esmf {
 
 namespace {
 
-constexpr int GK = 16;             // K step of the GEMM tiles
+constexpr int GK = 32;             // K step of the GEMM tiles
 
 // One problem of a grouped FP64 GEMM: C (M x N) = alpha op(A) op(B) + beta C,
 // row-major; op(A) is M x K (A stored K x M when ta), op(B) is K x N (B stored
@@ -43,13 +43,15 @@ struct GemmGroup {
     int count;
 };
 
-// Independent GEMMs in one launch (GB300's FP64 rate per SM is low, so the
-// small O(N^3) products must spread over all SMs).  Tile T x T outputs with
-// (T/4)^2 threads, each owning a 4 x 4 strided patch (rows ty + T/4 i,
-// columns tx + T/4 j).
-template <int T>
-__global__ void __launch_bounds__((T / 4) * (T / 4)) k_gemm_group(const __grid_constant__ GemmGroup g) {
-    constexpr int NT = (T / 4) * (T / 4), S = T / 4;
+// Independent GEMMs in one launch.  GB300's FP64 pipe is narrow (about two
+// FMAs per clock per SM), so the small O(N^3) products must spread over all
+// SMs: tile T x T outputs, (T/R)^2 threads each owning an R x R strided patch
+// (rows ty + (T/R) i, columns tx + (T/R) j); the tile's operand loads are
+// unrolled so their latencies overlap.
+template <int T, int R>
+__global__ void __launch_bounds__((T / R) * (T / R)) k_gemm_group(const __grid_constant__ GemmGroup g) {
+    constexpr int S = T / R, NT = S * S, LOADS = T * GK / NT;
+    static_assert(T * GK % NT == 0, "tile loads");
     __shared__ double As[GK][T + 1];
     __shared__ double Bs[GK][T + 1];
     int q = 0;
@@ -59,45 +61,48 @@ __global__ void __launch_bounds__((T / 4) * (T / 4)) k_gemm_group(const __grid_c
     const int tn = (P.N + T - 1) / T;
     const int m0 = (tile / tn) * T, n0 = (tile % tn) * T;
     const int t = threadIdx.x, tx = t % S, ty = t / S;
-    double acc[4][4] = {};
+    double acc[R][R] = {};
     for (int k0 = 0; k0 < P.K; k0 += GK) {
-        for (int e = t; e < T * GK; e += NT) {
-            int mm, kk;
-            if (P.ta) { mm = e % T; kk = e / T; }     // contiguous along m in memory
-            else { mm = e / GK; kk = e % GK; }        // contiguous along k
+        double va[LOADS], vb[LOADS];
+#pragma unroll
+        for (int r = 0; r < LOADS; ++r) {
+            const int e = t + NT * r;
+            const int mm = P.ta ? e % T : e / GK, kk = P.ta ? e / T : e % GK;
             const int gm = m0 + mm, gk = k0 + kk;
-            double v = 0.0;
-            if (gm < P.M && gk < P.K) v = P.ta ? P.A[(size_t)gk * P.lda + gm] : P.A[(size_t)gm * P.lda + gk];
-            As[kk][mm] = v;
-            int nn, kb;
-            if (P.tb) { nn = e / GK; kb = e % GK; }   // contiguous along k
-            else { nn = e % T; kb = e / T; }          // contiguous along n
+            va[r] = (gm < P.M && gk < P.K) ? (P.ta ? P.A[(size_t)gk * P.lda + gm] : P.A[(size_t)gm * P.lda + gk]) : 0.0;
+            const int nn = P.tb ? e / GK : e % T, kb = P.tb ? e % GK : e / T;
             const int gn = n0 + nn, gkb = k0 + kb;
-            double w = 0.0;
-            if (gn < P.N && gkb < P.K) w = P.tb ? P.B[(size_t)gn * P.ldb + gkb] : P.B[(size_t)gkb * P.ldb + gn];
-            Bs[kb][nn] = w;
+            vb[r] = (gn < P.N && gkb < P.K) ? (P.tb ? P.B[(size_t)gn * P.ldb + gkb] : P.B[(size_t)gkb * P.ldb + gn]) : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < LOADS; ++r) {
+            const int e = t + NT * r;
+            const int mm = P.ta ? e % T : e / GK, kk = P.ta ? e / T : e % GK;
+            As[kk][mm] = va[r];
+            const int nn = P.tb ? e / GK : e % T, kb = P.tb ? e % GK : e / T;
+            Bs[kb][nn] = vb[r];
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 8
         for (int kk = 0; kk < GK; ++kk) {
-            double a[4], b[4];
+            double a[R], b[R];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + S * i];
+            for (int i = 0; i < R; ++i) a[i] = As[kk][ty + S * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + S * j];
+            for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + S * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < R; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < R; ++i) {
         const int gm = m0 + ty + S * i;
         if (gm >= P.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < R; ++j) {
             const int gn = n0 + tx + S * j;
             if (gn >= P.N) continue;
             double *c = P.C + (size_t)gm * P.ldc + gn;
@@ -166,19 +171,25 @@ __global__ void __launch_bounds__(256) k_energy_dots(int n, int nsig, const doub
     }
 }
 
-// Sums the partials in a fixed order and forms E and dE/dc0 (Eq. eng_der_c0):
-// out = {E, dE/dc0}; sc = {E_HF, E, N2}.
+// Sums the partials in a fixed order (warp k sums scalar k) and forms E and
+// dE/dc0 (Eq. eng_der_c0): out = {E, dE/dc0}; sc = {E_HF, E, N2}.
 __global__ void k_energy_scalars(double c0, const double *__restrict__ partial, double *__restrict__ out,
                                  double *__restrict__ sc) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int b = 0; b < DOT_BLOCKS; ++b)
-        for (int k = 0; k < 5; ++k) s[k] += partial[b * 5 + k];
-    const double N2 = c0 * c0 + 2.0 * s[4];
-    const double ehf = s[0];
-    const double E = (N2 * ehf + 4.0 * c0 * s[1] + 2.0 * s[2] + 2.0 * s[3]) / N2;
+    __shared__ double tot[5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < 5) {
+        double v = 0.0;
+        for (int b = lane; b < DOT_BLOCKS; b += 32) v += partial[b * 5 + warp];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) tot[warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double N2 = c0 * c0 + 2.0 * tot[4];
+    const double ehf = tot[0];
+    const double E = (N2 * ehf + 4.0 * c0 * tot[1] + 2.0 * tot[2] + 2.0 * tot[3]) / N2;
     out[0] = E;
-    out[1] = (2.0 * c0 * ehf + 4.0 * s[1]) / N2 - 2.0 * c0 * E / N2;
+    out[1] = (2.0 * c0 * ehf + 4.0 * tot[1]) / N2 - 2.0 * c0 * E / N2;
     sc[0] = ehf;
     sc[1] = E;
     sc[2] = N2;
@@ -228,7 +239,7 @@ int check(const char *what) {
 }
 
 // Launches up to MAX_GROUP independent GEMMs together, with the largest tile
-// that still gives about two blocks per SM (GB300: 152 SMs).
+// that still gives about four blocks per SM (GB300: 152 SMs).
 int launch_group(const GemmProblem *ps, int count, cudaStream_t s) {
     GemmGroup g;
     g.count = 0;
@@ -239,14 +250,14 @@ int launch_group(const GemmProblem *ps, int count, cudaStream_t s) {
     for (int cand : {64, 32}) {
         int tot = 0;
         for (int i = 0; i < g.count; ++i) tot += tiles_of(g.p[i], cand);
-        if (tot >= 304) { T = cand; break; }
+        if (tot >= 608) { T = cand; break; }
     }
     g.tiles[0] = 0;
     for (int i = 0; i < g.count; ++i) g.tiles[i + 1] = g.tiles[i] + tiles_of(g.p[i], T);
     const int blocks = g.tiles[g.count];
-    if (T == 64) k_gemm_group<64><<<blocks, 256, 0, s>>>(g);
-    else if (T == 32) k_gemm_group<32><<<blocks, 64, 0, s>>>(g);
-    else k_gemm_group<16><<<blocks, 16, 0, s>>>(g);
+    if (T == 64) k_gemm_group<64, 4><<<blocks, 256, 0, s>>>(g);
+    else if (T == 32) k_gemm_group<32, 4><<<blocks, 64, 0, s>>>(g);
+    else k_gemm_group<16, 2><<<blocks, 64, 0, s>>>(g);
     return check("k_gemm_group");
 }
 
@@ -325,7 +336,7 @@ int launch_energy_finish(int n, int no, double c0, const double *G, const double
     RET_IF(check("k_energy_fock"));
     k_energy_dots<<<DOT_BLOCKS, 256, 0, s>>>(n, no * nv, G, w.Fk, w.F, w.D, sigma, w.partial);
     RET_IF(check("k_energy_dots"));
-    k_energy_scalars<<<1, 32, 0, s>>>(c0, w.partial, scalars, w.sc);
+    k_energy_scalars<<<1, 160, 0, s>>>(c0, w.partial, scalars, w.sc);
     RET_IF(check("k_energy_scalars"));
     if (!grad) return ESMF_OK;
     const GemmProblem g3[7] = {
