@@ -1,8 +1,9 @@
-"""Pins of the ESMF energy / gradient oracle (oracle/esmf_energy.py) against
-facts that do not come from the oracle itself: the HF special case of Eq.
-(esmf_eng_hf), the Slater-Condon CIS energy in the MO basis, finite
-differences of the energy, and the scale invariance of E in (c0, sigma).
-CPU only."""
+"""Pins of the ESMF energy / gradient / GVP oracle (oracle/esmf_energy.py)
+against facts that do not come from the oracle itself: the HF special case of
+Eq. (esmf_eng_hf), the Slater-Condon CIS energy in the MO basis, finite
+differences of the energy, of its gradient (the Hessian-vector tangent) and
+of the GVP objective of Eq. (esmf_gvb) through exact matrix exponentials, the
+scale invariance of E in (c0, sigma) and the GVP objective's limits.  CPU only."""
 import numpy as np
 import pytest
 
@@ -117,3 +118,94 @@ def test_printed_theta_derivative_disagrees_with_finite_differences(case):
                - 4 * s @ s.T @ Th @ FP + 4 * s @ Ga @ FT / N2) / N2
     _, _, _, dV = EE.energy_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc)
     assert np.max(np.abs(printed - dV[:st.nocc])) > 1e-2 * np.max(np.abs(dV[:st.nocc]))
+
+
+def richardson(f, h):
+    """Central difference at h and h/2, extrapolated (error O(h^4))."""
+    c = lambda t: (np.asarray(f(t)) - np.asarray(f(-t))) / (2 * t)
+    return (4.0 * c(h / 2) - c(h)) / 3.0
+
+
+def test_gradient_tangent_matches_finite_differences(case):
+    """energy_gradient_tangent (the product rule through every term of the
+    gradient) equals the directional derivative of energy_gradient."""
+    w, eri, jk = case
+    st = state(w, 8, 3, sigma_norm=0.4)
+    rng = np.random.default_rng(1)
+    dV = rng.standard_normal(st.V.shape)
+    ds = rng.standard_normal(st.sigma.shape)
+    dc = 0.7
+    prim, tan = EE.energy_gradient_tangent(jk, st.G, st.V, st.sigma, st.c0, st.nocc, dV, ds, dc)
+    ref = EE.energy_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc)
+    assert prim[0] == pytest.approx(ref[0], rel=1e-14)
+    g = lambda i: (lambda t: EE.energy_gradient(jk, st.G, st.V + t * dV, st.sigma + t * ds,
+                                                 st.c0 + t * dc, st.nocc)[i])
+    for i in range(4):
+        fd = richardson(g(i), 1e-4)
+        scale = max(1.0, float(np.max(np.abs(fd))))
+        assert np.max(np.abs(np.asarray(tan[i]) - fd)) < 1e-8 * scale, i
+
+
+def test_rotation_gradient_at_zero(case):
+    """The exact exp-map rotation gradient at X = 0 is Gam - Gam^T."""
+    w, eri, jk = case
+    st = state(w, 9, 3)
+    _, _, _, gV = EE.energy_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc)
+    a = EE.rotation_gradient(st.V, gV)
+    b = EE.rotation_gradient_at(jk, st.G, st.V, st.sigma, st.c0, st.nocc, np.zeros_like(st.V))
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def gvp_objective(jk, st, om, mu, chi, c0=None, s=None, X=None):
+    """L_mu,chi of Eq. (esmf_gvb) at (c0, sigma, X), |grad E|^2 with the exact
+    rotation gradient of V(X) = exp(X) V."""
+    from scipy.linalg import expm
+    c0 = st.c0 if c0 is None else c0
+    s = st.sigma if s is None else s
+    X = np.zeros_like(st.V) if X is None else X
+    V = expm(X) @ st.V
+    E, gc, gs, _ = EE.energy_gradient(jk, st.G, V, s, c0, st.nocc)
+    Gx = EE.rotation_gradient_at(jk, st.G, st.V, s, c0, st.nocc, X)
+    gn = gc * gc + np.sum(gs * gs) + 0.5 * np.sum(Gx * Gx)
+    return chi * (mu * (om - E) ** 2 + (1 - mu) * gn) + (1 - chi) * E
+
+
+@pytest.mark.parametrize("om,mu,chi", [(-2.5, 0.4, 0.8), (0.0, 0.0, 1.0)])
+def test_gvp_gradient_matches_finite_differences(case, om, mu, chi):
+    """dL/dc0, dL/dsigma and dL/dX of Eq. (esmf_l_gvp_der) (with the Hessian-
+    vector product) against finite differences of L itself."""
+    pytest.importorskip("scipy")
+    w, eri, jk = case
+    st = state(w, 5, 3, sigma_norm=0.4)
+    L, E, gn2, dLc, dLs, dLX = EE.gvp_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc, om, mu, chi)
+    assert L == pytest.approx(gvp_objective(jk, st, om, mu, chi), rel=1e-12)
+    h = 1e-4
+    assert dLc == pytest.approx(richardson(lambda t: gvp_objective(jk, st, om, mu, chi, c0=st.c0 + t), h),
+                                rel=1e-6)
+    for (i, a) in [(0, 0), (1, 2), (2, 5)]:
+        d = np.zeros_like(st.sigma)
+        d[i, a] = 1.0
+        fd = richardson(lambda t: gvp_objective(jk, st, om, mu, chi, s=st.sigma + t * d), h)
+        assert dLs[i, a] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+    for (p, q) in [(5, 1), (8, 4), (2, 0), (9, 7)]:
+        Z = np.zeros_like(st.V)
+        Z[p, q], Z[q, p] = 1.0, -1.0
+        fd = richardson(lambda t: gvp_objective(jk, st, om, mu, chi, X=t * Z), h)
+        assert dLX[p, q] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+    np.testing.assert_allclose(dLX, -dLX.T, atol=1e-12)
+
+
+def test_gvp_limits(case):
+    """chi = 0: L = E and dL = grad E.  chi = 1, mu = 1: dL = -2 (omega - E) grad E."""
+    w, eri, jk = case
+    st = state(w, 4, 3)
+    E, gc, gs, gV = EE.energy_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc)
+    Gx = EE.rotation_gradient(st.V, gV)
+    L, E0, _, dLc, dLs, dLX = EE.gvp_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc, 1.0, 0.3, 0.0)
+    assert L == pytest.approx(E, rel=1e-14) and dLc == pytest.approx(gc, rel=1e-13)
+    np.testing.assert_allclose(dLs, gs, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(dLX, Gx, rtol=1e-13, atol=1e-14)
+    L, _, _, dLc, dLs, dLX = EE.gvp_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc, 1.0, 1.0, 1.0)
+    f = -2.0 * (1.0 - E)
+    assert L == pytest.approx((1.0 - E) ** 2, rel=1e-13) and dLc == pytest.approx(f * gc, rel=1e-12)
+    np.testing.assert_allclose(dLX, f * Gx, rtol=1e-12, atol=1e-13)
