@@ -212,6 +212,19 @@ def run_ours(args):
               # k_gemm_group x5, k_dmax, k_dbank, k_jk_umma, k_finalize_blocked,
               # k_energy_fock, k_energy_dots, k_energy_scalars, k_energy_finish
               "gpu_launches_per_eval": 13 if args.precision in ("fp16x2", "bf16x2") else 11}
+    # GVP objective (Eq. esmf_gvb) and its derivatives: two grouped passes
+    for _ in range(2):
+        fb.gvp_gradient(Gd, Vd, Sd, es.c0, es.nocc, -3.0, 0.4, 0.8, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e_reps):
+        fb.gvp_gradient(Gd, Vd, Sd, es.c0, es.nocc, -3.0, 0.4, 0.8, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g_ms = e0.elapsed_time(e1) / e_reps
+    gvp = {"ms_per_eval": round(g_ms, 4), "evals_per_s": round(world * 1e3 / g_ms, 2),
+           "fock_builds_grouped": "3 + 3 (two passes)", "omega_mu_chi": [-3.0, 0.4, 0.8],
+           "what": "L, E, |grad E|^2, dL/dc0, dL/dsigma, dL/dX (esmf_gvp_gradient)"}
 
     # roofline of the dominant (contraction) kernel: algorithmic bytes =
     # kept unique integrals x bytes + D in + J, K out (FP64)
@@ -250,7 +263,8 @@ def run_ours(args):
            # CUDA-core path k_jk_cuda, k_finalize
            "gpu_launches": int((4 if args.precision in ("fp16x2", "bf16x2") else 2) * args.steps),
            "clocks": clk.summary(),
-           "esmf_energy_gradient": energy}
+           "esmf_energy_gradient": energy,
+           "esmf_gvp_gradient": gvp}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_seconds)
     if rank == 0:

@@ -61,6 +61,37 @@ int esmf_energy_gradient(esmf_fock_t *h, int n_occ, double c0, const double *G,
                          const double *V, const double *sigma, double *scalars,
                          double *dE_dsigma, double *dE_dV, void *stream);
 
+/*
+ * esmf_gvp_gradient -- the generalized-variational-principle objective of
+ * Eq. (esmf_gvb),
+ *     L = chi (mu (omega - E)^2 + (1 - mu) |grad E|^2) + (1 - chi) E,
+ * and its derivatives (Eq. esmf_l_gvp_der)
+ *     dL/dx = chi (-2 mu (omega - E) dE/dx + 2 (1 - mu) sum_y dE/dy d2E/dxdy)
+ *             + (1 - chi) dE/dx
+ * over the variables x = c0, sigma_ia and the orbital rotation X
+ * (antisymmetric, independent entries X_pq with p > q) of V(X) = exp(X) V at
+ * X = 0 (the paper's U -> U exp(-X), reset to zero after every step, Eq.
+ * redefine_U).  |grad E|^2 = (dE/dc0)^2 + |dE/dsigma|^2 + |Gx|^2 / 2 with
+ * Gx = (dE/dV) V^T - V (dE/dV)^T the rotation gradient.
+ * Two passes, as Sec. II.B.3 describes: pass 1 is esmf_energy_gradient (one
+ * grouped build of F[P], F[T], F[A]); pass 2 takes the gradient as the
+ * direction and builds, in one grouped pass, the three Fock-like matrices of
+ * the tangent densities P', T', A' (the paper's six pass-2 builds are pieces
+ * of these three), then forms the Hessian-vector product by the product rule
+ * and adds the second-order term of exp(X).
+ *   h, n_occ, c0, G, V, sigma, stream  as for esmf_energy_gradient
+ *   omega, mu, chi  the objective's target energy and weights (finite)
+ *   scalars    device, 4 doubles, receives {L, E, |grad E|^2, dL/dc0}
+ *   dL_dsigma  device, N_o x N_v
+ *   dL_dX      device, N x N, antisymmetric; entry (p, q), p > q, is dL/dX_pq
+ * Work memory: the energy's plus at most 31 N^2 doubles, owned by the handle.
+ * Errors as for esmf_energy_gradient.
+ */
+int esmf_gvp_gradient(esmf_fock_t *h, int n_occ, double c0, const double *G,
+                      const double *V, const double *sigma, double omega, double mu,
+                      double chi, double *scalars, double *dL_dsigma, double *dL_dX,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -618,12 +618,61 @@ int esmf_energy_gradient(esmf_fock_t *h, int n_occ, double c0, const double *G, 
         h->ework_n = need;
     }
     const EnergyWork w = energy_work_layout(h->ework, n, n_occ);
+    if (w.sc + 8 > h->ework + need) { set_error("internal: energy work layout"); return ESMF_ERR_CUDA; }
     cudaStream_t s = (cudaStream_t)stream;
     const bool grad = dE_dsigma != nullptr;
     RET(launch_energy_densities(n, n_occ, V, sigma, w, s));
     // one grouped build: F[P], F[T] (energy) and F[A] (gradient)
     RET(build_range(h, 0, h->nbricks, grad ? 3 : 2, w.D, w.J, w.K, w.F, nullptr, stream));
     return launch_energy_finish(n, n_occ, c0, G, V, sigma, w, scalars, dE_dsigma, dE_dV, s);
+}
+
+int esmf_gvp_gradient(esmf_fock_t *h, int n_occ, double c0, const double *G, const double *V,
+                      const double *sigma, double omega, double mu, double chi, double *scalars,
+                      double *dL_dsigma, double *dL_dX, void *stream) {
+    if (!h) { set_error("handle is NULL"); return ESMF_ERR_INVALID_ARG; }
+    const int n = h->n;
+    if (n_occ < 1 || n_occ >= n) {
+        set_error("n_occ = %d outside [1, %d)", n_occ, n);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    if (!is_finite(c0) || !is_finite(omega) || !is_finite(mu) || !is_finite(chi)) {
+        set_error("c0, omega, mu and chi must be finite");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    if (!G || !V || !sigma || !scalars || !dL_dsigma || !dL_dX) {
+        set_error("G, V, sigma, scalars, dL_dsigma and dL_dX are required");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
+    if (!is_device_ptr(G) || !is_device_ptr(V) || !is_device_ptr(sigma) || !is_device_ptr(scalars) ||
+        !is_device_ptr(dL_dsigma) || !is_device_ptr(dL_dX)) {
+        set_error("G, V, sigma, scalars, dL_dsigma and dL_dX must be device memory");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    const size_t ne = energy_work_doubles(n, n_occ), need = ne + gvp_work_doubles(n, n_occ);
+    if (need > h->ework_n) {
+        dfree(h, &h->ework, h->ework_n);
+        h->ework_n = 0;
+        RET(dalloc(h, &h->ework, need));
+        h->ework_n = need;
+    }
+    const EnergyWork w = energy_work_layout(h->ework, n, n_occ);
+    const GvpWork v = gvp_work_layout(h->ework + ne, n, n_occ);
+    if (w.sc + 8 > h->ework + ne || v.st + 8 > h->ework + need) {
+        set_error("internal: GVP work layout");
+        return ESMF_ERR_CUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // pass 1: E and its gradient from F[P], F[T], F[A]
+    RET(launch_energy_densities(n, n_occ, V, sigma, w, s));
+    RET(build_range(h, 0, h->nbricks, 3, w.D, w.J, w.K, w.F, nullptr, stream));
+    RET(launch_energy_finish(n, n_occ, c0, G, V, sigma, w, v.scE, v.gs, v.gV, s));
+    // pass 2: the tangent densities along the gradient, F[P'], F[T'], F[A']
+    RET(launch_gvp_tangent_densities(n, n_occ, V, sigma, w, v, s));
+    RET(build_range(h, 0, h->nbricks, 3, v.Dt, v.Jt, v.Kt, v.Ft, nullptr, stream));
+    return launch_gvp_finish(n, n_occ, c0, omega, mu, chi, G, V, sigma, w, v, scalars, dL_dsigma, dL_dX, s);
 }
 
 int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const double *D, double *J,

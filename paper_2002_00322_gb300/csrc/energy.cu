@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_energy_dots(int n, int nsig, const doub
 }
 
 // Sums the partials in a fixed order (warp k sums scalar k) and forms E and
-// dE/dc0 (Eq. eng_der_c0): out = {E, dE/dc0}; sc = {E_HF, E, N2}.
+// dE/dc0 (Eq. eng_der_c0): out = {E, dE/dc0}; sc = {E_HF, E, N2, Fk . T}.
 __global__ void k_energy_scalars(double c0, const double *__restrict__ partial, double *__restrict__ out,
                                  double *__restrict__ sc) {
     __shared__ double tot[5];
@@ -193,6 +193,7 @@ __global__ void k_energy_scalars(double c0, const double *__restrict__ partial, 
     sc[0] = ehf;
     sc[1] = E;
     sc[2] = N2;
+    sc[3] = tot[1];
 }
 
 // Final assembly with the device scalars sc = {E_HF, E, N2}:
@@ -218,6 +219,150 @@ __global__ void k_energy_finish(int n, int no, int nv, double c0, EnergyWork w, 
         } else {
             const size_t i = e - ns - nt;
             dV[nt + i] = (4.0 * c0 * w.X4[i] + 4.0 * w.Rg1[i] + 4.0 * w.Rg2[i]) * inv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- GVP
+// Up to 12 inner products x_k . y_k in one pass (per-block partials).
+constexpr int MAX_DOTS = 12;
+struct DotList {
+    const double *x[MAX_DOTS], *y[MAX_DOTS];
+    size_t len[MAX_DOTS];
+    int count;
+};
+__global__ void __launch_bounds__(256) k_dot_list(const __grid_constant__ DotList L, double *__restrict__ partial) {
+    __shared__ double red[8][MAX_DOTS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < L.count; ++k) {
+        double v = 0.0;
+        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < L.len[k]; e += (size_t)gridDim.x * blockDim.x)
+            v += L.x[k][e] * L.y[k][e];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < L.count) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+        partial[blockIdx.x * MAX_DOTS + threadIdx.x] = v;
+    }
+}
+
+// Gx = Gam - Gam^T (the rotation gradient, Eq. redefine_U at X = 0) and, in
+// place, X <- X + X^T for the two tangent densities built from one product.
+__global__ void k_antisym(int n, const double *__restrict__ Gam, double *__restrict__ Gx) {
+    const size_t nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = e / n, q = e % n;
+        Gx[e] = Gam[e] - Gam[q * n + p];
+    }
+}
+__global__ void k_symmetrize2(int n, double *__restrict__ X, double *__restrict__ Y) {
+    const size_t pairs = (size_t)n * (n + 1) / 2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * pairs; e += (size_t)gridDim.x * blockDim.x) {
+        double *M = e < pairs ? X : Y;
+        size_t r = e < pairs ? e : e - pairs;
+        size_t p = (size_t)((sqrt(8.0 * (double)r + 1.0) - 1.0) / 2.0);
+        while (p * (p + 1) / 2 > r) --p;
+        while ((p + 1) * (p + 2) / 2 <= r) ++p;
+        const size_t q = r - p * (p + 1) / 2;   // q <= p
+        const double v = M[p * n + q] + M[q * n + p];
+        M[p * n + q] = v;
+        M[q * n + p] = v;
+    }
+}
+
+// M1' = 4 c0' (F_T + F_T^T) + 4 c0 (F_T' + F_T'^T) + 2 (F_A' + F_A'^T), c0' = dE/dc0 (device).
+__global__ void k_gvp_m1t(int n, double c0, const double *__restrict__ gc0, const double *__restrict__ F,
+                          const double *__restrict__ Ft, double *__restrict__ M1t) {
+    const size_t nn = (size_t)n * n;
+    const double c0t = gc0[1];
+    const double *FT = F + nn, *FTt = Ft + nn, *FAt = Ft + 2 * nn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = e / n, q = e % n, tr = q * n + p;
+        M1t[e] = 4.0 * c0t * (FT[e] + FT[tr]) + 4.0 * c0 * (FTt[e] + FTt[tr]) + 2.0 * (FAt[e] + FAt[tr]);
+    }
+}
+
+// Scalars of the tangent pass and of the GVP objective (Eqs. esmf_gvb,
+// esmf_l_gvp_der).  d = tangent inner products (see launch_gvp_finish);
+// sc = {E_HF, E, N2, Fk . T}; scE = {E, dE/dc0}.
+// out = {L, E, |grad E|^2, dL/dc0}; st = {c0', N2', E', s0', a, b}.
+__global__ void k_gvp_scalars(double c0, double omega, double mu, double chi, const double *__restrict__ partial,
+                              const double *__restrict__ sc, const double *__restrict__ scE,
+                              double *__restrict__ out, double *__restrict__ st) {
+    __shared__ double d[MAX_DOTS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < MAX_DOTS; k += blockDim.x >> 5) {
+        double v = 0.0;
+        for (int b = lane; b < DOT_BLOCKS; b += 32) v += partial[b * MAX_DOTS + k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) d[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double s0 = sc[0], E = sc[1], N2 = sc[2], s1 = sc[3], gc0 = scE[1];
+    const double s0t = d[0] + d[1] + d[2], s1t = d[3] + d[4], s2t = d[5] + d[6], s3t = d[7] + d[8];
+    const double c0t = gc0;                                    // direction: the gradient itself
+    const double N2t = 2.0 * c0 * c0t + 4.0 * d[9];
+    const double numt = N2t * s0 + N2 * s0t + 4.0 * c0t * s1 + 4.0 * c0 * s1t + 2.0 * s2t + 2.0 * s3t;
+    const double Et = (numt - E * N2t) / N2;
+    const double Yct = 2.0 * c0t * s0 + 2.0 * c0 * s0t + 4.0 * s1t - 2.0 * c0t * E - 2.0 * c0 * Et;
+    const double Hc0 = (Yct - gc0 * N2t) / N2;
+    const double gn2 = gc0 * gc0 + d[10] + 0.5 * d[11];
+    const double a = chi * (-2.0 * mu * (omega - E)) + (1.0 - chi);
+    const double b = 2.0 * chi * (1.0 - mu);
+    out[0] = chi * (mu * (omega - E) * (omega - E) + (1.0 - mu) * gn2) + (1.0 - chi) * E;
+    out[1] = E;
+    out[2] = gn2;
+    out[3] = a * gc0 + b * Hc0;
+    st[0] = c0t;
+    st[1] = N2t;
+    st[2] = Et;
+    st[3] = s0t;
+    st[4] = a;
+    st[5] = b;
+}
+
+// Tangent of the gradient (the Hessian-vector product's c0/sigma/V parts):
+//   Hs  = dsigma' = (4 c0' Z1a + 4 c0 Z1a' + 4 Z1b' + 4 Z1c' - 4 Z3' + 4 (s0' - E') sigma
+//                    + 4 (s0 - E) g_s - N2' g_s) / N2
+//   Mt  = [dTheta'; dGamma'] with
+//   dTheta' = 4 X1' + (R1' + 4 R2' - 4 R3' + 4 c0' X2 + 4 c0 X2' - (g_Th - 4 X1) N2') / N2
+//   dGamma' = (4 c0' X4 + 4 c0 X4' + 4 Rg1' + 4 Rg2' - g_Ga N2') / N2
+__global__ void k_gvp_tangent(int n, int no, int nv, double c0, EnergyWork w, GvpWork v,
+                              const double *__restrict__ sigma) {
+    const double s0 = w.sc[0], E = w.sc[1], inv = 1.0 / w.sc[2];
+    const double c0t = v.st[0], N2t = v.st[1], Et = v.st[2], s0t = v.st[3];
+    const size_t ns = (size_t)no * nv, nt = (size_t)no * n, ng = (size_t)nv * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ns + nt + ng;
+         e += (size_t)gridDim.x * blockDim.x) {
+        if (e < ns) {
+            v.Hs[e] = (4.0 * c0t * w.Z1a[e] + 4.0 * c0 * v.Z1a[e] + 4.0 * v.Z1b[e] + 4.0 * v.Z1c[e] - 4.0 * v.Z3[e] +
+                       4.0 * (s0t - Et) * sigma[e] + 4.0 * (s0 - E) * v.gs[e] - N2t * v.gs[e]) * inv;
+        } else if (e < ns + nt) {
+            const size_t i = e - ns;
+            v.Mt[i] = 4.0 * v.X1[i] + (v.R1[i] + 4.0 * v.R2[i] - 4.0 * v.R3[i] + 4.0 * c0t * w.X2[i] +
+                                       4.0 * c0 * v.X2[i] - (v.gV[i] - 4.0 * w.X1[i]) * N2t) * inv;
+        } else {
+            const size_t i = e - ns - nt;
+            v.Mt[nt + i] = (4.0 * c0t * w.X4[i] + 4.0 * c0 * v.X4[i] + 4.0 * v.Rg1[i] + 4.0 * v.Rg2[i] -
+                            v.gV[nt + i] * N2t) * inv;
+        }
+    }
+}
+
+// dL/dsigma = a g_s + b Hs;  dL/dX = a Gx + b (Dd - Dd^T)   (Eq. esmf_l_gvp_der)
+__global__ void k_gvp_out(int n, int no, int nv, GvpWork v, double *__restrict__ dLs, double *__restrict__ dLX) {
+    const double a = v.st[4], b = v.st[5];
+    const size_t ns = (size_t)no * nv, nn = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < ns + nn; e += (size_t)gridDim.x * blockDim.x) {
+        if (e < ns) {
+            dLs[e] = a * v.gs[e] + b * v.Hs[e];
+        } else {
+            const size_t i = e - ns, p = i / n, q = i % n;
+            dLX[i] = a * v.Gx[i] + b * (v.Dd[i] - v.Dd[q * n + p]);
         }
     }
 }
@@ -361,6 +506,175 @@ int launch_energy_finish(int n, int no, double c0, const double *G, const double
     const size_t tot = (size_t)no * nv + non + (size_t)nv * n;
     k_energy_finish<<<grid_for(tot), 256, 0, s>>>(n, no, nv, c0, w, sigma, dsig, dV);
     return check("k_energy_finish");
+}
+
+size_t gvp_work_doubles(int n, int no) {
+    const size_t nn = (size_t)n * n, nv = (size_t)(n - no);
+    // gs, Z1a, Z1b, Z1c, Z3, Hs (no x nv); gV, Gam, Gx, Vt, Wct, Wmt, M1t, Mt, Dd and
+    // Dt, Jt, Kt, Ft (3 each): 21 N x N; six no x n, three nv x n, Z2; partials; scE, st
+    return 21 * nn + 6 * (size_t)no * nv + 6 * (size_t)no * n + 3 * nv * n + (size_t)no * no +
+           MAX_DOTS * DOT_BLOCKS + 16;
+}
+
+GvpWork gvp_work_layout(double *base, int n, int no) {
+    const size_t nn = (size_t)n * n, nv = (size_t)(n - no), non = (size_t)no * n, nvn = nv * n,
+                 nonv = (size_t)no * nv;
+    GvpWork v;
+    double *p = base;
+    v.gs = p; p += nonv;
+    v.gV = p; p += nn;
+    v.Gam = p; p += nn;
+    v.Gx = p; p += nn;
+    v.Vt = p; p += nn;
+    v.Wct = p; p += nn;
+    v.Wmt = p; p += nn;
+    v.Dt = p; p += 3 * nn;
+    v.Jt = p; p += 3 * nn;
+    v.Kt = p; p += 3 * nn;
+    v.Ft = p; p += 3 * nn;
+    v.M1t = p; p += nn;
+    v.Mt = p; p += nn;
+    v.Dd = p; p += nn;
+    v.X1 = p; p += non;
+    v.X2 = p; p += non;
+    v.X3 = p; p += non;
+    v.R1 = p; p += non;
+    v.R2 = p; p += non;
+    v.R3 = p; p += non;
+    v.X4 = p; p += nvn;
+    v.Rg1 = p; p += nvn;
+    v.Rg2 = p; p += nvn;
+    v.Z1a = p; p += nonv;
+    v.Z1b = p; p += nonv;
+    v.Z1c = p; p += nonv;
+    v.Z3 = p; p += nonv;
+    v.Hs = p; p += nonv;
+    v.Z2 = p; p += (size_t)no * no;
+    v.partial = p; p += MAX_DOTS * DOT_BLOCKS;
+    v.scE = p; p += 8;
+    v.st = p;
+    return v;
+}
+
+// After the first pass (v.gs, v.gV, v.scE hold dE/dsigma, dE/dV, {E, dE/dc0}):
+// the rotation gradient Gx = Gam - Gam^T (Gam = dE/dV V^T) and the tangent
+// densities of the direction (c0', sigma', V') = (dE/dc0, dE/dsigma, Gx V):
+//   W1' = sigma' Gamma + sigma Gamma', W2' = sigma'^T Theta + sigma^T Theta'
+//   P' = Theta'^T Theta + (.)^T, T' = Theta'^T W1 + Theta^T W1',
+//   A' = Wc'^T Wm + (.)^T   (Wc = [W1; W2], Wm = [W1; -W2])
+int launch_gvp_tangent_densities(int n, int no, const double *V, const double *sigma, const EnergyWork &w,
+                                 const GvpWork &v, cudaStream_t s) {
+    const int nv = n - no;
+    const size_t nn = (size_t)n * n, non = (size_t)no * n;
+    const double *Th = V, *Ga = V + non, *Tht = v.Vt, *Gat = v.Vt + non;
+    const GemmProblem a1[1] = {gp(false, true, n, n, n, 1.0, v.gV, n, V, n, 0.0, v.Gam, n)};
+    RET_IF(launch_group(a1, 1, s));
+    k_antisym<<<grid_for(nn), 256, 0, s>>>(n, v.Gam, v.Gx);
+    RET_IF(check("k_antisym"));
+    const GemmProblem a2[1] = {gp(false, false, n, n, n, 1.0, v.Gx, n, V, n, 0.0, v.Vt, n)};
+    RET_IF(launch_group(a2, 1, s));
+    const GemmProblem b0[4] = {
+        gp(false, false, no, n, nv, 1.0, v.gs, nv, Ga, n, 0.0, v.Wct, n),
+        gp(true, false, nv, n, no, 1.0, v.gs, nv, Th, n, 0.0, v.Wct + non, n),
+        gp(false, false, no, n, nv, 1.0, v.gs, nv, Ga, n, 0.0, v.Wmt, n),
+        gp(true, false, nv, n, no, -1.0, v.gs, nv, Th, n, 0.0, v.Wmt + non, n)};
+    RET_IF(launch_group(b0, 4, s));
+    const GemmProblem b1[4] = {
+        gp(false, false, no, n, nv, 1.0, sigma, nv, Gat, n, 1.0, v.Wct, n),
+        gp(true, false, nv, n, no, 1.0, sigma, nv, Tht, n, 1.0, v.Wct + non, n),
+        gp(false, false, no, n, nv, 1.0, sigma, nv, Gat, n, 1.0, v.Wmt, n),
+        gp(true, false, nv, n, no, -1.0, sigma, nv, Tht, n, 1.0, v.Wmt + non, n)};
+    RET_IF(launch_group(b1, 4, s));
+    const GemmProblem c0[3] = {
+        gp(true, false, n, n, no, 1.0, Tht, n, Th, n, 0.0, v.Dt, n),
+        gp(true, false, n, n, no, 1.0, Tht, n, w.Wc, n, 0.0, v.Dt + nn, n),
+        gp(true, false, n, n, n, 1.0, v.Wct, n, w.Wm, n, 0.0, v.Dt + 2 * nn, n)};
+    RET_IF(launch_group(c0, 3, s));
+    const GemmProblem c1[1] = {gp(true, false, n, n, no, 1.0, Th, n, v.Wct, n, 1.0, v.Dt + nn, n)};
+    RET_IF(launch_group(c1, 1, s));
+    k_symmetrize2<<<grid_for(nn), 256, 0, s>>>(n, v.Dt, v.Dt + 2 * nn);
+    return check("k_symmetrize2");
+}
+
+// Everything after the tangent build (v.Ft = [F_P', F_T', F_A']): tangent
+// scalars and the objective, the tangent of the gradient, the rotation part
+// of H g, dL/dx.
+int launch_gvp_finish(int n, int no, double c0, double omega, double mu, double chi, const double *G,
+                      const double *V, const double *sigma, const EnergyWork &w, const GvpWork &v,
+                      double *scalars, double *dLs, double *dLX, cudaStream_t s) {
+    const int nv = n - no;
+    const size_t nn = (size_t)n * n, non = (size_t)no * n, nonv = (size_t)no * nv;
+    const double *Th = V, *Ga = V + non, *Tht = v.Vt, *Gat = v.Vt + non;
+    const double *FT = w.F + nn, *FPt = v.Ft, *FTt = v.Ft + nn;
+    const double *W1 = w.Wc, *W2 = w.Wc + non, *W1t = v.Wct, *W2t = v.Wct + non;
+    // tangent inner products: s0' = F_P'.P + G.P' + Fk.P', s1' = F_P'.T + Fk.T',
+    // s2' = F_P'.A + Fk.A', s3' = F_T'.T + F_T.T', sigma.g_s, |g_s|^2, |Gx|^2
+    DotList L;
+    const double *xs[MAX_DOTS] = {FPt, G, w.Fk, FPt, w.Fk, FPt, w.Fk, FTt, FT, sigma, v.gs, v.Gx};
+    const double *ys[MAX_DOTS] = {w.D, v.Dt, v.Dt, w.D + nn, v.Dt + nn, w.D + 2 * nn, v.Dt + 2 * nn, w.D + nn,
+                                  v.Dt + nn, v.gs, v.gs, v.Gx};
+    for (int k = 0; k < MAX_DOTS; ++k) {
+        L.x[k] = xs[k];
+        L.y[k] = ys[k];
+        L.len[k] = (k == 9 || k == 10) ? nonv : nn;
+    }
+    L.count = MAX_DOTS;
+    k_dot_list<<<DOT_BLOCKS, 256, 0, s>>>(L, v.partial);
+    RET_IF(check("k_dot_list"));
+    k_gvp_scalars<<<1, 384, 0, s>>>(c0, omega, mu, chi, v.partial, w.sc, v.scE, scalars, v.st);
+    RET_IF(check("k_gvp_scalars"));
+    k_gvp_m1t<<<grid_for(nn), 256, 0, s>>>(n, c0, v.scE, w.F, v.Ft, v.M1t);
+    RET_IF(check("k_gvp_m1t"));
+    const GemmProblem t3[7] = {
+        gp(false, false, no, n, n, 1.0, Tht, n, w.Fk, n, 0.0, v.X1, n),
+        gp(false, false, no, n, n, 1.0, W1t, n, w.Fk, n, 0.0, v.X2, n),
+        gp(false, false, no, n, n, 1.0, Tht, n, FT, n, 0.0, v.X3, n),
+        gp(false, false, nv, n, n, 1.0, W2t, n, w.Fk, n, 0.0, v.X4, n),
+        gp(false, false, no, n, n, 1.0, Tht, n, w.M1, n, 0.0, v.R1, n),
+        gp(false, true, no, n, n, 1.0, W1t, n, FT, n, 0.0, v.R2, n),
+        gp(false, false, nv, n, n, 1.0, W2t, n, FT, n, 0.0, v.Rg2, n)};
+    RET_IF(launch_group(t3, 7, s));
+    const GemmProblem t4[7] = {
+        gp(false, false, no, n, n, 1.0, Th, n, FPt, n, 1.0, v.X1, n),
+        gp(false, false, no, n, n, 1.0, W1, n, FPt, n, 1.0, v.X2, n),
+        gp(false, false, no, n, n, 1.0, Th, n, FTt, n, 1.0, v.X3, n),
+        gp(false, false, nv, n, n, 1.0, W2, n, FPt, n, 1.0, v.X4, n),
+        gp(false, false, no, n, n, 1.0, Th, n, v.M1t, n, 1.0, v.R1, n),
+        gp(false, true, no, n, n, 1.0, W1, n, FTt, n, 1.0, v.R2, n),
+        gp(false, false, nv, n, n, 1.0, W2, n, FTt, n, 1.0, v.Rg2, n)};
+    RET_IF(launch_group(t4, 7, s));
+    const GemmProblem t5[6] = {
+        gp(false, true, no, nv, n, 1.0, v.X1, n, Ga, n, 0.0, v.Z1a, nv),
+        gp(false, true, no, nv, n, 1.0, v.X2, n, Ga, n, 0.0, v.Z1b, nv),
+        gp(false, true, no, nv, n, 1.0, v.X3, n, Ga, n, 0.0, v.Z1c, nv),
+        gp(false, true, no, no, n, 1.0, v.X1, n, Th, n, 0.0, v.Z2, no),
+        gp(false, false, no, n, nv, 1.0, v.gs, nv, w.X4, n, 0.0, v.R3, n),
+        gp(true, false, nv, n, no, 1.0, v.gs, nv, w.X2, n, 0.0, v.Rg1, n)};
+    RET_IF(launch_group(t5, 6, s));
+    const GemmProblem t6[6] = {
+        gp(false, true, no, nv, n, 1.0, w.X1, n, Gat, n, 1.0, v.Z1a, nv),
+        gp(false, true, no, nv, n, 1.0, w.X2, n, Gat, n, 1.0, v.Z1b, nv),
+        gp(false, true, no, nv, n, 1.0, w.X3, n, Gat, n, 1.0, v.Z1c, nv),
+        gp(false, true, no, no, n, 1.0, w.X1, n, Tht, n, 1.0, v.Z2, no),
+        gp(false, false, no, n, nv, 1.0, sigma, nv, v.X4, n, 1.0, v.R3, n),
+        gp(true, false, nv, n, no, 1.0, sigma, nv, v.X2, n, 1.0, v.Rg1, n)};
+    RET_IF(launch_group(t6, 6, s));
+    const GemmProblem t7[1] = {gp(false, false, no, nv, no, 1.0, v.Z2, no, sigma, nv, 0.0, v.Z3, nv)};
+    RET_IF(launch_group(t7, 1, s));
+    const GemmProblem t8[1] = {gp(false, false, no, nv, no, 1.0, w.Z2, no, v.gs, nv, 1.0, v.Z3, nv)};
+    RET_IF(launch_group(t8, 1, s));
+    const size_t tot = nonv + non + (size_t)nv * n;
+    k_gvp_tangent<<<grid_for(tot), 256, 0, s>>>(n, no, nv, c0, w, v, sigma);
+    RET_IF(check("k_gvp_tangent"));
+    // rotation part of H g: Dd = Mt V^T - (Gx Gam + Gam Gx) / 2
+    const GemmProblem d0[1] = {gp(false, true, n, n, n, 1.0, v.Mt, n, V, n, 0.0, v.Dd, n)};
+    RET_IF(launch_group(d0, 1, s));
+    const GemmProblem d1[1] = {gp(false, false, n, n, n, -0.5, v.Gx, n, v.Gam, n, 1.0, v.Dd, n)};
+    RET_IF(launch_group(d1, 1, s));
+    const GemmProblem d2[1] = {gp(false, false, n, n, n, -0.5, v.Gam, n, v.Gx, n, 1.0, v.Dd, n)};
+    RET_IF(launch_group(d2, 1, s));
+    k_gvp_out<<<grid_for(nonv + nn), 256, 0, s>>>(n, no, nv, v, dLs, dLX);
+    return check("k_gvp_out");
 }
 
 }  // namespace esmf

@@ -121,6 +121,26 @@ struct EnergyWork {
     double *Z1a, *Z1b, *Z1c, *Z3, *Z2;   // N_o x N_v (four), N_o x N_o
     double *partial, *sc;                // reduction partials; {E_HF, E, N2}
 };
+// GVP objective (second pass): the gradient kept internally and the tangent
+// (directional-derivative) copies of the energy intermediates
+struct GvpWork {
+    double *gs, *gV, *scE;               // dE/dsigma (N_o x N_v), dE/dV (N x N), {E, dE/dc0}
+    double *Gam, *Gx, *Vt, *Wct, *Wmt;   // N x N
+    double *Dt, *Jt, *Kt, *Ft;           // 3 x N x N each: P', T', A' and their J, K, F
+    double *M1t, *Mt, *Dd;               // N x N
+    double *X1, *X2, *X3, *R1, *R2, *R3; // tangents, N_o x N
+    double *X4, *Rg1, *Rg2;              // tangents, N_v x N
+    double *Z1a, *Z1b, *Z1c, *Z3, *Hs;   // N_o x N_v
+    double *Z2;                          // N_o x N_o
+    double *partial, *st;                // dot partials; tangent scalars
+};
+size_t gvp_work_doubles(int n, int no);
+GvpWork gvp_work_layout(double *base, int n, int no);
+int launch_gvp_tangent_densities(int n, int no, const double *V, const double *sigma, const EnergyWork &w,
+                                 const GvpWork &v, cudaStream_t s);
+int launch_gvp_finish(int n, int no, double c0, double omega, double mu, double chi, const double *G,
+                      const double *V, const double *sigma, const EnergyWork &w, const GvpWork &v,
+                      double *scalars, double *dLs, double *dLX, cudaStream_t s);
 size_t energy_work_doubles(int n, int no);
 EnergyWork energy_work_layout(double *base, int n, int no);
 int launch_energy_densities(int n, int no, const double *V, const double *sigma, const EnergyWork &w,

@@ -34,7 +34,7 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_autotune"]
 PATHS = {"auto": 0, "cuda_core": 1}
 # declared in include/esmf_energy.h
-ENERGY_EXPORTS = ["esmf_energy_gradient"]
+ENERGY_EXPORTS = ["esmf_energy_gradient", "esmf_gvp_gradient"]
 # declared in include/esmf_server.h, bound in server.py
 SERVER_EXPORTS = ["esmf_server_create", "esmf_server_register", "esmf_server_submit",
                   "esmf_server_wait", "esmf_server_stats", "esmf_server_reset_stats",
@@ -107,6 +107,9 @@ def load(path=None):
         L.esmf_fock_kernel_time.restype = C.c_int
         L.esmf_energy_gradient.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, vp, vp, vp]
         L.esmf_energy_gradient.restype = C.c_int
+        L.esmf_gvp_gradient.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, C.c_double, C.c_double,
+                                        C.c_double, vp, vp, vp, vp]
+        L.esmf_gvp_gradient.restype = C.c_int
         L.esmf_fock_destroy.argtypes = [vp]
         L.esmf_fock_destroy.restype = None
         L.esmf_strerror.argtypes = [C.c_int]
@@ -164,6 +167,13 @@ def esmf_energy_gradient(h, n_occ, c0, G, V, sigma, scalars, dE_dsigma=None, dE_
     rc = load().esmf_energy_gradient(h, int(n_occ), float(c0), _ptr(G), _ptr(V), _ptr(sigma), _ptr(scalars),
                                      _ptr(dE_dsigma), _ptr(dE_dV), _stream_ptr(stream))
     _check(rc, "esmf_energy_gradient")
+
+
+def esmf_gvp_gradient(h, n_occ, c0, G, V, sigma, omega, mu, chi, scalars, dL_dsigma, dL_dX, stream=None):
+    rc = load().esmf_gvp_gradient(h, int(n_occ), float(c0), _ptr(G), _ptr(V), _ptr(sigma), float(omega),
+                                  float(mu), float(chi), _ptr(scalars), _ptr(dL_dsigma), _ptr(dL_dX),
+                                  _stream_ptr(stream))
+    _check(rc, "esmf_gvp_gradient")
 
 
 def esmf_fock_build_noalloc(h, m, D, J, K, F=None, traces=None, stream=None):
@@ -312,6 +322,21 @@ class FockBuilder:
         dV = torch.empty_like(V) if gradient else None
         esmf_energy_gradient(self.h, n_occ, c0, G, V, sigma, scalars, ds, dV, stream)
         return scalars, ds, dV
+
+    def gvp_gradient(self, G, V, sigma, c0, n_occ, omega, mu, chi, stream=None):
+        """GVP objective and derivatives (esmf_gvp_gradient).  Returns device
+        tensors (scalars = [L, E, |grad E|^2, dL/dc0], dL_dsigma, dL_dX)."""
+        import torch
+        n = self.n
+        for name, t, shape in (("G", G, (n, n)), ("V", V, (n, n)), ("sigma", sigma, (n_occ, n - n_occ))):
+            if t.dtype != torch.float64 or not t.is_cuda or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be a CUDA float64 tensor of shape {shape}")
+        G, V, sigma = G.contiguous(), V.contiguous(), sigma.contiguous()
+        scalars = torch.empty(4, dtype=torch.float64, device=G.device)
+        ds = torch.empty_like(sigma)
+        dX = torch.empty_like(V)
+        esmf_gvp_gradient(self.h, n_occ, c0, G, V, sigma, omega, mu, chi, scalars, ds, dX, stream)
+        return scalars, ds, dX
 
     def build_host(self, D, J=None, K=None, traces=None, stream=None, timeout_ms=0):
         m = D.shape[0]

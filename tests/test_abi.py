@@ -56,6 +56,8 @@ def test_strerror_and_host_side_argument_errors(lib):
     assert lib.esmf_fock_build(None, 1, None, None, None, None, None, None) == fock.ESMF_ERR_INVALID_ARG
     assert lib.esmf_energy_gradient(None, 1, 1.0, None, None, None, None, None, None, None) == \
         fock.ESMF_ERR_INVALID_ARG
+    assert lib.esmf_gvp_gradient(None, 1, 1.0, None, None, None, 0.0, 0.5, 1.0, None, None, None, None) == \
+        fock.ESMF_ERR_INVALID_ARG
     st = fock.esmf_stats_t()
     assert lib.esmf_fock_stats(None, C.byref(st)) == fock.ESMF_ERR_INVALID_ARG
     lib.esmf_fock_destroy(None)

@@ -11,7 +11,8 @@ Tolerances: FP64 builds 1e-10 relative; FP32 and split-FP16 builds 2e-6 on E
 (the J/K bound, since E is a sum of F . D inner products with little
 cancellation) and 1e-5 relative Frobenius on the gradients, whose terms cancel
 (dE/dsigma is a difference of O(1) matrices that nearly vanishes near a
-stationary point).
+stationary point); 5e-6 on the GVP objective and its derivatives, which add
+a second pass of builds (the Hessian-vector product) to the same errors.
 """
 import numpy as np
 import pytest
@@ -156,3 +157,66 @@ def test_invalid_arguments(esmf, small):
             esmf.esmf_energy_gradient(fb.h, st.nocc, 1.0, G.cpu(), V, s, sc)
         with pytest.raises(esmf.EsmfError):      # only one of the two gradient outputs
             esmf.esmf_energy_gradient(fb.h, st.nocc, 1.0, G, V, s, sc, s.clone(), None)
+
+
+# ------------------------------------------------------------------ GVP objective
+def gpu_gvp(esmf, fb, st, om, mu, chi):
+    import torch
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    sc, ds, dX = fb.gvp_gradient(t(st.G), t(st.V), t(st.sigma), st.c0, st.nocc, om, mu, chi)
+    torch.cuda.synchronize()
+    return sc.cpu().numpy(), ds.cpu().numpy(), dX.cpu().numpy()
+
+
+GVP = (-3.0, 0.4, 0.8)      # omega, mu, chi
+
+
+@pytest.mark.parametrize("mode,prec,tol", [("stored", "fp64", 1e-10), ("stored", "fp16x2", 5e-6)])
+def test_gvp_matches_oracle(esmf, small, mode, prec, tol):
+    """L, E, |grad E|^2 and dL/d(c0, sigma, X) (two passes, Hessian-vector
+    product) against the oracle with its own J/K."""
+    w, st, _ = small
+    o = Oracle(w.basis)
+    jk = lambda D: o.jk_unique(D, w.tol)[:2]
+    L, E, gn2, dLc, dLs, dLX = EE.gvp_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc, *GVP)
+    with esmf.FockBuilder(w.basis, w.tol, mode, prec) as fb:
+        sc, dsg, dXg = gpu_gvp(esmf, fb, st, *GVP)
+    errs = (abs(sc[0] - L) / abs(L), abs(sc[1] - E) / abs(E), abs(sc[2] - gn2) / gn2,
+            abs(sc[3] - dLc) / max(abs(dLc), 1e-12), rel(dsg, dLs), rel(dXg, dLX))
+    print(f"\nGVP {w.name} {mode}/{prec}: L {errs[0]:.2e} E {errs[1]:.2e} |gE|^2 {errs[2]:.2e} "
+          f"dL/dc0 {errs[3]:.2e} dL/dsigma {errs[4]:.2e} dL/dX {errs[5]:.2e}")
+    assert max(errs) <= tol
+    np.testing.assert_allclose(dXg, -dXg.T, atol=1e-12 * np.max(np.abs(dXg)))
+
+
+def test_gvp_full_size(esmf, full):
+    """200 functions: GPU GVP derivatives against the oracle's assembly over the
+    library's FP64 J/K, the split-FP16 build against FP64, and the c0 and sigma
+    derivatives against Richardson-extrapolated differences of the GPU L."""
+    import torch
+    w, st = full
+    with esmf.FockBuilder(w.basis, w.tol, "stored", "fp64") as fb:
+        def jk(D):
+            J, K, _, _ = fb.build(torch.from_numpy(np.ascontiguousarray(D)).cuda(), want_traces=False)
+            return J.cpu().numpy(), K.cpu().numpy()
+        L, E, gn2, dLc, dLs, dLX = EE.gvp_gradient(jk, st.G, st.V, st.sigma, st.c0, st.nocc, *GVP)
+        sc, dsg, dXg = gpu_gvp(esmf, fb, st, *GVP)
+        assert abs(sc[0] - L) <= 1e-10 * abs(L) and abs(sc[3] - dLc) <= 1e-10 * max(abs(dLc), 1.0)
+        assert rel(dsg, dLs) <= 1e-10 and rel(dXg, dLX) <= 1e-10
+        Lof = lambda c0=st.c0, s=st.sigma: gpu_gvp(esmf, fb, W.EsmfState(st.G, st.V, s, c0, st.nocc), *GVP)[0][0]
+        h = 2e-3
+
+        def deriv(f):
+            c = lambda t: (f(t) - f(-t)) / (2 * t)
+            return (4.0 * c(h / 2) - c(h)) / 3.0
+
+        assert deriv(lambda t: Lof(c0=st.c0 + t)) == pytest.approx(sc[3], rel=1e-6, abs=1e-6)
+        d = np.random.default_rng(4).standard_normal(st.sigma.shape)
+        d /= np.linalg.norm(d)
+        assert deriv(lambda t: Lof(s=st.sigma + t * d)) == pytest.approx(np.sum(dsg * d), rel=1e-6, abs=1e-6)
+    with esmf.FockBuilder(w.basis, w.tol, "stored", "fp16x2") as fb:
+        sch, dsh, dXh = gpu_gvp(esmf, fb, st, *GVP)
+    errs = (abs(sch[0] - L) / abs(L), abs(sch[3] - dLc) / max(abs(dLc), 1e-12), rel(dsh, dLs), rel(dXh, dLX))
+    print(f"\nGVP stored_n200 stored/fp16x2 vs FP64: L {errs[0]:.2e} dL/dc0 {errs[1]:.2e} "
+          f"dL/dsigma {errs[2]:.2e} dL/dX {errs[3]:.2e}")
+    assert max(errs) <= 5e-6
