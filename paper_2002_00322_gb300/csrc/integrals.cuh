@@ -89,7 +89,8 @@ __device__ __forceinline__ T contracted_eri(const PairSmem<T, NPAIR, MAXPP_> &br
 }
 
 // Fill pair data for the 64 ordered pairs (p, q) of function blocks (PB, QB)
-// with local origin (ox, oy, oz).  Called by all threads of a block.
+// with local origin (ox, oy, oz), leaving out primitive pairs too small to
+// matter (below).  Called by all threads of a block.
 template <typename T, int MAXPP_>
 __device__ __forceinline__ void fill_pairs(PairSmem<T, 128, MAXPP_> &ps, int base, int PB, int QB,
                                            const double *center, const int *nprim, const int *poff,
@@ -104,16 +105,36 @@ __device__ __forceinline__ void fill_pairs(PairSmem<T, 128, MAXPP_> &ps, int bas
             const double ax = center[3 * p], ay = center[3 * p + 1], az = center[3 * p + 2];
             const double bx = center[3 * q], by = center[3 * q + 1], bz = center[3 * q + 2];
             const double ab2 = (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
+            double kws[MAXPP_];
+            float size[MAXPP_], smax = 0.0f;
             for (int i = 0; i < np_; ++i)
                 for (int j = 0; j < nq_; ++j) {
+                    const int k = i * nq_ + j;
                     const double a = exps[poff[p] + i], b = exps[poff[q] + j];
                     const double pe = a + b;
-                    const double kw = w[poff[p] + i] * w[poff[q] + j] * exp(-a * b / pe * ab2);
+                    kws[k] = w[poff[p] + i] * w[poff[q] + j] * exp(-a * b / pe * ab2) / pe;
+                    size[k] = fabsf((float)kws[k]) * rsqrtf((float)pe);
+                    smax = fmaxf(smax, size[k]);
+                }
+            // Primitive-pair screening: a pair whose weight K/p times p^(-1/2)
+            // (its contribution to any integral, up to the ket factors) is
+            // below eps of the largest pair of this function pair is left
+            // out; the relative change of an integral stays below about
+            // 1e4 eps (the ratio of Boys-function and prefactor extremes),
+            // under the precision of T (FP32: 1e-12; FP64 drops only
+            // underflowing pairs).
+            const float eps = sizeof(T) == 4 ? 1e-12f : 1e-30f;
+            for (int i = 0; i < np_; ++i)
+                for (int j = 0; j < nq_; ++j) {
+                    const int k = i * nq_ + j;
+                    if (!(size[k] >= eps * smax)) continue;
+                    const double a = exps[poff[p] + i], b = exps[poff[q] + j];
+                    const double pe = a + b;
                     ps.pe[slot][cnt] = (T)pe;
                     ps.px[slot][cnt] = (T)((a * ax + b * bx) / pe - ox);
                     ps.py[slot][cnt] = (T)((a * ay + b * by) / pe - oy);
                     ps.pz[slot][cnt] = (T)((a * az + b * bz) / pe - oz);
-                    ps.kw[slot][cnt] = (T)(kw / pe);
+                    ps.kw[slot][cnt] = (T)kws[k];
                     ++cnt;
                 }
         }
