@@ -167,6 +167,33 @@ int oracle_schwarz(int n, const double *center, const int32_t *nprim,
     return 0;
 }
 
+/*
+ * Pair screening as Sec. II.C states it: for every index pair (p, q) the
+ * largest |(pq|rs)| over all pairs (r, s); a pair is discarded when that
+ * maximum is at most the threshold.  Brute force over the unique quartets
+ * (pq >= rs), each updating both of its pairs.  out[p N + q] = out[q N + p].
+ */
+int oracle_pair_max(int n, const double *center, const int32_t *nprim,
+                    const double *exps, const double *w, double *out)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    for (int64_t i = 0; i < (int64_t)n * n; ++i) out[i] = 0.0;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q <= p; ++q)
+            for (int r = 0; r <= p; ++r)
+                for (int s = 0; s <= r; ++s) {
+                    if (r == p && s > q) continue;          /* pair(rs) <= pair(pq) */
+                    const double v = fabs(eri_c(&b, p, q, r, s));
+                    double *a1 = out + (int64_t)p * n + q, *a2 = out + (int64_t)r * n + s;
+                    if (v > *a1) *a1 = v;
+                    if (v > *a2) *a2 = v;
+                }
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < p; ++q) out[(int64_t)q * n + p] = out[(int64_t)p * n + q];
+    free(b.off);
+    return 0;
+}
+
 static int kept(const double *Q, int n, int p, int q, int r, int s, double tol)
 {
     return Q[(int64_t)p * n + q] * Q[(int64_t)r * n + s] >= tol;

@@ -61,6 +61,7 @@ def lib():
             L.oracle_jk_elements.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double, C.c_int,
                                              dp, C.c_int, ip, dp, C.c_int, ip, dp]
             L.oracle_fock_traces.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp]
+            L.oracle_pair_max.argtypes = [C.c_int, dp, ip, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -107,6 +108,18 @@ class Oracle:
             self._Q = Q
         return self._Q
 
+    def pair_max(self):
+        """max over (r, s) of |(pq|rs)| for every pair (Sec. II.C pair screening), N x N."""
+        out = np.zeros((self.n, self.n))
+        lib().oracle_pair_max(*self._b(), _d(out))
+        return out
+
+    def pair_mask_table(self, thr):
+        """Screening table of the paper's pair rule: 1 where max_rs |(pq|rs)| > thr,
+        else 0; with tol 0.5 the quartet rule Q_pq Q_rs >= tol then keeps exactly
+        the quartets of two surviving pairs."""
+        return (self.pair_max() > thr).astype(np.float64)
+
     def jk_brute(self, eri, D, tol):
         D = np.ascontiguousarray(D, dtype=np.float64)
         m = D.shape[0]
@@ -116,8 +129,10 @@ class Oracle:
         lib().oracle_jk_brute(self.n, _d(eri), _d(self.Q), tol, m, _d(D), _d(J), _d(K))
         return J, K
 
-    def jk_unique(self, D, tol, pair_range=None, eri_list=None):
+    def jk_unique(self, D, tol, pair_range=None, eri_list=None, Q=None):
+        """Q: screening table (default the Schwarz table)."""
         D = np.ascontiguousarray(D, dtype=np.float64)
+        Qt = np.ascontiguousarray(self.Q if Q is None else Q, dtype=np.float64)
         m = D.shape[0]
         J = np.zeros_like(D)
         K = np.zeros_like(D)
@@ -127,7 +142,7 @@ class Oracle:
         if eri_list is not None:
             eri_list = np.ascontiguousarray(eri_list, dtype=np.float64)
             el = _d(eri_list)
-        nk = lib().oracle_jk_unique(*self._b(), _d(self.Q), tol, m, _d(D), _d(J), _d(K),
+        nk = lib().oracle_jk_unique(*self._b(), _d(Qt), tol, m, _d(D), _d(J), _d(K),
                                      b, e, el)
         return J, K, int(nk)
 
@@ -137,8 +152,9 @@ class Oracle:
                                        pair_range[1], _d(out), cap)
         return out[:min(cnt, cap)], int(cnt)
 
-    def count_kept(self, tol):
-        return int(lib().oracle_count_kept(self.n, _d(self.Q), tol))
+    def count_kept(self, tol, Q=None):
+        Qt = np.ascontiguousarray(self.Q if Q is None else Q, dtype=np.float64)
+        return int(lib().oracle_count_kept(self.n, _d(Qt), tol))
 
     def jk_elements(self, D, tol, jidx, kidx):
         D = np.ascontiguousarray(D, dtype=np.float64)
