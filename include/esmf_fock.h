@@ -92,6 +92,8 @@ typedef struct {
     int32_t precision;          /* ESMF_PREC_*                                 */
     double  schwarz_tol;
     double  create_ms;          /* wall time of esmf_fock_create               */
+    int32_t screening;          /* ESMF_SCREEN_*                               */
+    int64_t n_pairs_kept;       /* pairs in at least one kept quartet          */
 } esmf_stats_t;
 
 /*
@@ -113,6 +115,29 @@ typedef struct {
 int esmf_fock_create(const esmf_basis_t *basis, double schwarz_tol, int mode,
                      int precision, int device, int64_t budget_bytes,
                      esmf_fock_t **out);
+
+/*
+ * esmf_fock_create_screened -- esmf_fock_create with a choice of screening
+ * rule (esmf_fock_create uses ESMF_SCREEN_SCHWARZ):
+ *   ESMF_SCREEN_SCHWARZ   quartet (pq|rs) kept iff Q_pq Q_rs >= tol (the
+ *                         Cauchy-Schwarz bound of the integral)
+ *   ESMF_SCREEN_PAIR_MAX  the pair rule as Sec. II.C states it: pair (p, q)
+ *                         is discarded when max_rs |(pq|rs)| <= tol (the
+ *                         paper uses 1e-9), and every quartet of two
+ *                         surviving pairs is kept.  The maximum is decided in
+ *                         FP64 at create time (one warp per pair, searching
+ *                         the pairs in descending Q order and stopping at
+ *                         the first integral above tol or the first Schwarz
+ *                         bound at or below it).
+ * Other arguments, outputs and errors as esmf_fock_create (INVALID_ARG also
+ * for an unknown screening value).  esmf_fock_schwarz still returns Q, and
+ * the split-16-bit store scale is still chosen from max Q^2.
+ */
+#define ESMF_SCREEN_SCHWARZ   0
+#define ESMF_SCREEN_PAIR_MAX  1
+int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screening,
+                              int mode, int precision, int device,
+                              int64_t budget_bytes, esmf_fock_t **out);
 
 /*
  * esmf_fock_build -- one grouped pass over the (stored or recomputed)

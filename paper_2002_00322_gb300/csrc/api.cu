@@ -40,6 +40,13 @@ struct esmf_fock {
     double *center = nullptr, *exps = nullptr, *w = nullptr, *coefs = nullptr;
     int *nprim = nullptr, *poff = nullptr;
     double *Q = nullptr;
+    // screening table and threshold of the quartet rule S_pq S_rs >= tol_s:
+    // the Schwarz table itself (S = Q, tol_s = tol), or the 0/1 table of the
+    // paper's pair rule (tol_s = 0.5)
+    double *S = nullptr;
+    double tol_s = 0.0;
+    int screening = ESMF_SCREEN_SCHWARZ;
+    int64_t n_pairs_kept = 0;
     // bricks and store (device)
     BrickDesc *bricks = nullptr;
     int64_t nbricks = 0;
@@ -181,7 +188,9 @@ std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
 void release(esmf_fock *h) {
     if (!h) return;
     cudaFree(h->center); cudaFree(h->exps); cudaFree(h->w); cudaFree(h->coefs);
-    cudaFree(h->nprim); cudaFree(h->poff); cudaFree(h->Q);
+    cudaFree(h->nprim); cudaFree(h->poff);
+    if (h->S != h->Q) cudaFree(h->S);
+    cudaFree(h->Q);
     cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts);
     cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
     if (h->err_host) cudaFreeHost(h->err_host);
@@ -248,8 +257,17 @@ const char *esmf_last_error(void) { return g_err; }
 
 int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precision, int device,
                      int64_t budget_bytes, esmf_fock_t **out) {
+    return esmf_fock_create_screened(basis, tol, ESMF_SCREEN_SCHWARZ, mode, precision, device, budget_bytes, out);
+}
+
+int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screening, int mode, int precision,
+                              int device, int64_t budget_bytes, esmf_fock_t **out) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!out) { set_error("out is NULL"); return ESMF_ERR_INVALID_ARG; }
+    if (screening != ESMF_SCREEN_SCHWARZ && screening != ESMF_SCREEN_PAIR_MAX) {
+        set_error("bad screening %d", screening);
+        return ESMF_ERR_INVALID_ARG;
+    }
     *out = nullptr;
     if (!basis || basis->n_basis <= 0 || !basis->center || !basis->n_prim || !basis->exps ||
         !basis->coefs) {
@@ -303,7 +321,7 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
 
     esmf_fock *h = new (std::nothrow) esmf_fock();
     if (!h) { set_error("host allocation failed"); return ESMF_ERR_OOM; }
-    h->device = device; h->n = n; h->tol = tol; h->prec = precision;
+    h->device = device; h->n = n; h->tol = tol; h->prec = precision; h->screening = screening;
     h->nb = (n + BLK - 1) / BLK;
     h->np = h->nb * BLK;
     const int np = h->np;
@@ -351,8 +369,50 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     const DevBasis db = h->dev();
     if ((rc = launch_normalize(db, h->coefs, h->w, s)) || (rc = launch_schwarz(db, h->Q, s))) return fail(rc);
     std::vector<double> hQ((size_t)np * np);
-    if (!ck(cudaMemcpyAsync(hQ.data(), h->Q, sizeof(double) * np * np, cudaMemcpyDeviceToHost, cs), "copy Q"))
+    if (!ck(cudaMemcpyAsync(hQ.data(), h->Q, sizeof(double) * np * np, cudaMemcpyDeviceToHost, cs), "copy Q") ||
+        !ck(cudaStreamSynchronize(cs), "Schwarz table"))
         return fail(ESMF_ERR_CUDA);
+    // the screening table: Schwarz (S = Q, keep Q_pq Q_rs >= tol), or the pair
+    // rule (S_pq = 1 iff max_rs |(pq|rs)| > tol, keep S_pq S_rs >= 0.5)
+    std::vector<double> hS;
+    if (screening == ESMF_SCREEN_SCHWARZ) {
+        h->S = h->Q;
+        h->tol_s = tol;
+        // pairs that take part in at least one kept quartet: Q_pq max Q >= tol
+        double qmax = 0.0;
+        for (double x : hQ) qmax = std::max(qmax, x);
+        int64_t cnt = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q <= p; ++q) cnt += hQ[(size_t)p * np + q] * qmax >= tol ? 1 : 0;
+        h->n_pairs_kept = cnt;
+    } else {
+        std::vector<int2> order;
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q <= p; ++q) order.push_back(make_int2(p, q));
+        std::stable_sort(order.begin(), order.end(), [&](const int2 &x, const int2 &y) {
+            return hQ[(size_t)x.x * np + x.y] > hQ[(size_t)y.x * np + y.y];
+        });
+        int2 *dorder = nullptr;
+        if ((rc = dalloc(h, &h->S, (size_t)np * np)) || (rc = dalloc(h, &dorder, order.size()))) {
+            dfree(h, &dorder, order.size());
+            return fail(rc);
+        }
+        bool ok = ck(cudaMemcpyAsync(dorder, order.data(), sizeof(int2) * order.size(), cudaMemcpyHostToDevice, cs),
+                     "copy pair order");
+        if (ok) ok = (rc = launch_pair_rule(db, h->Q, tol, dorder, (int64_t)order.size(), h->S, s)) == ESMF_OK;
+        hS.resize((size_t)np * np);
+        if (ok) ok = ck(cudaMemcpyAsync(hS.data(), h->S, sizeof(double) * np * np, cudaMemcpyDeviceToHost, cs), "copy S");
+        if (ok) ok = ck(cudaStreamSynchronize(cs), "pair rule");
+        dfree(h, &dorder, order.size());
+        if (!ok) return fail(rc ? rc : ESMF_ERR_CUDA);
+        h->tol_s = 0.5;
+        int64_t cnt = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q <= p; ++q) cnt += hS[(size_t)p * np + q] > 0.5 ? 1 : 0;
+        h->n_pairs_kept = cnt;
+    }
+    const std::vector<double> &hScr = screening == ESMF_SCREEN_SCHWARZ ? hQ : hS;
+    const double tol_s = h->tol_s;
 
     // block-level screening: Qblk = max over the 8x8 block; brick kept iff
     // Qblk(PQ) * Qblk(RS) >= tol (element-level screening inside the brick)
@@ -361,7 +421,7 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     for (int p = 0; p < np; ++p)
         for (int q = 0; q < np; ++q) {
             double &m_ = qblk[(size_t)(p / BLK) * nb + q / BLK];
-            m_ = std::max(m_, hQ[(size_t)p * np + q]);
+            m_ = std::max(m_, hScr[(size_t)p * np + q]);
         }
     std::vector<std::pair<int, int>> bp;
     std::vector<double> bq;
@@ -370,7 +430,7 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
     std::vector<BrickDesc> cand;
     for (size_t i = 0; i < bp.size(); ++i)
         for (size_t j = 0; j <= i; ++j)
-            if (bq[i] * bq[j] >= tol) {
+            if (bq[i] * bq[j] >= tol_s) {
                 BrickDesc d;
                 d.P = (int16_t)bp[i].first; d.Q = (int16_t)bp[i].second;
                 d.R = (int16_t)bp[j].first; d.S = (int16_t)bp[j].second;
@@ -388,7 +448,7 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
         }
         counts.resize(2 * ncand);
         bool ok = ck(cudaMemcpyAsync(dc, cand.data(), sizeof(BrickDesc) * ncand, cudaMemcpyHostToDevice, cs), "copy bricks");
-        if (ok) ok = (rc = launch_brick_count(db, h->Q, tol, dc, ncand, dcount, s)) == ESMF_OK;
+        if (ok) ok = (rc = launch_brick_count(db, h->S, tol_s, dc, ncand, dcount, s)) == ESMF_OK;
         if (ok) ok = ck(cudaMemcpyAsync(counts.data(), dcount, sizeof(int32_t) * 2 * ncand, cudaMemcpyDeviceToHost, cs), "copy counts");
         dfree(h, &dc, ncand);
         dfree(h, &dcount, 2 * ncand);
@@ -490,7 +550,7 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
             if (!ck(cudaMemcpyAsync(h->offsets, offs.data(), sizeof(int64_t) * (h->nbricks + 1), cudaMemcpyHostToDevice, cs), "copy offsets"))
                 return fail(ESMF_ERR_CUDA);
             if (!ck(cudaMemsetAsync(h->store, 0, (size_t)h->store_bytes, cs), "clear store")) return fail(ESMF_ERR_CUDA);
-            if ((rc = launch_brick_generate(db, h->Q, tol, h->bricks, h->nbricks, h->offsets, h->prec,
+            if ((rc = launch_brick_generate(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec,
                                             h->store, h->vscale, s)))
                 return fail(rc);
         }
@@ -533,7 +593,7 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
     if (traces) CKR(cudaMemsetAsync(traces, 0, sizeof(double) * m, s));
     if (b1 > b0) {
         JKArgs a;
-        a.b = h->dev(); a.Q = h->Q; a.tol = h->tol; a.bricks = h->bricks + b0; a.nbricks = b1 - b0;
+        a.b = h->dev(); a.Q = h->S; a.tol = h->tol_s; a.bricks = h->bricks + b0; a.nbricks = b1 - b0;
         a.offsets = h->offsets ? h->offsets + b0 : nullptr; a.store = h->store; a.precision = h->prec;
         a.mode = h->mode;
         a.m = m; a.D = D; a.Jacc = h->Jacc; a.Kacc = h->Kacc;
@@ -829,6 +889,8 @@ int esmf_fock_stats(const esmf_fock_t *h, esmf_stats_t *out) {
     out->precision = h->prec;
     out->schwarz_tol = h->tol;
     out->create_ms = h->create_ms;
+    out->screening = h->screening;
+    out->n_pairs_kept = h->n_pairs_kept;
     return ESMF_OK;
 }
 
@@ -855,7 +917,7 @@ namespace esmf {
 // touching its work memory (the caller supplies the accumulators).
 int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, int *device,
                            bool *split) {
-    a->b = h->dev(); a->Q = h->Q; a->tol = h->tol; a->bricks = h->bricks; a->nbricks = h->nbricks;
+    a->b = h->dev(); a->Q = h->S; a->tol = h->tol_s; a->bricks = h->bricks; a->nbricks = h->nbricks;
     a->offsets = h->offsets; a->store = h->store; a->precision = h->prec; a->mode = h->mode;
     a->m = m; a->D = D; a->Jacc = nullptr; a->Kacc = nullptr;
     a->vscale = h->vscale;

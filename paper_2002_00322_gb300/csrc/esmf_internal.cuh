@@ -58,6 +58,9 @@ void set_error(const char *fmt, ...);
 // ---- setup.cu
 int launch_normalize(const DevBasis &b, const double *coefs, double *w, cudaStream_t s);
 int launch_schwarz(const DevBasis &b, double *Q, cudaStream_t s);
+// pair rule of Sec. II.C into a 0/1 screening table S (np x np)
+int launch_pair_rule(const DevBasis &b, const double *Q, double thr, const int2 *order, int64_t npairs, double *S,
+                     cudaStream_t s);
 int launch_brick_count(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                        int64_t nbricks, int32_t *counts, cudaStream_t s);
 int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,

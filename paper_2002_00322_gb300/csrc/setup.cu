@@ -102,6 +102,79 @@ __global__ void k_schwarz(DevBasis b, double *Q) {
     }
 }
 
+// ---------------------------------------------------------------- pair rule
+// Contracted (pq|rs) in FP64 from the basis arrays (all primitive products).
+__device__ double eri_fp64(const DevBasis &b, int p, int q, int r, int s) {
+    double v = 0.0;
+    const double ax = b.center[3 * p], ay = b.center[3 * p + 1], az = b.center[3 * p + 2];
+    const double bx = b.center[3 * q], by = b.center[3 * q + 1], bz = b.center[3 * q + 2];
+    const double cx = b.center[3 * r], cy = b.center[3 * r + 1], cz = b.center[3 * r + 2];
+    const double dx = b.center[3 * s], dy = b.center[3 * s + 1], dz = b.center[3 * s + 2];
+    const double ab2 = (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
+    const double cd2 = (cx - dx) * (cx - dx) + (cy - dy) * (cy - dy) + (cz - dz) * (cz - dz);
+    for (int i = 0; i < b.nprim[p]; ++i)
+        for (int j = 0; j < b.nprim[q]; ++j) {
+            const double a1 = b.exps[b.poff[p] + i], a2 = b.exps[b.poff[q] + j], e1 = a1 + a2;
+            const double k1 = b.w[b.poff[p] + i] * b.w[b.poff[q] + j] * exp(-a1 * a2 / e1 * ab2);
+            const double Px = (a1 * ax + a2 * bx) / e1, Py = (a1 * ay + a2 * by) / e1, Pz = (a1 * az + a2 * bz) / e1;
+            for (int k = 0; k < b.nprim[r]; ++k)
+                for (int l = 0; l < b.nprim[s]; ++l) {
+                    const double a3 = b.exps[b.poff[r] + k], a4 = b.exps[b.poff[s] + l], e2 = a3 + a4;
+                    const double k2 = b.w[b.poff[r] + k] * b.w[b.poff[s] + l] * exp(-a3 * a4 / e2 * cd2);
+                    const double Qx = (a3 * cx + a4 * dx) / e2, Qy = (a3 * cy + a4 * dy) / e2,
+                                 Qz = (a3 * cz + a4 * dz) / e2;
+                    const double R2 = (Px - Qx) * (Px - Qx) + (Py - Qy) * (Py - Qy) + (Pz - Qz) * (Pz - Qz);
+                    v += k1 * k2 * kTwoPi52 / (e1 * e2 * sqrt(e1 + e2)) * boys0_d(e1 * e2 / (e1 + e2) * R2);
+                }
+        }
+    return v;
+}
+
+// The pair rule of Sec. II.C: pair (p, q) survives iff some (r, s) has
+// |(pq|rs)| > thr.  One warp per pair.  (pq|pq) = Q_pq^2 decides at once;
+// otherwise the candidates (r, s) are visited in descending Q order, 32 at a
+// time, and since |(pq|rs)| <= Q_pq Q_rs the search ends at the first
+// candidate whose bound is <= thr (no later one can exceed thr) or at the
+// first integral above thr.  S[p][q] = S[q][p] = 1 for survivors (S zeroed
+// by the caller); FP64 throughout, like the oracle's decision.
+__global__ void k_pair_rule(DevBasis b, const double *Q, double thr, const int2 *order, int64_t npairs,
+                            double *S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = wid; t < npairs; t += nw) {
+        const int2 pq = order[t];
+        const int p = pq.x, q = pq.y;
+        const double qpq = Q[(int64_t)p * b.np + q];
+        bool keep = qpq * qpq > thr;
+        for (int64_t base = 0; !keep && base < npairs; base += 32) {
+            const int64_t i = base + lane;
+            double v = 0.0;
+            bool live = false;
+            if (i < npairs) {
+                const int2 rs = order[i];
+                live = qpq * Q[(int64_t)rs.x * b.np + rs.y] > thr;
+                if (live) v = fabs(eri_fp64(b, p, q, rs.x, rs.y));
+            }
+            if (__any_sync(0xffffffffu, v > thr)) keep = true;
+            else if (!__all_sync(0xffffffffu, live)) break;
+        }
+        if (lane == 0 && keep) {
+            S[(int64_t)p * b.np + q] = 1.0;
+            S[(int64_t)q * b.np + p] = 1.0;
+        }
+    }
+}
+
+int launch_pair_rule(const DevBasis &b, const double *Q, double thr, const int2 *order, int64_t npairs, double *S,
+                     cudaStream_t s) {
+    CK(cudaMemsetAsync(S, 0, sizeof(double) * (size_t)b.np * b.np, s));
+    if (npairs == 0) return ESMF_OK;
+    k_pair_rule<<<grid_for(npairs * 32, 256, 152 * 8), 256, 0, s>>>(b, Q, thr, order, npairs, S);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
 int launch_schwarz(const DevBasis &b, double *Q, cudaStream_t s) {
     const int64_t npair = (int64_t)b.np * (b.np + 1) / 2;
     k_schwarz<<<grid_for(npair, 128), 128, 0, s>>>(b, Q);

@@ -31,7 +31,8 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_schwarz", "esmf_fock_destroy", "esmf_strerror", "esmf_last_error",
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
-           "esmf_fock_autotune"]
+           "esmf_fock_autotune", "esmf_fock_create_screened"]
+SCREENINGS = {"schwarz": 0, "pair_max": 1}
 PATHS = {"auto": 0, "cuda_core": 1}
 # declared in include/esmf_energy.h
 ENERGY_EXPORTS = ["esmf_energy_gradient", "esmf_gvp_gradient"]
@@ -58,7 +59,8 @@ class esmf_stats_t(C.Structure):
     _fields_ = [("n_basis", C.c_int64), ("n_pairs", C.c_int64), ("n_quartets_unique", C.c_int64),
                 ("n_quartets_kept", C.c_int64), ("n_bricks", C.c_int64), ("n_stored", C.c_int64),
                 ("store_bytes", C.c_int64), ("device_bytes", C.c_int64), ("mode", C.c_int32),
-                ("precision", C.c_int32), ("schwarz_tol", C.c_double), ("create_ms", C.c_double)]
+                ("precision", C.c_int32), ("schwarz_tol", C.c_double), ("create_ms", C.c_double),
+                ("screening", C.c_int32), ("n_pairs_kept", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,6 +85,9 @@ def load(path=None):
         L.esmf_fock_create.argtypes = [C.POINTER(esmf_basis_t), C.c_double, C.c_int, C.c_int, C.c_int,
                                        C.c_int64, C.POINTER(vp)]
         L.esmf_fock_create.restype = C.c_int
+        L.esmf_fock_create_screened.argtypes = [C.POINTER(esmf_basis_t), C.c_double, C.c_int, C.c_int, C.c_int,
+                                                C.c_int, C.c_int64, C.POINTER(vp)]
+        L.esmf_fock_create_screened.restype = C.c_int
         L.esmf_fock_build.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         L.esmf_fock_build.restype = C.c_int
         L.esmf_fock_build_noalloc.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
@@ -138,7 +143,8 @@ def _stream_ptr(stream):
 
 
 # ------------------------------------------------------------- C-ABI names
-def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0):
+def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0,
+                     screening="schwarz"):
     """Returns an opaque handle (c_void_p); see include/esmf_fock.h."""
     L = load()
     center = np.ascontiguousarray(basis.center, dtype=np.float64)
@@ -152,7 +158,12 @@ def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device
     h = C.c_void_p()
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    rc = L.esmf_fock_create(C.byref(b), float(schwarz_tol), m, p, int(device), int(budget_bytes), C.byref(h))
+    sc = SCREENINGS[screening] if isinstance(screening, str) else int(screening)
+    if sc == 0:
+        rc = L.esmf_fock_create(C.byref(b), float(schwarz_tol), m, p, int(device), int(budget_bytes), C.byref(h))
+    else:
+        rc = L.esmf_fock_create_screened(C.byref(b), float(schwarz_tol), sc, m, p, int(device),
+                                         int(budget_bytes), C.byref(h))
     _check(rc, "esmf_fock_create")
     return h
 
@@ -265,13 +276,14 @@ def esmf_last_error():
 class FockBuilder:
     """Owns one handle; D, J, K are torch float64 CUDA tensors (m, N, N)."""
 
-    def __init__(self, basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0):
+    def __init__(self, basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0,
+                 screening="schwarz"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("FockBuilder needs a CUDA device")
         self.n = int(basis.center.shape[0])
         self.device = int(device)
-        self.h = esmf_fock_create(basis, schwarz_tol, mode, precision, device, budget_bytes)
+        self.h = esmf_fock_create(basis, schwarz_tol, mode, precision, device, budget_bytes, screening)
 
     def stats(self):
         return esmf_fock_stats(self.h)

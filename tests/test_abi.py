@@ -54,6 +54,8 @@ def test_strerror_and_host_side_argument_errors(lib):
     b = fock.esmf_basis_t(0, None, None, None, None)
     assert lib.esmf_fock_create(C.byref(b), 0.0, 0, 0, 0, 0, None) == fock.ESMF_ERR_INVALID_ARG
     assert lib.esmf_fock_build(None, 1, None, None, None, None, None, None) == fock.ESMF_ERR_INVALID_ARG
+    bb = fock.esmf_basis_t(0, None, None, None, None)
+    assert lib.esmf_fock_create_screened(C.byref(bb), 0.0, 7, 0, 0, 0, 0, C.byref(h)) == fock.ESMF_ERR_INVALID_ARG
     assert lib.esmf_energy_gradient(None, 1, 1.0, None, None, None, None, None, None, None) == \
         fock.ESMF_ERR_INVALID_ARG
     assert lib.esmf_gvp_gradient(None, 1, 1.0, None, None, None, 0.0, 0.5, 1.0, None, None, None, None) == \
