@@ -226,6 +226,12 @@ def run_ours(args):
            "fock_builds_grouped": "3 + 3 (two passes)", "omega_mu_chi": [-3.0, 0.4, 0.8],
            "what": "L, E, |grad E|^2, dL/dc0, dL/dsigma, dL/dX (esmf_gvp_gradient)"}
 
+    # batching of uneven molecules: a mix of eight (60-300 functions, 4-16
+    # densities) and one of sixteen small ones (40-100 functions), each built
+    # one launch per molecule, in one batched launch, and as that launch
+    # replayed from a CUDA graph
+    batch = run_batched(fock, W, dev, stream, args.precision)
+
     # roofline of the dominant (contraction) kernel: algorithmic bytes =
     # kept unique integrals x bytes + D in + J, K out (FP64)
     eb = {"fp64": 8, "fp32": 4, "fp16x2": 4, "bf16x2": 4}[args.precision]
@@ -264,7 +270,8 @@ def run_ours(args):
            "gpu_launches": int((4 if args.precision in ("fp16x2", "bf16x2") else 2) * args.steps),
            "clocks": clk.summary(),
            "esmf_energy_gradient": energy,
-           "esmf_gvp_gradient": gvp}
+           "esmf_gvp_gradient": gvp,
+           "batched_uneven": batch}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_seconds)
     if rank == 0:
@@ -273,6 +280,69 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+BATCH_MIXES = {
+    "mixed_60_300": [(60, 4), (80, 8), (100, 12), (130, 16), (160, 6), (200, 10), (240, 14), (300, 16)],
+    "small_40_100": [(40 + 4 * i, 4 + (3 * i) % 13) for i in range(16)],
+}
+
+
+def run_batched(fock, W, dev, stream, precision):
+    if precision not in ("fp16x2", "bf16x2"):
+        return None
+    return {name: run_batch_mix(fock, W, dev, stream, precision, sizes, 900 + 50 * k)
+            for k, (name, sizes) in enumerate(BATCH_MIXES.items())}
+
+
+def run_batch_mix(fock, W, dev, stream, precision, sizes, seed0):
+    import torch
+    mols = [W.random_molecule(W.rng_for(W.BASE_SEED + seed0 + i), n, m) for i, (n, m) in enumerate(sizes)]
+    fbs = [fock.FockBuilder(w.basis, w.tol, "stored", precision, device=dev.index) for w in mols]
+    try:
+        Ds = [torch.from_numpy(w.D).to(dev) for w in mols]
+        Js = [torch.empty_like(D) for D in Ds]
+        Ks = [torch.empty_like(D) for D in Ds]
+        hs, ms = [fb.h for fb in fbs], [w.m for w in mols]
+
+        def seq():
+            for fb, D, J, K, m in zip(fbs, Ds, Js, Ks, ms):
+                fock.esmf_fock_build(fb.h, m, D, J, K, None, None, stream)
+
+        def bat():
+            fock.esmf_fock_build_batch(hs, ms, Ds, Js, Ks, stream=stream)
+
+        def timed(f, reps=20):
+            for _ in range(3):
+                f()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t_seq = timed(seq)
+        t_bat = timed(bat)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=torch.cuda.Stream(device=dev), capture_error_mode="thread_local"):
+            fock.esmf_fock_build_batch(hs, ms, Ds, Js, Ks)
+        t_graph = timed(g.replay)
+        quartets = sum(fb.stats()["n_quartets_kept"] for fb in fbs)
+        n = len(mols)
+        return {"molecules": [[w.basis.n, w.m] for w in mols],
+                "ms_per_round": {"one_launch_per_molecule": round(t_seq, 4), "batched": round(t_bat, 4),
+                                 "batched_graph": round(t_graph, 4)},
+                "builds_per_s": {"one_launch_per_molecule": round(n * 1e3 / t_seq, 1),
+                                 "batched": round(n * 1e3 / t_bat, 1),
+                                 "batched_graph": round(n * 1e3 / t_graph, 1)},
+                "quartets_per_s_batched_graph": round(quartets / (t_graph / 1e3), 1)}
+    finally:
+        for fb in fbs:
+            fb.close()
 
 
 # ------------------------------------------------------------------ oracle

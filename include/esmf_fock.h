@@ -161,6 +161,33 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J,
                     double *K, double *F, double *traces, void *stream);
 
 /*
+ * esmf_fock_build_batch -- esmf_fock_build for several handles (molecules of
+ * different sizes, each with its own density count) in ONE persistent
+ * tensor-core launch per pass of 16 densities (a single launch when every
+ * m <= 16): every CTA walks its cost-balanced slice of each handle's bricks
+ * in turn, so small molecules share the GPU instead of each filling a launch
+ * of its own.  The whole call allocates nothing once each handle has built
+ * with at least its m before, and can then be captured in a CUDA graph.
+ *   count   1 <= count <= ESMF_MAX_BATCH, distinct handles on one device, all
+ *           created stored with ESMF_PREC_FP16X2 or ESMF_PREC_BF16X2 (the
+ *           tensor-core path) and not switched to ESMF_PATH_CUDA_CORE
+ *   h, m    count handles and their density counts (host arrays)
+ *   D, J, K count device pointers each (host arrays of device pointers),
+ *           laid out as for esmf_fock_build with that entry's N and m
+ *   F, traces  NULL, or count device pointers each (entries may be NULL)
+ *   stream  cudaStream_t (NULL = legacy default stream)
+ * Asynchronous.  The error flag of the first handle records a device-side
+ * timeout (esmf_fock_device_error).  Errors: INVALID_ARG, UNSUPPORTED (a
+ * handle off the tensor-core path), OOM, CUDA.  The grouping of Sec. II.C
+ * (all densities of one molecule in one pass over its integrals) is kept per
+ * handle; batching across molecules has no counterpart in the paper.
+ */
+#define ESMF_MAX_BATCH 16
+int esmf_fock_build_batch(int count, esmf_fock_t *const *h, const int *m,
+                          const double *const *D, double *const *J, double *const *K,
+                          double *const *F, double *const *traces, void *stream);
+
+/*
  * esmf_fock_build_shard -- the part of esmf_fock_build contributed by shard
  * `shard` of `nshards` equal contiguous slices of the handle's kept brick
  * list.  J, K, F and the traces are linear in the integrals, so the element-

@@ -648,6 +648,63 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J, double *K
     return build_range(h, 0, h->nbricks, m, D, J, K, F, traces, stream);
 }
 
+int esmf_fock_build_batch(int count, esmf_fock_t *const *hs, const int *ms, const double *const *Ds,
+                          double *const *Js, double *const *Ks, double *const *Fs, double *const *traces,
+                          void *stream) {
+    if (count < 1 || count > ESMF_MAX_BATCH || !hs || !ms || !Ds || !Js || !Ks) {
+        set_error("batch: count must be in [1, %d] and h, m, D, J, K given", ESMF_MAX_BATCH);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    const int dev = hs[0] ? hs[0]->device : 0;
+    for (int i = 0; i < count; ++i) {
+        esmf_fock_t *h = hs[i];
+        if (!h) { set_error("batch: handle %d is NULL", i); return ESMF_ERR_INVALID_ARG; }
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == h) { set_error("batch: handle %d repeats handle %d", i, j); return ESMF_ERR_INVALID_ARG; }
+        if (h->device != dev) { set_error("batch: handles on different devices"); return ESMF_ERR_INVALID_ARG; }
+        if (ms[i] < 1 || ms[i] > ESMF_MAX_DENSITIES) { set_error("batch: m[%d] = %d", i, ms[i]); return ESMF_ERR_INVALID_ARG; }
+        if (!Ds[i] || !Js[i] || !Ks[i]) { set_error("batch: D, J, K of entry %d are required", i); return ESMF_ERR_INVALID_ARG; }
+        if (!(h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2) || h->path == ESMF_PATH_CUDA_CORE) {
+            set_error("batch: handle %d is not on the tensor-core path (stored FP16X2/BF16X2)", i);
+            return ESMF_ERR_UNSUPPORTED;
+        }
+    }
+    DeviceGuard g(dev);
+    if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
+    cudaStream_t s = (cudaStream_t)stream;
+    UmmaLaunch L[ESMF_MAX_BATCH];
+    for (int i = 0; i < count; ++i) {
+        esmf_fock_t *h = hs[i];
+        const int m = ms[i];
+        double *F = Fs ? Fs[i] : nullptr, *tr = traces ? traces[i] : nullptr;
+        if (!is_device_ptr(Ds[i]) || !is_device_ptr(Js[i]) || !is_device_ptr(Ks[i]) || (F && !is_device_ptr(F)) ||
+            (tr && !is_device_ptr(tr))) {
+            set_error("batch: entry %d buffers must be device memory", i);
+            return ESMF_ERR_INVALID_ARG;
+        }
+        RET(ensure_work(h, m));
+        const size_t acc = sizeof(double) * (size_t)m * h->np * h->np;
+        CKR(cudaMemsetAsync(h->Jacc, 0, acc, s));
+        CKR(cudaMemsetAsync(h->Kacc, 0, acc, s));
+        if (tr) CKR(cudaMemsetAsync(tr, 0, sizeof(double) * m, s));
+        UmmaLaunch &l = L[i];
+        l.bricks = h->bricks; l.nbricks = h->nbricks; l.offsets = h->offsets;
+        l.store = (const uint32_t *)h->store; l.kbank = h->kbank; l.jbank = h->jbank;
+        l.dmax_bits = h->dmax; l.D = Ds[i]; l.n = h->n; l.np = h->np; l.nb = h->nb; l.m = m;
+        l.bf16 = h->prec == ESMF_PREC_BF16X2; l.num_sms = h->num_sms; l.vscale = h->vscale;
+        l.Jacc = h->Jacc; l.Kacc = h->Kacc; l.error = hs[0]->err_dev;
+        l.chunk = 16;
+        if (h->parts) { l.part = h->parts; l.nparts = h->nparts; }
+    }
+    RET(launch_jk_umma_batch(L, count, s));
+    for (int i = 0; i < count; ++i) {
+        esmf_fock_t *h = hs[i];
+        RET(launch_finalize_blocked(h->dev(), ms[i], Ds[i], h->Jacc, h->Kacc, Js[i], Ks[i], Fs ? Fs[i] : nullptr,
+                                    traces ? traces[i] : nullptr, s));
+    }
+    return ESMF_OK;
+}
+
 int esmf_energy_gradient(esmf_fock_t *h, int n_occ, double c0, const double *G, const double *V,
                          const double *sigma, double *scalars, double *dE_dsigma, double *dE_dV,
                          void *stream) {
@@ -775,14 +832,16 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host, double *J_
     // bounded wait: poll the event, give up after timeout_ms
     const int limit = timeout_ms > 0 ? timeout_ms : 600000;
     const auto t0 = std::chrono::steady_clock::now();
-    int spin = 0;
     for (;;) {
         cudaError_t q = cudaEventQuery(h->done);
         if (q == cudaSuccess) break;
         if (q != cudaErrorNotReady) { set_error("build: %s", cudaGetErrorString(q)); return ESMF_ERR_CUDA; }
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (ms > limit) { set_error("build did not finish within %d ms", limit); return ESMF_ERR_TIMEOUT; }
-        if (++spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        // spin (yielding) for the first 5 ms so that a sub-millisecond build is
+        // picked up without sleep granularity, then poll every 20 us
+        if (ms < 5.0) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     if (*(volatile int *)h->err_host) {
         set_error("a bounded wait inside the contraction kernel expired (code %d)", *(volatile int *)h->err_host);

@@ -106,6 +106,7 @@ struct UmmaLaunch {
     int nparts = 0;
 };
 int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s);
+int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s);   // count <= 16
 int launch_finalize_blocked(const DevBasis &b, int m, const double *D, const double *Jb, const double *Kb,
                             double *J, double *K, double *F, double *tsum, cudaStream_t s);
 int umma_smem_bytes();

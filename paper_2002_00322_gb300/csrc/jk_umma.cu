@@ -74,24 +74,6 @@ struct Ctrl {
 };
 static_assert(sizeof(Ctrl) <= CTRL_BYTES, "control block");
 
-__constant__ int c_tup[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
-                                {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
-
-__device__ __forceinline__ unsigned tuple_activity(int P, int Q, int R, int S) {
-    const int bl[4] = {P, Q, R, S};
-    unsigned act = 0;
-    for (int t = 0; t < 8; ++t) {
-        bool dup = false;
-        for (int u = 0; u < t && !dup; ++u) {
-            bool same = true;
-            for (int x = 0; x < 4; ++x) same &= bl[c_tup[t][x]] == bl[c_tup[u][x]];
-            dup = same;
-        }
-        if (!dup) act |= 1u << t;
-    }
-    return act;
-}
-
 __device__ __forceinline__ float density_scale(const unsigned int *dmax_bits) {
     const float dm = __uint_as_float(*dmax_bits);
     if (!(dm > 0.f)) return 1.0f;
@@ -176,19 +158,47 @@ __global__ void k_dbank(const double *D, int n, int nb, int m, int d0, int mp, c
 }
 
 // ---------------------------------------------------------------- main kernel
-struct UmmaParams {
+// One entry of a launch: the bricks of one handle contracted with one chunk of
+// at most 16 of its densities.  A launch holds up to MAX_ENTRIES entries
+// (several molecules, uneven basis sizes and density counts) and every CTA
+// walks its own slice of every entry in turn.
+struct UmmaEntry {
     const BrickDesc *bricks;
     int64_t nbricks;
     const int64_t *offsets;        // record start, in 32-bit words
     const uint32_t *store;
     const uint16_t *kbank, *jbank;
-    int nb, np, mp, m, d0, mtot, bf16;
+    const int64_t *part;           // per-CTA brick ranges (nparts + 1), or null: even split by count
+    int nparts, nb, m, d0, mtot, bf16;
     float vscale;
     const unsigned int *dmax_bits;
-    double *Jacc, *Kacc;   // block-major: [X][Y][k][x][y], k < mtot
-    int *error;
-    const int64_t *part;   // per-CTA brick ranges, or null for an even split by count
+    double *Jacc, *Kacc;           // block-major: [X][Y][k][x][y], k < mtot
 };
+constexpr int MAX_ENTRIES = 16;
+struct UmmaParams {
+    UmmaEntry e[MAX_ENTRIES];
+    int nentries, mp;              // mp: density columns per pass, the same for every entry
+    int *error;
+};
+
+namespace {
+
+// This CTA's brick range of entry E.
+__device__ __forceinline__ void entry_range(const UmmaEntry &E, int64_t &beg, int64_t &end) {
+    if (E.part) {
+        if ((int)blockIdx.x < E.nparts) {
+            beg = E.part[blockIdx.x];
+            end = E.part[blockIdx.x + 1];
+        } else {
+            beg = end = 0;
+        }
+    } else {
+        beg = E.nbricks * blockIdx.x / gridDim.x;
+        end = E.nbricks * (blockIdx.x + 1) / gridDim.x;
+    }
+}
+
+}  // namespace
 
 namespace {
 
@@ -277,14 +287,17 @@ __device__ __forceinline__ void flush_block2(const float *hi, const float *lo, d
 
 }  // namespace
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__ UmmaParams P) {
     extern __shared__ __align__(1024) unsigned char sm[];
     Ctrl &c = *reinterpret_cast<Ctrl *>(sm + 2 * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t beg = a.part ? a.part[blockIdx.x] : a.nbricks * blockIdx.x / gridDim.x;
-    const int64_t end = a.part ? a.part[blockIdx.x + 1] : a.nbricks * (blockIdx.x + 1) / gridDim.x;
-    const int nloc = (int)(end - beg);
-    const int mp = a.mp;
+    int nloc = 0;                  // this CTA's bricks over all entries
+    for (int e = 0; e < P.nentries; ++e) {
+        int64_t b0, b1;
+        entry_range(P.e[e], b0, b1);
+        nloc += (int)(b1 - b0);
+    }
+    const int mp = P.mp;
     const uint32_t kbytes = 512u * mp, jbytes = 256u * mp;
     volatile int *abort_flag = &c.abort_flag;
 
@@ -308,7 +321,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
     const uint32_t tmem = c.tmem_base;
     auto fail = [&](int code) {
         *abort_flag = 1;
-        atomicExch(a.error, code);
+        atomicExch(P.error, code);
     };
 
     if (nloc > 0 && warp == 0 && lane == 0) {
@@ -316,34 +329,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         int issued = 0;
         // the next brick's descriptor and record offset are loaded one
         // iteration ahead, so their latency overlaps the wait for a free stage
-        BrickDesc dnext = a.bricks[beg];
-        int64_t onext = a.offsets[beg];
-        for (int i = 0; i < nloc; ++i) {
-            const int s = i & 1;
-            const BrickDesc d = dnext;
-            const int64_t off = onext;
-            if (i + 1 < nloc) {
-                dnext = a.bricks[beg + i + 1];
-                onext = a.offsets[beg + i + 1];
+        int i = 0;
+        bool stop = false;
+        for (int e = 0; e < P.nentries && !stop; ++e) {
+            const UmmaEntry &E = P.e[e];
+            int64_t beg, end;
+            entry_range(E, beg, end);
+            if (beg >= end) continue;
+            const BrickDesc *bricks = E.bricks;
+            const int64_t *offsets = E.offsets;
+            const uint32_t *store = E.store;
+            const uint16_t *kb = E.kbank, *jb = E.jbank;
+            const int enb = E.nb;
+            BrickDesc dnext = bricks[beg];
+            int64_t onext = offsets[beg];
+            for (int64_t ib = beg; ib < end; ++ib, ++i) {
+                const int s = i & 1;
+                const BrickDesc d = dnext;
+                const int64_t off = onext;
+                if (ib + 1 < end) {
+                    dnext = bricks[ib + 1];
+                    onext = offsets[ib + 1];
+                }
+                if (i >= 2 && !mbar_wait(&c.mmad[s], ((i - 2) >> 1) & 1, abort_flag)) { fail(2); stop = true; break; }
+                unsigned char *st = sm + s * STAGE_BYTES;
+                const uint32_t rec = ((512u + 4u * (uint32_t)d.nkept) + 15u) & ~15u;
+                const size_t kw = kbytes / 2, jw = jbytes / 2;
+                mbar_arrive_expect_tx(&c.full[s], rec + 4 * kbytes + 2 * jbytes);
+                bulk_g2s(st + OFF_IN, store + off, rec, &c.full[s]);
+                bulk_g2s(st + OFF_B1 + 0 * KB_BYTES_MAX, kb + ((size_t)d.Q * enb + d.S) * kw, kbytes, &c.full[s]);
+                bulk_g2s(st + OFF_B1 + 1 * KB_BYTES_MAX, kb + ((size_t)d.P * enb + d.S) * kw, kbytes, &c.full[s]);
+                bulk_g2s(st + OFF_B1 + 2 * KB_BYTES_MAX, kb + ((size_t)d.Q * enb + d.R) * kw, kbytes, &c.full[s]);
+                bulk_g2s(st + OFF_B1 + 3 * KB_BYTES_MAX, kb + ((size_t)d.P * enb + d.R) * kw, kbytes, &c.full[s]);
+                bulk_g2s(st + OFF_B5, jb + ((size_t)d.R * (d.R + 1) / 2 + d.S) * jw, jbytes, &c.full[s]);
+                bulk_g2s(st + OFF_B5 + JB_BYTES_MAX, jb + ((size_t)d.P * (d.P + 1) / 2 + d.Q) * jw, jbytes, &c.full[s]);
+                issued = i + 1;
             }
-            if (i >= 2 && !mbar_wait(&c.mmad[s], ((i - 2) >> 1) & 1, abort_flag)) { fail(2); break; }
-            unsigned char *st = sm + s * STAGE_BYTES;
-            const uint32_t rec = ((512u + 4u * (uint32_t)d.nkept) + 15u) & ~15u;
-            const uint16_t *kb = a.kbank, *jb = a.jbank;
-            const size_t kw = kbytes / 2, jw = jbytes / 2;
-            mbar_arrive_expect_tx(&c.full[s], rec + 4 * kbytes + 2 * jbytes);
-            bulk_g2s(st + OFF_IN, a.store + off, rec, &c.full[s]);
-            bulk_g2s(st + OFF_B1 + 0 * KB_BYTES_MAX, kb + ((size_t)d.Q * a.nb + d.S) * kw, kbytes, &c.full[s]);
-            bulk_g2s(st + OFF_B1 + 1 * KB_BYTES_MAX, kb + ((size_t)d.P * a.nb + d.S) * kw, kbytes, &c.full[s]);
-            bulk_g2s(st + OFF_B1 + 2 * KB_BYTES_MAX, kb + ((size_t)d.Q * a.nb + d.R) * kw, kbytes, &c.full[s]);
-            bulk_g2s(st + OFF_B1 + 3 * KB_BYTES_MAX, kb + ((size_t)d.P * a.nb + d.R) * kw, kbytes, &c.full[s]);
-            bulk_g2s(st + OFF_B5, jb + ((size_t)d.R * (d.R + 1) / 2 + d.S) * jw, jbytes, &c.full[s]);
-            bulk_g2s(st + OFF_B5 + JB_BYTES_MAX, jb + ((size_t)d.P * (d.P + 1) / 2 + d.Q) * jw, jbytes, &c.full[s]);
-            issued = i + 1;
         }
         // no copy may still be landing when the CTA leaves
-        for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
-            mbar_wait(&c.full[i & 1], (i >> 1) & 1, abort_flag);
+        for (int k = (issued > 2 ? issued - 2 : 0); k < issued; ++k)
+            mbar_wait(&c.full[k & 1], (k >> 1) & 1, abort_flag);
     } else if (nloc > 0 && warp == 1) {
         // ------------------------------------------------ MMA issuer
         // The whole warp runs the loop and takes every wait (decisions made
@@ -355,72 +380,83 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         // run regions V1, V2 at WV + rb*2RW (+RW); per-brick J2, J1 at
         // WJ + b*2mp (+mp).  At mp = 16: 320 + 128 + 64 = 512 columns.
         const uint32_t RW = 2 * mp, WV = 2 * SWIN * RW, WJ = WV + 4 * RW;
-        const uint32_t id_k = idesc_f16(64, RW, 0, a.bf16), idm_k = idesc_f16(64, RW, 1, a.bf16);
-        const uint32_t id_j = idesc_f16(64, mp, 0, a.bf16), idm_j = idesc_f16(64, mp, 1, a.bf16);
         const uint32_t klo = 256u * mp, jlo = 128u * mp;     // byte offset of the lo rows in B tiles
         int run = 0, item = 0, committed = 0;
         unsigned touched3 = 0, touched4 = 0;
-        BrickDesc dnext = a.bricks[beg];
-        for (int i = 0; i < nloc; ++i) {
-            const int s = i & 1, b = i & 1;
-            const BrickDesc d = dnext;
-            if (i + 1 < nloc) dnext = a.bricks[beg + i + 1];
-            const bool frun = (i == 0) || (d.pad & BRICK_RUN_FIRST);
-            const bool lrun = (i == nloc - 1) || (d.pad & BRICK_RUN_LAST);
-            const bool fitem = (i == 0) || (d.pad & BRICK_ITEM_FIRST);
-            const bool litem = (i == nloc - 1) || (d.pad & BRICK_ITEM_LAST);
-            const int rb = run & 1;
-            if (!__all_sync(~0u, mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag))) { fail(3); break; }
-            if (i >= 2 && !__all_sync(~0u, mbar_wait(&c.acce[b], ((i - 2) >> 1) & 1, abort_flag))) { fail(4); break; }
-            if (frun && run >= 2 && !__all_sync(~0u, mbar_wait(&c.runfree[rb], ((run - 2) >> 1) & 1, abort_flag))) { fail(5); break; }
-            if (fitem) { touched3 = 0; touched4 = 0; }
-            // window region w (V3[w] and V4[w]) is free once the epilogue has
-            // staged it at the end of the previous item
-            const int wreg = d.S % SWIN;
-            if (d.R != d.S && item >= 1 && !((touched3 | touched4) & (1u << wreg)) &&
-                !__all_sync(~0u, counter_wait(&c.wstaged[wreg], 4u * (unsigned)item, abort_flag))) { fail(10); break; }
-            tc_fence_after();
-            const bool pq_diff = d.P != d.Q, rs_diff = d.R != d.S;
-            const int w = d.S % SWIN;
-            const bool fresh3 = !(touched3 & (1u << w)), fresh4 = !(touched4 & (1u << w));
-            if (rs_diff) touched3 |= 1u << w;
-            if (rs_diff && pq_diff) touched4 |= 1u << w;
-            if (elect_one()) {
-                const uint32_t st = smem_u32(sm + s * STAGE_BYTES);
-                const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
-                const uint32_t B1 = st + OFF_B1, B2 = B1 + KB_BYTES_MAX, B3 = B2 + KB_BYTES_MAX,
-                               B4 = B3 + KB_BYTES_MAX, B5 = st + OFF_B5, B6 = B5 + JB_BYTES_MAX;
-                // three passes into the same columns: hi x [D|D^T]_hi, hi x [D|D^T]_lo, lo x [D|D^T]_hi
-                auto view = [&](uint32_t col, uint32_t AH, uint32_t AL, uint32_t kstep, uint32_t lbo, uint32_t sbo,
-                                uint32_t id, uint32_t B, uint32_t blo, bool fresh) {
-                    const uint64_t ah = sdesc(AH, lbo, sbo), al = ah + ((AL - AH) >> 4);
-                    const uint64_t bh = sdesc(B, 128, 1024), bl = bh + (blo >> 4);
-                    const uint32_t ks = kstep >> 4;
+        int i = 0;
+        bool stop = false;
+        for (int e = 0; e < P.nentries && !stop; ++e) {
+            const UmmaEntry &E = P.e[e];
+            int64_t beg, end;
+            entry_range(E, beg, end);
+            if (beg >= end) continue;
+            const BrickDesc *bricks = E.bricks;
+            // instruction descriptors of the entry (FP16 or BF16 halves)
+            const uint32_t id_k = idesc_f16(64, RW, 0, E.bf16), idm_k = idesc_f16(64, RW, 1, E.bf16);
+            const uint32_t id_j = idesc_f16(64, mp, 0, E.bf16), idm_j = idesc_f16(64, mp, 1, E.bf16);
+            BrickDesc dnext = bricks[beg];
+            for (int64_t ib = beg; ib < end; ++ib, ++i) {
+                const int s = i & 1, b = i & 1;
+                const BrickDesc d = dnext;
+                const bool sfirst = ib == beg, slast = ib == end - 1;
+                if (ib + 1 < end) dnext = bricks[ib + 1];
+                const bool frun = sfirst || (d.pad & BRICK_RUN_FIRST);
+                const bool lrun = slast || (d.pad & BRICK_RUN_LAST);
+                const bool fitem = sfirst || (d.pad & BRICK_ITEM_FIRST);
+                const bool litem = slast || (d.pad & BRICK_ITEM_LAST);
+                const int rb = run & 1;
+                if (!__all_sync(~0u, mbar_wait(&c.conv[s], (i >> 1) & 1, abort_flag))) { fail(3); stop = true; break; }
+                if (i >= 2 && !__all_sync(~0u, mbar_wait(&c.acce[b], ((i - 2) >> 1) & 1, abort_flag))) { fail(4); stop = true; break; }
+                if (frun && run >= 2 && !__all_sync(~0u, mbar_wait(&c.runfree[rb], ((run - 2) >> 1) & 1, abort_flag))) { fail(5); stop = true; break; }
+                if (fitem) { touched3 = 0; touched4 = 0; }
+                // window region w (V3[w] and V4[w]) is free once the epilogue has
+                // staged it at the end of the previous item
+                const int wreg = d.S % SWIN;
+                if (d.R != d.S && item >= 1 && !((touched3 | touched4) & (1u << wreg)) &&
+                    !__all_sync(~0u, counter_wait(&c.wstaged[wreg], 4u * (unsigned)item, abort_flag))) { fail(10); stop = true; break; }
+                tc_fence_after();
+                const bool pq_diff = d.P != d.Q, rs_diff = d.R != d.S;
+                const int w = d.S % SWIN;
+                const bool fresh3 = !(touched3 & (1u << w)), fresh4 = !(touched4 & (1u << w));
+                if (rs_diff) touched3 |= 1u << w;
+                if (rs_diff && pq_diff) touched4 |= 1u << w;
+                if (elect_one()) {
+                    const uint32_t st = smem_u32(sm + s * STAGE_BYTES);
+                    const uint32_t VH = st + OFF_VH, VL = st + OFF_VL, WH = st + OFF_WH, WL = st + OFF_WL;
+                    const uint32_t B1 = st + OFF_B1, B2 = B1 + KB_BYTES_MAX, B3 = B2 + KB_BYTES_MAX,
+                                   B4 = B3 + KB_BYTES_MAX, B5 = st + OFF_B5, B6 = B5 + JB_BYTES_MAX;
+                    // three passes into the same columns: hi x [D|D^T]_hi, hi x [D|D^T]_lo, lo x [D|D^T]_hi
+                    auto view = [&](uint32_t col, uint32_t AH, uint32_t AL, uint32_t kstep, uint32_t lbo, uint32_t sbo,
+                                    uint32_t id, uint32_t B, uint32_t blo, bool fresh) {
+                        const uint64_t ah = sdesc(AH, lbo, sbo), al = ah + ((AL - AH) >> 4);
+                        const uint64_t bh = sdesc(B, 128, 1024), bl = bh + (blo >> 4);
+                        const uint32_t ks = kstep >> 4;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        mma_f16(tmem + col, ah + j * ks, bh + 16 * j, id, (j > 0 || !fresh) ? 1u : 0u);
+                        for (int j = 0; j < 4; ++j)
+                            mma_f16(tmem + col, ah + j * ks, bh + 16 * j, id, (j > 0 || !fresh) ? 1u : 0u);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        mma_f16(tmem + col, ah + j * ks, bl + 16 * j, id, 1u);
+                        for (int j = 0; j < 4; ++j)
+                            mma_f16(tmem + col, ah + j * ks, bl + 16 * j, id, 1u);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        mma_f16(tmem + col, al + j * ks, bh + 16 * j, id, 1u);
-                };
-                // exchange: V1, V2 over the run; V3, V4 over the item (nothing when R == S,
-                // V2 and V4 nothing when P == Q: those permutations repeat others)
-                view(WV + rb * 2 * RW, VH, VL, 256, 128, 1024, id_k, B1, klo, frun);
-                if (pq_diff) view(WV + rb * 2 * RW + RW, VH, VL, 2048, 1024, 128, id_k, B2, klo, frun);
-                if (rs_diff) view(RW * w, VH, VL, 256, 128, 1024, idm_k, B3, klo, fresh3);
-                if (rs_diff && pq_diff) view(RW * (SWIN + w), VH, VL, 2048, 1024, 128, idm_k, B4, klo, fresh4);
-                // Coulomb views, per brick: J1 (K-major over W) and J2 (MN-major over W)
-                view(WJ + b * 2 * mp + mp, WH, WL, 256, 128, 1024, id_j, B5, jlo, true);
-                view(WJ + b * 2 * mp, WH, WL, 2048, 1024, 128, idm_j, B6, jlo, true);
-                mma_commit(&c.mmad[s]);
+                        for (int j = 0; j < 4; ++j)
+                            mma_f16(tmem + col, al + j * ks, bh + 16 * j, id, 1u);
+                    };
+                    // exchange: V1, V2 over the run; V3, V4 over the item (nothing when R == S,
+                    // V2 and V4 nothing when P == Q: those permutations repeat others)
+                    view(WV + rb * 2 * RW, VH, VL, 256, 128, 1024, id_k, B1, klo, frun);
+                    if (pq_diff) view(WV + rb * 2 * RW + RW, VH, VL, 2048, 1024, 128, id_k, B2, klo, frun);
+                    if (rs_diff) view(RW * w, VH, VL, 256, 128, 1024, idm_k, B3, klo, fresh3);
+                    if (rs_diff && pq_diff) view(RW * (SWIN + w), VH, VL, 2048, 1024, 128, idm_k, B4, klo, fresh4);
+                    // Coulomb views, per brick: J1 (K-major over W) and J2 (MN-major over W)
+                    view(WJ + b * 2 * mp + mp, WH, WL, 256, 128, 1024, id_j, B5, jlo, true);
+                    view(WJ + b * 2 * mp, WH, WL, 2048, 1024, 128, idm_j, B6, jlo, true);
+                    mma_commit(&c.mmad[s]);
+                }
+                __syncwarp();
+                committed = i + 1;
+                if (lrun) ++run;
+                if (litem) ++item;
             }
-            __syncwarp();
-            committed = i + 1;
-            if (lrun) ++run;
-            if (litem) ++item;
         }
         if (committed > 0) {
             const int i = committed - 1;
@@ -496,8 +532,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         const bool live = lane < 16;
         const int et = threadIdx.x - 192;               // 0..127
         const uint32_t tl = tmem + ((uint32_t)(slice * 32) << 16);
-        const float inv = 1.0f / (a.vscale * density_scale(a.dmax_bits));
-        const int m = a.m, nb = a.nb, mtot = a.mtot;
         const uint32_t RW = 2 * mp, WV = 2 * SWIN * RW, WJ = WV + 4 * RW;
         float *stA = reinterpret_cast<float *>(sm + 2 * STAGE_BYTES + CTRL_BYTES);
         float *stB = stA + STAGE_K_FLOATS;
@@ -507,7 +541,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         float j1h[MPMAX], j1l[MPMAX];
 #pragma unroll
         for (int k = 0; k < MPMAX; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
-        auto blk = [&](double *base, int X, int Y) { return base + ((int64_t)(X * nb + Y) * mtot + a.d0) * 64; };
+        // per-entry constants (refreshed when the stream enters a new entry)
+        int m = 0, nb = 0, mtot = 0, d0 = 0;
+        float inv = 1.0f;
+        double *Jacc = nullptr, *Kacc = nullptr;
+        auto blk = [&](double *base, int X, int Y) { return base + ((int64_t)(X * nb + Y) * mtot + d0) * 64; };
         auto stage = [&](uint32_t col, bool kview, float *dst) {
             if (mp == 16) {
                 if (kview) stage_view<16, true>(tl + col, live, row, m, inv, dst);
@@ -524,84 +562,96 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         };
         int run = 0;
         unsigned touched3 = 0, touched4 = 0;
-        for (int i = 0; i < nloc; ++i) {
-            const int s = i & 1, b = i & 1;
-            const BrickDesc d = a.bricks[beg + i];
-            const bool lrun = (i == nloc - 1) || (d.pad & BRICK_RUN_LAST);
-            const bool fitem = (i == 0) || (d.pad & BRICK_ITEM_FIRST);
-            const bool litem = (i == nloc - 1) || (d.pad & BRICK_ITEM_LAST);
-            const bool pq_diff = d.P != d.Q, rs_diff = d.R != d.S;
-            const bool diag = d.R == d.P && d.S == d.Q;
-            if (fitem) { touched3 = 0; touched4 = 0; }
-            if (rs_diff) touched3 |= 1u << (d.S % SWIN);
-            if (rs_diff && pq_diff) touched4 |= 1u << (d.S % SWIN);
-            if (!mbar_wait(&c.mmad[s], (i >> 1) & 1, abort_flag)) fail(7);
-            // leave together: every epilogue thread must reach the same named barriers
-            named_bar_sync(2, 128);
-            if (et == 0) c.edecide = *abort_flag;
-            named_bar_sync(2, 128);
-            if (c.edecide) break;
-            tc_fence_after();
-            // per brick: Coulomb view J2 -> J[R,S] (not for the (PQ|PQ) brick) is
-            // flushed; J1 -> J[P,Q] joins the item's compensated sum
-            stage(WJ + b * 2 * mp, false, stJ);
-            if (mp == 16) accumulate_row<16>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
-            else accumulate_row<8>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
-            release(&c.acce[b]);
-            if (!diag) {
+        int i = 0;
+        bool stop = false;
+        for (int e = 0; e < P.nentries && !stop; ++e) {
+            const UmmaEntry &E = P.e[e];
+            int64_t beg, end;
+            entry_range(E, beg, end);
+            if (beg >= end) continue;
+            const BrickDesc *bricks = E.bricks;
+            m = E.m; nb = E.nb; mtot = E.mtot; d0 = E.d0; Jacc = E.Jacc; Kacc = E.Kacc;
+            inv = 1.0f / (E.vscale * density_scale(E.dmax_bits));
+            for (int64_t ib = beg; ib < end; ++ib, ++i) {
+                const int s = i & 1, b = i & 1;
+                const BrickDesc d = bricks[ib];
+                const bool sfirst = ib == beg, slast = ib == end - 1;
+                const bool lrun = slast || (d.pad & BRICK_RUN_LAST);
+                const bool fitem = sfirst || (d.pad & BRICK_ITEM_FIRST);
+                const bool litem = slast || (d.pad & BRICK_ITEM_LAST);
+                const bool pq_diff = d.P != d.Q, rs_diff = d.R != d.S;
+                const bool diag = d.R == d.P && d.S == d.Q;
+                if (fitem) { touched3 = 0; touched4 = 0; }
+                if (rs_diff) touched3 |= 1u << (d.S % SWIN);
+                if (rs_diff && pq_diff) touched4 |= 1u << (d.S % SWIN);
+                if (!mbar_wait(&c.mmad[s], (i >> 1) & 1, abort_flag)) fail(7);
+                // leave together: every epilogue thread must reach the same named barriers
                 named_bar_sync(2, 128);
-                flush_block(stJ, blk(a.Jacc, d.R, d.S), m, et);
-            }
-            named_bar_sync(2, 128);
-            if (lrun) {
-                // V1 -> K[P,R] (and K[R,P] unless (PQ|PQ)), V2 -> K[Q,R], K[R,Q] (P != Q)
-                const int rb = run & 1;
-                stage(WV + rb * 2 * RW, true, stA);
-                if (pq_diff) stage(WV + rb * 2 * RW + RW, true, stB);
-                release(&c.runfree[rb]);
+                if (et == 0) c.edecide = *abort_flag;
                 named_bar_sync(2, 128);
-                flush_block(stA, blk(a.Kacc, d.P, d.R), m, et);
-                if (!diag) flush_block(stA + MPMAX * 64, blk(a.Kacc, d.R, d.P), m, et);
-                if (pq_diff) {
-                    flush_block(stB, blk(a.Kacc, d.Q, d.R), m, et);
-                    if (!diag) flush_block(stB + MPMAX * 64, blk(a.Kacc, d.R, d.Q), m, et);
+                if (c.edecide) { stop = true; break; }
+                tc_fence_after();
+                // per brick: Coulomb view J2 -> J[R,S] (not for the (PQ|PQ) brick) is
+                // flushed; J1 -> J[P,Q] joins the item's compensated sum
+                stage(WJ + b * 2 * mp, false, stJ);
+                if (mp == 16) accumulate_row<16>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
+                else accumulate_row<8>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
+                release(&c.acce[b]);
+                if (!diag) {
+                    named_bar_sync(2, 128);
+                    flush_block(stJ, blk(Jacc, d.R, d.S), m, et);
                 }
                 named_bar_sync(2, 128);
-                ++run;
-            }
-            if (litem) {
-                if (live) {
-#pragma unroll
-                    for (int k = 0; k < MPMAX; ++k)
-                        if (k < m) { stJ1[k * 64 + row] = j1h[k]; stJ1lo[k * 64 + row] = j1l[k]; }
+                if (lrun) {
+                    // V1 -> K[P,R] (and K[R,P] unless (PQ|PQ)), V2 -> K[Q,R], K[R,Q] (P != Q)
+                    const int rb = run & 1;
+                    stage(WV + rb * 2 * RW, true, stA);
+                    if (pq_diff) stage(WV + rb * 2 * RW + RW, true, stB);
+                    release(&c.runfree[rb]);
+                    named_bar_sync(2, 128);
+                    flush_block(stA, blk(Kacc, d.P, d.R), m, et);
+                    if (!diag) flush_block(stA + MPMAX * 64, blk(Kacc, d.R, d.P), m, et);
+                    if (pq_diff) {
+                        flush_block(stB, blk(Kacc, d.Q, d.R), m, et);
+                        if (!diag) flush_block(stB + MPMAX * 64, blk(Kacc, d.R, d.Q), m, et);
+                    }
+                    named_bar_sync(2, 128);
+                    ++run;
                 }
+                if (litem) {
+                    if (live) {
 #pragma unroll
-                for (int k = 0; k < MPMAX; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
-                named_bar_sync(2, 128);
-                flush_block2(stJ1, stJ1lo, blk(a.Jacc, d.P, d.Q), m, et);
-                named_bar_sync(2, 128);
-                // window regions: V3 -> K[P,S], K[S,P]; V4 -> K[Q,S], K[S,Q] (D^T parts
-                // not for the (PQ|PQ) item)
-                const int S0 = d.S - d.S % SWIN;
-                for (int w = 0; w < SWIN; ++w) {
-                    const bool h3 = touched3 & (1u << w), h4 = touched4 & (1u << w);
-                    if (h3) stage(RW * w, true, stA);
-                    if (h4) stage(RW * (SWIN + w), true, stB);
-                    tc_fence_before();                  // every region, once per item
-                    __syncwarp();
-                    if (lane == 0) counter_release_add(&c.wstaged[w]);
-                    if (!h3 && !h4) continue;
-                    named_bar_sync(2, 128);
-                    const int S = S0 + w;
-                    if (h3) {
-                        flush_block(stA, blk(a.Kacc, d.P, S), m, et);
-                        if (!diag) flush_block(stA + MPMAX * 64, blk(a.Kacc, S, d.P), m, et);
+                        for (int k = 0; k < MPMAX; ++k)
+                            if (k < m) { stJ1[k * 64 + row] = j1h[k]; stJ1lo[k * 64 + row] = j1l[k]; }
                     }
-                    if (h4) {
-                        flush_block(stB, blk(a.Kacc, d.Q, S), m, et);
-                        if (!diag) flush_block(stB + MPMAX * 64, blk(a.Kacc, S, d.Q), m, et);
-                    }
+#pragma unroll
+                    for (int k = 0; k < MPMAX; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
                     named_bar_sync(2, 128);
+                    flush_block2(stJ1, stJ1lo, blk(Jacc, d.P, d.Q), m, et);
+                    named_bar_sync(2, 128);
+                    // window regions: V3 -> K[P,S], K[S,P]; V4 -> K[Q,S], K[S,Q] (D^T parts
+                    // not for the (PQ|PQ) item)
+                    const int S0 = d.S - d.S % SWIN;
+                    for (int w = 0; w < SWIN; ++w) {
+                        const bool h3 = touched3 & (1u << w), h4 = touched4 & (1u << w);
+                        if (h3) stage(RW * w, true, stA);
+                        if (h4) stage(RW * (SWIN + w), true, stB);
+                        tc_fence_before();                  // every region, once per item
+                        __syncwarp();
+                        if (lane == 0) counter_release_add(&c.wstaged[w]);
+                        if (!h3 && !h4) continue;
+                        named_bar_sync(2, 128);
+                        const int S = S0 + w;
+                        if (h3) {
+                            flush_block(stA, blk(Kacc, d.P, S), m, et);
+                            if (!diag) flush_block(stA + MPMAX * 64, blk(Kacc, S, d.P), m, et);
+                        }
+                        if (h4) {
+                            flush_block(stB, blk(Kacc, d.Q, S), m, et);
+                            if (!diag) flush_block(stB + MPMAX * 64, blk(Kacc, S, d.Q), m, et);
+                        }
+                        named_bar_sync(2, 128);
+                    }
                 }
             }
         }
@@ -612,6 +662,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(UmmaParams a) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
+}
+
+// Several handles in one persistent launch per pass of 16 densities: pass c
+// contracts density chunk c of every handle with more than 16c densities
+// (one launch when every m <= 16).  Each handle keeps its own density bank
+// and accumulators; every CTA walks its cost-balanced slice of each handle.
+int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s) {
+    if (count < 1 || count > MAX_ENTRIES) {
+        set_error("batch of %d handles outside [1, %d]", count, MAX_ENTRIES);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_jk_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TOTAL);
+    if (e != cudaSuccess) { set_error("smem attribute: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+    int mmax = 0, grid = 1;
+    for (int i = 0; i < count; ++i) {
+        const UmmaLaunch &L = Ls[i];
+        const int64_t nn = (int64_t)L.n * L.n;
+        e = cudaMemsetAsync(L.dmax_bits, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) { set_error("memset dmax: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+        k_dmax<<<256, 256, 0, s>>>(L.D, (int64_t)L.m * nn, L.dmax_bits);
+        mmax = L.m > mmax ? L.m : mmax;
+        const int g = L.part ? L.nparts : (L.nbricks < L.num_sms ? (int)L.nbricks : L.num_sms);
+        grid = g > grid ? g : grid;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("k_dmax: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+    for (int d0 = 0; d0 < mmax; d0 += MPMAX) {
+        UmmaParams p;
+        p.nentries = 0;
+        p.mp = MPMAX;
+        p.error = Ls[0].error;
+        for (int i = 0; i < count; ++i) {
+            const UmmaLaunch &L = Ls[i];
+            if (d0 >= L.m) continue;
+            const int mc = (L.m - d0) < MPMAX ? (L.m - d0) : MPMAX;
+            const int64_t work = (int64_t)L.nb * L.nb * 4 * MPMAX * 64 + (int64_t)L.nb * (L.nb + 1) / 2 * 2 * MPMAX * 64;
+            int g = (int)((work + 255) / 256);
+            if (g > 4096) g = 4096;
+            k_dbank<<<g, 256, 0, s>>>(L.D, L.n, L.nb, mc, d0, MPMAX, L.dmax_bits, L.bf16, L.kbank, L.jbank);
+            if (L.nbricks == 0) continue;
+            UmmaEntry &E = p.e[p.nentries++];
+            E.bricks = L.bricks; E.nbricks = L.nbricks; E.offsets = L.offsets; E.store = L.store;
+            E.kbank = L.kbank; E.jbank = L.jbank; E.part = L.part; E.nparts = L.nparts;
+            E.nb = L.nb; E.m = mc; E.d0 = d0; E.mtot = L.m; E.bf16 = L.bf16;
+            E.vscale = L.vscale; E.dmax_bits = L.dmax_bits; E.Jacc = L.Jacc; E.Kacc = L.Kacc;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error("k_dbank: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+        if (p.nentries == 0) continue;
+        k_jk_umma<<<grid, NTHREADS, SMEM_TOTAL, s>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error("k_jk_umma: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
+    }
+    return ESMF_OK;
 }
 
 int umma_smem_bytes() { return SMEM_TOTAL; }
@@ -640,12 +744,14 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
         if (e != cudaSuccess) { set_error("k_dbank: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
         if (L.nbricks == 0) continue;
         UmmaParams p;
-        p.bricks = L.bricks; p.nbricks = L.nbricks; p.offsets = L.offsets; p.store = L.store;
-        p.kbank = L.kbank; p.jbank = L.jbank; p.nb = L.nb; p.np = L.np; p.mp = mp; p.m = mc; p.d0 = d0;
-        p.mtot = L.m;
-        p.bf16 = L.bf16; p.vscale = L.vscale; p.dmax_bits = L.dmax_bits; p.Jacc = L.Jacc; p.Kacc = L.Kacc;
+        p.nentries = 1;
+        p.mp = mp;
         p.error = L.error;
-        p.part = L.part;
+        UmmaEntry &E = p.e[0];
+        E.bricks = L.bricks; E.nbricks = L.nbricks; E.offsets = L.offsets; E.store = L.store;
+        E.kbank = L.kbank; E.jbank = L.jbank; E.part = L.part; E.nparts = L.nparts;
+        E.nb = L.nb; E.m = mc; E.d0 = d0; E.mtot = L.m; E.bf16 = L.bf16;
+        E.vscale = L.vscale; E.dmax_bits = L.dmax_bits; E.Jacc = L.Jacc; E.Kacc = L.Kacc;
         int grid = L.num_sms;
         if (grid > L.nbricks) grid = (int)L.nbricks;
         if (L.part) grid = L.nparts;

@@ -31,7 +31,8 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_schwarz", "esmf_fock_destroy", "esmf_strerror", "esmf_last_error",
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
-           "esmf_fock_autotune", "esmf_fock_create_screened"]
+           "esmf_fock_autotune", "esmf_fock_create_screened", "esmf_fock_build_batch"]
+MAX_BATCH = 16
 SCREENINGS = {"schwarz": 0, "pair_max": 1}
 PATHS = {"auto": 0, "cuda_core": 1}
 # declared in include/esmf_energy.h
@@ -90,6 +91,8 @@ def load(path=None):
         L.esmf_fock_create_screened.restype = C.c_int
         L.esmf_fock_build.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         L.esmf_fock_build.restype = C.c_int
+        L.esmf_fock_build_batch.argtypes = [C.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.esmf_fock_build_batch.restype = C.c_int
         L.esmf_fock_build_noalloc.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp]
         L.esmf_fock_build_noalloc.restype = C.c_int
         L.esmf_fock_autotune.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int, vp, C.POINTER(C.c_int)]
@@ -185,6 +188,29 @@ def esmf_gvp_gradient(h, n_occ, c0, G, V, sigma, omega, mu, chi, scalars, dL_dsi
                                   float(mu), float(chi), _ptr(scalars), _ptr(dL_dsigma), _ptr(dL_dX),
                                   _stream_ptr(stream))
     _check(rc, "esmf_gvp_gradient")
+
+
+def esmf_fock_build_batch(handles, ms, Ds, Js, Ks, Fs=None, traces=None, stream=None):
+    """One batched build over several handles (see include/esmf_fock.h)."""
+    n = len(handles)
+    hv = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    mv = (C.c_int * n)(*[int(m) for m in ms])
+    arr = lambda ts: (C.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in ts])
+    rc = load().esmf_fock_build_batch(n, hv, mv, arr(Ds), arr(Js), arr(Ks),
+                                      arr(Fs) if Fs is not None else None,
+                                      arr(traces) if traces is not None else None, _stream_ptr(stream))
+    _check(rc, "esmf_fock_build_batch")
+
+
+def build_batch(builders, Ds, stream=None):
+    """Batched build for FockBuilders and their (m, N, N) CUDA float64 densities;
+    returns [(J, K)] device tensors."""
+    import torch
+    Js = [torch.empty_like(D) for D in Ds]
+    Ks = [torch.empty_like(D) for D in Ds]
+    esmf_fock_build_batch([b.h for b in builders], [D.shape[0] for D in Ds], [D.contiguous() for D in Ds],
+                          Js, Ks, stream=stream)
+    return list(zip(Js, Ks))
 
 
 def esmf_fock_build_noalloc(h, m, D, J, K, F=None, traces=None, stream=None):
