@@ -51,13 +51,15 @@ template <> struct Boys<float> {
 // Primitive-pair data of one function pair, structure of arrays in shared
 // memory: exponent sum p, product center P (relative to a local origin),
 // and weight K/p with K = w_a w_b exp(-ab/p |AB|^2).
+// Indexed [primitive pair][function pair], so that the lanes of a warp reading
+// primitive pair k of consecutive function pairs hit consecutive banks.
 template <typename T, int NPAIR, int MAXPP_>
 struct PairSmem {
-    T pe[NPAIR][MAXPP_];
-    T px[NPAIR][MAXPP_];
-    T py[NPAIR][MAXPP_];
-    T pz[NPAIR][MAXPP_];
-    T kw[NPAIR][MAXPP_];
+    T pe[MAXPP_][NPAIR];
+    T px[MAXPP_][NPAIR];
+    T py[MAXPP_][NPAIR];
+    T pz[MAXPP_][NPAIR];
+    T kw[MAXPP_][NPAIR];
     int npp[NPAIR];
 };
 
@@ -71,17 +73,17 @@ __device__ __forceinline__ T contracted_eri(const PairSmem<T, NPAIR, MAXPP_> &br
     T acc = T(0);
     const int nb = bra.npp[ib], nk = ket.npp[ik];
     for (int i = 0; i < nb; ++i) {
-        const T p = bra.pe[ib][i];
-        const T Px = bra.px[ib][i], Py = bra.py[ib][i], Pz = bra.pz[ib][i];
-        const T kb = bra.kw[ib][i] * T(kTwoPi52);
+        const T p = bra.pe[i][ib];
+        const T Px = bra.px[i][ib], Py = bra.py[i][ib], Pz = bra.pz[i][ib];
+        const T kb = bra.kw[i][ib] * T(kTwoPi52);
         T part = T(0);
         for (int k = 0; k < nk; ++k) {
-            const T q = ket.pe[ik][k];
-            const T dx = Px - ket.px[ik][k], dy = Py - ket.py[ik][k], dz = Pz - ket.pz[ik][k];
+            const T q = ket.pe[k][ik];
+            const T dx = Px - ket.px[k][ik], dy = Py - ket.py[k][ik], dz = Pz - ket.pz[k][ik];
             const T r2 = dx * dx + dy * dy + dz * dz;
             const T r = Boys<T>::rsq(p + q);
             const T rho = p * q * r * r;
-            part += ket.kw[ik][k] * r * Boys<T>::f0(rho * r2);
+            part += ket.kw[k][ik] * r * Boys<T>::f0(rho * r2);
         }
         acc += kb * part;
     }
@@ -130,11 +132,11 @@ __device__ __forceinline__ void fill_pairs(PairSmem<T, 128, MAXPP_> &ps, int bas
                     if (!(size[k] >= eps * smax)) continue;
                     const double a = exps[poff[p] + i], b = exps[poff[q] + j];
                     const double pe = a + b;
-                    ps.pe[slot][cnt] = (T)pe;
-                    ps.px[slot][cnt] = (T)((a * ax + b * bx) / pe - ox);
-                    ps.py[slot][cnt] = (T)((a * ay + b * by) / pe - oy);
-                    ps.pz[slot][cnt] = (T)((a * az + b * bz) / pe - oz);
-                    ps.kw[slot][cnt] = (T)kws[k];
+                    ps.pe[cnt][slot] = (T)pe;
+                    ps.px[cnt][slot] = (T)((a * ax + b * bx) / pe - ox);
+                    ps.py[cnt][slot] = (T)((a * ay + b * by) / pe - oy);
+                    ps.pz[cnt][slot] = (T)((a * az + b * bz) / pe - oz);
+                    ps.kw[cnt][slot] = (T)kws[k];
                     ++cnt;
                 }
         }

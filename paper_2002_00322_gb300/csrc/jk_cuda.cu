@@ -43,6 +43,29 @@ __device__ __forceinline__ bool kept_e(const double *qb, const double *qk, int e
     return qb[p * 8 + q] * qk[r * 8 + s] >= tol;
 }
 
+// Bank-conflict-free placement of the dense 8^4 tile in shared memory: element
+// (p q | r s), logical index ((p*8+q)*8+r)*8+s, is stored at
+//   logical XOR H(logical >> 5),
+// H linear over GF(2) (one 5-bit vector per index bit 5..11, found by search
+// and checked exhaustively).  In the contraction the 32 lanes of a warp take
+// 4 consecutive values of one index and all 8 of another, for every ordered
+// pair of the four indices; with H these 32 elements fall into 32 different
+// banks (FP32) or 16 different 8-byte slots twice (FP64).  H is linear and the
+// four indices occupy disjoint bit fields, so the placement of a sum of
+// per-index offsets is the XOR of their placements.
+__device__ __forceinline__ int tile_swizzle(int x) {
+    const int hi = x >> 5;
+    int h = 0;
+    if (hi & 1) h ^= 21;
+    if (hi & 2) h ^= 20;
+    if (hi & 4) h ^= 11;
+    if (hi & 8) h ^= 18;
+    if (hi & 16) h ^= 12;
+    if (hi & 32) h ^= 27;
+    if (hi & 64) h ^= 17;
+    return x ^ h;
+}
+
 __device__ __forceinline__ int scan256(int v, int *wsum) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int x = v;
@@ -72,20 +95,31 @@ struct JKSmem {
     int wsum[16];
     int active[12];
     int blk[4];
+    int tsw[4][8];            // tile_swizzle(v * stride[dim]) for each index and value
 };
 template <typename TA, int MC>
 struct JKSmemDirect : JKSmem<TA, MC, true> {
     PairSmem<TA, 128, MAXPP> pairs;
 };
 
+// CTAs of 256 threads that fit one SM by shared memory (at most 4): the
+// register budget is capped so that as many fit by registers too.
+template <typename TA, int MC, int SRC>
+constexpr int jk_ctas_per_sm() {
+    constexpr size_t bytes = SRC == 4 ? sizeof(JKSmemDirect<TA, MC>) : sizeof(JKSmem<TA, MC, false>);
+    constexpr int k = (int)((227 * 1024) / (bytes + 1024));
+    return k < 1 ? 1 : (k > 4 ? 4 : k);
+}
+
 // SRC: 0 fp64 store, 1 fp32 store, 2 fp16 hi+lo, 3 bf16 hi+lo, 4 direct (evaluated in TA)
 template <typename TA, int MC, int SRC>
-__global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a) {
+__global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cuda(JKArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     using SM = typename std::conditional<SRC == 4, JKSmemDirect<TA, MC>, JKSmem<TA, MC, false>>::type;
     SM &sm = *reinterpret_cast<SM *>(smraw);
     const int n = a.b.n, np = a.b.np;
     const int64_t nn = (int64_t)n * n, npnp = (int64_t)np * np;
+    if (threadIdx.x < 32) sm.tsw[threadIdx.x >> 3][threadIdx.x & 7] = tile_swizzle((threadIdx.x & 7) * c_stride[threadIdx.x >> 3]);
 
     for (int64_t bi = blockIdx.x; bi < a.nbricks; bi += gridDim.x) {
         const BrickDesc d = a.bricks[bi];
@@ -128,12 +162,23 @@ __global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a) {
             for (int j = 0; j < 16; ++j)
                 if (kept_e(sm.qb, sm.qk, e0 + j, a.tol, n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
             if constexpr (SRC == 4) {
+                // kept local indices listed in ascending order (in the density
+                // tiles' space, unused until the first chunk's barrier), then
+                // evaluated round-robin: a warp takes 32 consecutive kept
+                // elements, mostly of one bra pair, and the work is shared evenly
+                static_assert(sizeof(sm.Ds) >= BRICK * sizeof(unsigned short), "list does not fit");
+                unsigned short *klist = reinterpret_cast<unsigned short *>(&sm.Ds[0][0][0]);
+                int pos = scan256(__popc(mask), sm.wsum);
+                const int total = sm.wsum[15];
                 for (int j = 0; j < 16; ++j) {
                     const int e = e0 + j;
-                    TA v = TA(0);
-                    if (mask & (1u << j))
-                        v = contracted_eri<TA, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
-                    sm.V[e] = v;
+                    if (mask & (1u << j)) klist[pos++] = (unsigned short)e;
+                    else sm.V[tile_swizzle(e)] = TA(0);
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                    const int e = klist[i];
+                    sm.V[tile_swizzle(e)] = contracted_eri<TA, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
                 }
             } else {
                 int pos = scan256(__popc(mask), sm.wsum);
@@ -158,7 +203,7 @@ __global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a) {
                             v = (TA)((hi + lo) * inv);
                         }
                     }
-                    sm.V[e0 + j] = v;
+                    sm.V[tile_swizzle(e0 + j)] = v;
                 }
             }
         }
@@ -179,30 +224,35 @@ __global__ void __launch_bounds__(256) k_jk_cuda(JKArgs a) {
                 const bool isJ = slot >= 8;
                 const int tu = isJ ? (slot - 8) * 2 : slot;
                 const int A = c_tuple[tu][0], B = c_tuple[tu][1], C = c_tuple[tu][2], E = c_tuple[tu][3];
-                int base, s1, s2, dab, orow, ocol;
+                int base, dx, dab, orow, ocol;
                 if (!isJ) {   // output (a in A, c in C), terms (b in B, d in E)
                     const int ia = e >> 3, ic = e & 7;
-                    base = ia * c_stride[A] + ic * c_stride[C];
-                    s1 = c_stride[B]; s2 = c_stride[E];
+                    base = sm.tsw[A][ia] ^ sm.tsw[C][ic];
+                    dx = B;
                     dab = B * 4 + E;
                     orow = sm.blk[A] * 8 + ia; ocol = sm.blk[C] * 8 + ic;
                 } else {      // output (a in A, b in B), terms (c in C, d in E)
                     const int ia = e >> 3, ib = e & 7;
-                    base = ia * c_stride[A] + ib * c_stride[B];
-                    s1 = c_stride[C]; s2 = c_stride[E];
+                    base = sm.tsw[A][ia] ^ sm.tsw[B][ib];
+                    dx = C;
                     dab = C * 4 + E;
                     orow = sm.blk[A] * 8 + ia; ocol = sm.blk[B] * 8 + ib;
                 }
+                // placement of y * stride[E] from its three bits (the swizzle is linear)
+                const int t1 = sm.tsw[E][1], t2 = sm.tsw[E][2], t4 = sm.tsw[E][4];
                 TA acc[MC];
 #pragma unroll
                 for (int dd = 0; dd < MC; ++dd) acc[dd] = TA(0);
-                for (int x = 0; x < 8; ++x)
+                for (int x = 0; x < 8; ++x) {
+                    const int bx = base ^ sm.tsw[dx][x];
+#pragma unroll
                     for (int y = 0; y < 8; ++y) {
-                        const TA v = sm.V[base + x * s1 + y * s2];
+                        const TA v = sm.V[bx ^ ((y & 1) ? t1 : 0) ^ ((y & 2) ? t2 : 0) ^ ((y & 4) ? t4 : 0)];
                         const TA *dp = sm.Ds[dab][x * 8 + y];
 #pragma unroll
                         for (int dd = 0; dd < MC; ++dd) acc[dd] += v * dp[dd];
                     }
+                }
                 double *out = isJ ? a.Jacc : a.Kacc;
 #pragma unroll
                 for (int dd = 0; dd < MC; ++dd)

@@ -290,6 +290,7 @@ struct GenSmem {
     PairSmem<T, 128, MAXPP> pairs;
     double qb[64], qk[64];
     int wsum[16];
+    unsigned short klist[BRICK];   // local indices of the kept elements, ascending
 };
 
 // precision: 0 FP64 store (T = double), 1 FP32 store, 2 FP16 hi+lo, 3 BF16 hi+lo
@@ -317,51 +318,49 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
             sm.qk[t] = Q[(int64_t)(d.R * 8 + (t >> 3)) * b.np + d.S * 8 + (t & 7)];
         }
         __syncthreads();
+        // Thread t tests the 16 local indices [16t, 16t+16); the kept ones are
+        // listed in ascending order and then evaluated round-robin, so a warp
+        // takes 32 consecutive kept elements (mostly one bra pair: broadcast
+        // bra reads, distinct ket pairs) and the threads share the work evenly.
         const int e0 = threadIdx.x * 16;
         unsigned mask = 0;
         for (int j = 0; j < 16; ++j)
             if (elem_kept(sm.qb, sm.qk, e0 + j, tol, b.n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
         int total;
         int pos = block_excl_scan256(__popc(mask), sm.wsum, total);
-        T vals[16];
-        for (int j = 0; j < 16; ++j) {
-            T v = T(0);
-            if (mask & (1u << j)) {
-                const int e = e0 + j;
-                v = contracted_eri<T, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
-            }
-            vals[j] = v;
-        }
+        for (int j = 0; j < 16; ++j)
+            if (mask & (1u << j)) sm.klist[pos++] = (unsigned short)(e0 + j);
         const int64_t base = offsets[bi];
-        if (PREC == 0 || PREC == 1) {
-            T *out = reinterpret_cast<T *>(store) + base;
-            for (int j = 0; j < 16; ++j)
-                if (mask & (1u << j)) out[pos++] = vals[j];
-        } else {
+        uint32_t *rec = reinterpret_cast<uint32_t *>(store) + (PREC >= 2 ? base : 0);
+        if (PREC >= 2) {
             // record: 512-byte keep mask, then the kept values as (hi | lo << 16)
             // words of the value times the store's power-of-two scale
-            uint32_t *rec = reinterpret_cast<uint32_t *>(store) + base;
             unsigned char *mk = reinterpret_cast<unsigned char *>(rec);
             mk[2 * threadIdx.x] = (unsigned char)(mask & 0xffu);
             mk[2 * threadIdx.x + 1] = (unsigned char)(mask >> 8);
-            uint32_t *out = rec + MASK_WORDS;
-            for (int j = 0; j < 16; ++j)
-                if (mask & (1u << j)) {
-                    const double xs = (double)vals[j] * (double)vscale;
-                    uint16_t hb, lb;
-                    if (PREC == 2) {
-                        __half h = __double2half(xs);
-                        __half l = __double2half(xs - (double)__half2float(h));
-                        hb = __half_as_ushort(h);
-                        lb = __half_as_ushort(l);
-                    } else {
-                        __nv_bfloat16 h = __double2bfloat16(xs);
-                        __nv_bfloat16 l = __double2bfloat16(xs - (double)__bfloat162float(h));
-                        hb = __bfloat16_as_ushort(h);
-                        lb = __bfloat16_as_ushort(l);
-                    }
-                    out[pos++] = (uint32_t)hb | ((uint32_t)lb << 16);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int e = sm.klist[i];
+            const T v = contracted_eri<T, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
+            if (PREC == 0 || PREC == 1) {
+                reinterpret_cast<T *>(store)[base + i] = v;
+            } else {
+                const double xs = (double)v * (double)vscale;
+                uint16_t hb, lb;
+                if (PREC == 2) {
+                    __half h = __double2half(xs);
+                    __half l = __double2half(xs - (double)__half2float(h));
+                    hb = __half_as_ushort(h);
+                    lb = __half_as_ushort(l);
+                } else {
+                    __nv_bfloat16 h = __double2bfloat16(xs);
+                    __nv_bfloat16 l = __double2bfloat16(xs - (double)__bfloat162float(h));
+                    hb = __bfloat16_as_ushort(h);
+                    lb = __bfloat16_as_ushort(l);
                 }
+                rec[MASK_WORDS + i] = (uint32_t)hb | ((uint32_t)lb << 16);
+            }
         }
     }
 }
