@@ -464,6 +464,53 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ serving
+def serve_against_plain_fp64(args, mols, reqs, dens, budget, local):
+    """The plain FP64 GPU build on a bounded prefix of the same request stream:
+    one request at a time, FP64 integral stores (integral-direct when a store
+    is over budget), no batching or graphs, cold start; requests are taken in
+    order until about --serve-fp64-seconds have passed.  The served form
+    (split FP16 stores on tensor cores, concurrent slots, graph replay) then
+    serves the same prefix from a cold start, and its J, K are compared with
+    the FP64 results (worst relative Frobenius error over requests and k)."""
+    import numpy as np
+    from paper_2002_00322_gb300.server import Server
+    plain = []
+    with Server(budget, max_inflight=1, precision="fp64", use_graphs=False, device=local) as srv:
+        ids = {}
+        t0 = time.perf_counter()
+        for (i, _, _), D in zip(reqs, dens):
+            if plain and time.perf_counter() - t0 >= args.serve_fp64_seconds:
+                break
+            if i not in ids:
+                ids[i] = srv.register(mols[i].basis, mols[i].tol)
+            J, K, _ = srv.wait(srv.submit(ids[i], D))
+            plain.append((J, K))
+        plain_s = time.perf_counter() - t0
+        st_plain = srv.stats()
+    k = len(plain)
+    with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True,
+                device=local) as srv:
+        ids = {}
+        for (i, _, _) in reqs[:k]:
+            if i not in ids:
+                ids[i] = srv.register(mols[i].basis, mols[i].tol)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(ids[i], D) for (i, _, _), D in zip(reqs[:k], dens[:k])]
+        served = [srv.wait(t) for t in tickets]
+        served_s = time.perf_counter() - t0
+
+    def worst(a, b):
+        return max(float(np.linalg.norm(x - r) / max(np.linalg.norm(r), 1e-300)) for x, r in zip(a, b))
+    ej = max(worst(s[0], p[0]) for s, p in zip(served, plain))
+    ek = max(worst(s[1], p[1]) for s, p in zip(served, plain))
+    return {"requests": k, "n_basis": [int(mols[i].basis.n) for (i, _, _) in reqs[:k]],
+            "plain_fp64_seconds": round(plain_s, 3), "plain_fp64_builds_per_s": round(k / plain_s, 3),
+            "plain_fp64_creates": st_plain["creates"], "plain_fp64_p50_ms": round(st_plain["p50_ms"], 2),
+            "served_seconds": round(served_s, 3), "served_builds_per_s": round(k / served_s, 3),
+            "speedup": round(plain_s / served_s, 2),
+            "served_vs_fp64_max_rel_err": {"J": ej, "K": ek}}
+
+
 def run_serving(args):
     """Serving workload: 256 requests over a pool of 32 random molecules
     (N uniform in [50, 600], m uniform in [4, 32]) on one build server with a
@@ -511,6 +558,7 @@ def run_serving(args):
             srv.wait(t)
         open_s = time.perf_counter() - t0
         st_open = srv.stats()
+    out["vs_plain_fp64"] = serve_against_plain_fp64(args, mols, reqs, dens, budget, local)
     out["value"] = round(len(reqs) / closed_s, 3)
     out["closed_loop"] = {"seconds": round(closed_s, 3), "creates": st_closed["creates"],
                           "evictions": st_closed["evictions"], "graph_launches": st_closed["graph_launches"],
@@ -544,6 +592,8 @@ def main():
     ap.add_argument("--serve-nmax", type=int, default=600)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-fp64-seconds", type=float, default=60.0,
+                    help="time bound of the plain FP64 leg of --serving (a prefix of the stream)")
     args = ap.parse_args()
     if args.serving:
         run_serving(args)
