@@ -487,21 +487,35 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     }
     offs.push_back(off);
     // runs share (P, Q, R) inside an item; items share (P, Q, S window); the
-    // brick (P Q | P Q) is a run and an item of its own
+    // brick (P Q | P Q) is a run and an item of its own.  An item holds at
+    // most kItemRuns runs: its window regions sum every run's contributions in
+    // FP32 tensor memory before their FP64 flush, so the cap bounds that
+    // accumulation length (and its rounding error) for large molecules; up to
+    // 8 * kItemRuns functions no item is split.
     {
+        constexpr int kItemRuns = 32;
         auto diag = [&](size_t i) { return kept[i].R == kept[i].P && kept[i].S == kept[i].Q; };
-        auto same_item = [&](size_t i, size_t j) {
+        auto same_window = [&](size_t i, size_t j) {
             return kept[i].P == kept[j].P && kept[i].Q == kept[j].Q && kept[i].S / SWIN == kept[j].S / SWIN &&
                    !diag(i) && !diag(j);
         };
-        auto same_run = [&](size_t i, size_t j) { return same_item(i, j) && kept[i].R == kept[j].R; };
-        for (size_t i = 0; i < kept.size(); ++i) {
-            const bool fr = i == 0 || !same_run(i, i - 1);
-            const bool lr = i + 1 == kept.size() || !same_run(i, i + 1);
-            const bool fi = i == 0 || !same_item(i, i - 1);
-            const bool li = i + 1 == kept.size() || !same_item(i, i + 1);
-            kept[i].pad = (fr ? BRICK_RUN_FIRST : 0) | (lr ? BRICK_RUN_LAST : 0) | (fi ? BRICK_ITEM_FIRST : 0) |
-                          (li ? BRICK_ITEM_LAST : 0);
+        const size_t nk = kept.size();
+        std::vector<char> first_run(nk), first_item(nk);
+        int runs = 0;
+        for (size_t i = 0; i < nk; ++i) {
+            bool fi = i == 0 || !same_window(i, i - 1);
+            const bool fr = fi || kept[i].R != kept[i - 1].R;
+            if (!fi && fr && runs == kItemRuns) fi = true;
+            if (fi) runs = 0;
+            if (fr) ++runs;
+            first_run[i] = fr;
+            first_item[i] = fi;
+        }
+        for (size_t i = 0; i < nk; ++i) {
+            const bool lr = i + 1 == nk || first_run[i + 1];
+            const bool li = i + 1 == nk || first_item[i + 1];
+            kept[i].pad = (first_run[i] ? BRICK_RUN_FIRST : 0) | (lr ? BRICK_RUN_LAST : 0) |
+                          (first_item[i] ? BRICK_ITEM_FIRST : 0) | (li ? BRICK_ITEM_LAST : 0);
         }
     }
     // split 16-bit stores: one power-of-two scale with |value * scale| < 2^14
