@@ -109,50 +109,44 @@ __device__ __forceinline__ int tile_off(int row, int k) {
     return (row & 7) * 16 + (k & 7) * 2 + (k >> 3) * 128 + (row >> 3) * 1024;
 }
 
+// Density tiles of one pass (densities d0 .. d0+mp-1; rows kk >= m are zero):
+// K bank, tile (X,Y) of nb*nb, rows kk / mp+kk / 2mp+kk / 3mp+kk hold D_hi,
+// D^T_hi, D_lo, D^T_lo at k = b*8 + d (D[X*8+b][Y*8+d], and for the
+// transposed parts D[Y*8+d][X*8+b]); J bank, lower block triangle X >= Y,
+// rows kk / mp+kk hold the hi / lo halves of D[X*8+b][Y*8+d] + D[Y*8+d][X*8+b]
+// (the first term alone on the diagonal block).  One block per (row p of the
+// padded matrix, kk): each thread converts one element (p, q) once and writes
+// its four K-bank halves and, for X >= Y, its two J-bank halves, so every
+// position of both banks is written exactly once per pass.
 __global__ void k_dbank(const double *D, int n, int nb, int m, int d0, int mp, const unsigned int *dmax_bits,
                         int bf16, uint16_t *kbank, uint16_t *jbank) {
-    const float sD = density_scale(dmax_bits);
-    const int64_t nn = (int64_t)n * n;
+    const double sD = (double)density_scale(dmax_bits);
+    const int np = nb * 8;
+    const int p = blockIdx.x, kk = blockIdx.y;
+    const int X = p >> 3, b = p & 7;
     const int F = 4 * mp, G = 2 * mp;
-    const int64_t kcount = (int64_t)nb * nb * F * 64;
-    const int64_t jcount = (int64_t)nb * (nb + 1) / 2 * G * 64;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kcount + jcount;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        if (e < kcount) {
-            const int kidx = (int)(e & 63);
-            const int row = (int)((e >> 6) % F);
-            const int64_t t = (e >> 6) / F;
-            const int X = (int)(t / nb), Y = (int)(t % nb);
-            const int kk = row % mp, part = row / mp;           // 0 D_hi, 1 D^T_hi, 2 D_lo, 3 D^T_lo
-            const int b = kidx >> 3, dd = kidx & 7;
-            const int k = d0 + kk;
-            double v = 0.0;
-            int r0, c0;
-            if (part & 1) { r0 = Y * 8 + dd; c0 = X * 8 + b; }
-            else { r0 = X * 8 + b; c0 = Y * 8 + dd; }
-            if (kk < m && r0 < n && c0 < n) v = D[(int64_t)k * nn + (int64_t)r0 * n + c0];
-            const float x = (float)(v * (double)sD);
-            kbank[t * (F * 64) + (tile_off(row, kidx) >> 1)] = split16(x, part >= 2, bf16);
-        } else {
-            const int64_t f = e - kcount;
-            const int kidx = (int)(f & 63);
-            const int row = (int)((f >> 6) % G);
-            const int64_t t = (f >> 6) / G;
-            int X = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-            while ((int64_t)X * (X + 1) / 2 > t) --X;
-            while ((int64_t)(X + 1) * (X + 2) / 2 <= t) ++X;
-            const int Y = (int)(t - (int64_t)X * (X + 1) / 2);
-            const int kk = row % mp, part = row / mp;           // 0 Dj_hi, 1 Dj_lo
-            const int b = kidx >> 3, dd = kidx & 7;
-            const int k = d0 + kk;
-            double v = 0.0;
-            const int r0 = X * 8 + b, c0 = Y * 8 + dd;
-            if (kk < m && r0 < n && c0 < n) {
-                v = D[(int64_t)k * nn + (int64_t)r0 * n + c0];
-                if (X != Y) v += D[(int64_t)k * nn + (int64_t)c0 * n + r0];
-            }
-            const float x = (float)(v * (double)sD);
-            jbank[t * (G * 64) + (tile_off(row, kidx) >> 1)] = split16(x, part, bf16);
+    const bool live = kk < m && p < n;
+    const double *Dk = D + (int64_t)(d0 + kk) * n * n;
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+        const int Y = q >> 3, d = q & 7;
+        const bool in = live && q < n;
+        const double v = in ? Dk[(int64_t)p * n + q] : 0.0;
+        const float x = (float)(v * sD);
+        const uint16_t hi = split16(x, 0, bf16), lo = split16(x, 1, bf16);
+        uint16_t *kt = kbank + ((int64_t)X * nb + Y) * (F * 64);
+        const int o1 = tile_off(kk, b * 8 + d) >> 1, o3 = tile_off(2 * mp + kk, b * 8 + d) >> 1;
+        kt[o1] = hi;
+        kt[o3] = lo;
+        uint16_t *kt2 = kbank + ((int64_t)Y * nb + X) * (F * 64);
+        kt2[tile_off(mp + kk, d * 8 + b) >> 1] = hi;
+        kt2[tile_off(3 * mp + kk, d * 8 + b) >> 1] = lo;
+        if (X >= Y) {
+            double vj = v;
+            if (X != Y && in) vj += Dk[(int64_t)q * n + p];
+            const float xj = (X != Y) ? (float)(vj * sD) : x;
+            uint16_t *jt = jbank + ((int64_t)X * (X + 1) / 2 + Y) * (G * 64);
+            jt[tile_off(kk, b * 8 + d) >> 1] = split16(xj, 0, bf16);
+            jt[tile_off(mp + kk, b * 8 + d) >> 1] = split16(xj, 1, bf16);
         }
     }
 }
@@ -697,10 +691,8 @@ int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s) {
             const UmmaLaunch &L = Ls[i];
             if (d0 >= L.m) continue;
             const int mc = (L.m - d0) < MPMAX ? (L.m - d0) : MPMAX;
-            const int64_t work = (int64_t)L.nb * L.nb * 4 * MPMAX * 64 + (int64_t)L.nb * (L.nb + 1) / 2 * 2 * MPMAX * 64;
-            int g = (int)((work + 255) / 256);
-            if (g > 4096) g = 4096;
-            k_dbank<<<g, 256, 0, s>>>(L.D, L.n, L.nb, mc, d0, MPMAX, L.dmax_bits, L.bf16, L.kbank, L.jbank);
+            k_dbank<<<dim3(L.nb * 8, MPMAX), 256, 0, s>>>(L.D, L.n, L.nb, mc, d0, MPMAX, L.dmax_bits, L.bf16,
+                                                          L.kbank, L.jbank);
             if (L.nbricks == 0) continue;
             UmmaEntry &E = p.e[p.nentries++];
             E.bricks = L.bricks; E.nbricks = L.nbricks; E.offsets = L.offsets; E.store = L.store;
@@ -736,10 +728,7 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
     for (int d0 = 0; d0 < L.m; d0 += chunk) {
         const int mc = (L.m - d0) < chunk ? (L.m - d0) : chunk;
         const int mp = mc <= 8 ? 8 : 16;
-        const int64_t work = (int64_t)L.nb * L.nb * 4 * mp * 64 + (int64_t)L.nb * (L.nb + 1) / 2 * 2 * mp * 64;
-        int g = (int)((work + 255) / 256);
-        if (g > 4096) g = 4096;
-        k_dbank<<<g, 256, 0, s>>>(L.D, L.n, L.nb, mc, d0, mp, L.dmax_bits, L.bf16, L.kbank, L.jbank);
+        k_dbank<<<dim3(L.nb * 8, mp), 256, 0, s>>>(L.D, L.n, L.nb, mc, d0, mp, L.dmax_bits, L.bf16, L.kbank, L.jbank);
         e = cudaGetLastError();
         if (e != cudaSuccess) { set_error("k_dbank: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
         if (L.nbricks == 0) continue;
@@ -765,23 +754,24 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
 }
 
 // J from the lower block triangle of the block-major accumulators, F = 2J - K,
-// t_k = sum_pq D_k[pq] F_k[pq]; outputs in the caller's [k][p][q] layout.
+// t_k = sum_pq D_k[pq] F_k[pq]; outputs in the caller's [k][p][q] layout.  One
+// block per (row p, density k), threads over the columns q.
 __global__ void k_finalize_blocked(int n, int nb, int m, const double *D, const double *Jb,
                                    const double *Kb, double *J, double *K, double *F, double *tsum) {
-    const int k = blockIdx.y;
-    const int64_t nn = (int64_t)n * n;
+    const int p = blockIdx.x, k = blockIdx.y;
+    const int X = p >> 3, x = p & 7;
+    const int64_t row = (int64_t)k * n * n + (int64_t)p * n;
     double part = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
-        const int p = (int)(e / n), q = (int)(e % n);
-        const int X = p >> 3, Y = q >> 3, x = p & 7, y = q & 7;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int Y = q >> 3, y = q & 7;
         const double jv = (X >= Y) ? Jb[(((int64_t)X * nb + Y) * m + k) * 64 + x * 8 + y]
                                    : Jb[(((int64_t)Y * nb + X) * m + k) * 64 + y * 8 + x];
         const double kv = Kb[(((int64_t)X * nb + Y) * m + k) * 64 + x * 8 + y];
         const double fv = 2.0 * jv - kv;
-        J[k * nn + e] = jv;
-        K[k * nn + e] = kv;
-        if (F) F[k * nn + e] = fv;
-        part += D[k * nn + e] * fv;
+        J[row + q] = jv;
+        K[row + q] = kv;
+        if (F) F[row + q] = fv;
+        part += D[row + q] * fv;
     }
     if (tsum) {
         __shared__ double red[8];
@@ -798,10 +788,9 @@ __global__ void k_finalize_blocked(int n, int nb, int m, const double *D, const 
 
 int launch_finalize_blocked(const DevBasis &b, int m, const double *D, const double *Jb, const double *Kb,
                             double *J, double *K, double *F, double *tsum, cudaStream_t s) {
-    const int64_t nn = (int64_t)b.n * b.n;
-    int gx = (int)((nn + 255) / 256);
-    if (gx > 512) gx = 512;
-    k_finalize_blocked<<<dim3(gx, m), 256, 0, s>>>(b.n, b.nb, m, D, Jb, Kb, J, K, F, tsum);
+    if (b.n < 1 || m < 1) return ESMF_OK;
+    const int threads = b.n <= 128 ? 128 : 256;
+    k_finalize_blocked<<<dim3(b.n, m), threads, 0, s>>>(b.n, b.nb, m, D, Jb, Kb, J, K, F, tsum);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_error("k_finalize_blocked: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
     return ESMF_OK;

@@ -68,3 +68,23 @@ def test_full_c4_sampled(esmf, prec, tol):
     ek = max(np.max(np.abs(K[k][kidx[:, 0], kidx[:, 1]] - Ke[k])) / np.max(np.abs(K[k])) for k in range(w.m))
     print(f"\nPRECISION {w.name} stored/{prec} sampled elements (relative to max|X_k|): J {ej:.2e} K {ek:.2e}")
     assert ej <= tol and ek <= tol
+
+
+def test_full_c4_split_against_fp32(esmf):
+    """Whole matrices at the full C4 size (400 functions, 50 function blocks,
+    so the tensor-core path splits items at 32 R blocks): the split FP16 build
+    against the FP32 CUDA-core build (itself within about 2e-7 of FP64),
+    relative Frobenius error of every J_k and K_k."""
+    import torch
+    w = W.precision()
+    D = torch.from_numpy(w.D).cuda()
+    out = {}
+    for prec in ("fp32", "fp16x2"):
+        with esmf.FockBuilder(w.basis, w.tol, "stored", prec) as fb:
+            J, K, _, _ = fb.build(D, want_traces=False)
+            out[prec] = (J.cpu().numpy(), K.cpu().numpy())
+    (J32, K32), (J16, K16) = out["fp32"], out["fp16x2"]
+    ej = max(rel(J16[k], J32[k]) for k in range(w.m))
+    ek = max(rel(K16[k], K32[k]) for k in range(w.m))
+    print(f"\nPRECISION {w.name} stored/fp16x2 vs stored/fp32, whole matrices: J {ej:.2e} K {ek:.2e}")
+    assert ej <= 2e-6 and ek <= 2e-6
