@@ -52,6 +52,11 @@ struct esmf_fock {
     int64_t nbricks = 0;
     int64_t *offsets = nullptr;
     void *store = nullptr;
+    // integral-direct mode: primitive-pair table, one entry per block pair a
+    // kept brick uses (entry of (B1, B2) at pslot[B1 * nb + B2])
+    void *ptab = nullptr;
+    int *pslot = nullptr, *pblocks = nullptr;
+    int n_ptab = 0;
     float vscale = 1.0f;           // power-of-two scale of split 16-bit stores
     int path = ESMF_PATH_AUTO;
     std::vector<std::pair<int, int>> tuned;   // (m, densities per pass) picked by esmf_fock_autotune
@@ -192,6 +197,7 @@ void release(esmf_fock *h) {
     if (h->S != h->Q) cudaFree(h->S);
     cudaFree(h->Q);
     cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts);
+    cudaFree(h->ptab); cudaFree(h->pslot); cudaFree(h->pblocks);
     cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
     if (h->err_host) cudaFreeHost(h->err_host);
     cudaFree(h->Jacc); cudaFree(h->Kacc); cudaFree(h->ework);
@@ -548,6 +554,7 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     h->mode = use_mode;
     if (use_mode != ESMF_MODE_STORED) h->store_bytes = 0;
 
+    std::vector<int> pslot_h, pblocks_h;
     if (h->nbricks > 0) {
         if ((rc = dalloc(h, &h->bricks, h->nbricks))) return fail(rc);
         if (!ck(cudaMemcpyAsync(h->bricks, kept.data(), sizeof(BrickDesc) * h->nbricks, cudaMemcpyHostToDevice, cs), "copy kept bricks"))
@@ -567,6 +574,28 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
             if ((rc = launch_brick_generate(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec,
                                             h->store, h->vscale, s)))
                 return fail(rc);
+        } else {
+            // integral-direct: the primitive pairs of every block pair that a
+            // kept brick uses as bra or ket, formed once here instead of in
+            // every brick of every build
+            pslot_h.assign((size_t)h->nb * h->nb, -1);
+            auto use = [&](int X, int Y) {
+                int &e = pslot_h[(size_t)X * h->nb + Y];
+                if (e < 0) {
+                    e = (int)(pblocks_h.size() / 2);
+                    pblocks_h.push_back(X);
+                    pblocks_h.push_back(Y);
+                }
+            };
+            for (const BrickDesc &d : kept) { use(d.P, d.Q); use(d.R, d.S); }
+            h->n_ptab = (int)(pblocks_h.size() / 2);
+            if ((rc = dalloc(h, &h->pslot, pslot_h.size())) || (rc = dalloc(h, &h->pblocks, pblocks_h.size())) ||
+                (rc = dalloc(h, (unsigned char **)&h->ptab, (size_t)h->n_ptab * pair_table_entry_bytes(h->prec))))
+                return fail(rc);
+            if (!ck(cudaMemcpyAsync(h->pslot, pslot_h.data(), sizeof(int) * pslot_h.size(), cudaMemcpyHostToDevice, cs), "copy pair slots") ||
+                !ck(cudaMemcpyAsync(h->pblocks, pblocks_h.data(), sizeof(int) * pblocks_h.size(), cudaMemcpyHostToDevice, cs), "copy pair blocks"))
+                return fail(ESMF_ERR_CUDA);
+            if ((rc = launch_pair_table(db, h->pblocks, h->n_ptab, h->prec, h->ptab, s))) return fail(rc);
         }
     }
     if (!ck(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming), "event")) return fail(ESMF_ERR_CUDA);
@@ -611,6 +640,7 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
         a.offsets = h->offsets ? h->offsets + b0 : nullptr; a.store = h->store; a.precision = h->prec;
         a.mode = h->mode;
         a.m = m; a.D = D; a.Jacc = h->Jacc; a.Kacc = h->Kacc;
+        a.ptab = h->ptab; a.pslot = h->pslot;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->timing && h->ev_used < 65536) {
             if (h->ev_used == h->ev_pool.size()) {
@@ -994,6 +1024,7 @@ int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, in
     a->offsets = h->offsets; a->store = h->store; a->precision = h->prec; a->mode = h->mode;
     a->m = m; a->D = D; a->Jacc = nullptr; a->Kacc = nullptr;
     a->vscale = h->vscale;
+    a->ptab = h->ptab; a->pslot = h->pslot;
     *device = h->device;
     *split = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
     return ESMF_OK;

@@ -68,6 +68,12 @@ int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const 
                           float vscale, cudaStream_t s);
 
 // ---- jk_cuda.cu (CUDA-core contraction)
+// primitive-pair table of integral-direct handles: one entry per function-
+// block pair (B1, B2), B1 >= B2, that some kept brick uses as bra or ket
+size_t pair_table_entry_bytes(int precision);
+int launch_pair_table(const DevBasis &b, const int *blocks, int nentries, int precision, void *tab,
+                      cudaStream_t s);
+
 struct JKArgs {
     DevBasis b;
     const double *Q;
@@ -83,6 +89,8 @@ struct JKArgs {
     double *Jacc, *Kacc;      // m x np x np accumulators (zeroed by caller)
     float vscale;             // store scale of the split 16-bit precisions
     int mc = 0;               // densities per pass (0: default for the precision)
+    const void *ptab = nullptr;     // direct mode: pair table (PairTable<TA> entries)
+    const int *pslot = nullptr;     // direct mode: entry of block pair (B1, B2) at B1 * nb + B2
 };
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s);
 int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s);

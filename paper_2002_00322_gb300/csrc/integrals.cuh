@@ -90,9 +90,51 @@ __device__ __forceinline__ T contracted_eri(const PairSmem<T, NPAIR, MAXPP_> &br
     return acc;
 }
 
+// Primitive pairs of the function pair (p, q), leaving out those too small
+// to matter: calls out(c, p_ab, Px, Py, Pz, K_ab / p_ab) for c = 0, 1, ...
+// with the absolute product center in FP64, and returns the count.
+// Primitive-pair screening: a pair whose weight K/p times p^(-1/2) (its
+// contribution to any integral, up to the ket factors) is below eps of the
+// largest pair of this function pair is left out; the relative change of an
+// integral stays below about 1e4 eps (the ratio of Boys-function and
+// prefactor extremes), under the precision of T (FP32: 1e-12; FP64 drops
+// only underflowing pairs).  Shared by the per-brick fill below and by the
+// pair table of integral-direct handles, so both give the same integrals.
+template <typename T, int MAXPP_, typename Out>
+__device__ __forceinline__ int pair_prims(int p, int q, const double *center, const int *nprim, const int *poff,
+                                          const double *exps, const double *w, Out &&out) {
+    const int np_ = nprim[p], nq_ = nprim[q];
+    const double ax = center[3 * p], ay = center[3 * p + 1], az = center[3 * p + 2];
+    const double bx = center[3 * q], by = center[3 * q + 1], bz = center[3 * q + 2];
+    const double ab2 = (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
+    double kws[MAXPP_];
+    float size[MAXPP_], smax = 0.0f;
+    for (int i = 0; i < np_; ++i)
+        for (int j = 0; j < nq_; ++j) {
+            const int k = i * nq_ + j;
+            const double a = exps[poff[p] + i], b = exps[poff[q] + j];
+            const double pe = a + b;
+            kws[k] = w[poff[p] + i] * w[poff[q] + j] * exp(-a * b / pe * ab2) / pe;
+            size[k] = fabsf((float)kws[k]) * rsqrtf((float)pe);
+            smax = fmaxf(smax, size[k]);
+        }
+    const float eps = sizeof(T) == 4 ? 1e-12f : 1e-30f;
+    int cnt = 0;
+    for (int i = 0; i < np_; ++i)
+        for (int j = 0; j < nq_; ++j) {
+            const int k = i * nq_ + j;
+            if (!(size[k] >= eps * smax)) continue;
+            const double a = exps[poff[p] + i], b = exps[poff[q] + j];
+            const double pe = a + b;
+            const double Px = (a * ax + b * bx) / pe, Py = (a * ay + b * by) / pe, Pz = (a * az + b * bz) / pe;
+            out(cnt, pe, Px, Py, Pz, kws[k]);
+            ++cnt;
+        }
+    return cnt;
+}
+
 // Fill pair data for the 64 ordered pairs (p, q) of function blocks (PB, QB)
-// with local origin (ox, oy, oz), leaving out primitive pairs too small to
-// matter (below).  Called by all threads of a block.
+// with local origin (ox, oy, oz).  Called by all threads of a block.
 template <typename T, int MAXPP_>
 __device__ __forceinline__ void fill_pairs(PairSmem<T, 128, MAXPP_> &ps, int base, int PB, int QB,
                                            const double *center, const int *nprim, const int *poff,
@@ -102,45 +144,51 @@ __device__ __forceinline__ void fill_pairs(PairSmem<T, 128, MAXPP_> &ps, int bas
         const int p = PB * 8 + (t >> 3), q = QB * 8 + (t & 7);
         const int slot = base + t;
         int cnt = 0;
-        if (p < np && q < np) {
-            const int np_ = nprim[p], nq_ = nprim[q];
-            const double ax = center[3 * p], ay = center[3 * p + 1], az = center[3 * p + 2];
-            const double bx = center[3 * q], by = center[3 * q + 1], bz = center[3 * q + 2];
-            const double ab2 = (ax - bx) * (ax - bx) + (ay - by) * (ay - by) + (az - bz) * (az - bz);
-            double kws[MAXPP_];
-            float size[MAXPP_], smax = 0.0f;
-            for (int i = 0; i < np_; ++i)
-                for (int j = 0; j < nq_; ++j) {
-                    const int k = i * nq_ + j;
-                    const double a = exps[poff[p] + i], b = exps[poff[q] + j];
-                    const double pe = a + b;
-                    kws[k] = w[poff[p] + i] * w[poff[q] + j] * exp(-a * b / pe * ab2) / pe;
-                    size[k] = fabsf((float)kws[k]) * rsqrtf((float)pe);
-                    smax = fmaxf(smax, size[k]);
-                }
-            // Primitive-pair screening: a pair whose weight K/p times p^(-1/2)
-            // (its contribution to any integral, up to the ket factors) is
-            // below eps of the largest pair of this function pair is left
-            // out; the relative change of an integral stays below about
-            // 1e4 eps (the ratio of Boys-function and prefactor extremes),
-            // under the precision of T (FP32: 1e-12; FP64 drops only
-            // underflowing pairs).
-            const float eps = sizeof(T) == 4 ? 1e-12f : 1e-30f;
-            for (int i = 0; i < np_; ++i)
-                for (int j = 0; j < nq_; ++j) {
-                    const int k = i * nq_ + j;
-                    if (!(size[k] >= eps * smax)) continue;
-                    const double a = exps[poff[p] + i], b = exps[poff[q] + j];
-                    const double pe = a + b;
-                    ps.pe[cnt][slot] = (T)pe;
-                    ps.px[cnt][slot] = (T)((a * ax + b * bx) / pe - ox);
-                    ps.py[cnt][slot] = (T)((a * ay + b * by) / pe - oy);
-                    ps.pz[cnt][slot] = (T)((a * az + b * bz) / pe - oz);
-                    ps.kw[cnt][slot] = (T)kws[k];
-                    ++cnt;
-                }
-        }
+        if (p < np && q < np)
+            cnt = pair_prims<T, MAXPP_>(p, q, center, nprim, poff, exps, w,
+                                        [&](int c, double pe, double Px, double Py, double Pz, double kw) {
+                                            ps.pe[c][slot] = (T)pe;
+                                            ps.px[c][slot] = (T)(Px - ox);
+                                            ps.py[c][slot] = (T)(Py - oy);
+                                            ps.pz[c][slot] = (T)(Pz - oz);
+                                            ps.kw[c][slot] = (T)kw;
+                                        });
         ps.npp[slot] = cnt;
+    }
+}
+
+// Primitive-pair data of one function-block pair (B1, B2), B1 >= B2, for
+// integral-direct builds: the 64 ordered function pairs (B1*8 + t/8,
+// B2*8 + t%8), entries c < npp[t] valid, product centers absolute in FP64
+// (a brick subtracts its local origin when it loads them).
+template <typename T, int MAXPP_>
+struct PairTable {
+    T pe[MAXPP_][64];
+    double px[MAXPP_][64], py[MAXPP_][64], pz[MAXPP_][64];
+    T kw[MAXPP_][64];
+    int npp[64];
+};
+
+// Load the bra (slot base 0) and ket (slot base 64) pair data of a brick from
+// two table entries, subtracting the local origin.  Called by all threads.
+template <typename T, int MAXPP_>
+__device__ __forceinline__ void load_pairs(PairSmem<T, 128, MAXPP_> &ps, const PairTable<T, MAXPP_> &bra,
+                                           const PairTable<T, MAXPP_> &ket, double ox, double oy, double oz) {
+    for (int t = threadIdx.x; t < 2 * 64 * MAXPP_; t += blockDim.x) {
+        const int side = t >= 64 * MAXPP_;
+        const int u = side ? t - 64 * MAXPP_ : t;
+        const int c = u >> 6, s = u & 63;
+        const PairTable<T, MAXPP_> &src = side ? ket : bra;
+        const int slot = side * 64 + s;
+        const int n = src.npp[s];
+        if (c == 0) ps.npp[slot] = n;
+        if (c < n) {
+            ps.pe[c][slot] = src.pe[c][s];
+            ps.px[c][slot] = (T)(src.px[c][s] - ox);
+            ps.py[c][slot] = (T)(src.py[c][s] - oy);
+            ps.pz[c][slot] = (T)(src.pz[c][s] - oz);
+            ps.kw[c][slot] = src.kw[c][s];
+        }
     }
 }
 

@@ -149,10 +149,10 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
         if constexpr (SRC == 4) {
             const int o = d.P * 8;
             const double ox = a.b.center[3 * o], oy = a.b.center[3 * o + 1], oz = a.b.center[3 * o + 2];
-            fill_pairs<TA, MAXPP>(sm.pairs, 0, d.P, d.Q, a.b.center, a.b.nprim, a.b.poff, a.b.exps,
-                                  a.b.w, np, ox, oy, oz);
-            fill_pairs<TA, MAXPP>(sm.pairs, 64, d.R, d.S, a.b.center, a.b.nprim, a.b.poff, a.b.exps,
-                                  a.b.w, np, ox, oy, oz);
+            // primitive pairs of (P,Q) and (R,S) from the handle's table
+            const PairTable<TA, MAXPP> *tab = reinterpret_cast<const PairTable<TA, MAXPP> *>(a.ptab);
+            load_pairs<TA, MAXPP>(sm.pairs, tab[a.pslot[d.P * a.b.nb + d.Q]], tab[a.pslot[d.R * a.b.nb + d.S]],
+                                  ox, oy, oz);
         }
         __syncthreads();
         // ---- dense brick tile
@@ -295,6 +295,10 @@ static int jk_launch_mc(const JKArgs &a, cudaStream_t s) {
 
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
     if (a.mode == ESMF_MODE_DIRECT) {
+        if (a.nbricks > 0 && (!a.ptab || !a.pslot)) {
+            set_error("launch_jk_cuda: integral-direct build without a pair table");
+            return ESMF_ERR_INVALID_ARG;
+        }
         if (a.precision == ESMF_PREC_FP64) return jk_launch_mc<double, 4>(a, s);
         return jk_launch_mc<float, 4>(a, s);
     }

@@ -365,6 +365,45 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
     }
 }
 
+// ---------------------------------------------------------------- pair table
+// Entry e holds the primitive pairs of function-block pair (blocks[2e],
+// blocks[2e+1]) for integral-direct builds; one 64-thread block per entry.
+template <typename T>
+__global__ void __launch_bounds__(64) k_pair_table(DevBasis b, const int *blocks, int nentries,
+                                                   PairTable<T, MAXPP> *tab) {
+    const int e = blockIdx.x;
+    if (e >= nentries) return;
+    PairTable<T, MAXPP> &te = tab[e];
+    const int t = threadIdx.x;
+    const int p = blocks[2 * e] * 8 + (t >> 3), q = blocks[2 * e + 1] * 8 + (t & 7);
+    int cnt = 0;
+    if (p < b.np && q < b.np)
+        cnt = pair_prims<T, MAXPP>(p, q, b.center, b.nprim, b.poff, b.exps, b.w,
+                                   [&](int c, double pe, double Px, double Py, double Pz, double kw) {
+                                       te.pe[c][t] = (T)pe;
+                                       te.px[c][t] = Px;
+                                       te.py[c][t] = Py;
+                                       te.pz[c][t] = Pz;
+                                       te.kw[c][t] = (T)kw;
+                                   });
+    te.npp[t] = cnt;
+}
+
+size_t pair_table_entry_bytes(int precision) {
+    return precision == ESMF_PREC_FP64 ? sizeof(PairTable<double, MAXPP>) : sizeof(PairTable<float, MAXPP>);
+}
+
+int launch_pair_table(const DevBasis &b, const int *blocks, int nentries, int precision, void *tab,
+                      cudaStream_t s) {
+    if (nentries < 1) return ESMF_OK;
+    if (precision == ESMF_PREC_FP64)
+        k_pair_table<double><<<nentries, 64, 0, s>>>(b, blocks, nentries, (PairTable<double, MAXPP> *)tab);
+    else
+        k_pair_table<float><<<nentries, 64, 0, s>>>(b, blocks, nentries, (PairTable<float, MAXPP> *)tab);
+    CK(cudaGetLastError());
+    return ESMF_OK;
+}
+
 template <typename T, int PREC>
 static int gen_launch(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                       int64_t nbricks, const int64_t *offsets, void *store, float vscale,
