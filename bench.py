@@ -272,8 +272,8 @@ def run_ours(args):
            "esmf_energy_gradient": energy,
            "esmf_gvp_gradient": gvp,
            "batched_uneven": batch}
-    if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_seconds)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_baseline(w, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     fb.close()
@@ -438,20 +438,98 @@ def cpu_baseline(w, budget_s=15.0, sample_pairs=None):
             "eval_s": round(t_eval, 2)}
 
 
+def _oracle_worker(lo, hi, rounds, seconds, barrier, results):
+    """One all-cores baseline worker (spawned process): integrals of bra pairs
+    [lo, hi) evaluated untimed, then `rounds` timed rounds of the grouped
+    contraction over them (about `seconds` each), each started together with
+    the other workers."""
+    sys.path.insert(0, ROOT)
+    from oracle.oracle import Oracle
+    from paper_2002_00322_gb300 import workloads as W
+    w = W.stored()
+    o = Oracle(w.basis)
+    lst, cnt = o.unique_list(w.tol, (lo, hi), 5_000_000)
+    for r in range(rounds):
+        barrier.wait(timeout=600)
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            o.jk_unique(w.D, w.tol, pair_range=(lo, hi), eri_list=lst)
+            reps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        results.put((r, cnt, (time.perf_counter() - t0) / reps))
+
+
+def cpu_baseline_all_cores(w, rounds=1, sample_pairs=20, seconds=4.0):
+    """The oracle loop in one spawned process per host core, each on its own
+    bra-pair sample, timed together: per round, the sum of their rates (kept-
+    quartet fraction per second = builds/s).  Returns (rates, description) or
+    (None, reason) when the processes could not run."""
+    import multiprocessing as mp
+    from oracle.oracle import Oracle
+    ncore = os.cpu_count() or 1
+    n = w.basis.n
+    npair = n * (n + 1) // 2
+    total = Oracle(w.basis).count_kept(w.tol)
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(ncore)
+    results = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker,
+                         args=(npair // 2 + i * sample_pairs, npair // 2 + (i + 1) * sample_pairs,
+                               rounds, seconds, barrier, results)) for i in range(ncore)]
+    per_round = [[] for _ in range(rounds)]
+    try:
+        for p in procs:
+            p.start()
+        for _ in range(rounds * ncore):
+            r, cnt, dt = results.get(timeout=600)
+            per_round[r].append(cnt / dt)
+    except Exception as e:
+        return None, f"{type(e).__name__}: {e}"
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    return [sum(x) / total for x in per_round], {
+        "cores": ncore,
+        "sample": f"{ncore} processes, each the grouped contraction over the stored kept integrals of its "
+                  f"own {sample_pairs} bra pairs from pair {npair // 2}, timed together (about {seconds} s); "
+                  f"rate = sum over processes of (kept-quartet fraction / seconds)"}
+
+
+def oracle_baseline(w, budget_s):
+    """cpu_baseline of the bench line: the oracle on all host cores, with the
+    single-core figure beside it (the single-core loop alone if the processes
+    cannot run)."""
+    single = cpu_baseline(w, budget_s=budget_s)
+    rates, info = cpu_baseline_all_cores(w)
+    if rates is None:
+        single["all_cores_unavailable"] = info
+        return single
+    return {"value": round(rates[0], 6), "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+            "sample": info["sample"], "single_core": single}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
     from paper_2002_00322_gb300 import workloads as W
     w = W.stored()
-    vals = []
-    cb = None
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(w, budget_s=4.0, sample_pairs=20)
-        if i >= args.warmup:
-            vals.append(cb["value"])
-    v = statistics.median(vals)
-    cb["value"] = round(v, 6)
+    rates, info = cpu_baseline_all_cores(w, rounds=args.warmup + args.steps, seconds=2.0)
+    single = cpu_baseline(w, budget_s=4.0, sample_pairs=20)
+    if rates is not None:
+        v = statistics.median(rates[args.warmup:])
+        cb = {"value": round(v, 6), "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+              "sample": info["sample"], "single_core": single}
+    else:                       # one core, one bounded sample per step
+        vals = [single["value"]]
+        for _ in range(args.steps - 1):
+            vals.append(cpu_baseline(w, budget_s=4.0, sample_pairs=20)["value"])
+        v = statistics.median(vals)
+        cb = dict(single, value=round(v, 6), all_cores_unavailable=info)
     out = {"metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 / v, 3) if v > 0 else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
