@@ -12,7 +12,10 @@
  * free, so requests that arrive while others run start as soon as resources
  * allow and their work overlaps on the device (one non-blocking CUDA stream
  * per slot).  Builds of one molecule are serialised; different molecules run
- * concurrently.  Each build can be replayed from a captured CUDA graph.
+ * concurrently.  Each build can be replayed from a captured CUDA graph, or,
+ * with batched ticks, the builds admitted together on the tensor-core path
+ * run as one esmf_fock_build_batch call: one persistent launch per pass of 16
+ * densities for all of them.
  *
  * Conventions as in esmf_fock.h: 0 or a negative ESMF_ERR_* code; buffers are
  * row-major float64; the caller owns them.
@@ -39,6 +42,8 @@ typedef struct {
     int64_t peak_inflight;      /* most requests on the device at once           */
     double p50_ms, p99_ms, mean_ms, max_ms;   /* submit-to-ready latency          */
     double span_s;              /* first submit to last completion               */
+    int64_t batch_launches;     /* batched ticks issued (ESMF_SERVER_BATCH)      */
+    int64_t batched_builds;     /* builds that ran inside a batched tick         */
 } esmf_server_stats_t;
 
 /*
@@ -46,12 +51,24 @@ typedef struct {
  *   budget_bytes  device memory the resident handles may hold (> 0)
  *   max_inflight  concurrent requests on the device, 1..64
  *   precision     ESMF_PREC_* used for every molecule's integral store
- *   use_graphs    non-zero: capture each (molecule, m, slot) build into a
- *                 CUDA graph once and replay it
- * Errors: INVALID_ARG, CUDA, OOM.
+ *   flags         ESMF_SERVER_GRAPHS: capture each (molecule, m, slot) build
+ *                 into a CUDA graph once and replay it;
+ *                 ESMF_SERVER_BATCH: batched ticks -- every pass of the
+ *                 worker collects the requests it admits whose molecule is on
+ *                 the tensor-core path (stored FP16X2/BF16X2), copies their
+ *                 inputs on their slots' streams and builds them together
+ *                 with esmf_fock_build_batch (up to ESMF_MAX_BATCH per call)
+ *                 on a stream of its own; other requests (molecules that fell
+ *                 back to integral-direct FP32 under the budget, or FP64/FP32
+ *                 servers) run as single builds, replayed from graphs when
+ *                 ESMF_SERVER_GRAPHS is also set.  The batching across
+ *                 molecules has no counterpart in the paper.
+ * Errors: INVALID_ARG (also for unknown flag bits), CUDA, OOM.
  */
+#define ESMF_SERVER_GRAPHS 1
+#define ESMF_SERVER_BATCH  2
 int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int precision,
-                       int use_graphs, esmf_server_t **out);
+                       int flags, esmf_server_t **out);
 
 /* Register a molecule (the basis is copied); returns its id in *basis_id.
  * The handle is created on the molecule's first request.  Errors: INVALID_ARG. */

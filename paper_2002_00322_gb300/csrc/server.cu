@@ -1,6 +1,8 @@
 // Build server (include/esmf_server.h): admission by device-memory budget, a
 // residency cache of per-molecule handles, continuous batching over
-// non-blocking streams, optional CUDA-graph replay, latency statistics.
+// non-blocking streams, optional CUDA-graph replay, optional batched ticks
+// (the tensor-path builds admitted together run as one persistent launch),
+// latency statistics.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,6 +57,7 @@ struct Request {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_in = nullptr;     // inputs copied (batched ticks wait on it)
     size_t cap = 0;           // doubles per matrix batch (m * N * N)
     int tcap = 0;
     double *dD = nullptr, *dJ = nullptr, *dK = nullptr, *dt = nullptr;
@@ -70,6 +73,9 @@ struct esmf_server {
     int max_inflight = 1;
     int precision = ESMF_PREC_FP16X2;
     bool use_graphs = false;
+    bool batch = false;              // batched ticks
+    cudaStream_t tick_stream = nullptr;
+    cudaEvent_t tick_ev = nullptr;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::thread worker;
@@ -84,6 +90,7 @@ struct esmf_server {
     int inflight = 0;
     // statistics
     int64_t submitted = 0, completed = 0, failed = 0, creates = 0, evictions = 0, graph_launches = 0;
+    int64_t batch_launches = 0, batched_builds = 0;
     int64_t peak_inflight = 0;
     std::vector<double> lat_ms;
     Clock::time_point first_submit, last_done;
@@ -244,8 +251,72 @@ int issue_build(esmf_server *s, int slot_idx, Molecule &mol, int mol_idx, int m)
     return ESMF_OK;
 }
 
-// try to start request r in a free slot; returns false if it must wait
-bool try_admit(esmf_server *s, const std::shared_ptr<Request> &r) {
+// results back to the slot's page-locked buffers, then the completion event
+int issue_outputs(Slot &sl, size_t cnt, int m) {
+    if (cudaMemcpyAsync(sl.hJ, sl.dJ, cnt * sizeof(double), cudaMemcpyDeviceToHost, sl.stream) ||
+        cudaMemcpyAsync(sl.hK, sl.dK, cnt * sizeof(double), cudaMemcpyDeviceToHost, sl.stream) ||
+        cudaMemcpyAsync(sl.ht, sl.dt, m * sizeof(double), cudaMemcpyDeviceToHost, sl.stream) ||
+        cudaEventRecord(sl.ev, sl.stream))
+        return ESMF_ERR_CUDA;
+    return ESMF_OK;
+}
+
+void fail_slot(esmf_server *s, int slot_idx, int rc) {
+    Slot &sl = s->slots[slot_idx];
+    std::snprintf(sl.req->err, sizeof(sl.req->err), "%s", esmf_last_error());
+    cudaGetLastError();
+    cudaStreamSynchronize(sl.stream);
+    finish(s, sl, rc);
+}
+
+bool on_tensor_path(esmf_fock_t *h) {
+    esmf_stats_t st;
+    return esmf_fock_stats(h, &st) == ESMF_OK && st.mode == ESMF_MODE_STORED && st.precision >= ESMF_PREC_FP16X2;
+}
+
+// One batched tick: the builds of the slots in `tick` (distinct molecules on
+// the tensor path, inputs being copied on their own streams) as one
+// esmf_fock_build_batch call on the tick stream, i.e. one persistent launch
+// per pass of 16 densities for all of them; each slot's result copies wait
+// for the tick.
+void issue_tick(esmf_server *s, const std::vector<int> &tick) {
+    const int count = (int)tick.size();
+    esmf_fock_t *hs[ESMF_MAX_BATCH];
+    int ms[ESMF_MAX_BATCH];
+    const double *Ds[ESMF_MAX_BATCH];
+    double *Js[ESMF_MAX_BATCH], *Ks[ESMF_MAX_BATCH], *ts[ESMF_MAX_BATCH];
+    int rc = ESMF_OK;
+    for (int i = 0; i < count && rc == ESMF_OK; ++i) {
+        Slot &sl = s->slots[tick[i]];
+        hs[i] = s->mols[sl.req->mol].h;
+        ms[i] = sl.req->m;
+        Ds[i] = sl.dD; Js[i] = sl.dJ; Ks[i] = sl.dK; ts[i] = sl.dt;
+        if (cudaStreamWaitEvent(s->tick_stream, sl.ev_in, 0) != cudaSuccess) rc = ESMF_ERR_CUDA;
+    }
+    if (rc == ESMF_OK) rc = esmf_fock_build_batch(count, hs, ms, Ds, Js, Ks, nullptr, ts, s->tick_stream);
+    if (rc == ESMF_OK && cudaEventRecord(s->tick_ev, s->tick_stream) != cudaSuccess) rc = ESMF_ERR_CUDA;
+    if (rc == ESMF_OK) {
+        ++s->batch_launches;
+        s->batched_builds += count;
+    } else {
+        cudaStreamSynchronize(s->tick_stream);
+    }
+    for (int i = 0; i < count; ++i) {
+        Slot &sl = s->slots[tick[i]];
+        int r = rc;
+        if (r == ESMF_OK && cudaStreamWaitEvent(sl.stream, s->tick_ev, 0) != cudaSuccess) r = ESMF_ERR_CUDA;
+        if (r == ESMF_OK) {
+            const Molecule &mol = s->mols[sl.req->mol];
+            r = issue_outputs(sl, (size_t)sl.req->m * mol.n * mol.n, sl.req->m);
+        }
+        if (r != ESMF_OK) fail_slot(s, tick[i], r);
+    }
+}
+
+// try to start request r in a free slot; returns false if it must wait.  With
+// batched ticks, a tensor-path build is not issued here: its slot joins
+// `tick` once its inputs are on their way.
+bool try_admit(esmf_server *s, const std::shared_ptr<Request> &r, std::vector<int> &tick) {
     Molecule &mol = s->mols[r->mol];
     if (mol.busy) return false;
     int slot_idx = -1;
@@ -280,20 +351,22 @@ bool try_admit(esmf_server *s, const std::shared_ptr<Request> &r) {
         const size_t cnt = (size_t)r->m * mol.n * mol.n;
         std::memcpy(sl.hD, r->D, cnt * sizeof(double));
         if (cudaMemcpyAsync(sl.dD, sl.hD, cnt * sizeof(double), cudaMemcpyHostToDevice, sl.stream)) rc = ESMF_ERR_CUDA;
+        if (rc == ESMF_OK && s->batch && on_tensor_path(mol.h)) {
+            if (cudaEventRecord(sl.ev_in, sl.stream) != cudaSuccess) {
+                rc = ESMF_ERR_CUDA;
+            } else {
+                tick.push_back(slot_idx);
+                if ((int)tick.size() == ESMF_MAX_BATCH) {
+                    issue_tick(s, tick);
+                    tick.clear();
+                }
+                return true;
+            }
+        }
         if (rc == ESMF_OK) rc = issue_build(s, slot_idx, mol, r->mol, r->m);
-        if (rc == ESMF_OK &&
-            (cudaMemcpyAsync(sl.hJ, sl.dJ, cnt * sizeof(double), cudaMemcpyDeviceToHost, sl.stream) ||
-             cudaMemcpyAsync(sl.hK, sl.dK, cnt * sizeof(double), cudaMemcpyDeviceToHost, sl.stream) ||
-             cudaMemcpyAsync(sl.ht, sl.dt, r->m * sizeof(double), cudaMemcpyDeviceToHost, sl.stream) ||
-             cudaEventRecord(sl.ev, sl.stream)))
-            rc = ESMF_ERR_CUDA;
+        if (rc == ESMF_OK) rc = issue_outputs(sl, cnt, r->m);
     }
-    if (rc != ESMF_OK) {
-        std::snprintf(r->err, sizeof(r->err), "%s", esmf_last_error());
-        cudaGetLastError();
-        cudaStreamSynchronize(sl.stream);
-        finish(s, sl, rc);
-    }
+    if (rc != ESMF_OK) fail_slot(s, slot_idx, rc);
     return true;
 }
 
@@ -317,13 +390,16 @@ void worker_main(esmf_server *s) {
         // resident (no integral evaluation needed); then the others, which
         // may create handles and evict idle molecules.  A request whose
         // molecule is busy waits without blocking the requests behind it.
+        // With batched ticks, the tensor-path builds admitted in this pass
+        // run together as one batched build.
+        std::vector<int> tick;
         for (int pass = 0; pass < 2; ++pass) {
             for (auto it = s->pending.begin(); it != s->pending.end();) {
                 if (s->inflight >= s->max_inflight) break;
                 Molecule &mol = s->mols[(*it)->mol];
                 if (pass == 0 && !mol.h) { ++it; continue; }
                 --mol.queued;
-                if (try_admit(s, *it)) {
+                if (try_admit(s, *it, tick)) {
                     it = s->pending.erase(it);
                 } else {
                     ++mol.queued;
@@ -331,6 +407,7 @@ void worker_main(esmf_server *s) {
                 }
             }
         }
+        if (!tick.empty()) issue_tick(s, tick);
         if (s->inflight > 0) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -345,10 +422,10 @@ void worker_main(esmf_server *s) {
 
 extern "C" {
 
-int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int precision, int use_graphs,
+int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int precision, int flags,
                        esmf_server_t **out) {
     if (!out || budget_bytes <= 0 || max_inflight < 1 || max_inflight > 64 || precision < ESMF_PREC_FP64 ||
-        precision > ESMF_PREC_BF16X2) {
+        precision > ESMF_PREC_BF16X2 || (flags & ~(ESMF_SERVER_GRAPHS | ESMF_SERVER_BATCH)) != 0) {
         set_error("bad server arguments");
         return ESMF_ERR_INVALID_ARG;
     }
@@ -365,11 +442,22 @@ int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int p
     esmf_server *s = new (std::nothrow) esmf_server();
     if (!s) { set_error("host allocation failed"); return ESMF_ERR_OOM; }
     s->device = device; s->budget = budget_bytes; s->max_inflight = max_inflight;
-    s->precision = precision; s->use_graphs = use_graphs != 0;
+    s->precision = precision;
+    s->use_graphs = (flags & ESMF_SERVER_GRAPHS) != 0;
+    s->batch = (flags & ESMF_SERVER_BATCH) != 0;
     s->slots.resize(max_inflight);
+    if (s->batch && (cudaStreamCreateWithFlags(&s->tick_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&s->tick_ev, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        set_error("stream creation failed");
+        esmf_server_destroy(s);
+        cudaSetDevice(prev);
+        return ESMF_ERR_CUDA;
+    }
     for (auto &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev_in, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             set_error("stream creation failed");
             esmf_server_destroy(s);
@@ -455,6 +543,7 @@ int esmf_server_stats(esmf_server_t *s, esmf_server_stats_t *out) {
     std::memset(out, 0, sizeof(*out));
     out->submitted = s->submitted; out->completed = s->completed; out->failed = s->failed;
     out->creates = s->creates; out->evictions = s->evictions; out->graph_launches = s->graph_launches;
+    out->batch_launches = s->batch_launches; out->batched_builds = s->batched_builds;
     out->resident_bytes = resident_bytes(s);
     out->peak_inflight = s->peak_inflight;
     if (!s->lat_ms.empty()) {
@@ -479,6 +568,7 @@ int esmf_server_reset_stats(esmf_server_t *s) {
     if (!s) { set_error("server is NULL"); return ESMF_ERR_INVALID_ARG; }
     std::lock_guard<std::mutex> lk(s->mu);
     s->submitted = s->completed = s->failed = s->creates = s->evictions = s->graph_launches = 0;
+    s->batch_launches = s->batched_builds = 0;
     s->peak_inflight = s->inflight;
     s->lat_ms.clear();
     s->have_first = false;
@@ -503,8 +593,14 @@ void esmf_server_destroy(esmf_server_t *s) {
         cudaFree(sl.dD); cudaFree(sl.dJ); cudaFree(sl.dK); cudaFree(sl.dt);
         cudaFreeHost(sl.hD); cudaFreeHost(sl.hJ); cudaFreeHost(sl.hK); cudaFreeHost(sl.ht);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.ev_in) cudaEventDestroy(sl.ev_in);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (s->tick_stream) {
+        cudaStreamSynchronize(s->tick_stream);
+        cudaStreamDestroy(s->tick_stream);
+    }
+    if (s->tick_ev) cudaEventDestroy(s->tick_ev);
     cudaSetDevice(prev);
     delete s;
 }

@@ -11,6 +11,9 @@ import numpy as np
 
 from . import fock
 
+SERVER_GRAPHS = 1      # ESMF_SERVER_GRAPHS
+SERVER_BATCH = 2       # ESMF_SERVER_BATCH
+
 SERVER_EXPORTS = ["esmf_server_create", "esmf_server_register", "esmf_server_submit",
                   "esmf_server_wait", "esmf_server_stats", "esmf_server_reset_stats",
                   "esmf_server_destroy"]
@@ -21,7 +24,8 @@ class esmf_server_stats_t(C.Structure):
                 ("creates", C.c_int64), ("evictions", C.c_int64), ("graph_launches", C.c_int64),
                 ("resident_bytes", C.c_int64), ("peak_inflight", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
-                ("max_ms", C.c_double), ("span_s", C.c_double)]
+                ("max_ms", C.c_double), ("span_s", C.c_double),
+                ("batch_launches", C.c_int64), ("batched_builds", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -53,12 +57,16 @@ def _lib():
 class Server:
     """Requests use host numpy arrays; keep them alive until wait() returns."""
 
-    def __init__(self, budget_bytes, max_inflight=4, precision="fp16x2", use_graphs=True, device=0):
+    def __init__(self, budget_bytes, max_inflight=4, precision="fp16x2", use_graphs=True, device=0,
+                 batch=False):
+        """use_graphs: replay single builds from CUDA graphs; batch: build the
+        tensor-path requests admitted together in one batched launch."""
         L = _lib()
         self.h = C.c_void_p()
         p = fock.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        flags = (SERVER_GRAPHS if use_graphs else 0) | (SERVER_BATCH if batch else 0)
         fock._check(L.esmf_server_create(int(device), int(budget_bytes), int(max_inflight), p,
-                                         int(bool(use_graphs)), C.byref(self.h)), "esmf_server_create")
+                                         flags, C.byref(self.h)), "esmf_server_create")
         self._keep = {}
         self.n = {}
 

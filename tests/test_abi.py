@@ -63,6 +63,11 @@ def test_strerror_and_host_side_argument_errors(lib):
     st = fock.esmf_stats_t()
     assert lib.esmf_fock_stats(None, C.byref(st)) == fock.ESMF_ERR_INVALID_ARG
     lib.esmf_fock_destroy(None)
+    # server: unknown flag bits, bad slot count and budget are rejected before any CUDA call
+    from paper_2002_00322_gb300 import server
+    server._lib()
+    for args in ((0, 1 << 30, 4, 2, 4), (0, 1 << 30, 0, 2, server.SERVER_BATCH), (0, 0, 4, 2, 1)):
+        assert lib.esmf_server_create(*args, C.byref(h)) == fock.ESMF_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("bad", ["exp", "nprim", "coef", "tol", "mode", "prec", "direct16"])

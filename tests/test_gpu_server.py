@@ -21,9 +21,10 @@ def molecules():
     return [W.small_random(n, 1, 40 + i, tol=1e-10, edge=4.0 + n / 5) for i, n in enumerate((24, 37, 52))]
 
 
-@pytest.mark.parametrize("prec,graphs,budget,inflight", [("fp16x2", True, 1 << 34, 4), ("fp64", False, 1 << 34, 4),
-                                                         ("fp16x2", True, 0, 1)])
-def test_mixed_requests_equal_standalone(esmf, prec, graphs, budget, inflight):
+@pytest.mark.parametrize("prec,graphs,batch,budget,inflight", [
+    ("fp16x2", True, False, 1 << 34, 4), ("fp64", False, False, 1 << 34, 4), ("fp16x2", True, False, 0, 1),
+    ("fp16x2", False, True, 1 << 34, 8), ("fp16x2", True, True, 0, 3)])
+def test_mixed_requests_equal_standalone(esmf, prec, graphs, batch, budget, inflight):
     import torch
     from paper_2002_00322_gb300.server import Server
     mols = molecules()
@@ -43,14 +44,24 @@ def test_mixed_requests_equal_standalone(esmf, prec, graphs, budget, inflight):
         m = int(rng.integers(1, 20))
         D = rng.standard_normal((m, mols[i].basis.n, mols[i].basis.n))
         reqs.append((i, D))
-    with Server(budget, max_inflight=inflight, precision=prec, use_graphs=graphs) as srv:
+    with Server(budget, max_inflight=inflight, precision=prec, use_graphs=graphs, batch=batch) as srv:
         ids = [srv.register(w.basis, w.tol) for w in mols]
         tickets = [srv.submit(ids[i], D) for i, D in reqs]
         outs = [srv.wait(t, 600000) for t in tickets]
         st = srv.stats()
     assert st["completed"] == len(reqs) and st["failed"] == 0
     assert st["p99_ms"] >= st["p50_ms"] > 0
-    if budget < (1 << 30):
+    if batch:       # tensor-path builds ran inside batched ticks, any others as (graph-replayed) singles
+        assert 1 <= st["batch_launches"] <= st["batched_builds"] <= len(reqs)
+        if graphs:
+            assert st["batched_builds"] + st["graph_launches"] == len(reqs)
+        else:
+            assert st["batched_builds"] == len(reqs) and st["graph_launches"] == 0
+    else:
+        assert st["batch_launches"] == 0
+    if budget < (1 << 30) and inflight == 1:
+        # one slot: every switch of molecule must evict (with more slots, busy
+        # molecules stay and a new one falls back to integral-direct under the budget)
         assert st["evictions"] > 0
     for (i, D), (J, K, tr) in zip(reqs, outs):
         with esmf.FockBuilder(mols[i].basis, mols[i].tol, "stored", prec) as fb:
