@@ -281,10 +281,10 @@ bool on_tensor_path(esmf_fock_t *h) {
 // for the tick.
 void issue_tick(esmf_server *s, const std::vector<int> &tick) {
     const int count = (int)tick.size();
-    esmf_fock_t *hs[ESMF_MAX_BATCH];
-    int ms[ESMF_MAX_BATCH];
-    const double *Ds[ESMF_MAX_BATCH];
-    double *Js[ESMF_MAX_BATCH], *Ks[ESMF_MAX_BATCH], *ts[ESMF_MAX_BATCH];
+    esmf_fock_t *hs[ESMF_MAX_BATCH] = {};
+    int ms[ESMF_MAX_BATCH] = {};
+    const double *Ds[ESMF_MAX_BATCH] = {};
+    double *Js[ESMF_MAX_BATCH] = {}, *Ks[ESMF_MAX_BATCH] = {}, *ts[ESMF_MAX_BATCH] = {};
     int rc = ESMF_OK;
     for (int i = 0; i < count && rc == ESMF_OK; ++i) {
         Slot &sl = s->slots[tick[i]];
