@@ -176,8 +176,10 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J,
  *           laid out as for esmf_fock_build with that entry's N and m
  *   F, traces  NULL, or count device pointers each (entries may be NULL)
  *   stream  cudaStream_t (NULL = legacy default stream)
- * Asynchronous.  The error flag of the first handle records a device-side
- * timeout (esmf_fock_device_error).  Errors: INVALID_ARG, UNSUPPORTED (a
+ * Asynchronous.  A device-side timeout (an expired bounded wait in the
+ * launch) sets the error flag of EVERY handle of the batch, since a CTA that
+ * gives up leaves its share of all of them unfinished; read each handle's flag
+ * with esmf_fock_device_error.  Errors: INVALID_ARG, UNSUPPORTED (a
  * handle off the tensor-core path), OOM, CUDA.  The grouping of Sec. II.C
  * (all densities of one molecule in one pass over its integrals) is kept per
  * handle; batching across molecules has no counterpart in the paper.
@@ -260,7 +262,14 @@ int esmf_fock_kernel_time(esmf_fock_t *h, double *ms, int64_t *launches, int res
  * synchronise the device and stall unrelated streams.  The paper has no
  * counterpart; it is a property of this library's memory handling only.
  *
- * Same arguments, results and asynchrony as esmf_fock_build.  The FP64 J/K
+ * Same arguments and asynchrony as esmf_fock_build.  Stored FP64 and FP32
+ * handles and integral-direct handles run the same CUDA-core kernels as
+ * esmf_fock_build (with the handle's autotuned densities per pass), so the
+ * results are the same.  Handles with split 16-bit stores (FP16X2 / BF16X2)
+ * run the CUDA-core kernel over that store here, not the tensor-core kernel
+ * (which needs per-handle density tiles in work memory): their results equal
+ * esmf_fock_build's within the precision's tolerance (2e-6 relative for
+ * FP16X2, 3e-5 for BF16X2), and the call is slower.  The FP64 J/K
  * accumulators are taken from one static device array of
  * ESMF_NOALLOC_MAX_SCRATCH_DOUBLES doubles (32 MiB) that the library holds on
  * every device it is loaded on until the process exits; nothing is allocated

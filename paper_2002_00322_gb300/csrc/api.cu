@@ -736,7 +736,7 @@ int esmf_fock_build_batch(int count, esmf_fock_t *const *hs, const int *ms, cons
         l.store = (const uint32_t *)h->store; l.kbank = h->kbank; l.jbank = h->jbank;
         l.dmax_bits = h->dmax; l.D = Ds[i]; l.n = h->n; l.np = h->np; l.nb = h->nb; l.m = m;
         l.bf16 = h->prec == ESMF_PREC_BF16X2; l.num_sms = h->num_sms; l.vscale = h->vscale;
-        l.Jacc = h->Jacc; l.Kacc = h->Kacc; l.error = hs[0]->err_dev;
+        l.Jacc = h->Jacc; l.Kacc = h->Kacc; l.error = h->err_dev;
         l.chunk = 16;
         if (h->parts) { l.part = h->parts; l.nparts = h->nparts; }
     }
@@ -1025,6 +1025,14 @@ int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, in
     a->m = m; a->D = D; a->Jacc = nullptr; a->Kacc = nullptr;
     a->vscale = h->vscale;
     a->ptab = h->ptab; a->pslot = h->pslot;
+    // densities per pass as esmf_fock_build picks them (autotuned or forced);
+    // a tensor-core choice of 16 has no CUDA-core meaning for FP64 and falls
+    // back to that kernel's default
+    int chunk = h->force_chunk;
+    if (!chunk)
+        for (auto &t : h->tuned)
+            if (t.first == m) chunk = t.second;
+    a->mc = chunk;
     *device = h->device;
     *split = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
     return ESMF_OK;

@@ -29,10 +29,16 @@ __device__ __forceinline__ double boys0_d(double T) {
     return kHalfSqrtPi * erf(x) / x;
 }
 
-// F0 in float: series below 1e-3 (truncation < 1e-14), erf form above; for
-// T > 16 erff(sqrt T) rounds to 1.
+// F0 for the FP32 paths: near the small-T limit (below 1e-3; truncation
+// < 1e-14) the series is summed in FP64 and rounded once, so F0 there is
+// correctly rounded to FP32; the erf form above; for T > 16 erff(sqrt T)
+// rounds to 1.  Small T occurs only for nearly concentric primitive pairs, so
+// the FP64 branch is rare.
 __device__ __forceinline__ float boys0_f(float T) {
-    if (T < 1e-3f) return 1.0f - T * (1.0f / 3.0f) + T * T * 0.1f - T * T * T * (1.0f / 42.0f);
+    if (T < 1e-3f) {
+        const double t = (double)T;
+        return (float)(1.0 - t * (1.0 / 3.0) + t * t * 0.1 - t * t * t * (1.0 / 42.0));
+    }
     float r = rsqrtf(T);
     if (T > 16.0f) return (float)kHalfSqrtPi * r;
     return (float)kHalfSqrtPi * erff(T * r) * r;

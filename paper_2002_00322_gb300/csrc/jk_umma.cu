@@ -167,12 +167,12 @@ struct UmmaEntry {
     float vscale;
     const unsigned int *dmax_bits;
     double *Jacc, *Kacc;           // block-major: [X][Y][k][x][y], k < mtot
+    int *error;                    // the entry's handle's device error flag
 };
 constexpr int MAX_ENTRIES = 16;
 struct UmmaParams {
     UmmaEntry e[MAX_ENTRIES];
     int nentries, mp;              // mp: density columns per pass, the same for every entry
-    int *error;
 };
 
 namespace {
@@ -313,9 +313,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = c.tmem_base;
+    // A CTA that gives up leaves the rest of its slice of every entry
+    // unprocessed, so every entry of the launch is marked incomplete.
     auto fail = [&](int code) {
         *abort_flag = 1;
-        atomicExch(P.error, code);
+        for (int e = 0; e < P.nentries; ++e)
+            if (P.e[e].error) atomicExch(P.e[e].error, code);
     };
 
     if (nloc > 0 && warp == 0 && lane == 0) {
@@ -686,7 +689,6 @@ int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s) {
         UmmaParams p;
         p.nentries = 0;
         p.mp = MPMAX;
-        p.error = Ls[0].error;
         for (int i = 0; i < count; ++i) {
             const UmmaLaunch &L = Ls[i];
             if (d0 >= L.m) continue;
@@ -699,6 +701,7 @@ int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s) {
             E.kbank = L.kbank; E.jbank = L.jbank; E.part = L.part; E.nparts = L.nparts;
             E.nb = L.nb; E.m = mc; E.d0 = d0; E.mtot = L.m; E.bf16 = L.bf16;
             E.vscale = L.vscale; E.dmax_bits = L.dmax_bits; E.Jacc = L.Jacc; E.Kacc = L.Kacc;
+            E.error = L.error;
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) { set_error("k_dbank: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
@@ -735,12 +738,12 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
         UmmaParams p;
         p.nentries = 1;
         p.mp = mp;
-        p.error = L.error;
         UmmaEntry &E = p.e[0];
         E.bricks = L.bricks; E.nbricks = L.nbricks; E.offsets = L.offsets; E.store = L.store;
         E.kbank = L.kbank; E.jbank = L.jbank; E.part = L.part; E.nparts = L.nparts;
         E.nb = L.nb; E.m = mc; E.d0 = d0; E.mtot = L.m; E.bf16 = L.bf16;
         E.vscale = L.vscale; E.dmax_bits = L.dmax_bits; E.Jacc = L.Jacc; E.Kacc = L.Kacc;
+        E.error = L.error;
         int grid = L.num_sms;
         if (grid > L.nbricks) grid = (int)L.nbricks;
         if (L.part) grid = L.nparts;

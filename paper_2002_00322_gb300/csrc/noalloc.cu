@@ -4,10 +4,14 @@
 // host application owns every device allocation (a pool handed out by a
 // framework or a serving process with a fixed memory plan), and latency-bound
 // loops where a cudaMalloc/cudaFree pair would synchronise the device and
-// stall other streams.  esmf_fock_build_noalloc serves them: it runs the same
-// grouped contraction and finalisation kernels as esmf_fock_build, but its
-// FP64 J/K accumulators (the contraction kernel's scratch memory) live in the
-// file-scope device array below instead of handle memory grown on demand.
+// stall other streams.  esmf_fock_build_noalloc serves them: for stored FP64
+// and FP32 handles and integral-direct handles it runs the same CUDA-core
+// contraction and finalisation kernels as esmf_fock_build; for split 16-bit
+// stores it runs the CUDA-core kernel over the store (the tensor-core kernel
+// needs density tiles in handle work memory), equal to esmf_fock_build within
+// that precision's tolerance.  Its FP64 J/K accumulators (the contraction
+// kernel's scratch memory) live in the file-scope device array below instead
+// of handle memory grown on demand.
 //
 // The array is sized once, at library load, on every device the library is
 // used on, and stays resident until the process exits.  All calls share it,

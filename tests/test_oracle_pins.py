@@ -89,6 +89,59 @@ def test_two_center_gaussian_charges():
         assert abs(o.eri(0, 0, 1, 1) - ref) <= 1e-13 * ref
 
 
+def test_contracted_two_center_charge_clouds():
+    """Contracted (mu mu|nu nu), mu on A and nu on B (three primitives each):
+    the product of two s Gaussians on one center is a Gaussian charge of
+    exponent p = a_i + a_j and charge (pi/p)^{3/2}, and two such clouds at
+    distance R interact by erf(sqrt(pq/(p+q)) R) / R (2 sqrt(rho/pi) at R = 0),
+    so (mu mu|nu nu) = sum_ijkl w_i w_j w_k w_l (pi/p)^{3/2} (pi/q)^{3/2}
+    erf(sqrt(rho) R)/R.  The weights w come from a radial quadrature of the
+    contraction's norm, not from the oracle.  This pins the contracted sum of
+    the primitive quartets: a slip that counted the diagonal primitive pairs
+    twice, or dropped the cross pairs, changes the value by far more than the
+    tolerance (checked below)."""
+    rng = np.random.default_rng(19)
+
+    def weights(a, d):
+        g = d * (2 * a / np.pi) ** 0.75
+        f = lambda r: 4 * np.pi * r * r * np.sum(g * np.exp(-a * r * r)) ** 2
+        nrm, _ = integrate.quad(f, 0, np.inf, epsabs=1e-14, epsrel=1e-13)
+        return g / math.sqrt(nrm)
+
+    def cloud_sum(wa, a, wb, b, R, diag=1.0, cross=1.0):
+        tot = 0.0
+        for i in range(3):
+            for j in range(3):
+                fij = diag if i == j else cross
+                p = a[i] + a[j]
+                for k in range(3):
+                    for l in range(3):
+                        fkl = diag if k == l else cross
+                        q = b[k] + b[l]
+                        rho = p * q / (p + q)
+                        inter = (2 * math.sqrt(rho / math.pi) if R == 0.0
+                                 else special.erf(math.sqrt(rho) * R) / R)
+                        tot += fij * fkl * wa[i] * wa[j] * wb[k] * wb[l] * \
+                            (math.pi / p) ** 1.5 * (math.pi / q) ** 1.5 * inter
+        return tot
+
+    for R in (0.0, 0.7, 2.5, 9.0):
+        a = np.exp(rng.uniform(np.log(0.1), np.log(10), size=3))
+        b = np.exp(rng.uniform(np.log(0.1), np.log(10), size=3))
+        da, db = rng.uniform(0.1, 1.0, size=3), rng.uniform(0.1, 1.0, size=3)
+        basis = W.Basis(np.array([[0.0, 0.0, 0.0], [0.0, R * 0.8, -R * 0.6]]),
+                        np.array([3, 3], dtype=np.int32), np.concatenate([a, b]),
+                        np.concatenate([da, db]))
+        o = Oracle(basis)
+        wa, wb = weights(a, da), weights(b, db)
+        ref = cloud_sum(wa, a, wb, b, R)
+        assert abs(o.eri(0, 0, 1, 1) - ref) <= 1e-12 * ref, R
+        assert abs(o.eri(1, 1, 0, 0) - ref) <= 1e-12 * ref, R
+        # the pin's sensitivity to the slips it is meant to catch
+        assert abs(cloud_sum(wa, a, wb, b, R, diag=2.0) - ref) > 1e-3 * ref
+        assert abs(cloud_sum(wa, a, wb, b, R, cross=0.0) - ref) > 1e-3 * ref
+
+
 def test_four_center_integral_by_quadrature():
     """General (ab|cd) against 1/r = (2/sqrt(pi)) int_0^inf exp(-t^2 r^2) dt,
     with the six-dimensional Gaussian integral done in closed form and the
