@@ -359,6 +359,47 @@ int oracle_jk_elements(int n, const double *center, const int32_t *nprim,
     return 0;
 }
 
+/*
+ * Whole rows of J and K for selected row indices p (rows[i] = p):
+ *   Jrow[k][i][q] = sum_{r,s} kept (pq|rs) D_k[r][s]
+ *   Krow[k][i][r] = sum_{q,s} kept (pq|rs) D_k[q][s]
+ * i.e. Eq. (J_and_K) for the elements J_pq and K_pr of row p, both sums
+ * running over every integral (pq|rs) with first index p; each such integral
+ * is evaluated once and used by both.  Outputs are laid out [k][i][column]
+ * and overwritten.
+ */
+int oracle_jk_rows(int n, const double *center, const int32_t *nprim,
+                   const double *exps, const double *w, const double *Q,
+                   double tol, int m, const double *D,
+                   int nrows, const int32_t *rows, double *Jrow, double *Krow)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    int64_t nn = (int64_t)n * n;
+    double qmax = 0.0;
+    for (int64_t e = 0; e < nn; ++e) if (Q[e] > qmax) qmax = Q[e];
+    memset(Jrow, 0, sizeof(double) * (size_t)m * nrows * n);
+    memset(Krow, 0, sizeof(double) * (size_t)m * nrows * n);
+    for (int i = 0; i < nrows; ++i) {
+        int p = rows[i];
+        for (int q = 0; q < n; ++q) {
+            /* no (pq|rs) can be kept when Q_pq times the largest Q is below tol */
+            if (Q[(int64_t)p * n + q] * qmax < tol) continue;
+            for (int r = 0; r < n; ++r)
+                for (int s = 0; s < n; ++s) {
+                    if (!kept(Q, n, p, q, r, s, tol)) continue;
+                    double v = eri_c(&b, p, q, r, s);
+                    for (int k = 0; k < m; ++k) {
+                        const double *Dk = D + k * nn;
+                        Jrow[((int64_t)k * nrows + i) * n + q] += Dk[(int64_t)r * n + s] * v;
+                        Krow[((int64_t)k * nrows + i) * n + r] += Dk[(int64_t)q * n + s] * v;
+                    }
+                }
+        }
+    }
+    free(b.off);
+    return 0;
+}
+
 /* F_k = 2 J_k - K_k and t_k = D_k . F_k = sum_pq D_k[pq] F_k[pq] (Table I) */
 int oracle_fock_traces(int n, int m, const double *D, const double *J,
                        const double *K, double *F, double *t)

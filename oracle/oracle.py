@@ -60,6 +60,8 @@ def lib():
             L.oracle_count_kept.restype = C.c_int64
             L.oracle_jk_elements.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double, C.c_int,
                                              dp, C.c_int, ip, dp, C.c_int, ip, dp]
+            L.oracle_jk_rows.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double, C.c_int,
+                                         dp, C.c_int, ip, dp, dp]
             L.oracle_fock_traces.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp]
             L.oracle_pair_max.argtypes = [C.c_int, dp, ip, dp, dp, dp]
             _lib = L
@@ -166,6 +168,19 @@ class Oracle:
         lib().oracle_jk_elements(*self._b(), _d(self.Q), tol, m, _d(D),
                                  jidx.shape[0], _i(jidx), _d(Jo), kidx.shape[0], _i(kidx), _d(Ko))
         return Jo, Ko
+
+    def jk_rows(self, D, tol, rows):
+        """Whole rows J[k][p][:] and K[k][p][:] for each p in rows, from the
+        definition (every integral with first index p evaluated once);
+        returns arrays of shape (m, len(rows), N)."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        m = D.shape[0]
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int32).ravel())
+        Jr = np.zeros((m, rows.size, self.n))
+        Kr = np.zeros((m, rows.size, self.n))
+        lib().oracle_jk_rows(*self._b(), _d(np.ascontiguousarray(self.Q)), tol, m, _d(D),
+                             rows.size, _i(rows), _d(Jr), _d(Kr))
+        return Jr, Kr
 
     @staticmethod
     def fock_traces(D, J, K):

@@ -329,6 +329,20 @@ def test_screening_bound():
     assert np.max(np.abs(Js - Jf)) > 0
 
 
+def test_rows_equal_the_unique_loop():
+    """Whole rows of J and K (each integral with first index p evaluated once)
+    equal the rows of the unique-quartet build, with screening and a
+    non-symmetric density."""
+    w = W.small_random(21, 3, 4, tol=1e-7, edge=9.25)
+    D = w.D + 0.3 * np.random.default_rng(1).standard_normal(w.D.shape)
+    o = Oracle(w.basis)
+    J, K, _ = o.jk_unique(D, w.tol)
+    rows = [0, 5, 7, 8, w.basis.n - 1]
+    Jr, Kr = o.jk_rows(D, w.tol, rows)
+    assert np.max(np.abs(Jr - J[:, rows, :])) <= 1e-13 * np.max(np.abs(J))
+    assert np.max(np.abs(Kr - K[:, rows, :])) <= 1e-13 * np.max(np.abs(K))
+
+
 def test_elements_and_ranges_and_stored_list(tiny):
     w, o, _ = tiny
     J, K, nk = o.jk_unique(w.D, 0.0)
