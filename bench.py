@@ -114,6 +114,134 @@ def ncu_traffic(kernel, precision):
 
 
 # ------------------------------------------------------------------ ours
+DTYPES = {"fp64": "f64", "fp32": "f32", "fp16x2": "f16x2+f32acc", "bf16x2": "bf16x2+f32acc"}
+ELEM_BYTES = {"fp64": 8, "fp32": 4, "fp16x2": 4, "bf16x2": 4}
+
+
+def measured_alu_peaks(local):
+    """FP64 and FP32 FMA rates of this GPU, measured in this process with the
+    library's FMA-chain kernel (CUDA events; no clock or power setting touched)."""
+    from paper_2002_00322_gb300 import fock
+    return {p: round(max(fock.esmf_measure_fma_peak(p, local) for _ in range(2)), 2) for p in ("fp64", "fp32")}
+
+
+def contraction_roofline(prec, st, m, n, kern_s, alu_peaks):
+    """Roofline of the contraction kernel of one stored build.  FP64 / FP32
+    stores: CUDA-core FMAs against the measured FMA rate, counting the
+    algorithmic 20 m flops per kept unique quartet (2 J + 8 K FMAs per
+    density); split 16-bit stores: HBM, counting kept quartets x 4 B + D in +
+    J, K out."""
+    kname = "k_jk_umma" if prec in ("fp16x2", "bf16x2") else "k_jk_cuda"
+    if prec in ("fp64", "fp32"):
+        flops = st["n_quartets_kept"] * 20 * m
+        ach = flops / kern_s / 1e12
+        pk = alu_peaks[prec]
+        return {"bound": "alu", "achieved": round(ach, 3), "peak": pk, "unit": "TFLOP/s",
+                "frac": round(ach / pk, 4), "traffic": ncu_traffic(kname, prec),
+                "peak_source": f"measured {prec.upper()} FMA rate (esmf_measure_fma_peak, this process)",
+                "kernel": kname, "kernel_ms": round(kern_s * 1e3, 4), "algorithmic_flops": flops}
+    alg_bytes = st["n_quartets_kept"] * ELEM_BYTES[prec] + 3 * m * n * n * 8
+    hbm, src, _ = peaks()
+    ach = alg_bytes / kern_s / 1e9
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "traffic": ncu_traffic(kname, prec), "peak_source": src,
+            "kernel": kname, "kernel_ms": round(kern_s * 1e3, 4), "stored_bytes": st["store_bytes"],
+            "algorithmic_bytes": alg_bytes}
+
+
+def timed_builds(fock, fb, m, D, J, K, F, t, stream, steps, warmup):
+    """Device time of `steps` builds (after `warmup`), and the contraction
+    kernel's average launch time from the handle's own CUDA events."""
+    import torch
+    for _ in range(warmup):
+        fock.esmf_fock_build(fb.h, m, D, J, K, F, t, stream)
+    torch.cuda.synchronize()
+    fock.esmf_fock_set_timing(fb.h, True)
+    fock.esmf_fock_kernel_time(fb.h, reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fock.esmf_fock_build(fb.h, m, D, J, K, F, t, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kern_ms, kern_n = fock.esmf_fock_kernel_time(fb.h, reset=True)
+    fock.esmf_fock_set_timing(fb.h, False)
+    return e0.elapsed_time(e1) / steps, kern_ms / max(kern_n, 1) / 1e3
+
+
+def sub_stored(fock, W, dev, stream, prec, alu_peaks, steps=20):
+    """stored_n200_m16 at another store precision: builds/s and its roofline."""
+    import torch
+    w = W.stored()
+    n, m = w.basis.n, w.m
+    with fock.FockBuilder(w.basis, w.tol, "stored", prec, device=dev.index) as fb:
+        st = fb.stats()
+        D = torch.from_numpy(w.D).to(dev)
+        J, K, F = torch.empty_like(D), torch.empty_like(D), torch.empty_like(D)
+        t = torch.empty(m, dtype=torch.float64, device=dev)
+        chunk = fock.esmf_fock_autotune(fb.h, m, D, J, K, 3, stream)
+        ms, ks = timed_builds(fock, fb, m, D, J, K, F, t, stream, steps, 3)
+        return {"dtype": DTYPES[prec], "ms_per_step": round(ms, 4), "value": round(1e3 / ms, 3),
+                "quartets_per_s": round(st["n_quartets_kept"] / (ms / 1e3), 1), "densities_per_pass": chunk,
+                "setup_ms": round(st["create_ms"], 1), "store_bytes": st["store_bytes"],
+                "roofline": contraction_roofline(prec, st, m, n, ks, alu_peaks)}
+
+
+def sub_precision(fock, W, dev, stream, steps=10):
+    """precision_n400_m64 (split FP16 hi+lo on tensor cores, 64 densities):
+    builds/s and the error of whole stored oracle rows of J and K."""
+    import torch
+    w = W.precision()
+    n, m = w.basis.n, w.m
+    with fock.FockBuilder(w.basis, w.tol, "stored", "fp16x2", device=dev.index) as fb:
+        st = fb.stats()
+        D = torch.from_numpy(w.D).to(dev)
+        J, K, F = torch.empty_like(D), torch.empty_like(D), torch.empty_like(D)
+        t = torch.empty(m, dtype=torch.float64, device=dev)
+        chunk = fock.esmf_fock_autotune(fb.h, m, D, J, K, 2, stream)
+        ms, ks = timed_builds(fock, fb, m, D, J, K, F, t, stream, steps, 2)
+        out = {"dtype": DTYPES["fp16x2"], "ms_per_step": round(ms, 4), "value": round(1e3 / ms, 3),
+               "density_builds_per_s": round(m * 1e3 / ms, 1), "densities_per_pass": chunk,
+               "quartets_per_s": round(st["n_quartets_kept"] / (ms / 1e3), 1),
+               "setup_ms": round(st["create_ms"], 1), "store_bytes": st["store_bytes"],
+               "roofline": contraction_roofline("fp16x2", st, m, n, ks, None)}
+        g = os.path.join(ROOT, "tests", "golden", "c4_precision_n400_m64.npz")
+        if os.path.exists(g):
+            gd = np.load(g)
+            rows = gd["rows"]
+            Jh, Kh = J.cpu().numpy(), K.cpu().numpy()
+            rel = lambda x, r: float(np.linalg.norm(x - r) / max(np.linalg.norm(r), 1e-300))
+            ej = [rel(Jh[k][rows], gd["J_rows"][k]) for k in range(m)]
+            ek = [rel(Kh[k][rows], gd["K_rows"][k]) for k in range(m)]
+            out["error_vs_fp64_oracle_rows"] = {"rows": len(rows), "J_max": max(ej), "K_max": max(ek),
+                                                "J_median": float(np.median(ej)), "K_median": float(np.median(ek))}
+        return out
+
+
+def sub_direct(fock, W, dev, stream, alu_peaks, steps=2):
+    """direct_n2000_m32 (integral-direct FP32 on the 2000-function ribbon)."""
+    import torch
+    w = W.direct()
+    n, m = w.basis.n, w.m
+    with fock.FockBuilder(w.basis, w.tol, "direct", "fp32", device=dev.index) as fb:
+        st = fb.stats()
+        D = torch.from_numpy(w.D).to(dev)
+        J, K = torch.empty_like(D), torch.empty_like(D)
+        ms, ks = timed_builds(fock, fb, m, D, J, K, None, None, stream, steps, 1)
+        flops = st["n_quartets_kept"] * (81 * 25 + 20 * m)
+        ach = flops / ks / 1e12
+        return {"dtype": "f32", "ms_per_step": round(ms, 3), "value": round(1e3 / ms, 4),
+                "quartets_per_s": round(st["n_quartets_kept"] / (ms / 1e3), 1),
+                "setup_ms": round(st["create_ms"], 1), "quartets_kept": st["n_quartets_kept"],
+                "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": alu_peaks["fp32"],
+                             "unit": "TFLOP/s", "frac": round(ach / alu_peaks["fp32"], 4), "traffic": None,
+                             "peak_source": "measured FP32 FMA rate (esmf_measure_fma_peak, this process)",
+                             "kernel": "k_jk_cuda", "kernel_ms": round(ks * 1e3, 3),
+                             "algorithmic_flops": flops,
+                             "flops_per_quartet": "81 primitive quartets x 25 + 20 m"}}
+
+
 def run_ours(args):
     import torch
     from paper_2002_00322_gb300 import fock
@@ -125,6 +253,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    alu_peaks = measured_alu_peaks(local)
     w = W.stored()
     n, m = w.basis.n, w.m
     fb = fock.FockBuilder(w.basis, w.tol, "stored", args.precision, device=local)
@@ -206,12 +335,14 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1) / e_reps
+    split = args.precision in ("fp16x2", "bf16x2")
     energy = {"ms_per_eval": round(e_ms, 4), "evals_per_s": round(world * 1e3 / e_ms, 2),
-              "n_occ": es.nocc, "fock_builds_grouped": 3,
+              "n_occ": es.nocc, "fock_builds_grouped": 3, "precision": args.precision,
               "what": "E, dE/dc0, dE/dsigma, dE/dV (esmf_energy_gradient)",
-              # k_gemm_group x5, k_dmax, k_dbank, k_jk_umma, k_finalize_blocked,
-              # k_energy_fock, k_energy_dots, k_energy_scalars, k_energy_finish
-              "gpu_launches_per_eval": 13 if args.precision in ("fp16x2", "bf16x2") else 11}
+              # k_gemm_group x5, k_dmax, k_dbank, k_jk_umma, k_finalize_blocked (or
+              # k_jk_cuda, k_finalize), k_energy_fock, k_energy_dots, k_energy_scalars,
+              # k_energy_finish
+              "gpu_launches_per_eval": 13 if split else 11}
     # GVP objective (Eq. esmf_gvb) and its derivatives: two grouped passes
     for _ in range(2):
         fb.gvp_gradient(Gd, Vd, Sd, es.c0, es.nocc, -3.0, 0.4, 0.8, stream=stream)
@@ -224,33 +355,15 @@ def run_ours(args):
     g_ms = e0.elapsed_time(e1) / e_reps
     gvp = {"ms_per_eval": round(g_ms, 4), "evals_per_s": round(world * 1e3 / g_ms, 2),
            "fock_builds_grouped": "3 + 3 (two passes)", "omega_mu_chi": [-3.0, 0.4, 0.8],
+           "precision": args.precision,
            "what": "L, E, |grad E|^2, dL/dc0, dL/dsigma, dL/dX (esmf_gvp_gradient)"}
+    fb.close()
 
-    # batching of uneven molecules: a mix of eight (60-300 functions, 4-16
-    # densities) and one of sixteen small ones (40-100 functions), each built
-    # one launch per molecule, in one batched launch, and as that launch
-    # replayed from a CUDA graph
-    batch = run_batched(fock, W, dev, stream, args.precision)
-
-    # roofline of the dominant (contraction) kernel: algorithmic bytes =
-    # kept unique integrals x bytes + D in + J, K out (FP64)
-    eb = {"fp64": 8, "fp32": 4, "fp16x2": 4, "bf16x2": 4}[args.precision]
-    alg_bytes = st["n_quartets_kept"] * eb + 3 * m * n * n * 8
-    kern_avg_s = (kern_ms / max(kern_n, 1)) / 1e3
-    hbm, src, _ = peaks()
-    achieved = alg_bytes / kern_avg_s / 1e9
-    kname = "k_jk_umma" if args.precision in ("fp16x2", "bf16x2") else "k_jk_cuda"
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": ncu_traffic(kname, args.precision),
-            "peak_source": src, "kernel": kname,
-            "kernel_ms": round(kern_avg_s * 1e3, 4),
-            "stored_bytes": st["store_bytes"], "algorithmic_bytes": alg_bytes}
-
+    roof = contraction_roofline(args.precision, st, m, n, (kern_ms / max(kern_n, 1)) / 1e3, alu_peaks)
     out = {"metric": METRIC, "value": round(world * 1e3 / ms_step, 3), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16x2": "f16x2+f32acc",
-                                          "bf16x2": "bf16x2+f32acc"}[args.precision],
+           "vs_baseline": None, "dtype": DTYPES[args.precision],
            "data": "synthetic (seeded s-type basis; stands in for cc-pVDZ molecules)",
            "config": {"workload": "stored_n200_m16", "n_basis": n, "m": m, "schwarz_tol": w.tol,
                       "mode": "stored", "precision": args.precision,
@@ -262,21 +375,34 @@ def run_ours(args):
            "quartets_per_s": round(world * st["n_quartets_kept"] / (ms_step / 1e3), 1),
            "density_builds_per_s": round(world * m * 1e3 / ms_step, 1),
            "roofline": roof,
+           "measured_alu_peaks_tflops": alu_peaks,
            "e2e": {"value": round(world / e2e_s, 3), "unit": UNIT,
                    "h2d_bytes_per_step": int(D.numel() * 8),
                    "d2h_bytes_per_step": int(2 * D.numel() * 8 + m * 8)},
            # our kernels per step: tensor path k_dmax, k_dbank, k_jk_umma, k_finalize_blocked;
            # CUDA-core path k_jk_cuda, k_finalize
-           "gpu_launches": int((4 if args.precision in ("fp16x2", "bf16x2") else 2) * args.steps),
+           "gpu_launches": int((4 if split else 2) * args.steps),
            "clocks": clk.summary(),
            "esmf_energy_gradient": energy,
-           "esmf_gvp_gradient": gvp,
-           "batched_uneven": batch}
+           "esmf_gvp_gradient": gvp}
+    if not args.headline_only:
+        # the other store precisions of the same workload, the 400-function
+        # 64-density split build, the integral-direct ribbon, batched uneven
+        # molecules and the serving stream, each with its own roofline
+        subs = {}
+        for prec in ("fp64", "fp32", "fp16x2"):
+            if prec != args.precision:
+                subs[f"stored_n200_m16_{prec}"] = sub_stored(fock, W, dev, stream, prec, alu_peaks)
+        subs["precision_n400_m64_fp16x2"] = sub_precision(fock, W, dev, stream)
+        subs["direct_n2000_m32_fp32"] = sub_direct(fock, W, dev, stream, alu_peaks)
+        subs["batched_uneven_fp16x2"] = run_batched(fock, W, dev, stream, "fp16x2")
+        out["configs"] = subs
+        if rank == 0 and world == 1 and not args.no_serving:
+            out["configs"]["serving"] = run_serving(args, quick=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = oracle_baseline(w, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    fb.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -320,7 +446,7 @@ def run_direct(args):
     # about 25 operations each (one erf, exp and rsqrt among them) plus 20 m
     # contraction flops; the FP32 peak is derived from the unit counts
     flops = st["n_quartets_kept"] * (81 * 25 + 20 * m)
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    peak = fock.esmf_measure_fma_peak("fp32", local)
     achieved = flops / kern_s / 1e12
     out = {"metric": METRIC, "value": round(1e3 / ms_step, 4), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -333,7 +459,7 @@ def run_direct(args):
            "quartets_per_s": round(st["n_quartets_kept"] / (ms_step / 1e3), 1),
            "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                        "peak_source": "measured FP32 FMA rate (esmf_measure_fma_peak, this process)",
                         "kernel": "k_jk_cuda", "kernel_ms": round(kern_s * 1e3, 3),
                         "algorithmic_flops": flops},
            "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
@@ -543,63 +669,86 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ serving
 def serve_against_plain_fp64(args, mols, reqs, dens, budget, local):
-    """The plain FP64 GPU build on a bounded prefix of the same request stream:
-    one request at a time, FP64 integral stores (integral-direct when a store
-    is over budget), no batching or graphs, cold start; requests are taken in
-    order until about --serve-fp64-seconds have passed.  The served form
-    (split FP16 stores on tensor cores, concurrent slots, graph replay) then
-    serves the same prefix from a cold start, and its J, K are compared with
-    the FP64 results (worst relative Frobenius error over requests and k)."""
+    """The plain FP64 GPU build on a prefix of the same request stream: one
+    request at a time, FP64 integral stores (integral-direct FP64 when a store
+    is over budget), no batching or graphs.  Requests are taken in order until
+    about --serve-fp64-seconds of cold serving (FP64 integral creation
+    included) have passed; that prefix is then served again WARM (stores
+    resident) and timed.  The served form (split FP16 stores on tensor cores,
+    concurrent slots, batched ticks, graph replay) serves the same prefix the
+    same way, cold then warm, and its J, K are compared with the FP64 results
+    (worst relative Frobenius error over requests and densities)."""
     import numpy as np
     from paper_2002_00322_gb300.server import Server
-    plain = []
+
+    def serve(srv, ids, k, keep):
+        res = []
+        t0 = time.perf_counter()
+        tickets = [srv.submit(ids[i], D) for (i, _, _), D in zip(reqs[:k], dens[:k])]
+        for t in tickets:
+            J, K, _ = srv.wait(t)
+            if keep:
+                res.append((J, K))
+        return time.perf_counter() - t0, res
+
     with Server(budget, max_inflight=1, precision="fp64", use_graphs=False, device=local) as srv:
         ids = {}
         t0 = time.perf_counter()
+        k = 0
         for (i, _, _), D in zip(reqs, dens):
-            if plain and time.perf_counter() - t0 >= args.serve_fp64_seconds:
+            if k and time.perf_counter() - t0 >= args.serve_fp64_seconds:
                 break
             if i not in ids:
                 ids[i] = srv.register(mols[i].basis, mols[i].tol)
-            J, K, _ = srv.wait(srv.submit(ids[i], D))
-            plain.append((J, K))
-        plain_s = time.perf_counter() - t0
-        st_plain = srv.stats()
-    k = len(plain)
-    with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True,
+            srv.wait(srv.submit(ids[i], D))
+            k += 1
+        cold_s = time.perf_counter() - t0
+        creates_cold = srv.stats()["creates"]
+        srv.reset_stats()
+        warm_s, plain = serve(srv, ids, k, True)
+        st_warm = srv.stats()
+    with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True, batch=True,
                 device=local) as srv:
         ids = {}
         for (i, _, _) in reqs[:k]:
             if i not in ids:
                 ids[i] = srv.register(mols[i].basis, mols[i].tol)
-        t0 = time.perf_counter()
-        tickets = [srv.submit(ids[i], D) for (i, _, _), D in zip(reqs[:k], dens[:k])]
-        served = [srv.wait(t) for t in tickets]
-        served_s = time.perf_counter() - t0
+        served_cold_s, _ = serve(srv, ids, k, False)
+        srv.reset_stats()
+        served_warm_s, served = serve(srv, ids, k, True)
+        st_served = srv.stats()
 
     def worst(a, b):
         return max(float(np.linalg.norm(x - r) / max(np.linalg.norm(r), 1e-300)) for x, r in zip(a, b))
-    ej = max(worst(s[0], p[0]) for s, p in zip(served, plain))
-    ek = max(worst(s[1], p[1]) for s, p in zip(served, plain))
+    ej = max(worst(s_[0], p_[0]) for s_, p_ in zip(served, plain))
+    ek = max(worst(s_[1], p_[1]) for s_, p_ in zip(served, plain))
     return {"requests": k, "n_basis": [int(mols[i].basis.n) for (i, _, _) in reqs[:k]],
-            "plain_fp64_seconds": round(plain_s, 3), "plain_fp64_builds_per_s": round(k / plain_s, 3),
-            "plain_fp64_creates": st_plain["creates"], "plain_fp64_p50_ms": round(st_plain["p50_ms"], 2),
-            "served_seconds": round(served_s, 3), "served_builds_per_s": round(k / served_s, 3),
-            "speedup": round(plain_s / served_s, 2),
+            "m": [int(m) for (_, m, _) in reqs[:k]],
+            "plain_fp64_cold_seconds": round(cold_s, 3), "plain_fp64_creates": creates_cold,
+            "plain_fp64_warm_seconds": round(warm_s, 3), "plain_fp64_warm_builds_per_s": round(k / warm_s, 3),
+            "plain_fp64_warm_creates": st_warm["creates"],
+            "served_cold_seconds": round(served_cold_s, 3),
+            "served_warm_seconds": round(served_warm_s, 3), "served_warm_builds_per_s": round(k / served_warm_s, 3),
+            "served_warm_creates": st_served["creates"],
+            "warm_speedup": round(warm_s / served_warm_s, 2), "cold_speedup": round(cold_s / served_cold_s, 2),
             "served_vs_fp64_max_rel_err": {"J": ej, "K": ek}}
 
 
-def run_serving(args):
+def run_serving(args, quick=False):
     """Serving workload: 256 requests over a pool of 32 random molecules
     (N uniform in [50, 600], m uniform in [4, 32]) on one build server with a
-    60 GB device budget.  Closed loop first (all requests queued at once:
-    builds/s), then Poisson arrivals at 0.8x that rate (p50/p99 latency)."""
+    60 GB device budget, in the served form (split FP16 hi+lo stores on tensor
+    cores, concurrent slots, batched ticks, CUDA-graph replay).  Closed loop
+    first (all requests queued at once: builds/s), then Poisson arrivals at
+    0.8x that rate (p50/p99 latency), then the comparison with the plain FP64
+    GPU build on a prefix of the stream.  With quick=True the record is
+    returned (the bench line's serving sub-record) instead of printed."""
     import numpy as np
     from paper_2002_00322_gb300 import workloads as W
     from paper_2002_00322_gb300.server import Server
     rank, world, local = env_rank()
     if rank != 0:
-        return
+        return None
     mols, reqs = W.serving_requests(args.serve_requests, pool=args.serve_pool,
                                     nmax=args.serve_nmax)
     budget = int(args.serve_budget_gb * (1 << 30))
@@ -608,8 +757,8 @@ def run_serving(args):
            "n_gpus": 1, "higher_is_better": True, "dtype": "f16x2+f32acc", "data": "synthetic",
            "config": {"workload": f"serving_{len(reqs)}req_pool{len(mols)}_n50-{args.serve_nmax}_m4-32",
                       "budget_gb": args.serve_budget_gb, "max_inflight": args.serve_inflight,
-                      "precision": "fp16x2", "graphs": True}}
-    with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True,
+                      "precision": "fp16x2", "graphs": True, "batched_ticks": True}}
+    with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True, batch=True,
                 device=local) as srv:
         ids = [srv.register(w.basis, w.tol) for w in mols]
         # closed loop
@@ -636,35 +785,27 @@ def run_serving(args):
             srv.wait(t)
         open_s = time.perf_counter() - t0
         st_open = srv.stats()
-    # the same closed loop with batched ticks: the tensor-path builds admitted
-    # together run as one persistent launch (single builds still replay graphs)
-    with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True, batch=True,
-                device=local) as srv:
-        ids = [srv.register(w.basis, w.tol) for w in mols]
-        t0 = time.perf_counter()
-        tickets = [srv.submit(ids[i], D) for (i, _, _), D in zip(reqs, dens)]
-        for t in tickets:
-            srv.wait(t)
-        batched_s = time.perf_counter() - t0
-        st_b = srv.stats()
-    out["closed_loop_batched_ticks"] = {
-        "seconds": round(batched_s, 3), "builds_per_s": round(len(reqs) / batched_s, 3),
-        "batch_launches": st_b["batch_launches"], "batched_builds": st_b["batched_builds"],
-        "graph_launches": st_b["graph_launches"], "creates": st_b["creates"], "evictions": st_b["evictions"],
-        "p50_ms": round(st_b["p50_ms"], 2), "p99_ms": round(st_b["p99_ms"], 2)}
     out["vs_plain_fp64"] = serve_against_plain_fp64(args, mols, reqs, dens, budget, local)
     out["value"] = round(len(reqs) / closed_s, 3)
-    out["closed_loop"] = {"seconds": round(closed_s, 3), "creates": st_closed["creates"],
-                          "evictions": st_closed["evictions"], "graph_launches": st_closed["graph_launches"],
+    out["closed_loop"] = {"seconds": round(closed_s, 3), "builds_per_s": round(len(reqs) / closed_s, 3),
+                          "creates": st_closed["creates"], "evictions": st_closed["evictions"],
+                          "graph_launches": st_closed["graph_launches"],
+                          "batch_launches": st_closed["batch_launches"],
+                          "batched_builds": st_closed["batched_builds"],
                           "peak_inflight": st_closed["peak_inflight"], "p50_ms": round(st_closed["p50_ms"], 2),
                           "p99_ms": round(st_closed["p99_ms"], 2)}
     out["open_loop"] = {"arrival_rate_per_s": round(rate, 3), "seconds": round(open_s, 3),
                         "builds_per_s": round(len(reqs) / open_s, 3), "p50_ms": round(st_open["p50_ms"], 2),
                         "p99_ms": round(st_open["p99_ms"], 2), "mean_ms": round(st_open["mean_ms"], 2),
                         "creates": st_open["creates"], "evictions": st_open["evictions"],
+                        "graph_launches": st_open["graph_launches"],
+                        "batch_launches": st_open["batch_launches"],
                         "peak_inflight": st_open["peak_inflight"], "failed": st_open["failed"]}
     out["density_builds"] = int(sum(m for (_, m, _) in reqs))
+    if quick:
+        return out
     print(json.dumps(out), flush=True)
+    return None
 
 
 def main():
@@ -673,7 +814,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp16x2", choices=["fp64", "fp32", "fp16x2", "bf16x2"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16x2", "bf16x2"],
+                    help="store precision of the headline build (default FP64, the paper's arithmetic)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the other configurations (sub-records under 'configs')")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sub-record")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -686,7 +831,7 @@ def main():
     ap.add_argument("--serve-nmax", type=int, default=600)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--serve-inflight", type=int, default=4)
-    ap.add_argument("--serve-fp64-seconds", type=float, default=60.0,
+    ap.add_argument("--serve-fp64-seconds", type=float, default=45.0,
                     help="time bound of the plain FP64 leg of --serving (a prefix of the stream)")
     args = ap.parse_args()
     if args.serving:

@@ -287,6 +287,20 @@ int esmf_fock_kernel_time(esmf_fock_t *h, double *ms, int64_t *launches, int res
 int esmf_fock_build_noalloc(esmf_fock_t *h, int m, const double *D, double *J,
                             double *K, double *F, double *traces, void *stream);
 
+/*
+ * esmf_measure_fma_peak -- measured CUDA-core fused-multiply-add throughput of
+ * a device, the denominator of the FP64 / FP32 ALU rooflines of the CUDA-core
+ * contraction kernels (a measurement aid; the paper has no counterpart).
+ * Runs independent FMA chains on every SM (grid a multiple of the SM count,
+ * one warm-up launch, best of three timed with CUDA events on a private
+ * stream) and writes the rate in TFLOP/s (2 flops per FMA) to *tflops.
+ * Changes no clock, power or other device setting.  Takes about 0.5 s.
+ *   precision  ESMF_PREC_FP64 or ESMF_PREC_FP32
+ *   device     CUDA device ordinal
+ * Errors: INVALID_ARG, CUDA.
+ */
+int esmf_measure_fma_peak(int precision, int device, double *tflops);
+
 /* Statistics of a handle (host struct filled in).  Errors: INVALID_ARG. */
 int esmf_fock_stats(const esmf_fock_t *h, esmf_stats_t *out);
 

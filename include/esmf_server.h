@@ -44,6 +44,7 @@ typedef struct {
     double span_s;              /* first submit to last completion               */
     int64_t batch_launches;     /* batched ticks issued (ESMF_SERVER_BATCH)      */
     int64_t batched_builds;     /* builds that ran inside a batched tick         */
+    int64_t tick_graph_launches;/* batched ticks replayed from a captured graph  */
 } esmf_server_stats_t;
 
 /*
@@ -58,11 +59,16 @@ typedef struct {
  *                 the tensor-core path (stored FP16X2/BF16X2), copies their
  *                 inputs on their slots' streams and builds them together
  *                 with esmf_fock_build_batch (up to ESMF_MAX_BATCH per call)
- *                 on a stream of its own; other requests (molecules that fell
- *                 back to integral-direct FP32 under the budget, or FP64/FP32
- *                 servers) run as single builds, replayed from graphs when
- *                 ESMF_SERVER_GRAPHS is also set.  The batching across
- *                 molecules has no counterpart in the paper.
+ *                 on a stream of its own; with ESMF_SERVER_GRAPHS also set,
+ *                 each tick composition (molecules, density counts, slots) is
+ *                 captured into a CUDA graph once and the tick's persistent
+ *                 launches are replayed from it (up to 128 compositions are
+ *                 kept; graphs are dropped when a member's memory moves).
+ *                 Other requests (molecules that fell back to integral-direct
+ *                 FP32 under the budget, or FP64/FP32 servers) run as single
+ *                 builds, replayed from graphs when ESMF_SERVER_GRAPHS is set.
+ *                 The batching across molecules has no counterpart in the
+ *                 paper.
  * Errors: INVALID_ARG (also for unknown flag bits), CUDA, OOM.
  */
 #define ESMF_SERVER_GRAPHS 1

@@ -95,6 +95,11 @@ struct esmf_fock {
     }
 };
 
+// Most runs (R blocks) per item of the tensor-core brick order (see below).
+#ifndef ESMF_ITEM_RUNS
+#define ESMF_ITEM_RUNS 32
+#endif
+
 namespace {
 
 struct DeviceGuard {
@@ -465,7 +470,7 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     const int eb = elem_bytes(precision);
     const int align_elems = 16 / eb;     // every brick's record starts on 16 bytes
     const bool split16 = precision >= ESMF_PREC_FP16X2;
-    const int head = split16 ? MASK_WORDS : 0;   // keep mask ahead of the values
+    const int head = MASK_BYTES / eb;            // keep mask ahead of the values
     int64_t unique = 0;
     std::vector<int64_t> order;
     for (int64_t i = 0; i < ncand; ++i) {
@@ -499,7 +504,7 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     // accumulation length (and its rounding error) for large molecules; up to
     // 8 * kItemRuns functions no item is split.
     {
-        constexpr int kItemRuns = 32;
+        constexpr int kItemRuns = ESMF_ITEM_RUNS;
         auto diag = [&](size_t i) { return kept[i].R == kept[i].P && kept[i].S == kept[i].Q; };
         auto same_window = [&](size_t i, size_t j) {
             return kept[i].P == kept[j].P && kept[i].Q == kept[j].Q && kept[i].S / SWIN == kept[j].S / SWIN &&

@@ -34,11 +34,14 @@ struct BrickDesc {          // 16 bytes
 constexpr int SWIN = 5;
 enum : int { BRICK_RUN_FIRST = 1, BRICK_RUN_LAST = 2, BRICK_ITEM_FIRST = 4, BRICK_ITEM_LAST = 8 };
 
-// Split 16-bit stores (FP16X2 / BF16X2) hold one record per brick: a 512-byte
-// keep mask (byte v = p*64 + q*8 + r, bit s) followed by the kept values as
-// 32-bit words (hi half in the low 16 bits, lo half in the high 16 bits),
-// all scaled by one power of two (the handle's vscale).
-constexpr int MASK_WORDS = 128;
+// Every stored record starts with a 512-byte keep mask (byte v = p*64 + q*8 +
+// r, bit s), followed by the kept values in local-index order: FP64 or FP32
+// values, or, for split 16-bit stores (FP16X2 / BF16X2), 32-bit words (hi
+// half in the low 16 bits, lo half in the high 16 bits) of the value times
+// one power of two (the handle's vscale).  The mask spans MASK_BYTES / eb
+// store elements of eb bytes.
+constexpr int MASK_BYTES = 512;
+constexpr int MASK_WORDS = MASK_BYTES / 4;
 
 // device view of the basis: functions padded to a multiple of BLK; padded
 // functions have nprim = 0 and Q = 0 and are never kept

@@ -3,16 +3,21 @@
 //
 // One CTA processes one brick (P Q | R S) at a time.  The brick's kept
 // integrals are expanded into a dense 8^4 tile in shared memory (from the
-// packed store, or evaluated in place in direct mode), and every DISTINCT
-// ordered block tuple of its permutation orbit
+// packed store, whose records carry their keep masks, or evaluated in place
+// in direct mode), and every DISTINCT ordered block tuple of its permutation
+// orbit
 //   (P Q R S) (Q P R S) (P Q S R) (Q P S R) (R S P Q) (S R P Q) (R S Q P) (S R Q P)
 // contributes, for every density k,
 //   K[a][c] += sum_{b,d} (ab|cd) D_k[b][d]      (tuple (A,B,C,E), a in A ...)
-//   J[a][b] += sum_{c,d} (ab|cd) D_k[c][d]      (only tuples with A >= B)
-// which is the ordered-tuple form of Eq. J_and_K.  Each output element is a
-// 64-term dot product accumulated in registers (TA) and flushed to the FP64
-// accumulators with one atomic add per brick.  J is accumulated only on the
-// lower block triangle and mirrored by the finalisation kernel.
+//   J[a][b] += sum_{c,d} (ab|cd) D_k[c][d]      (tuples with A >= B)
+// which is the ordered-tuple form of Eq. J_and_K.  The Coulomb updates of a
+// tuple and of its (C,E)-swapped partner share the output block, so they are
+// formed once against Dj[C,E] = D[C,E] + [C != E] D[E,C]^T: J[P,Q] from
+// Dj[R,S] and J[R,S] from Dj[P,Q] (ten output blocks per brick, not twelve).
+// Each output element is a 64-term dot product accumulated in registers (TA)
+// and flushed to the FP64 accumulators with one atomic add per brick.  J is
+// accumulated only on the lower block triangle and mirrored by the
+// finalisation kernel.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -35,6 +40,13 @@ namespace esmf {
 __constant__ int c_tuple[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
                                   {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
 __constant__ int c_stride[4] = {512, 64, 8, 1};
+// Output slots of a brick: 0-7 exchange (tuple t), 8 Coulomb J[P,Q] (terms
+// over R x S against Dj[R,S]), 9 Coulomb J[R,S] (terms over P x Q against
+// Dj[P,Q]).  Per slot the brick index position of the output row index, the
+// output column index, and the two summed indices.
+__constant__ int c_slot[10][4] = {{0, 2, 1, 3}, {1, 2, 0, 3}, {0, 3, 1, 2}, {1, 3, 0, 2},
+                                  {2, 0, 3, 1}, {3, 0, 2, 1}, {2, 1, 3, 0}, {3, 1, 2, 0},
+                                  {0, 1, 2, 3}, {2, 3, 0, 1}};
 
 __device__ __forceinline__ bool kept_e(const double *qb, const double *qk, int e, double tol, int n,
                                        int P, int Q, int R, int S) {
@@ -87,13 +99,16 @@ __device__ __forceinline__ int scan256(int v, int *wsum) {
     return ((wid > 0) ? wsum[8 + wid - 1] : 0) + x - v;
 }
 
+// density tiles of one brick: 0-7 D[B][E] of exchange tuple t (its summed
+// blocks), 8 Dj[R,S], 9 Dj[P,Q]
 template <typename TA, int MC, bool DIRECT>
 struct JKSmem {
     TA V[BRICK];
-    TA Ds[16][64][MC];
+    TA Ds[10][64][MC];
     double qb[64], qk[64];
     int wsum[16];
-    int active[12];
+    int slots[10];            // active output slots of the brick
+    int nslots;
     int blk[4];
     int tsw[4][8];            // tile_swizzle(v * stride[dim]) for each index and value
 };
@@ -127,6 +142,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
         if (threadIdx.x == 0) {
             sm.blk[0] = d.P; sm.blk[1] = d.Q; sm.blk[2] = d.R; sm.blk[3] = d.S;
             const int bl[4] = {d.P, d.Q, d.R, d.S};
+            int ns = 0, act4 = 0;
             for (int t = 0; t < 8; ++t) {
                 int act = 1;
                 for (int u = 0; u < t; ++u) {
@@ -134,14 +150,15 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                     for (int x = 0; x < 4; ++x) same &= bl[c_tuple[t][x]] == bl[c_tuple[u][x]];
                     if (same) { act = 0; break; }
                 }
-                sm.active[t] = act;
+                if (act) sm.slots[ns++] = t;
+                if (t == 4) act4 = act;
             }
-            sm.active[8] = sm.active[0];
-            sm.active[9] = sm.active[2];
-            sm.active[10] = sm.active[4];
-            sm.active[11] = sm.active[6];
+            // J[P,Q] always; J[R,S] unless (R,S) = (P,Q) (tuple 4 repeats tuple 0)
+            sm.slots[ns++] = 8;
+            if (act4) sm.slots[ns++] = 9;
+            sm.nslots = ns;
         }
-        if (threadIdx.x < 64) {
+        if (SRC == 4 && threadIdx.x < 64) {
             const int t = threadIdx.x;
             sm.qb[t] = a.Q[(int64_t)(d.P * 8 + (t >> 3)) * np + d.Q * 8 + (t & 7)];
             sm.qk[t] = a.Q[(int64_t)(d.R * 8 + (t >> 3)) * np + d.S * 8 + (t & 7)];
@@ -159,8 +176,15 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
         {
             const int e0 = threadIdx.x * 16;
             unsigned mask = 0;
-            for (int j = 0; j < 16; ++j)
-                if (kept_e(sm.qb, sm.qk, e0 + j, a.tol, n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
+            constexpr int EB = SRC == 0 ? 8 : 4;   // bytes per store element
+            if constexpr (SRC == 4) {
+                for (int j = 0; j < 16; ++j)
+                    if (kept_e(sm.qb, sm.qk, e0 + j, a.tol, n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
+            } else {
+                // the record's keep mask: bytes 2t and 2t + 1 cover elements 16t .. 16t + 15
+                const unsigned char *mk = reinterpret_cast<const unsigned char *>(a.store) + a.offsets[bi] * EB;
+                mask = (unsigned)mk[2 * threadIdx.x] | ((unsigned)mk[2 * threadIdx.x + 1] << 8);
+            }
             if constexpr (SRC == 4) {
                 // kept local indices listed in ascending order (in the density
                 // tiles' space, unused until the first chunk's barrier), then
@@ -182,7 +206,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                 }
             } else {
                 int pos = scan256(__popc(mask), sm.wsum);
-                const int64_t base = a.offsets[bi] + (SRC >= 2 ? MASK_WORDS : 0);
+                const int64_t base = a.offsets[bi] + MASK_BYTES / EB;
                 const float inv = (SRC >= 2) ? 1.0f / a.vscale : 1.0f;
                 for (int j = 0; j < 16; ++j) {
                     TA v = TA(0);
@@ -210,50 +234,53 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
         // ---- densities in chunks of MC
         for (int d0 = 0; d0 < a.m; d0 += MC) {
             __syncthreads();
-            for (int t = threadIdx.x; t < 16 * 64 * MC; t += blockDim.x) {
-                const int dd = t % MC, ij = (t / MC) & 63, ab = t / (MC * 64);
-                const int ra = sm.blk[ab >> 2] * 8 + (ij >> 3), cb = sm.blk[ab & 3] * 8 + (ij & 7);
+            for (int t = threadIdx.x; t < 10 * 64 * MC; t += blockDim.x) {
+                const int dd = t % MC, ij = (t / MC) & 63, tile = t / (MC * 64);
+                const int x = ij >> 3, y = ij & 7;
                 TA v = TA(0);
-                if (d0 + dd < a.m && ra < n && cb < n) v = (TA)a.D[(int64_t)(d0 + dd) * nn + (int64_t)ra * n + cb];
-                sm.Ds[ab][ij][dd] = v;
+                if (d0 + dd < a.m) {
+                    const double *Dk = a.D + (int64_t)(d0 + dd) * nn;
+                    if (tile < 8) {
+                        const int ra = sm.blk[c_tuple[tile][1]] * 8 + x, cb = sm.blk[c_tuple[tile][3]] * 8 + y;
+                        if (ra < n && cb < n) v = (TA)Dk[(int64_t)ra * n + cb];
+                    } else {
+                        // Dj of the summed blocks (C, E): D[C,E] + [C != E] D[E,C]^T
+                        const int C = sm.blk[tile == 8 ? 2 : 0], E = sm.blk[tile == 8 ? 3 : 1];
+                        const int ra = C * 8 + x, cb = E * 8 + y;
+                        if (ra < n && cb < n) {
+                            double w = Dk[(int64_t)ra * n + cb];
+                            if (C != E) w += Dk[(int64_t)cb * n + ra];
+                            v = (TA)w;
+                        }
+                    }
+                }
+                sm.Ds[tile][ij][dd] = v;
             }
             __syncthreads();
-            for (int task = threadIdx.x; task < 12 * 64; task += blockDim.x) {
-                const int slot = task >> 6, e = task & 63;
-                if (!sm.active[slot]) continue;
-                const bool isJ = slot >= 8;
-                const int tu = isJ ? (slot - 8) * 2 : slot;
-                const int A = c_tuple[tu][0], B = c_tuple[tu][1], C = c_tuple[tu][2], E = c_tuple[tu][3];
-                int base, dx, dab, orow, ocol;
-                if (!isJ) {   // output (a in A, c in C), terms (b in B, d in E)
-                    const int ia = e >> 3, ic = e & 7;
-                    base = sm.tsw[A][ia] ^ sm.tsw[C][ic];
-                    dx = B;
-                    dab = B * 4 + E;
-                    orow = sm.blk[A] * 8 + ia; ocol = sm.blk[C] * 8 + ic;
-                } else {      // output (a in A, b in B), terms (c in C, d in E)
-                    const int ia = e >> 3, ib = e & 7;
-                    base = sm.tsw[A][ia] ^ sm.tsw[B][ib];
-                    dx = C;
-                    dab = C * 4 + E;
-                    orow = sm.blk[A] * 8 + ia; ocol = sm.blk[B] * 8 + ib;
-                }
-                // placement of y * stride[E] from its three bits (the swizzle is linear)
-                const int t1 = sm.tsw[E][1], t2 = sm.tsw[E][2], t4 = sm.tsw[E][4];
+            const int ntask = sm.nslots * 64;
+            for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+                const int slot = sm.slots[task >> 6], e = task & 63;
+                const int A = c_slot[slot][0], C = c_slot[slot][1], X = c_slot[slot][2], Y = c_slot[slot][3];
+                // output (a in block A, c in block C), terms (x in block X, y in block Y)
+                const int ia = e >> 3, ic = e & 7;
+                const int base = sm.tsw[A][ia] ^ sm.tsw[C][ic];
+                const int orow = sm.blk[A] * 8 + ia, ocol = sm.blk[C] * 8 + ic;
+                // placement of y * stride[Y] from its three bits (the swizzle is linear)
+                const int t1 = sm.tsw[Y][1], t2 = sm.tsw[Y][2], t4 = sm.tsw[Y][4];
                 TA acc[MC];
 #pragma unroll
                 for (int dd = 0; dd < MC; ++dd) acc[dd] = TA(0);
                 for (int x = 0; x < 8; ++x) {
-                    const int bx = base ^ sm.tsw[dx][x];
+                    const int bx = base ^ sm.tsw[X][x];
 #pragma unroll
                     for (int y = 0; y < 8; ++y) {
                         const TA v = sm.V[bx ^ ((y & 1) ? t1 : 0) ^ ((y & 2) ? t2 : 0) ^ ((y & 4) ? t4 : 0)];
-                        const TA *dp = sm.Ds[dab][x * 8 + y];
+                        const TA *dp = sm.Ds[slot][x * 8 + y];
 #pragma unroll
                         for (int dd = 0; dd < MC; ++dd) acc[dd] += v * dp[dd];
                     }
                 }
-                double *out = isJ ? a.Jacc : a.Kacc;
+                double *out = slot >= 8 ? a.Jacc : a.Kacc;
 #pragma unroll
                 for (int dd = 0; dd < MC; ++dd)
                     if (d0 + dd < a.m) atomicAdd(out + (int64_t)(d0 + dd) * npnp + (int64_t)orow * np + ocol, (double)acc[dd]);

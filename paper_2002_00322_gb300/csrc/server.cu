@@ -85,12 +85,15 @@ struct esmf_server {
     std::map<int64_t, std::shared_ptr<Request>> tickets;
     std::vector<Slot> slots;
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;   // (molecule, m, slot)
+    // batched ticks captured once per composition: (molecule, m, slot) of
+    // every entry in tick order
+    std::map<std::vector<std::tuple<int, int, int>>, cudaGraphExec_t> tick_graphs;
     int64_t next_ticket = 1;
     uint64_t use_clock = 0;
     int inflight = 0;
     // statistics
     int64_t submitted = 0, completed = 0, failed = 0, creates = 0, evictions = 0, graph_launches = 0;
-    int64_t batch_launches = 0, batched_builds = 0;
+    int64_t batch_launches = 0, batched_builds = 0, tick_graph_launches = 0;
     int64_t peak_inflight = 0;
     std::vector<double> lat_ms;
     Clock::time_point first_submit, last_done;
@@ -108,6 +111,21 @@ int64_t resident_bytes(const esmf_server *s) {
 // Captured graphs hold the device addresses of a molecule's work memory and of
 // a slot's I/O buffers: drop them whenever either is reallocated or freed.
 // (Only called for an idle molecule or a free slot, so none of them runs.)
+// Batched-tick graphs that contain molecule `mol` (field 0) or slot `slot`
+// (field 2) of any entry; a negative argument matches nothing.
+void drop_tick_graphs(esmf_server *s, int mol, int slot) {
+    for (auto it = s->tick_graphs.begin(); it != s->tick_graphs.end();) {
+        bool hit = false;
+        for (const auto &e : it->first) hit |= std::get<0>(e) == mol || std::get<2>(e) == slot;
+        if (hit) {
+            cudaGraphExecDestroy(it->second);
+            it = s->tick_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 void drop_graphs_of(esmf_server *s, int mol) {
     for (auto it = s->graphs.begin(); it != s->graphs.end();) {
         if (std::get<0>(it->first) == mol) {
@@ -117,6 +135,7 @@ void drop_graphs_of(esmf_server *s, int mol) {
             ++it;
         }
     }
+    drop_tick_graphs(s, mol, -1);
 }
 
 void drop_graphs_of_slot(esmf_server *s, int slot) {
@@ -128,6 +147,7 @@ void drop_graphs_of_slot(esmf_server *s, int slot) {
             ++it;
         }
     }
+    drop_tick_graphs(s, -1, slot);
 }
 
 void evict(esmf_server *s, int idx) {
@@ -274,11 +294,62 @@ bool on_tensor_path(esmf_fock_t *h) {
     return esmf_fock_stats(h, &st) == ESMF_OK && st.mode == ESMF_MODE_STORED && st.precision >= ESMF_PREC_FP16X2;
 }
 
+// Most batched-tick compositions kept as instantiated graphs; beyond it the
+// cache starts over (a stream of ever-new compositions then costs a capture
+// per tick, as many as without the cache).
+constexpr size_t kMaxTickGraphs = 128;
+
+// The batched build of one tick from its captured graph: captured on first
+// use of this composition (molecules, density counts and slots), replayed
+// after.  The handles' work memory for these m was reserved at admission, so
+// the captured build allocates nothing.
+int launch_tick_graph(esmf_server *s, const std::vector<std::tuple<int, int, int>> &key, int count,
+                      esmf_fock_t *const *hs, const int *ms, const double *const *Ds, double *const *Js,
+                      double *const *Ks, double *const *ts) {
+    auto it = s->tick_graphs.find(key);
+    if (it == s->tick_graphs.end()) {
+        if (s->tick_graphs.size() >= kMaxTickGraphs) {
+            for (auto &g : s->tick_graphs) cudaGraphExecDestroy(g.second);
+            s->tick_graphs.clear();
+        }
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        if (cudaStreamBeginCapture(s->tick_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("begin capture of a batched tick failed");
+            return ESMF_ERR_CUDA;
+        }
+        const int rc = esmf_fock_build_batch(count, hs, ms, Ds, Js, Ks, nullptr, ts, s->tick_stream);
+        const cudaError_t e = cudaStreamEndCapture(s->tick_stream, &g);
+        if (rc != ESMF_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (rc == ESMF_OK) set_error("capture of a batched tick failed");
+            return rc != ESMF_OK ? rc : ESMF_ERR_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            cudaGetLastError();
+            set_error("instantiating a batched tick failed");
+            return ESMF_ERR_CUDA;
+        }
+        it = s->tick_graphs.emplace(key, ge).first;
+    }
+    if (cudaGraphLaunch(it->second, s->tick_stream) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("launching a batched tick graph failed");
+        return ESMF_ERR_CUDA;
+    }
+    ++s->tick_graph_launches;
+    return ESMF_OK;
+}
+
 // One batched tick: the builds of the slots in `tick` (distinct molecules on
 // the tensor path, inputs being copied on their own streams) as one
 // esmf_fock_build_batch call on the tick stream, i.e. one persistent launch
-// per pass of 16 densities for all of them; each slot's result copies wait
-// for the tick.
+// per pass of 16 densities for all of them, replayed from a CUDA graph when
+// graphs are on; each slot's result copies wait for the tick.
 void issue_tick(esmf_server *s, const std::vector<int> &tick) {
     const int count = (int)tick.size();
     esmf_fock_t *hs[ESMF_MAX_BATCH] = {};
@@ -286,14 +357,19 @@ void issue_tick(esmf_server *s, const std::vector<int> &tick) {
     const double *Ds[ESMF_MAX_BATCH] = {};
     double *Js[ESMF_MAX_BATCH] = {}, *Ks[ESMF_MAX_BATCH] = {}, *ts[ESMF_MAX_BATCH] = {};
     int rc = ESMF_OK;
+    std::vector<std::tuple<int, int, int>> key;
     for (int i = 0; i < count && rc == ESMF_OK; ++i) {
         Slot &sl = s->slots[tick[i]];
         hs[i] = s->mols[sl.req->mol].h;
         ms[i] = sl.req->m;
         Ds[i] = sl.dD; Js[i] = sl.dJ; Ks[i] = sl.dK; ts[i] = sl.dt;
+        key.emplace_back(sl.req->mol, sl.req->m, tick[i]);
         if (cudaStreamWaitEvent(s->tick_stream, sl.ev_in, 0) != cudaSuccess) rc = ESMF_ERR_CUDA;
     }
-    if (rc == ESMF_OK) rc = esmf_fock_build_batch(count, hs, ms, Ds, Js, Ks, nullptr, ts, s->tick_stream);
+    if (rc == ESMF_OK) {
+        rc = s->use_graphs ? launch_tick_graph(s, key, count, hs, ms, Ds, Js, Ks, ts)
+                           : esmf_fock_build_batch(count, hs, ms, Ds, Js, Ks, nullptr, ts, s->tick_stream);
+    }
     if (rc == ESMF_OK && cudaEventRecord(s->tick_ev, s->tick_stream) != cudaSuccess) rc = ESMF_ERR_CUDA;
     if (rc == ESMF_OK) {
         ++s->batch_launches;
@@ -544,6 +620,7 @@ int esmf_server_stats(esmf_server_t *s, esmf_server_stats_t *out) {
     out->submitted = s->submitted; out->completed = s->completed; out->failed = s->failed;
     out->creates = s->creates; out->evictions = s->evictions; out->graph_launches = s->graph_launches;
     out->batch_launches = s->batch_launches; out->batched_builds = s->batched_builds;
+    out->tick_graph_launches = s->tick_graph_launches;
     out->resident_bytes = resident_bytes(s);
     out->peak_inflight = s->peak_inflight;
     if (!s->lat_ms.empty()) {
@@ -568,7 +645,7 @@ int esmf_server_reset_stats(esmf_server_t *s) {
     if (!s) { set_error("server is NULL"); return ESMF_ERR_INVALID_ARG; }
     std::lock_guard<std::mutex> lk(s->mu);
     s->submitted = s->completed = s->failed = s->creates = s->evictions = s->graph_launches = 0;
-    s->batch_launches = s->batched_builds = 0;
+    s->batch_launches = s->batched_builds = s->tick_graph_launches = 0;
     s->peak_inflight = s->inflight;
     s->lat_ms.clear();
     s->have_first = false;
@@ -587,6 +664,7 @@ void esmf_server_destroy(esmf_server_t *s) {
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.second);
+    for (auto &g : s->tick_graphs) cudaGraphExecDestroy(g.second);
     for (auto &mol : s->mols) if (mol.h) esmf_fock_destroy(mol.h);
     for (auto &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);

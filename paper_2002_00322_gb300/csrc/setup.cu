@@ -330,21 +330,22 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
         int pos = block_excl_scan256(__popc(mask), sm.wsum, total);
         for (int j = 0; j < 16; ++j)
             if (mask & (1u << j)) sm.klist[pos++] = (unsigned short)(e0 + j);
+        // record: 512-byte keep mask, then the kept values (FP64 / FP32, or
+        // (hi | lo << 16) words of the value times the store's power-of-two
+        // scale); offsets count store elements of sizeof(element) bytes
+        constexpr int EB = PREC == 0 ? 8 : 4;
         const int64_t base = offsets[bi];
-        uint32_t *rec = reinterpret_cast<uint32_t *>(store) + (PREC >= 2 ? base : 0);
-        if (PREC >= 2) {
-            // record: 512-byte keep mask, then the kept values as (hi | lo << 16)
-            // words of the value times the store's power-of-two scale
-            unsigned char *mk = reinterpret_cast<unsigned char *>(rec);
-            mk[2 * threadIdx.x] = (unsigned char)(mask & 0xffu);
-            mk[2 * threadIdx.x + 1] = (unsigned char)(mask >> 8);
-        }
+        unsigned char *mk = reinterpret_cast<unsigned char *>(store) + base * EB;
+        mk[2 * threadIdx.x] = (unsigned char)(mask & 0xffu);
+        mk[2 * threadIdx.x + 1] = (unsigned char)(mask >> 8);
+        const int64_t vbase = base + MASK_BYTES / EB;
+        uint32_t *rec = reinterpret_cast<uint32_t *>(store) + (PREC >= 2 ? vbase : 0);
         __syncthreads();
         for (int i = threadIdx.x; i < total; i += blockDim.x) {
             const int e = sm.klist[i];
             const T v = contracted_eri<T, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
             if (PREC == 0 || PREC == 1) {
-                reinterpret_cast<T *>(store)[base + i] = v;
+                reinterpret_cast<T *>(store)[vbase + i] = v;
             } else {
                 const double xs = (double)v * (double)vscale;
                 uint16_t hb, lb;
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
                     hb = __bfloat16_as_ushort(h);
                     lb = __bfloat16_as_ushort(l);
                 }
-                rec[MASK_WORDS + i] = (uint32_t)hb | ((uint32_t)lb << 16);
+                rec[i] = (uint32_t)hb | ((uint32_t)lb << 16);
             }
         }
     }

@@ -31,7 +31,8 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_schwarz", "esmf_fock_destroy", "esmf_strerror", "esmf_last_error",
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
-           "esmf_fock_autotune", "esmf_fock_create_screened", "esmf_fock_build_batch"]
+           "esmf_fock_autotune", "esmf_fock_create_screened", "esmf_fock_build_batch",
+           "esmf_measure_fma_peak"]
 MAX_BATCH = 16
 SCREENINGS = {"schwarz": 0, "pair_max": 1}
 PATHS = {"auto": 0, "cuda_core": 1}
@@ -118,6 +119,8 @@ def load(path=None):
         L.esmf_gvp_gradient.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, C.c_double, C.c_double,
                                         C.c_double, vp, vp, vp, vp]
         L.esmf_gvp_gradient.restype = C.c_int
+        L.esmf_measure_fma_peak.argtypes = [C.c_int, C.c_int, dp]
+        L.esmf_measure_fma_peak.restype = C.c_int
         L.esmf_fock_destroy.argtypes = [vp]
         L.esmf_fock_destroy.restype = None
         L.esmf_strerror.argtypes = [C.c_int]
@@ -283,6 +286,14 @@ def esmf_fock_kernel_time(h, reset=True):
     _check(load().esmf_fock_kernel_time(h, C.byref(ms), C.byref(n), int(bool(reset))),
            "esmf_fock_kernel_time")
     return ms.value, n.value
+
+
+def esmf_measure_fma_peak(precision="fp64", device=0):
+    """Measured CUDA-core FMA rate of the device in TFLOP/s (FP64 or FP32)."""
+    out = C.c_double(0.0)
+    _check(load().esmf_measure_fma_peak(PRECISIONS[precision], int(device), C.byref(out)),
+           "esmf_measure_fma_peak")
+    return out.value
 
 
 def esmf_fock_destroy(h):

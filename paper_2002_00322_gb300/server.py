@@ -25,7 +25,8 @@ class esmf_server_stats_t(C.Structure):
                 ("resident_bytes", C.c_int64), ("peak_inflight", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_ms", C.c_double), ("span_s", C.c_double),
-                ("batch_launches", C.c_int64), ("batched_builds", C.c_int64)]
+                ("batch_launches", C.c_int64), ("batched_builds", C.c_int64),
+                ("tick_graph_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -153,43 +153,7 @@ def test_invalid_build_arguments(esmf, tiny_ref):
 
 
 # ------------------------------------------------------------- full sizes
-def sampled_check(esmf, w, mode, prec, n_j=6, n_k=10, seed=0, tol=None):
-    """Full-size build vs oracle elements computed one by one."""
-    J, K, F, t, st = gpu_build(esmf, w, mode, prec)
-    o = Oracle(w.basis)
-    rng = np.random.default_rng(seed)
-    n = w.basis.n
-    jidx = rng.integers(0, n, size=(n_j, 2))
-    # exchange elements near the diagonal carry the largest values; mix both
-    kidx = np.concatenate([rng.integers(0, n, size=(n_k // 2, 2)),
-                           np.stack([r := rng.integers(0, n, size=n_k - n_k // 2),
-                                     np.clip(r + rng.integers(-6, 7, size=r.size), 0, n - 1)], 1)])
-    Je, Ke = o.jk_elements(w.D, w.tol, jidx, kidx)
-    tol = tol if tol is not None else TOL[prec]
-    for k in range(w.m):
-        # per-element error relative to the matrix scale of the GPU result
-        sj, sk = np.max(np.abs(J[k])), np.max(np.abs(K[k]))
-        ej = np.max(np.abs(J[k][jidx[:, 0], jidx[:, 1]] - Je[k])) / sj
-        ek = np.max(np.abs(K[k][kidx[:, 0], kidx[:, 1]] - Ke[k])) / sk
-        assert ej <= tol and ek <= tol, (k, ej, ek)
-    # properties that hold at any size
-    Jm = J.transpose(0, 2, 1)
-    assert np.max(np.abs(J - Jm)) <= tol * np.max(np.abs(J))      # J is symmetric
-    return J, K, st
-
-
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16x2"])
-def test_stored_full_size_sampled(esmf, prec):
-    w = W.stored()
-    J, K, st = sampled_check(esmf, w, "stored", prec)
-    assert st["n_bricks"] == 52975
-
-
-def test_precision_full_size_sampled(esmf):
-    w = W.precision()
-    sampled_check(esmf, w, "stored", "fp16x2", n_j=3, n_k=8)
-
-
+# Whole-matrix parity at the full workload sizes lives in test_gpu_fullsize.py.
 def test_direct_small_ribbon_full(esmf):
     w = W.direct(length=6, m=5)
     o = Oracle(w.basis)
@@ -223,41 +187,6 @@ def test_tensor_path_matches_cuda_core_path(esmf, prec, case):
     for k in range(w.m):
         assert relerr(J1[k].cpu().numpy(), J2[k].cpu().numpy()) <= tol
         assert relerr(K1[k].cpu().numpy(), K2[k].cpu().numpy()) <= tol
-
-
-@pytest.mark.parametrize("mode,prec", [("direct", "fp32"), ("stored", "fp16x2")])
-def test_direct_full_ribbon_sampled(esmf, mode, prec):
-    """The 2000-function ribbon (m = 32, tol 1e-10) at full size, integral-
-    direct and with its 7.3e9 kept integrals stored (about 32 GB): sampled J
-    and K elements against the oracle computed one by one."""
-    import time
-    import torch
-    w = W.direct()
-    with esmf.FockBuilder(w.basis, w.tol, mode, prec) as fb:
-        D = torch.from_numpy(w.D).cuda()
-        t0 = time.perf_counter()
-        J, K, _, _ = fb.build(D)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        st = fb.stats()
-        t1 = time.perf_counter()
-        fb.build(D)                         # second build: warm
-        torch.cuda.synchronize()
-        dt2 = time.perf_counter() - t1
-    print(f"\nRIBBON {mode}/{prec} n={w.basis.n} m={w.m}: build {dt:.3f} s (warm {dt2:.3f} s), "
-          f"bricks {st['n_bricks']}, kept quartets {st['n_quartets_kept']}, store {st['store_bytes'] / 1e9:.1f} GB, "
-          f"create {st['create_ms']:.0f} ms")
-    J, K = J.cpu().numpy(), K.cpu().numpy()
-    rng = np.random.default_rng(23)
-    n = w.basis.n
-    jidx = rng.integers(0, n, size=(2, 2))
-    r = rng.integers(0, n, size=6)
-    kidx = np.stack([r, np.clip(r + rng.integers(-4, 5, size=6), 0, n - 1)], 1)
-    Je, Ke = Oracle(w.basis).jk_elements(w.D, w.tol, jidx, kidx)
-    for k in range(w.m):
-        ej = np.max(np.abs(J[k][jidx[:, 0], jidx[:, 1]] - Je[k])) / np.max(np.abs(J[k]))
-        ek = np.max(np.abs(K[k][kidx[:, 0], kidx[:, 1]] - Ke[k])) / np.max(np.abs(K[k]))
-        assert ej <= 2e-6 and ek <= 2e-6, (k, ej, ek)
 
 
 @pytest.mark.parametrize("prec", ["fp16x2", "fp32", "fp64"])

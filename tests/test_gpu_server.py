@@ -54,9 +54,12 @@ def test_mixed_requests_equal_standalone(esmf, prec, graphs, batch, budget, infl
     if batch:       # tensor-path builds ran inside batched ticks, any others as (graph-replayed) singles
         assert 1 <= st["batch_launches"] <= st["batched_builds"] <= len(reqs)
         if graphs:
+            # every batched tick runs from its composition's captured graph
             assert st["batched_builds"] + st["graph_launches"] == len(reqs)
+            assert st["tick_graph_launches"] == st["batch_launches"]
         else:
             assert st["batched_builds"] == len(reqs) and st["graph_launches"] == 0
+            assert st["tick_graph_launches"] == 0
     else:
         assert st["batch_launches"] == 0
     if budget < (1 << 30) and inflight == 1:
