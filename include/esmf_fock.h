@@ -213,6 +213,25 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host,
                          double *traces_host, void *stream, int timeout_ms);
 
 /*
+ * esmf_fock_set_density_screening -- density-weighted screening for later
+ * builds on this handle (0 turns it off; the default).  On top of the
+ * create-time screening, a quartet is dropped from a build when
+ *     Q_pq Q_rs max(W_rs, W_pq, W_qs, W_ps, W_qr, W_pr) < tol_d,
+ *     W_xy = max over the build's densities k of max(|D_k[x][y]|, |D_k[y][x]|),
+ * i.e. when every update of Eq. (J_and_K) it makes (each multiplies it by one
+ * of those density elements, and |(pq|rs)| <= Q_pq Q_rs) is below tol_d in
+ * magnitude.  The weights are formed on the device from each build's D; a
+ * brick whose largest Schwarz product times largest weight is below tol_d is
+ * skipped whole.  The paper screens by integral size only (Sec. II.C); this
+ * is the density-weighted variant of the same Schwarz bound.  Builds with
+ * screening on run the CUDA-core kernels (split 16-bit stores included) and
+ * are not accepted by esmf_fock_build_batch (UNSUPPORTED) or
+ * esmf_fock_build_noalloc (UNSUPPORTED: it needs per-build work memory).
+ * Errors: INVALID_ARG (NULL handle, negative or non-finite tol_d).
+ */
+int esmf_fock_set_density_screening(esmf_fock_t *h, double tol_d);
+
+/*
  * Contraction kernel choice for split 16-bit stores (FP16X2 / BF16X2):
  * ESMF_PATH_AUTO uses the tensor-core kernel, ESMF_PATH_CUDA_CORE the
  * CUDA-core kernel (same results within rounding; kept as a cross-check).

@@ -282,6 +282,84 @@ int64_t oracle_jk_unique(int n, const double *center, const int32_t *nprim,
     return nkept;
 }
 
+/*
+ * Density weight of each index pair for density-weighted screening:
+ * Wd[x][y] = max over k of max(|D_k[x][y]|, |D_k[y][x]|)  (symmetric).
+ */
+int oracle_density_weight(int n, int m, const double *D, double *Wd)
+{
+    int64_t nn = (int64_t)n * n;
+    for (int x = 0; x < n; ++x)
+        for (int y = 0; y < n; ++y) {
+            double v = 0.0;
+            for (int k = 0; k < m; ++k) {
+                double a = fabs(D[k * nn + (int64_t)x * n + y]);
+                double b = fabs(D[k * nn + (int64_t)y * n + x]);
+                if (a > v) v = a;
+                if (b > v) v = b;
+            }
+            Wd[(int64_t)x * n + y] = v;
+        }
+    return 0;
+}
+
+/*
+ * Density-weighted screening: the unique-quartet loop of oracle_jk_unique in
+ * which a Schwarz-kept quartet (Q_pq Q_rs >= tol) is also dropped when
+ *   Q_pq Q_rs max(Wd[r][s], Wd[p][q], Wd[q][s], Wd[p][s], Wd[q][r], Wd[p][r]) < tol_d.
+ * Every update of Eq. (J_and_K) that the quartet makes multiplies it by one
+ * of those density elements (J: D_rs, D_pq and transposes; K: D_qs, D_ps,
+ * D_qr, D_pr and transposes), and |(pq|rs)| <= Q_pq Q_rs, so each dropped
+ * update is below tol_d in magnitude.  The weight is shared by all m
+ * densities of the grouped build.  Full range; J, K zeroed first.  Returns
+ * the number of kept unique quartets.
+ */
+int64_t oracle_jk_unique_dw(int n, const double *center, const int32_t *nprim,
+                            const double *exps, const double *w, const double *Q,
+                            double tol, double tol_d, int m, const double *D,
+                            double *J, double *K)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    int64_t nn = (int64_t)n * n;
+    double *Wd = (double *)malloc(sizeof(double) * (size_t)nn);
+    oracle_density_weight(n, m, D, Wd);
+    memset(J, 0, sizeof(double) * (size_t)(nn * m));
+    memset(K, 0, sizeof(double) * (size_t)(nn * m));
+    int64_t nkept = 0;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q <= p; ++q)
+            for (int r = 0; r <= p; ++r)
+                for (int s = 0; s <= r; ++s) {
+                    if (pidx(r, s) > pidx(p, q)) continue;
+                    if (!kept(Q, n, p, q, r, s, tol)) continue;
+                    double wt = Wd[(int64_t)r * n + s];
+                    double c[5] = {Wd[(int64_t)p * n + q], Wd[(int64_t)q * n + s], Wd[(int64_t)p * n + s],
+                                   Wd[(int64_t)q * n + r], Wd[(int64_t)p * n + r]};
+                    for (int i = 0; i < 5; ++i) if (c[i] > wt) wt = c[i];
+                    if (Q[(int64_t)p * n + q] * Q[(int64_t)r * n + s] * wt < tol_d) continue;
+                    double v = eri_c(&b, p, q, r, s);
+                    ++nkept;
+                    int t[8][4] = {{p, q, r, s}, {q, p, r, s}, {p, q, s, r}, {q, p, s, r},
+                                   {r, s, p, q}, {s, r, p, q}, {r, s, q, p}, {s, r, q, p}};
+                    for (int a = 0; a < 8; ++a) {
+                        int dup = 0;
+                        for (int c2 = 0; c2 < a; ++c2)
+                            if (t[a][0] == t[c2][0] && t[a][1] == t[c2][1] &&
+                                t[a][2] == t[c2][2] && t[a][3] == t[c2][3]) { dup = 1; break; }
+                        if (dup) continue;
+                        int i0 = t[a][0], i1 = t[a][1], i2 = t[a][2], i3 = t[a][3];
+                        for (int k = 0; k < m; ++k) {
+                            const double *Dk = D + k * nn;
+                            J[k * nn + (int64_t)i0 * n + i1] += Dk[(int64_t)i2 * n + i3] * v;
+                            K[k * nn + (int64_t)i0 * n + i2] += Dk[(int64_t)i1 * n + i3] * v;
+                        }
+                    }
+                }
+    free(Wd);
+    free(b.off);
+    return nkept;
+}
+
 /* The kept unique integrals in the loop order of oracle_jk_unique over
  * [pair_begin, pair_end); returns how many were written (at most cap). */
 int64_t oracle_unique_list(int n, const double *center, const int32_t *nprim,
@@ -397,6 +475,61 @@ int oracle_jk_rows(int n, const double *center, const int32_t *nprim,
         }
     }
     free(b.off);
+    return 0;
+}
+
+/*
+ * Density fitting (the route the paper names as a future acceleration):
+ * integrals with auxiliary s Gaussians chi_P(r) = exp(-c_P |r - C_P|^2)
+ * (raw; the fitted J and K do not depend on how the auxiliaries are scaled).
+ * Textbook closed forms, the ket of the four-centre formula reduced to one
+ * Gaussian (q = c, Q = C, no ket prefactor):
+ *   [ab|c] = 2 pi^{5/2} / (p c sqrt(p + c)) exp(-ab/p |AB|^2) F0(pc/(p+c) |PC|^2)
+ *   [c|d]  = 2 pi^{5/2} / (c d sqrt(c + d)) F0(cd/(c+d) |CD|^2)
+ * out3[(P n + p) n + q] = (pq|P) over the contracted orbitals; out2[P naux + Q] = (P|Q).
+ */
+static double prim_eri3(double a, const double *A, double b, const double *B,
+                        double c, const double *C)
+{
+    double p = a + b, P[3], ab2 = 0, pc2 = 0;
+    for (int x = 0; x < 3; ++x) {
+        P[x] = (a * A[x] + b * B[x]) / p;
+        ab2 += (A[x] - B[x]) * (A[x] - B[x]);
+    }
+    for (int x = 0; x < 3; ++x) pc2 += (P[x] - C[x]) * (P[x] - C[x]);
+    return 2.0 * pow(OR_PI, 2.5) / (p * c * sqrt(p + c)) * exp(-a * b / p * ab2) *
+           oracle_boys0(p * c / (p + c) * pc2);
+}
+
+int oracle_eri3(int n, const double *center, const int32_t *nprim, const double *exps,
+                const double *w, int naux, const double *acenter, const double *aexp,
+                double *out3)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    for (int P = 0; P < naux; ++P)
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                double v = 0.0;
+                for (int64_t i = b.off[p]; i < b.off[p + 1]; ++i)
+                    for (int64_t j = b.off[q]; j < b.off[q + 1]; ++j)
+                        v += w[i] * w[j] * prim_eri3(exps[i], center + 3 * p, exps[j], center + 3 * q,
+                                                     aexp[P], acenter + 3 * P);
+                out3[((int64_t)P * n + p) * n + q] = v;
+            }
+    free(b.off);
+    return 0;
+}
+
+int oracle_eri2(int naux, const double *acenter, const double *aexp, double *out2)
+{
+    for (int P = 0; P < naux; ++P)
+        for (int Q = 0; Q < naux; ++Q) {
+            double c = aexp[P], d = aexp[Q], r2 = 0.0;
+            for (int x = 0; x < 3; ++x)
+                r2 += (acenter[3 * P + x] - acenter[3 * Q + x]) * (acenter[3 * P + x] - acenter[3 * Q + x]);
+            out2[(int64_t)P * naux + Q] = 2.0 * pow(OR_PI, 2.5) / (c * d * sqrt(c + d)) *
+                                          oracle_boys0(c * d / (c + d) * r2);
+        }
     return 0;
 }
 

@@ -62,6 +62,12 @@ def lib():
                                              dp, C.c_int, ip, dp, C.c_int, ip, dp]
             L.oracle_jk_rows.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double, C.c_int,
                                          dp, C.c_int, ip, dp, dp]
+            L.oracle_density_weight.argtypes = [C.c_int, C.c_int, dp, dp]
+            L.oracle_jk_unique_dw.argtypes = [C.c_int, dp, ip, dp, dp, dp, C.c_double, C.c_double,
+                                              C.c_int, dp, dp, dp]
+            L.oracle_jk_unique_dw.restype = C.c_int64
+            L.oracle_eri3.argtypes = [C.c_int, dp, ip, dp, dp, C.c_int, dp, dp, dp]
+            L.oracle_eri2.argtypes = [C.c_int, dp, dp, dp]
             L.oracle_fock_traces.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp]
             L.oracle_pair_max.argtypes = [C.c_int, dp, ip, dp, dp, dp]
             _lib = L
@@ -181,6 +187,57 @@ class Oracle:
         lib().oracle_jk_rows(*self._b(), _d(np.ascontiguousarray(self.Q)), tol, m, _d(D),
                              rows.size, _i(rows), _d(Jr), _d(Kr))
         return Jr, Kr
+
+    def density_weight(self, D):
+        """Wd[x][y] = max over k of |D_k[x][y]|, |D_k[y][x]| (N x N)."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        out = np.zeros((self.n, self.n))
+        lib().oracle_density_weight(self.n, D.shape[0], _d(D), _d(out))
+        return out
+
+    def jk_unique_dw(self, D, tol, tol_d):
+        """J, K with Schwarz (tol) and density-weighted (tol_d) screening:
+        a quartet is also dropped when Q_pq Q_rs times the largest density
+        weight of its six index pairs is below tol_d.  Returns J, K, kept."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        m = D.shape[0]
+        J = np.zeros_like(D)
+        K = np.zeros_like(D)
+        nk = lib().oracle_jk_unique_dw(*self._b(), _d(np.ascontiguousarray(self.Q)), tol, tol_d, m,
+                                       _d(D), _d(J), _d(K))
+        return J, K, int(nk)
+
+    def eri3(self, acenter, aexp):
+        """(pq|P) for auxiliary s Gaussians exp(-aexp_P |r - acenter_P|^2): (naux, N, N)."""
+        acenter = np.ascontiguousarray(acenter, dtype=np.float64).reshape(-1, 3)
+        aexp = np.ascontiguousarray(aexp, dtype=np.float64)
+        out = np.zeros((aexp.size, self.n, self.n))
+        lib().oracle_eri3(*self._b(), aexp.size, _d(acenter), _d(aexp), _d(out))
+        return out
+
+    @staticmethod
+    def eri2(acenter, aexp):
+        """(P|Q) between auxiliary s Gaussians: (naux, naux)."""
+        acenter = np.ascontiguousarray(acenter, dtype=np.float64).reshape(-1, 3)
+        aexp = np.ascontiguousarray(aexp, dtype=np.float64)
+        out = np.zeros((aexp.size, aexp.size))
+        lib().oracle_eri2(aexp.size, _d(acenter), _d(aexp), _d(out))
+        return out
+
+    def jk_df(self, D, acenter, aexp):
+        """J and K of Eq. (J_and_K) with the density-fitted integrals
+        (pq|rs) ~ sum_PQ (pq|P) [V^-1]_PQ (Q|rs), V_PQ = (P|Q) (Coulomb-metric
+        fitting): J = T^T V^-1 T D and K_pq = sum_rs D_rs (pr|qs)_fit, with
+        V = L L^T and B = L^-1 T so that (pq|rs)_fit = sum_P B_Ppq B_Prs."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        T = self.eri3(acenter, aexp)
+        V = self.eri2(acenter, aexp)
+        L = np.linalg.cholesky(V)
+        B = np.linalg.solve(L, T.reshape(T.shape[0], -1)).reshape(T.shape)
+        g = np.einsum("Prs,krs->kP", B, D)
+        J = np.einsum("Ppq,kP->kpq", B, g)
+        K = np.einsum("Ppr,krs,Pqs->kpq", B, D, B, optimize=True)
+        return J, K
 
     @staticmethod
     def fock_traces(D, J, K):

@@ -94,8 +94,14 @@ struct JKArgs {
     int mc = 0;               // densities per pass (0: default for the precision)
     const void *ptab = nullptr;     // direct mode: pair table (PairTable<TA> entries)
     const int *pslot = nullptr;     // direct mode: entry of block pair (B1, B2) at B1 * nb + B2
+    // density-weighted screening (off when dw is null): dw = np x np weights
+    // max_k max(|D_k[x][y]|, |D_k[y][x]|), dwb = nb x nb block maxima of dw
+    const double *dw = nullptr, *dwb = nullptr;
+    double tol_d = 0.0;
 };
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s);
+// density weights of one build for density-weighted screening (dwb zeroed here)
+int launch_density_weight(const DevBasis &b, int m, const double *D, double *dw, double *dwb, cudaStream_t s);
 int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s);
 
 // ---- jk_umma.cu (tensor-core contraction for split 16-bit stores)

@@ -109,6 +109,9 @@ struct JKSmem {
     int wsum[16];
     int slots[10];            // active output slots of the brick
     int nslots;
+    int skip;                 // brick dropped by density-weighted screening
+    double wblk;              // largest density weight of the brick's six block pairs
+    double dwt[6][64];        // density weights of (R,S) (P,Q) (Q,S) (P,S) (Q,R) (P,R)
     int blk[4];
     int tsw[4][8];            // tile_swizzle(v * stride[dim]) for each index and value
 };
@@ -158,10 +161,24 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
             if (act4) sm.slots[ns++] = 9;
             sm.nslots = ns;
         }
-        if (SRC == 4 && threadIdx.x < 64) {
+        const bool dens = a.dw != nullptr;
+        if ((SRC == 4 || dens) && threadIdx.x < 64) {
             const int t = threadIdx.x;
             sm.qb[t] = a.Q[(int64_t)(d.P * 8 + (t >> 3)) * np + d.Q * 8 + (t & 7)];
             sm.qk[t] = a.Q[(int64_t)(d.R * 8 + (t >> 3)) * np + d.S * 8 + (t & 7)];
+        }
+        if (dens) {
+            // weights of the six block pairs a quartet's updates multiply by
+            const int bx[6] = {d.R, d.P, d.Q, d.P, d.Q, d.P}, by[6] = {d.S, d.Q, d.S, d.S, d.R, d.R};
+            for (int t = threadIdx.x; t < 6 * 64; t += blockDim.x) {
+                const int j = t >> 6, e = t & 63;
+                sm.dwt[j][e] = a.dw[(int64_t)(bx[j] * 8 + (e >> 3)) * np + by[j] * 8 + (e & 7)];
+            }
+            if (threadIdx.x == 0) {
+                double wm = 0.0;
+                for (int j = 0; j < 6; ++j) wm = fmax(wm, a.dwb[bx[j] * a.b.nb + by[j]]);
+                sm.wblk = wm;
+            }
         }
         if constexpr (SRC == 4) {
             const int o = d.P * 8;
@@ -172,14 +189,44 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                                   ox, oy, oz);
         }
         __syncthreads();
+        if (dens) {
+            // brick-level bound of density-weighted screening: when the largest
+            // Schwarz product times the largest weight is below tol_d, no
+            // element of the brick survives
+            if (threadIdx.x < 32) {
+                double qm = fmax(fmax(sm.qb[threadIdx.x], sm.qb[threadIdx.x + 32]), 0.0);
+                double km = fmax(sm.qk[threadIdx.x], sm.qk[threadIdx.x + 32]);
+                for (int o = 16; o > 0; o >>= 1) {
+                    qm = fmax(qm, __shfl_xor_sync(0xffffffffu, qm, o));
+                    km = fmax(km, __shfl_xor_sync(0xffffffffu, km, o));
+                }
+                if (threadIdx.x == 0) sm.skip = qm * km * sm.wblk < a.tol_d;
+            }
+            __syncthreads();
+            if (sm.skip) continue;
+        }
         // ---- dense brick tile
         {
             const int e0 = threadIdx.x * 16;
-            unsigned mask = 0;
+            unsigned mask = 0, dmask = 0xffffu;
             constexpr int EB = SRC == 0 ? 8 : 4;   // bytes per store element
+            if (dens) {
+                // element-level rule: Q_pq Q_rs times the largest weight of the
+                // quartet's six index pairs must reach tol_d
+                dmask = 0;
+                for (int j = 0; j < 16; ++j) {
+                    const int e = e0 + j;
+                    const int p = e >> 9, q = (e >> 6) & 7, r = (e >> 3) & 7, s_ = e & 7;
+                    double wt = fmax(fmax(sm.dwt[0][r * 8 + s_], sm.dwt[1][p * 8 + q]),
+                                     fmax(sm.dwt[2][q * 8 + s_], sm.dwt[3][p * 8 + s_]));
+                    wt = fmax(wt, fmax(sm.dwt[4][q * 8 + r], sm.dwt[5][p * 8 + r]));
+                    if (sm.qb[p * 8 + q] * sm.qk[r * 8 + s_] * wt >= a.tol_d) dmask |= 1u << j;
+                }
+            }
             if constexpr (SRC == 4) {
                 for (int j = 0; j < 16; ++j)
                     if (kept_e(sm.qb, sm.qk, e0 + j, a.tol, n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
+                mask &= dmask;
             } else {
                 // the record's keep mask: bytes 2t and 2t + 1 cover elements 16t .. 16t + 15
                 const unsigned char *mk = reinterpret_cast<const unsigned char *>(a.store) + a.offsets[bi] * EB;
@@ -212,6 +259,10 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                     TA v = TA(0);
                     if (mask & (1u << j)) {
                         const int64_t i = base + pos++;
+                        if (!(dmask & (1u << j))) {          // kept by Schwarz, dropped by the density rule
+                            sm.V[tile_swizzle(e0 + j)] = TA(0);
+                            continue;
+                        }
                         if (SRC == 0) v = (TA)reinterpret_cast<const double *>(a.store)[i];
                         else if (SRC == 1) v = (TA)reinterpret_cast<const float *>(a.store)[i];
                         else {
@@ -308,15 +359,21 @@ static int jk_launch(const JKArgs &a, cudaStream_t s) {
 }
 
 // MC (densities per pass over a brick's shared-memory tile) is a tuning
-// parameter: 4/8/16 for float arithmetic, 4/8 for double (0 = default).
+// parameter: 4/8/16 for float arithmetic, 4/8 for double (0 = default).  The
+// defaults are the autotuner's choices on GB300 for the 200-function stored
+// and 2000-function integral-direct workloads: 8 for stored FP64 and FP32,
+// 16 for the split-store cross-check, 4 for integral-direct (its evaluation
+// phase then fits two CTAs per SM: 1.74 s per 2000-function build against
+// 2.22 s at 16).
 template <typename TA, int SRC>
 static int jk_launch_mc(const JKArgs &a, cudaStream_t s) {
+    const int mc = a.mc ? a.mc : (SRC == 4 ? 4 : (SRC <= 1 ? 8 : 16));
     if (sizeof(TA) == 8) {
-        if (a.mc == 4) return jk_launch<TA, 4, SRC>(a, s);
+        if (mc == 4) return jk_launch<TA, 4, SRC>(a, s);
         return jk_launch<TA, 8, SRC>(a, s);
     }
-    if (a.mc == 4) return jk_launch<TA, 4, SRC>(a, s);
-    if (a.mc == 8) return jk_launch<TA, 8, SRC>(a, s);
+    if (mc == 4) return jk_launch<TA, 4, SRC>(a, s);
+    if (mc == 8) return jk_launch<TA, 8, SRC>(a, s);
     return jk_launch<TA, 16, SRC>(a, s);
 }
 
@@ -344,6 +401,32 @@ int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s) {
     if (a.precision == ESMF_PREC_BF16X2) return jk_launch_mc<float, 3>(a, s);
     set_error("launch_jk_cuda_split: bad precision %d", a.precision);
     return ESMF_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------- density weights
+// dw[x][y] = max over k of max(|D_k[x][y]|, |D_k[y][x]|) on the padded grid
+// (zero outside N), and dwb[X][Y] its 8 x 8 block maxima.  One block per row x.
+// Non-negative doubles order like their bit patterns, so the block maxima are
+// 64-bit integer atomic maxima.
+__global__ void k_density_weight(int n, int np, int nb, int m, const double *D, double *dw,
+                                 unsigned long long *dwb) {
+    const int x = blockIdx.x;
+    const int64_t nn = (int64_t)n * n;
+    for (int y = threadIdx.x; y < np; y += blockDim.x) {
+        double v = 0.0;
+        if (x < n && y < n)
+            for (int k = 0; k < m; ++k)
+                v = fmax(v, fmax(fabs(D[k * nn + (int64_t)x * n + y]), fabs(D[k * nn + (int64_t)y * n + x])));
+        dw[(int64_t)x * np + y] = v;
+        atomicMax(dwb + (x >> 3) * nb + (y >> 3), (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+int launch_density_weight(const DevBasis &b, int m, const double *D, double *dw, double *dwb, cudaStream_t s) {
+    CK(cudaMemsetAsync(dwb, 0, sizeof(double) * b.nb * b.nb, s));
+    k_density_weight<<<b.np, 256, 0, s>>>(b.n, b.np, b.nb, m, D, dw, reinterpret_cast<unsigned long long *>(dwb));
+    CK(cudaGetLastError());
+    return ESMF_OK;
 }
 
 // ---------------------------------------------------------------- finalise

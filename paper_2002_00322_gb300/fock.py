@@ -32,7 +32,7 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
            "esmf_fock_autotune", "esmf_fock_create_screened", "esmf_fock_build_batch",
-           "esmf_measure_fma_peak"]
+           "esmf_measure_fma_peak", "esmf_fock_set_density_screening"]
 MAX_BATCH = 16
 SCREENINGS = {"schwarz": 0, "pair_max": 1}
 PATHS = {"auto": 0, "cuda_core": 1}
@@ -119,6 +119,8 @@ def load(path=None):
         L.esmf_gvp_gradient.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, C.c_double, C.c_double,
                                         C.c_double, vp, vp, vp, vp]
         L.esmf_gvp_gradient.restype = C.c_int
+        L.esmf_fock_set_density_screening.argtypes = [vp, C.c_double]
+        L.esmf_fock_set_density_screening.restype = C.c_int
         L.esmf_measure_fma_peak.argtypes = [C.c_int, C.c_int, dp]
         L.esmf_measure_fma_peak.restype = C.c_int
         L.esmf_fock_destroy.argtypes = [vp]
@@ -288,6 +290,10 @@ def esmf_fock_kernel_time(h, reset=True):
     return ms.value, n.value
 
 
+def esmf_fock_set_density_screening(h, tol_d):
+    _check(load().esmf_fock_set_density_screening(h, float(tol_d)), "esmf_fock_set_density_screening")
+
+
 def esmf_measure_fma_peak(precision="fp64", device=0):
     """Measured CUDA-core FMA rate of the device in TFLOP/s (FP64 or FP32)."""
     out = C.c_double(0.0)
@@ -330,6 +336,9 @@ class FockBuilder:
         J = torch.empty_like(D)
         K = torch.empty_like(D)
         return esmf_fock_autotune(self.h, D.shape[0], D, J, K, reps)
+
+    def set_density_screening(self, tol_d):
+        esmf_fock_set_density_screening(self.h, tol_d)
 
     def set_path(self, path):
         esmf_fock_set_path(self.h, path)

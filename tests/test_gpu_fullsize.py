@@ -6,7 +6,7 @@ results (tests/golden/make_golden.py writes them from oracle/ alone).
   precision_n400_m64   whole rows J[k][p][:] and K[k][p][:] for a seeded set
                        of rows p, including both edges of function blocks; at
                        50 function blocks the tensor-core path splits its
-                       items at 32 R blocks, so these rows cover that split
+                       items at 16 R blocks, so these rows cover that split
   direct_n2000_m32     whole rows of the 2000-function ribbon
 
 Metric: relative Frobenius error of each J_k and K_k (for the row sets: of

@@ -54,7 +54,7 @@ def test_per_result_errors_small(esmf, c4_small, mode, prec, tol):
 
 def test_full_c4_split_against_fp32(esmf):
     """Whole matrices at the full C4 size (400 functions, 50 function blocks,
-    so the tensor-core path splits items at 32 R blocks): the split FP16 build
+    so the tensor-core path splits items at 16 R blocks): the split FP16 build
     against the FP32 CUDA-core build (itself within about 2e-7 of FP64),
     relative Frobenius error of every J_k and K_k."""
     import torch

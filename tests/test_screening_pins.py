@@ -57,3 +57,61 @@ def test_pair_rule_jk_is_the_masked_contraction(small, thr):
     keep = [S[p, q] > 0.5 for (p, q) in iu]
     expect = sum(1 for i in range(len(iu)) for j in range(i + 1) if keep[i] and keep[j])
     assert nk == expect == o.count_kept(0.5, Q=S)
+
+
+# ------------------------------------------------- density-weighted screening
+@pytest.mark.parametrize("tol_d", [1e-5, 1e-3])
+def test_density_weighted_jk_is_the_masked_contraction(small, tol_d):
+    """The density-weighted rule keeps a Schwarz-kept quartet iff Q_pq Q_rs
+    times the largest |D_k| over its six index pairs (both orders, all k)
+    reaches tol_d.  J and K equal Eq. (J_and_K) over the tensor with every
+    dropped quartet zeroed; the weight is formed here with numpy."""
+    w, o, eri = small
+    n = w.basis.n
+    D = W.esmf_densities(W.rng_for(5), n, 3, 4)
+    D = D + 0.05 * np.random.default_rng(2).standard_normal(D.shape)       # non-symmetric
+    Wd = np.max(np.maximum(np.abs(D), np.abs(D.transpose(0, 2, 1))), axis=0)
+    np.testing.assert_array_equal(o.density_weight(D), Wd)
+    Q = o.Q
+    QQ = Q[:, :, None, None] * Q[None, None, :, :]
+    wt = np.maximum.reduce([Wd[None, None, :, :] + 0 * QQ,                 # r s
+                            Wd[:, :, None, None] + 0 * QQ,                 # p q
+                            Wd[None, :, None, :] + 0 * QQ,                 # q s
+                            Wd[:, None, None, :] + 0 * QQ,                 # p s
+                            Wd[None, :, :, None] + 0 * QQ,                 # q r
+                            Wd[:, None, :, None] + 0 * QQ])                # p r
+    mask = (QQ * wt >= tol_d).astype(float)
+    assert 0 < mask.mean() < 1                                             # the rule bites
+    e = eri * mask
+    J, K, nk = o.jk_unique_dw(D, 0.0, tol_d)
+    np.testing.assert_allclose(J, np.einsum("rspq,krs->kpq", e, D), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(K, np.einsum("prqs,krs->kpq", e, D), rtol=1e-12, atol=1e-13)
+    # kept unique quartets: the mask is invariant under the 8 permutations
+    iu = [(p, q) for p in range(n) for q in range(p + 1)]
+    expect = sum(1 for i in range(len(iu)) for j in range(i + 1)
+                 if mask[iu[i][0], iu[i][1], iu[j][0], iu[j][1]] > 0)
+    assert nk == expect
+
+
+def test_density_weighted_zero_tolerance_is_schwarz_alone(small):
+    w, o, _ = small
+    D = W.esmf_densities(W.rng_for(6), w.basis.n, 3, 2)
+    J0, K0, n0 = o.jk_unique(D, 1e-9)
+    J1, K1, n1 = o.jk_unique_dw(D, 1e-9, 0.0)
+    assert n0 == n1
+    np.testing.assert_array_equal(J0, J1)
+    np.testing.assert_array_equal(K0, K1)
+
+
+def test_density_weighted_error_bound(small):
+    """Each dropped update is below tol_d, so |X_dw - X|_pq <= tol_d times the
+    number of ordered quartets that update element pq (N^2 for J and K)."""
+    w, o, _ = small
+    n = w.basis.n
+    D = W.esmf_densities(W.rng_for(8), n, 3, 3)
+    tol_d = 1e-4
+    J0, K0, _ = o.jk_unique(D, 0.0)
+    J1, K1, nk = o.jk_unique_dw(D, 0.0, tol_d)
+    assert nk < n * (n + 1) // 2 * (n * (n + 1) // 2 + 1) // 2
+    assert np.max(np.abs(J1 - J0)) <= tol_d * n * n
+    assert np.max(np.abs(K1 - K0)) <= tol_d * n * n
