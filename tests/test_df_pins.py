@@ -1,0 +1,93 @@
+"""Pins of the oracle's density-fitting route (the acceleration the paper
+names as future work, Sec. I): its three- and two-centre integrals against
+the Gaussian-charge closed forms, and the fit itself against the exact
+integrals when the auxiliary set spans every orbital product.  CPU only."""
+import math
+
+import numpy as np
+from scipy import special
+
+from oracle.oracle import Oracle
+from paper_2002_00322_gb300 import workloads as W
+from test_oracle_pins import one_prim_basis
+
+
+def test_three_centre_is_two_gaussian_charges():
+    """(mu mu|P) for one normalised primitive mu of exponent a at A and a raw
+    auxiliary exp(-c |r - C|^2): a charge of exponent 2a and weight
+    (2a/pi)^{3/2} (pi/2a)^{3/2} = 1 against one of charge (pi/c)^{3/2}:
+    (pi/c)^{3/2} erf(sqrt(2ac/(2a + c)) R) / R."""
+    rng = np.random.default_rng(3)
+    for _ in range(8):
+        a, c = np.exp(rng.uniform(np.log(0.1), np.log(10), size=2))
+        R = rng.uniform(0.05, 9.0)
+        o = Oracle(one_prim_basis([[0.0, 0.0, 0.0]], [a]))
+        v = o.eri3([[0.0, R * 0.6, R * 0.8]], [c])[0, 0, 0]
+        ref = (math.pi / c) ** 1.5 * special.erf(math.sqrt(2 * a * c / (2 * a + c)) * R) / R
+        assert abs(v - ref) <= 1e-13 * ref
+
+
+def test_two_centre_metric_is_two_gaussian_charges():
+    rng = np.random.default_rng(4)
+    cen = rng.uniform(-3, 3, size=(5, 3))
+    ex = np.exp(rng.uniform(np.log(0.1), np.log(10), size=5))
+    V = Oracle.eri2(cen, ex)
+    for P in range(5):
+        for Q in range(5):
+            c, d = ex[P], ex[Q]
+            R = np.linalg.norm(cen[P] - cen[Q])
+            rho = c * d / (c + d)
+            inter = 2 * math.sqrt(rho / math.pi) if R == 0 else special.erf(math.sqrt(rho) * R) / R
+            ref = (math.pi / c) ** 1.5 * (math.pi / d) ** 1.5 * inter
+            assert abs(V[P, Q] - ref) <= 1e-13 * ref
+    assert np.all(np.linalg.eigvalsh(V) > 0)          # a Coulomb metric is positive definite
+
+
+def product_aux(basis):
+    """One auxiliary per product of two primitives: exponent a + b at the
+    product centre (a A + b B)/(a + b)."""
+    off = np.concatenate([[0], np.cumsum(basis.nprim)])
+    ac, ae = [], []
+    for mu in range(basis.n):
+        for nu in range(mu + 1):
+            for i in range(off[mu], off[mu + 1]):
+                for j in range(off[nu], off[nu + 1]):
+                    a, b = basis.exps[i], basis.exps[j]
+                    ac.append((a * basis.center[mu] + b * basis.center[nu]) / (a + b))
+                    ae.append(a + b)
+    return np.array(ac), np.array(ae)
+
+
+def test_fit_is_exact_when_the_auxiliaries_span_the_products():
+    """With every orbital product inside the auxiliary span, the Coulomb-
+    metric fit reproduces (pq|rs) exactly, so the fitted J and K equal the
+    exact ones (non-symmetric densities)."""
+    b = one_prim_basis([[0, 0, 0], [1.2, 0.3, -0.4], [-0.5, 1.7, 0.9]], [0.4, 1.3, 3.1])
+    o = Oracle(b)
+    ac, ae = product_aux(b)
+    D = np.random.default_rng(1).standard_normal((3, 3, 3))
+    J, K = o.jk_df(D, ac, ae)
+    Jr, Kr = o.jk_brute(o.eri_tensor(), D, 0.0)
+    np.testing.assert_allclose(J, Jr, rtol=0, atol=1e-13 * np.abs(Jr).max())
+    np.testing.assert_allclose(K, Kr, rtol=0, atol=1e-13 * np.abs(Kr).max())
+
+
+def test_fit_with_an_even_tempered_set_is_close_and_keeps_the_symmetries():
+    """A per-centre even-tempered set does not span the two-centre products:
+    the fit is approximate (here below 1e-2 relative), but J stays symmetric,
+    K[D^T] = K[D]^T and both stay linear in D."""
+    w = W.small_random(12, 2, 12, edge=5.0)
+    o = Oracle(w.basis)
+    cen = np.unique(w.basis.center, axis=0)
+    et = 0.2 * 2.5 ** np.arange(7)
+    ac, ae = np.repeat(cen, et.size, axis=0), np.tile(et, cen.shape[0])
+    D = w.D + 0.1 * np.random.default_rng(2).standard_normal(w.D.shape)
+    J, K = o.jk_df(D, ac, ae)
+    Jr, Kr, _ = o.jk_unique(D, 0.0)
+    assert np.linalg.norm(J - Jr) <= 1e-2 * np.linalg.norm(Jr)
+    assert np.linalg.norm(K - Kr) <= 1e-2 * np.linalg.norm(Kr)
+    np.testing.assert_allclose(J, J.transpose(0, 2, 1), atol=1e-13 * np.abs(J).max())
+    Jt, Kt = o.jk_df(D.transpose(0, 2, 1).copy(), ac, ae)
+    np.testing.assert_allclose(Kt, K.transpose(0, 2, 1), atol=1e-13 * np.abs(K).max())
+    J2, K2 = o.jk_df(2.0 * D[:1] - D[1:], ac, ae)
+    np.testing.assert_allclose(K2, 2.0 * K[:1] - K[1:], atol=1e-12 * np.abs(K).max())
