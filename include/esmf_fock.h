@@ -49,6 +49,7 @@ extern "C" {
 #define ESMF_MODE_STORED  0   /* screened unique integrals stored at create   */
 #define ESMF_MODE_DIRECT  1   /* integrals recomputed inside every build      */
 #define ESMF_MODE_AUTO    2   /* stored if it fits the device budget          */
+#define ESMF_MODE_DF      3   /* density fitting (esmf_fock_create_df)        */
 
 /* arithmetic of the integral x density products (accumulation is FP64) */
 #define ESMF_PREC_FP64    0   /* FP64 integrals, FP64 products                */
@@ -138,6 +139,37 @@ int esmf_fock_create(const esmf_basis_t *basis, double schwarz_tol, int mode,
 int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screening,
                               int mode, int precision, int device,
                               int64_t budget_bytes, esmf_fock_t **out);
+
+/*
+ * esmf_fock_create_df -- a handle whose builds use density-fitted integrals,
+ * the acceleration the paper names as future work (Sec. I), in the Coulomb-
+ * metric form (pq|rs) ~ sum_PQ (pq|P) [V^-1]_PQ (Q|rs), V_PQ = (P|Q), over
+ * auxiliary s Gaussians chi_P(r) = exp(-e_P |r - C_P|^2).  At create time the
+ * three-centre integrals T_P,pq = (pq|P) and the metric V are evaluated on the
+ * device in FP64, V = L L^T is factored on the host, and B = L^-1 T is formed
+ * (one FP64 GEMM) and kept in the handle in the build arithmetic, in two
+ * layouts ([P][p][q] and [p][P][q]).  Every build is then dense GEMMs:
+ * J_k = B^T (B vec(D_k)) and K_k[p][q] = sum_{P,s} (B''_p D_k)[P][s] B''_q[P][s].
+ * There is no integral screening; esmf_fock_build and esmf_fock_build_host
+ * accept the handle (m densities per build as usual); the batched, shard,
+ * no-alloc and autotune entries reject it (UNSUPPORTED).
+ *   basis      as for esmf_fock_create
+ *   aux        host description of the auxiliary set (read during this call)
+ *   precision  ESMF_PREC_FP64 or ESMF_PREC_FP32 (GEMM arithmetic; the fit
+ *              itself is always formed in FP64)
+ *   device, out  as for esmf_fock_create
+ * Device memory: about 2 n_aux N^2 elements for B and B'', plus n_aux N^2
+ * elements of per-build work.  Errors: INVALID_ARG (bad basis or auxiliary
+ * set, or a metric that is not positive definite), UNSUPPORTED (split 16-bit
+ * precisions), OOM, CUDA.
+ */
+typedef struct {
+    int32_t       n_aux;      /* number of auxiliary functions, > 0          */
+    const double *center;     /* n_aux x 3 centres, bohr                      */
+    const double *exps;       /* n_aux exponents, bohr^-2, finite and > 0     */
+} esmf_aux_t;
+int esmf_fock_create_df(const esmf_basis_t *basis, const esmf_aux_t *aux, int precision,
+                        int device, esmf_fock_t **out);
 
 /*
  * esmf_fock_build -- one grouped pass over the (stored or recomputed)

@@ -95,6 +95,142 @@ static double prim_eri(double a, const double *A, double b, const double *B,
            exp(-a * b / p * ab2) * exp(-c * d / q * cd2) * oracle_boys0(T);
 }
 
+/*
+ * Cartesian p functions (angular momentum 1).  A function's Cartesian label
+ * cart = 0 (s), 1, 2, 3 (p_x, p_y, p_z) makes its primitives
+ * (r - A)_i exp(-a |r - A|^2).  Integrals over them follow the Obara-Saika
+ * recurrences (Obara & Saika, J. Chem. Phys. 84, 3963 (1986)): the vertical
+ * recurrence builds [e0|f0]^(m) from the Boys functions F_m, the horizontal
+ * one (Head-Gordon & Pople, J. Chem. Phys. 89, 5777 (1988)) moves angular
+ * momentum from the first to the second function of a pair:
+ *   [e+1_i 0|f0]^(m) = PA_i [e0|f0]^(m) + WP_i [e0|f0]^(m+1)
+ *       + e_i/(2p) ([e-1_i 0|f0]^(m) - rho/p [e-1_i 0|f0]^(m+1))
+ *       + f_i/(2(p+q)) [e0|f-1_i 0]^(m+1)
+ *   [00|f+1_i 0]^(m) = QC_i [00|f0]^(m) + WQ_i [00|f0]^(m+1)
+ *       + f_i/(2q) ([00|f-1_i 0]^(m) - rho/q [00|f-1_i 0]^(m+1))
+ *   [a, b+1_j| = [a+1_j, b| + (A - B)_j [a, b|     (and the same for the ket)
+ * with W = (pP + qQ)/(p + q), rho = pq/(p + q) and
+ * [00|00]^(m) = 2 pi^{5/2}/(pq sqrt(p+q)) exp(-ab/p |AB|^2) exp(-cd/q |CD|^2) F_m(T).
+ */
+
+/* F_m(T) = int_0^1 u^{2m} exp(-T u^2) du for m <= mmax: the top order from
+ * the positive series F_M(T) = exp(-T) sum_k (2T)^k / ((2M+1)(2M+3)...(2M+2k+1)),
+ * then downward recursion F_{m-1} = (2T F_m + exp(-T)) / (2m - 1). */
+static void boys_all(int mmax, double T, double *F)
+{
+    double term = 1.0 / (2 * mmax + 1), sum = term;
+    for (int k = 1; k < 2000; ++k) {
+        term *= 2.0 * T / (2 * mmax + 2 * k + 1);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    double e = exp(-T);
+    F[mmax] = e * sum;
+    for (int m = mmax; m > 0; --m) F[m - 1] = (2.0 * T * F[m] + e) / (2 * m - 1);
+}
+
+double oracle_boys(int m, double T)
+{
+    double F[32];
+    if (m < 0 || m > 30) return 0.0;
+    boys_all(m, T, F);
+    return F[m];
+}
+
+typedef struct {
+    double PA[3], WP[3], QC[3], WQ[3], p, q, rho, K, F[8];
+} osdata;
+
+/* [e0|f0]^(m) by the vertical recurrence (e, f: Cartesian exponent triples) */
+static double os_vrr(const osdata *o, const int *e, const int *f, int m)
+{
+    int i;
+    for (i = 0; i < 3 && e[i] == 0; ++i) {}
+    if (i < 3) {
+        int e1[3] = {e[0], e[1], e[2]};
+        e1[i] -= 1;
+        double v = o->PA[i] * os_vrr(o, e1, f, m) + o->WP[i] * os_vrr(o, e1, f, m + 1);
+        if (e1[i] > 0) {
+            int e2[3] = {e1[0], e1[1], e1[2]};
+            e2[i] -= 1;
+            v += e1[i] / (2.0 * o->p) * (os_vrr(o, e2, f, m) - o->rho / o->p * os_vrr(o, e2, f, m + 1));
+        }
+        if (f[i] > 0) {
+            int f1[3] = {f[0], f[1], f[2]};
+            f1[i] -= 1;
+            v += f[i] / (2.0 * (o->p + o->q)) * os_vrr(o, e1, f1, m + 1);
+        }
+        return v;
+    }
+    for (i = 0; i < 3 && f[i] == 0; ++i) {}
+    if (i == 3) return o->K * o->F[m];
+    int f1[3] = {f[0], f[1], f[2]};
+    f1[i] -= 1;
+    double v = o->QC[i] * os_vrr(o, e, f1, m) + o->WQ[i] * os_vrr(o, e, f1, m + 1);
+    if (f1[i] > 0) {
+        int f2[3] = {f1[0], f1[1], f1[2]};
+        f2[i] -= 1;
+        v += f1[i] / (2.0 * o->q) * (os_vrr(o, e, f2, m) - o->rho / o->q * os_vrr(o, e, f2, m + 1));
+    }
+    return v;
+}
+
+/* [a b|c d] by the horizontal recurrence down to [e0|f0]^(0) */
+static double os_hrr(const osdata *o, const double *AB, const double *CD,
+                     const int *a, const int *b, const int *c, const int *d)
+{
+    int j;
+    for (j = 0; j < 3 && b[j] == 0; ++j) {}
+    if (j < 3) {
+        int a1[3] = {a[0], a[1], a[2]}, b1[3] = {b[0], b[1], b[2]};
+        a1[j] += 1;
+        b1[j] -= 1;
+        return os_hrr(o, AB, CD, a1, b1, c, d) + AB[j] * os_hrr(o, AB, CD, a, b1, c, d);
+    }
+    for (j = 0; j < 3 && d[j] == 0; ++j) {}
+    if (j < 3) {
+        int c1[3] = {c[0], c[1], c[2]}, d1[3] = {d[0], d[1], d[2]};
+        c1[j] += 1;
+        d1[j] -= 1;
+        return os_hrr(o, AB, CD, a, b, c1, d1) + CD[j] * os_hrr(o, AB, CD, a, b, c, d1);
+    }
+    return os_vrr(o, a, c, 0);
+}
+
+static void cart_vec(int cart, int *v)
+{
+    v[0] = cart == 1; v[1] = cart == 2; v[2] = cart == 3;
+}
+
+/* primitive [ab|cd] over raw Cartesian primitives with labels la..ld */
+static double prim_eri_l(double a, const double *A, int la, double b, const double *B, int lb,
+                         double c, const double *C, int lc, double d, const double *D, int ld)
+{
+    osdata o;
+    double p = a + b, q = c + d, P[3], Q[3], W[3], AB[3], CD[3], ab2 = 0, cd2 = 0, pq2 = 0;
+    for (int x = 0; x < 3; ++x) {
+        P[x] = (a * A[x] + b * B[x]) / p;
+        Q[x] = (c * C[x] + d * D[x]) / q;
+        W[x] = (p * P[x] + q * Q[x]) / (p + q);
+        AB[x] = A[x] - B[x];
+        CD[x] = C[x] - D[x];
+        ab2 += AB[x] * AB[x];
+        cd2 += CD[x] * CD[x];
+        pq2 += (P[x] - Q[x]) * (P[x] - Q[x]);
+        o.PA[x] = P[x] - A[x];
+        o.WP[x] = W[x] - P[x];
+        o.QC[x] = Q[x] - C[x];
+        o.WQ[x] = W[x] - Q[x];
+    }
+    o.p = p; o.q = q; o.rho = p * q / (p + q);
+    o.K = 2.0 * pow(OR_PI, 2.5) / (p * q * sqrt(p + q)) * exp(-a * b / p * ab2) * exp(-c * d / q * cd2);
+    int L = (la > 0) + (lb > 0) + (lc > 0) + (ld > 0);
+    boys_all(L, o.rho * pq2, o.F);
+    int va[3], vb[3], vc[3], vd[3];
+    cart_vec(la, va); cart_vec(lb, vb); cart_vec(lc, vc); cart_vec(ld, vd);
+    return os_hrr(&o, AB, CD, va, vb, vc, vd);
+}
+
 typedef struct {
     int n;
     const double *center;
@@ -102,6 +238,7 @@ typedef struct {
     const double *exps;
     const double *w;
     int64_t *off;
+    const int32_t *cart;      /* NULL: every function is s */
 } obasis;
 
 static obasis mk_basis(int n, const double *center, const int32_t *nprim,
@@ -110,12 +247,26 @@ static obasis mk_basis(int n, const double *center, const int32_t *nprim,
     obasis b;
     b.n = n; b.center = center; b.nprim = nprim; b.exps = exps; b.w = w;
     b.off = prim_offsets(n, nprim);
+    b.cart = NULL;
     return b;
 }
 
 /* contracted (pq|rs): sum over all primitive products */
 static double eri_c(const obasis *b, int p, int q, int r, int s)
 {
+    if (b->cart && (b->cart[p] || b->cart[q] || b->cart[r] || b->cart[s])) {
+        double v = 0.0;
+        for (int64_t i = b->off[p]; i < b->off[p + 1]; ++i)
+            for (int64_t j = b->off[q]; j < b->off[q + 1]; ++j)
+                for (int64_t k = b->off[r]; k < b->off[r + 1]; ++k)
+                    for (int64_t l = b->off[s]; l < b->off[s + 1]; ++l)
+                        v += b->w[i] * b->w[j] * b->w[k] * b->w[l] *
+                             prim_eri_l(b->exps[i], b->center + 3 * p, b->cart[p],
+                                        b->exps[j], b->center + 3 * q, b->cart[q],
+                                        b->exps[k], b->center + 3 * r, b->cart[r],
+                                        b->exps[l], b->center + 3 * s, b->cart[s]);
+        return v;
+    }
     double v = 0.0;
     for (int64_t i = b->off[p]; i < b->off[p + 1]; ++i)
         for (int64_t j = b->off[q]; j < b->off[q + 1]; ++j)
@@ -240,13 +391,36 @@ static int64_t pidx(int p, int q) { return (int64_t)p * (p + 1) / 2 + q; }
  * in loop order (stored mode) instead of evaluating them.
  * Returns the number of kept unique quartets.
  */
+static int64_t jk_unique_core(obasis b, const double *Q, double tol, int m, const double *D,
+                              double *J, double *K, int64_t pair_begin, int64_t pair_end,
+                              const double *eri_list);
+
 int64_t oracle_jk_unique(int n, const double *center, const int32_t *nprim,
                          const double *exps, const double *w, const double *Q,
                          double tol, int m, const double *D, double *J, double *K,
                          int64_t pair_begin, int64_t pair_end,
                          const double *eri_list)
 {
+    return jk_unique_core(mk_basis(n, center, nprim, exps, w), Q, tol, m, D, J, K,
+                          pair_begin, pair_end, eri_list);
+}
+
+/* oracle_jk_unique for a basis with Cartesian p functions */
+int64_t oracle_jk_unique_l(int n, const double *center, const int32_t *nprim,
+                           const double *exps, const double *w, const int32_t *cart,
+                           const double *Q, double tol, int m, const double *D,
+                           double *J, double *K, int64_t pair_begin, int64_t pair_end)
+{
     obasis b = mk_basis(n, center, nprim, exps, w);
+    b.cart = cart;
+    return jk_unique_core(b, Q, tol, m, D, J, K, pair_begin, pair_end, NULL);
+}
+
+static int64_t jk_unique_core(obasis b, const double *Q, double tol, int m, const double *D,
+                              double *J, double *K, int64_t pair_begin, int64_t pair_end,
+                              const double *eri_list)
+{
+    int n = b.n;
     int64_t nn = (int64_t)n * n;
     int64_t nkept = 0, pos = 0;
     /* walk all bra pairs, skip those outside the range */
@@ -530,6 +704,75 @@ int oracle_eri2(int naux, const double *acenter, const double *aexp, double *out
             out2[(int64_t)P * naux + Q] = 2.0 * pow(OR_PI, 2.5) / (c * d * sqrt(c + d)) *
                                           oracle_boys0(c * d / (c + d) * r2);
         }
+    return 0;
+}
+
+/*
+ * Entry points for bases with Cartesian p functions (cart[i] in 0..3).
+ * Normalisation (textbook): a p primitive N (x - A_x) exp(-a r^2) has
+ * <g|g> = 1 for N = (2a/pi)^{3/4} 2 sqrt(a); two p_x primitives on one centre
+ * overlap N_k N_l (pi/(a_k+a_l))^{3/2} / (2 (a_k + a_l)).  w_k = c d_k N_k.
+ */
+int oracle_normalize_l(int n, const int32_t *nprim, const double *exps,
+                       const double *coefs, const int32_t *cart, double *w)
+{
+    if (n <= 0) return -1;
+    int64_t *off = prim_offsets(n, nprim);
+    for (int mu = 0; mu < n; ++mu) {
+        int l = cart[mu] ? 1 : 0;
+        double s = 0.0;
+        for (int64_t k = off[mu]; k < off[mu + 1]; ++k)
+            for (int64_t j = off[mu]; j < off[mu + 1]; ++j) {
+                double ak = exps[k], aj = exps[j];
+                double nk = pow(2.0 * ak / OR_PI, 0.75) * (l ? 2.0 * sqrt(ak) : 1.0);
+                double nj = pow(2.0 * aj / OR_PI, 0.75) * (l ? 2.0 * sqrt(aj) : 1.0);
+                double ov = pow(OR_PI / (ak + aj), 1.5) * (l ? 1.0 / (2.0 * (ak + aj)) : 1.0);
+                s += coefs[k] * coefs[j] * nk * nj * ov;
+            }
+        double c = 1.0 / sqrt(s);
+        for (int64_t k = off[mu]; k < off[mu + 1]; ++k)
+            w[k] = c * coefs[k] * pow(2.0 * exps[k] / OR_PI, 0.75) * (l ? 2.0 * sqrt(exps[k]) : 1.0);
+    }
+    free(off);
+    return 0;
+}
+
+double oracle_eri_l(int n, const double *center, const int32_t *nprim, const double *exps,
+                    const double *w, const int32_t *cart, int p, int q, int r, int s)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    b.cart = cart;
+    double v = eri_c(&b, p, q, r, s);
+    free(b.off);
+    return v;
+}
+
+int oracle_eri_tensor_l(int n, const double *center, const int32_t *nprim, const double *exps,
+                        const double *w, const int32_t *cart, double *out)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    b.cart = cart;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q < n; ++q)
+            for (int r = 0; r < n; ++r)
+                for (int s = 0; s < n; ++s)
+                    out[(((int64_t)p * n + q) * n + r) * n + s] = eri_c(&b, p, q, r, s);
+    free(b.off);
+    return 0;
+}
+
+int oracle_schwarz_l(int n, const double *center, const int32_t *nprim, const double *exps,
+                     const double *w, const int32_t *cart, double *Q)
+{
+    obasis b = mk_basis(n, center, nprim, exps, w);
+    b.cart = cart;
+    for (int p = 0; p < n; ++p)
+        for (int q = 0; q <= p; ++q) {
+            double v = eri_c(&b, p, q, p, q);
+            Q[(int64_t)p * n + q] = sqrt(v > 0.0 ? v : 0.0);
+            Q[(int64_t)q * n + p] = Q[(int64_t)p * n + q];
+        }
+    free(b.off);
     return 0;
 }
 

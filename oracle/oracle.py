@@ -68,6 +68,16 @@ def lib():
             L.oracle_jk_unique_dw.restype = C.c_int64
             L.oracle_eri3.argtypes = [C.c_int, dp, ip, dp, dp, C.c_int, dp, dp, dp]
             L.oracle_eri2.argtypes = [C.c_int, dp, dp, dp]
+            L.oracle_boys.argtypes = [C.c_int, C.c_double]
+            L.oracle_boys.restype = C.c_double
+            L.oracle_normalize_l.argtypes = [C.c_int, ip, dp, dp, ip, dp]
+            L.oracle_eri_l.argtypes = [C.c_int, dp, ip, dp, dp, ip, C.c_int, C.c_int, C.c_int, C.c_int]
+            L.oracle_eri_l.restype = C.c_double
+            L.oracle_eri_tensor_l.argtypes = [C.c_int, dp, ip, dp, dp, ip, dp]
+            L.oracle_schwarz_l.argtypes = [C.c_int, dp, ip, dp, dp, ip, dp]
+            L.oracle_jk_unique_l.argtypes = [C.c_int, dp, ip, dp, dp, ip, dp, C.c_double, C.c_int,
+                                             dp, dp, dp, C.c_int64, C.c_int64]
+            L.oracle_jk_unique_l.restype = C.c_int64
             L.oracle_fock_traces.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp]
             L.oracle_pair_max.argtypes = [C.c_int, dp, ip, dp, dp, dp]
             _lib = L
@@ -92,32 +102,52 @@ class Oracle:
         self.exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
         self.coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
         self.w = np.zeros_like(self.exps)
-        rc = lib().oracle_normalize(self.n, _i(self.nprim), _d(self.exps), _d(self.coefs), _d(self.w))
+        # Cartesian p functions (basis.cart): the Obara-Saika integrals
+        self.cart = None
+        if getattr(basis, "cart", None) is not None and np.any(np.asarray(basis.cart) != 0):
+            self.cart = np.ascontiguousarray(basis.cart, dtype=np.int32)
+            rc = lib().oracle_normalize_l(self.n, _i(self.nprim), _d(self.exps), _d(self.coefs),
+                                          _i(self.cart), _d(self.w))
+        else:
+            rc = lib().oracle_normalize(self.n, _i(self.nprim), _d(self.exps), _d(self.coefs), _d(self.w))
         if rc != 0:
             raise ValueError("oracle_normalize failed")
         self._Q = None
+
+    def _no_p(self, what):
+        if self.cart is not None:
+            raise NotImplementedError(f"{what} covers s functions only")
 
     def _b(self):
         return (self.n, _d(self.center), _i(self.nprim), _d(self.exps), _d(self.w))
 
     def eri(self, p, q, r, s):
+        if self.cart is not None:
+            return lib().oracle_eri_l(*self._b(), _i(self.cart), p, q, r, s)
         return lib().oracle_eri(*self._b(), p, q, r, s)
 
     def eri_tensor(self):
         out = np.zeros((self.n,) * 4)
-        lib().oracle_eri_tensor(*self._b(), _d(out))
+        if self.cart is not None:
+            lib().oracle_eri_tensor_l(*self._b(), _i(self.cart), _d(out))
+        else:
+            lib().oracle_eri_tensor(*self._b(), _d(out))
         return out
 
     @property
     def Q(self):
         if self._Q is None:
             Q = np.zeros((self.n, self.n))
-            lib().oracle_schwarz(*self._b(), _d(Q))
+            if self.cart is not None:
+                lib().oracle_schwarz_l(*self._b(), _i(self.cart), _d(Q))
+            else:
+                lib().oracle_schwarz(*self._b(), _d(Q))
             self._Q = Q
         return self._Q
 
     def pair_max(self):
         """max over (r, s) of |(pq|rs)| for every pair (Sec. II.C pair screening), N x N."""
+        self._no_p("pair_max")
         out = np.zeros((self.n, self.n))
         lib().oracle_pair_max(*self._b(), _d(out))
         return out
@@ -146,6 +176,11 @@ class Oracle:
         K = np.zeros_like(D)
         npair = self.n * (self.n + 1) // 2
         b, e = pair_range if pair_range is not None else (0, npair)
+        if self.cart is not None:
+            if eri_list is not None:
+                raise NotImplementedError("stored integral lists cover s functions only")
+            nk = lib().oracle_jk_unique_l(*self._b(), _i(self.cart), _d(Qt), tol, m, _d(D), _d(J), _d(K), b, e)
+            return J, K, int(nk)
         el = None
         if eri_list is not None:
             eri_list = np.ascontiguousarray(eri_list, dtype=np.float64)
@@ -155,6 +190,7 @@ class Oracle:
         return J, K, int(nk)
 
     def unique_list(self, tol, pair_range, cap):
+        self._no_p("unique_list")
         out = np.zeros(cap)
         cnt = lib().oracle_unique_list(*self._b(), _d(self.Q), tol, pair_range[0],
                                        pair_range[1], _d(out), cap)
@@ -165,6 +201,7 @@ class Oracle:
         return int(lib().oracle_count_kept(self.n, _d(Qt), tol))
 
     def jk_elements(self, D, tol, jidx, kidx):
+        self._no_p("jk_elements")
         D = np.ascontiguousarray(D, dtype=np.float64)
         m = D.shape[0]
         jidx = np.ascontiguousarray(np.asarray(jidx, dtype=np.int32).reshape(-1, 2))
@@ -179,6 +216,7 @@ class Oracle:
         """Whole rows J[k][p][:] and K[k][p][:] for each p in rows, from the
         definition (every integral with first index p evaluated once);
         returns arrays of shape (m, len(rows), N)."""
+        self._no_p("jk_rows")
         D = np.ascontiguousarray(D, dtype=np.float64)
         m = D.shape[0]
         rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int32).ravel())
@@ -199,6 +237,7 @@ class Oracle:
         """J, K with Schwarz (tol) and density-weighted (tol_d) screening:
         a quartet is also dropped when Q_pq Q_rs times the largest density
         weight of its six index pairs is below tol_d.  Returns J, K, kept."""
+        self._no_p("jk_unique_dw")
         D = np.ascontiguousarray(D, dtype=np.float64)
         m = D.shape[0]
         J = np.zeros_like(D)
@@ -209,6 +248,7 @@ class Oracle:
 
     def eri3(self, acenter, aexp):
         """(pq|P) for auxiliary s Gaussians exp(-aexp_P |r - acenter_P|^2): (naux, N, N)."""
+        self._no_p("eri3")
         acenter = np.ascontiguousarray(acenter, dtype=np.float64).reshape(-1, 3)
         aexp = np.ascontiguousarray(aexp, dtype=np.float64)
         out = np.zeros((aexp.size, self.n, self.n))
@@ -252,3 +292,8 @@ class Oracle:
 
 def boys0(T):
     return lib().oracle_boys0(float(T))
+
+
+def boys(m, T):
+    """F_m(T) by the positive series and downward recursion (any T >= 0)."""
+    return lib().oracle_boys(int(m), float(T))

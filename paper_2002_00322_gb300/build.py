@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libesmf_fock.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "setup.cu", "jk_cuda.cu", "jk_umma.cu", "noalloc.cu", "server.cu", "energy.cu", "peak.cu"]
+SOURCES = ["api.cu", "setup.cu", "jk_cuda.cu", "jk_umma.cu", "noalloc.cu", "server.cu", "energy.cu", "peak.cu", "df.cu"]
 
 
 def nvcc():
@@ -67,7 +67,7 @@ def build(verbose=False, extra=None, force=False):
                 print(err, file=sys.stderr)
     if force or jobs or not os.path.exists(LIB) or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([cc] + ARCH + ["-shared", "-o", tmp] + objs)
+        run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -62,6 +62,13 @@ struct esmf_fock {
     // density-weighted screening threshold (0: off) and its per-build weights
     double tol_d = 0.0;
     double *dw = nullptr, *dwb = nullptr;
+    // density fitting (mode ESMF_MODE_DF): auxiliary set, fitted factor in two
+    // layouts (arithmetic type), per-build work for up to df_m densities
+    void *cublas = nullptr;
+    int naux = 0;
+    void *dfB = nullptr, *dfB2 = nullptr;
+    void *dfDt = nullptr, *dfJt = nullptr, *dfKt = nullptr, *dfg = nullptr, *dfY = nullptr;
+    int df_m = 0;
     std::vector<std::pair<int, int>> tuned;   // (m, densities per pass) picked by esmf_fock_autotune
     int force_chunk = 0;                      // set while the autotuner times a candidate
     int num_sms = 0;
@@ -214,6 +221,9 @@ void release(esmf_fock *h) {
     if (h->err_host) cudaFreeHost(h->err_host);
     cudaFree(h->Jacc); cudaFree(h->Kacc); cudaFree(h->ework);
     cudaFree(h->dw); cudaFree(h->dwb);
+    cudaFree(h->dfB); cudaFree(h->dfB2); cudaFree(h->dfDt); cudaFree(h->dfJt); cudaFree(h->dfKt);
+    cudaFree(h->dfg); cudaFree(h->dfY);
+    df_cublas_destroy(h->cublas);
     cudaFree(h->sD); cudaFree(h->sJ); cudaFree(h->sK); cudaFree(h->sF); cudaFree(h->st);
     if (h->done) cudaEventDestroy(h->done);
     for (auto &e : h->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -260,6 +270,76 @@ int ensure_work(esmf_fock *h, int m) {
     return ESMF_OK;
 }
 
+// Checks of a basis description (host memory); sets *nprim_tot.
+int check_basis(const esmf_basis_t *basis, int64_t *nprim_tot_out) {
+    if (!basis || basis->n_basis <= 0 || !basis->center || !basis->n_prim || !basis->exps ||
+        !basis->coefs) {
+        set_error("basis missing or empty");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    const int n = basis->n_basis;
+    if (n > 8 * 32767) { set_error("n_basis %d too large", n); return ESMF_ERR_INVALID_ARG; }
+    int64_t nprim_tot = 0;
+    for (int i = 0; i < n; ++i) {
+        const int k = basis->n_prim[i];
+        if (k < 1 || k > ESMF_MAX_PRIM) { set_error("n_prim[%d] = %d outside [1, %d]", i, k, ESMF_MAX_PRIM); return ESMF_ERR_INVALID_ARG; }
+        for (int x = 0; x < 3; ++x)
+            if (!is_finite(basis->center[3 * i + x])) { set_error("center[%d] not finite", i); return ESMF_ERR_INVALID_ARG; }
+        nprim_tot += k;
+    }
+    for (int64_t j = 0; j < nprim_tot; ++j) {
+        if (!(basis->exps[j] > 0.0) || !is_finite(basis->exps[j])) { set_error("exps[%lld] must be finite and > 0", (long long)j); return ESMF_ERR_INVALID_ARG; }
+        if (!is_finite(basis->coefs[j])) { set_error("coefs[%lld] not finite", (long long)j); return ESMF_ERR_INVALID_ARG; }
+    }
+    // every contraction must have a positive norm
+    {
+        int64_t o = 0;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < basis->n_prim[i]; ++k)
+                for (int l = 0; l < basis->n_prim[i]; ++l) {
+                    const double ak = basis->exps[o + k], al = basis->exps[o + l];
+                    s += basis->coefs[o + k] * basis->coefs[o + l] * std::pow(2.0 * std::sqrt(ak * al) / (ak + al), 1.5);
+                }
+            if (!(s > 0.0)) { set_error("contraction %d has zero norm", i); return ESMF_ERR_INVALID_ARG; }
+            o += basis->n_prim[i];
+        }
+    }
+    *nprim_tot_out = nprim_tot;
+    return ESMF_OK;
+}
+
+// Device copies of the basis (padded to the block size), normalised weights
+// and the Schwarz table, on stream cs.
+int upload_basis(esmf_fock *h, const esmf_basis_t *basis, int64_t nprim_tot, cudaStream_t cs) {
+    const int n = h->n, np = h->np;
+    int rc;
+    std::vector<double> hc((size_t)np * 3, 0.0);
+    std::vector<int> hn(np, 0), ho(np, 0);
+    std::memcpy(hc.data(), basis->center, sizeof(double) * 3 * n);
+    int64_t o = 0;
+    for (int i = 0; i < np; ++i) {
+        ho[i] = (int)o;
+        if (i < n) { hn[i] = basis->n_prim[i]; o += hn[i]; }
+    }
+    if ((rc = dalloc(h, &h->center, (size_t)np * 3)) || (rc = dalloc(h, &h->nprim, np)) ||
+        (rc = dalloc(h, &h->poff, np)) || (rc = dalloc(h, &h->exps, nprim_tot)) ||
+        (rc = dalloc(h, &h->coefs, nprim_tot)) || (rc = dalloc(h, &h->w, nprim_tot)) ||
+        (rc = dalloc(h, &h->Q, (size_t)np * np)))
+        return rc;
+    CKR(cudaMemcpyAsync(h->center, hc.data(), sizeof(double) * np * 3, cudaMemcpyHostToDevice, cs));
+    CKR(cudaMemcpyAsync(h->nprim, hn.data(), sizeof(int) * np, cudaMemcpyHostToDevice, cs));
+    CKR(cudaMemcpyAsync(h->poff, ho.data(), sizeof(int) * np, cudaMemcpyHostToDevice, cs));
+    CKR(cudaMemcpyAsync(h->exps, basis->exps, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs));
+    CKR(cudaMemcpyAsync(h->coefs, basis->coefs, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs));
+    const DevBasis db = h->dev();
+    RET(launch_normalize(db, h->coefs, h->w, cs));
+    RET(launch_schwarz(db, h->Q, cs));
+    // the host copies above must outlive the copies
+    CKR(cudaStreamSynchronize(cs));
+    return ESMF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -292,43 +372,14 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
         return ESMF_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (!basis || basis->n_basis <= 0 || !basis->center || !basis->n_prim || !basis->exps ||
-        !basis->coefs) {
-        set_error("basis missing or empty");
-        return ESMF_ERR_INVALID_ARG;
-    }
+    if (!basis) { set_error("basis missing or empty"); return ESMF_ERR_INVALID_ARG; }
     if (!(tol >= 0.0) || !is_finite(tol)) { set_error("schwarz_tol must be finite and >= 0"); return ESMF_ERR_INVALID_ARG; }
     if (mode < ESMF_MODE_STORED || mode > ESMF_MODE_AUTO) { set_error("bad mode %d", mode); return ESMF_ERR_INVALID_ARG; }
     if (precision < ESMF_PREC_FP64 || precision > ESMF_PREC_BF16X2) { set_error("bad precision %d", precision); return ESMF_ERR_INVALID_ARG; }
     if (budget_bytes < 0) { set_error("budget_bytes < 0"); return ESMF_ERR_INVALID_ARG; }
     const int n = basis->n_basis;
-    if (n > 8 * 32767) { set_error("n_basis %d too large", n); return ESMF_ERR_INVALID_ARG; }
     int64_t nprim_tot = 0;
-    for (int i = 0; i < n; ++i) {
-        const int k = basis->n_prim[i];
-        if (k < 1 || k > ESMF_MAX_PRIM) { set_error("n_prim[%d] = %d outside [1, %d]", i, k, ESMF_MAX_PRIM); return ESMF_ERR_INVALID_ARG; }
-        for (int x = 0; x < 3; ++x)
-            if (!is_finite(basis->center[3 * i + x])) { set_error("center[%d] not finite", i); return ESMF_ERR_INVALID_ARG; }
-        nprim_tot += k;
-    }
-    for (int64_t j = 0; j < nprim_tot; ++j) {
-        if (!(basis->exps[j] > 0.0) || !is_finite(basis->exps[j])) { set_error("exps[%lld] must be finite and > 0", (long long)j); return ESMF_ERR_INVALID_ARG; }
-        if (!is_finite(basis->coefs[j])) { set_error("coefs[%lld] not finite", (long long)j); return ESMF_ERR_INVALID_ARG; }
-    }
-    // every contraction must have a positive norm
-    {
-        int64_t o = 0;
-        for (int i = 0; i < n; ++i) {
-            double s = 0.0;
-            for (int k = 0; k < basis->n_prim[i]; ++k)
-                for (int l = 0; l < basis->n_prim[i]; ++l) {
-                    const double ak = basis->exps[o + k], al = basis->exps[o + l];
-                    s += basis->coefs[o + k] * basis->coefs[o + l] * std::pow(2.0 * std::sqrt(ak * al) / (ak + al), 1.5);
-                }
-            if (!(s > 0.0)) { set_error("contraction %d has zero norm", i); return ESMF_ERR_INVALID_ARG; }
-            o += basis->n_prim[i];
-        }
-    }
+    RET(check_basis(basis, &nprim_tot));
     if (mode == ESMF_MODE_DIRECT && precision >= ESMF_PREC_FP16X2) {
         set_error("split 16-bit precisions need stored integrals");
         return ESMF_ERR_UNSUPPORTED;
@@ -364,33 +415,13 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     auto fail = [&](int code) { cudaStreamSynchronize(cs); cudaGetLastError(); release(h); return code; };
     int rc;
 
-    // padded host copies
-    std::vector<double> hc((size_t)np * 3, 0.0);
-    std::vector<int> hn(np, 0), ho(np, 0);
-    std::memcpy(hc.data(), basis->center, sizeof(double) * 3 * n);
-    int64_t o = 0;
-    for (int i = 0; i < np; ++i) {
-        ho[i] = (int)o;
-        if (i < n) { hn[i] = basis->n_prim[i]; o += hn[i]; }
-    }
-    if ((rc = dalloc(h, &h->center, (size_t)np * 3)) || (rc = dalloc(h, &h->nprim, np)) ||
-        (rc = dalloc(h, &h->poff, np)) || (rc = dalloc(h, &h->exps, nprim_tot)) ||
-        (rc = dalloc(h, &h->coefs, nprim_tot)) || (rc = dalloc(h, &h->w, nprim_tot)) ||
-        (rc = dalloc(h, &h->Q, (size_t)np * np)))
-        return fail(rc);
+    if ((rc = upload_basis(h, basis, nprim_tot, cs))) return fail(rc);
     cudaStream_t s = cs;
     auto ck = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess) { set_error("%s: %s", what, cudaGetErrorString(e)); return false; }
         return true;
     };
-    if (!ck(cudaMemcpyAsync(h->center, hc.data(), sizeof(double) * np * 3, cudaMemcpyHostToDevice, cs), "copy centers") ||
-        !ck(cudaMemcpyAsync(h->nprim, hn.data(), sizeof(int) * np, cudaMemcpyHostToDevice, cs), "copy nprim") ||
-        !ck(cudaMemcpyAsync(h->poff, ho.data(), sizeof(int) * np, cudaMemcpyHostToDevice, cs), "copy poff") ||
-        !ck(cudaMemcpyAsync(h->exps, basis->exps, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs), "copy exps") ||
-        !ck(cudaMemcpyAsync(h->coefs, basis->coefs, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs), "copy coefs"))
-        return fail(ESMF_ERR_CUDA);
     const DevBasis db = h->dev();
-    if ((rc = launch_normalize(db, h->coefs, h->w, s)) || (rc = launch_schwarz(db, h->Q, s))) return fail(rc);
     std::vector<double> hQ((size_t)np * np);
     if (!ck(cudaMemcpyAsync(hQ.data(), h->Q, sizeof(double) * np * np, cudaMemcpyDeviceToHost, cs), "copy Q") ||
         !ck(cudaStreamSynchronize(cs), "Schwarz table"))
@@ -626,9 +657,183 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     return ESMF_OK;
 }
 
+// Cholesky factor V = L L^T (lower, row-major, FP64) and L^-1, on the host;
+// false when V is not numerically positive definite (a pivot at or below
+// 1e-13 of its diagonal element: an auxiliary that the others reproduce).
+static bool cholesky_inverse(int n, std::vector<double> &V, std::vector<double> &Linv) {
+    for (int j = 0; j < n; ++j) {
+        const double vjj = V[(size_t)j * n + j];
+        double d = vjj;
+        for (int k = 0; k < j; ++k) d -= V[(size_t)j * n + k] * V[(size_t)j * n + k];
+        if (!(d > 1e-13 * vjj)) return false;
+        const double l = std::sqrt(d);
+        V[(size_t)j * n + j] = l;
+        for (int i = j + 1; i < n; ++i) {
+            double x = V[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) x -= V[(size_t)i * n + k] * V[(size_t)j * n + k];
+            V[(size_t)i * n + j] = x / l;
+        }
+    }
+    // forward substitution for each column of the identity: L X = I
+    Linv.assign((size_t)n * n, 0.0);
+    for (int c = 0; c < n; ++c)
+        for (int i = c; i < n; ++i) {
+            double x = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) x -= V[(size_t)i * n + k] * Linv[(size_t)k * n + c];
+            Linv[(size_t)i * n + c] = x / V[(size_t)i * n + i];
+        }
+    return true;
+}
+
+int esmf_fock_create_df(const esmf_basis_t *basis, const esmf_aux_t *aux, int precision, int device,
+                        esmf_fock_t **out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) { set_error("out is NULL"); return ESMF_ERR_INVALID_ARG; }
+    *out = nullptr;
+    int64_t nprim_tot = 0;
+    RET(check_basis(basis, &nprim_tot));
+    if (!aux || aux->n_aux <= 0 || aux->n_aux > 8192 || !aux->center || !aux->exps) {
+        set_error("auxiliary set missing, empty or above 8192 functions");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    for (int P = 0; P < aux->n_aux; ++P) {
+        if (!(aux->exps[P] > 0.0) || !is_finite(aux->exps[P])) { set_error("aux exps[%d] must be finite and > 0", P); return ESMF_ERR_INVALID_ARG; }
+        for (int x = 0; x < 3; ++x)
+            if (!is_finite(aux->center[3 * P + x])) { set_error("aux center[%d] not finite", P); return ESMF_ERR_INVALID_ARG; }
+    }
+    if (precision != ESMF_PREC_FP64 && precision != ESMF_PREC_FP32) {
+        set_error("density fitting runs in FP64 or FP32");
+        return precision >= ESMF_PREC_FP16X2 && precision <= ESMF_PREC_BF16X2 ? ESMF_ERR_UNSUPPORTED : ESMF_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("device %d not available (%d devices)", device, ndev);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    if (!g.ok) { set_error("cudaSetDevice(%d) failed", device); return ESMF_ERR_CUDA; }
+    esmf_fock *h = new (std::nothrow) esmf_fock();
+    if (!h) { set_error("host allocation failed"); return ESMF_ERR_OOM; }
+    const int n = basis->n_basis, naux = aux->n_aux;
+    h->device = device; h->n = n; h->prec = precision; h->mode = ESMF_MODE_DF;
+    h->nb = (n + BLK - 1) / BLK;
+    h->np = h->nb * BLK;
+    h->naux = naux;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_error("cudaStreamCreate failed");
+        return ESMF_ERR_CUDA;
+    }
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } cs_guard{cs};
+    double *acen = nullptr, *aexp = nullptr, *T = nullptr, *V = nullptr, *Linv = nullptr, *B = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(cs);
+        cudaFree(acen); cudaFree(aexp); cudaFree(T); cudaFree(V); cudaFree(Linv); cudaFree(B);
+    };
+    auto fail = [&](int code) { cleanup(); cudaGetLastError(); release(h); return code; };
+    int rc;
+    if ((rc = upload_basis(h, basis, nprim_tot, cs))) return fail(rc);
+    if ((rc = df_cublas_create(&h->cublas))) return fail(rc);
+    const size_t nn = (size_t)n * n, es = precision == ESMF_PREC_FP32 ? 4 : 8;
+    if (cudaMalloc(&acen, sizeof(double) * 3 * naux) || cudaMalloc(&aexp, sizeof(double) * naux) ||
+        cudaMalloc(&T, sizeof(double) * naux * nn) || cudaMalloc(&V, sizeof(double) * naux * naux) ||
+        cudaMalloc(&Linv, sizeof(double) * naux * naux) || cudaMalloc(&B, sizeof(double) * naux * nn)) {
+        cudaGetLastError();
+        set_error("density-fitting set-up memory (%zu bytes of three-centre integrals)", sizeof(double) * naux * nn);
+        return fail(ESMF_ERR_OOM);
+    }
+    if (cudaMemcpyAsync(acen, aux->center, sizeof(double) * 3 * naux, cudaMemcpyHostToDevice, cs) ||
+        cudaMemcpyAsync(aexp, aux->exps, sizeof(double) * naux, cudaMemcpyHostToDevice, cs)) {
+        set_error("copy auxiliary set failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    if ((rc = launch_df_integrals(h->dev(), naux, acen, aexp, T, V, cs))) return fail(rc);
+    std::vector<double> hV((size_t)naux * naux), hL;
+    if (cudaMemcpyAsync(hV.data(), V, sizeof(double) * naux * naux, cudaMemcpyDeviceToHost, cs) ||
+        cudaStreamSynchronize(cs)) {
+        set_error("metric copy failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    if (!cholesky_inverse(naux, hV, hL)) {
+        set_error("the auxiliary Coulomb metric is not positive definite (near-duplicate auxiliaries?)");
+        return fail(ESMF_ERR_INVALID_ARG);
+    }
+    if (cudaMemcpyAsync(Linv, hL.data(), sizeof(double) * naux * naux, cudaMemcpyHostToDevice, cs)) {
+        set_error("copy L^-1 failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    if ((rc = df_gemm_fold(h->cublas, naux, (int64_t)nn, Linv, T, B, cs))) return fail(rc);
+    if ((rc = dalloc(h, (unsigned char **)&h->dfB2, naux * nn * es)) ||
+        (rc = dalloc(h, (unsigned char **)&h->dfY, naux * nn * es)))
+        return fail(rc);
+    if (es == 4) {
+        if ((rc = dalloc(h, (unsigned char **)&h->dfB, naux * nn * es))) return fail(rc);
+        if ((rc = launch_df_layouts(naux, n, B, 1, h->dfB, h->dfB2, cs))) return fail(rc);
+    } else {
+        if ((rc = launch_df_layouts(naux, n, B, 0, nullptr, h->dfB2, cs))) return fail(rc);
+        h->dfB = B;                       // the FP64 factor itself is the [P][p][q] layout
+        h->device_bytes += (int64_t)(naux * nn * es);
+        B = nullptr;
+    }
+    h->store_bytes = (int64_t)(2 * naux * nn * es);
+    if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc((void **)&h->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&h->err_dev, h->err_host, 0) != cudaSuccess) {
+        set_error("event / error flag creation failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    *h->err_host = 0;
+    cleanup();
+    if (cudaGetLastError() != cudaSuccess) { set_error("density-fitting set-up kernels failed"); release(h); return ESMF_ERR_CUDA; }
+    h->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return ESMF_OK;
+}
+
 }  // extern "C"
 
 namespace {
+
+// One density-fitted build: per-build work grown for m densities, then the
+// GEMM sequence of df.cu.
+int build_df(esmf_fock_t *h, int m, const double *D, double *J, double *K, double *F, double *traces,
+             cudaStream_t s) {
+    const size_t es = h->prec == ESMF_PREC_FP32 ? 4 : 8;
+    const size_t nn = (size_t)h->n * h->n;
+    if (m > h->df_m) {
+        dfree(h, (unsigned char **)&h->dfDt, h->df_m * nn * es); dfree(h, (unsigned char **)&h->dfJt, h->df_m * nn * es);
+        dfree(h, (unsigned char **)&h->dfKt, h->df_m * nn * es); dfree(h, (unsigned char **)&h->dfg, (size_t)h->df_m * h->naux * es);
+        h->df_m = 0;
+        RET(dalloc(h, (unsigned char **)&h->dfDt, es == 4 ? m * nn * es : 1));
+        RET(dalloc(h, (unsigned char **)&h->dfJt, m * nn * es));
+        RET(dalloc(h, (unsigned char **)&h->dfKt, m * nn * es));
+        RET(dalloc(h, (unsigned char **)&h->dfg, (size_t)m * h->naux * es));
+        h->df_m = m;
+    }
+    DfBuild a;
+    a.cublas = h->cublas; a.n = h->n; a.naux = h->naux; a.m = m; a.fp32 = h->prec == ESMF_PREC_FP32;
+    a.B = h->dfB; a.B2 = h->dfB2; a.D = D;
+    a.Dt = h->dfDt; a.Jt = h->dfJt; a.Kt = h->dfKt; a.g = h->dfg; a.Y = h->dfY;
+    a.J = J; a.K = K; a.F = F; a.traces = traces;
+    if (h->timing && h->ev_used < 65536) {
+        if (h->ev_used == h->ev_pool.size()) {
+            cudaEvent_t x, y;
+            CKR(cudaEventCreate(&x));
+            CKR(cudaEventCreate(&y));
+            h->ev_pool.push_back({x, y});
+        }
+        a.ev_start = h->ev_pool[h->ev_used].first;
+        a.ev_stop = h->ev_pool[h->ev_used].second;
+        ++h->ev_used;
+    }
+    return df_build(a, s);
+}
 
 // the build over kept bricks [b0, b1) of the handle's list; J, K, F and the
 // traces are linear in the integrals, so builds over a partition of the list
@@ -644,6 +849,10 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
         (traces && !is_device_ptr(traces))) {
         set_error("D, J, K, F and traces must be device memory");
         return ESMF_ERR_INVALID_ARG;
+    }
+    if (h->mode == ESMF_MODE_DF) {
+        if (b0 != 0 || b1 != h->nbricks) { set_error("density-fitted handles build whole only"); return ESMF_ERR_UNSUPPORTED; }
+        return build_df(h, m, D, J, K, F, traces, (cudaStream_t)stream);
     }
     RET(ensure_work(h, m));
     cudaStream_t s = (cudaStream_t)stream;
@@ -867,6 +1076,7 @@ int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const d
         set_error("shard %d of %d", shard, nshards);
         return ESMF_ERR_INVALID_ARG;
     }
+    if (h->mode == ESMF_MODE_DF) { set_error("density-fitted handles are not sharded"); return ESMF_ERR_UNSUPPORTED; }
     const int64_t b0 = h->nbricks * shard / nshards, b1 = h->nbricks * (shard + 1) / nshards;
     return build_range(h, b0, b1, m, D, J, K, F, traces, stream);
 }
@@ -936,6 +1146,7 @@ int esmf_fock_set_path(esmf_fock_t *h, int path) {
 int esmf_fock_autotune(esmf_fock_t *h, int m, const double *D, double *J, double *K, int reps,
                        void *stream, int *chosen) {
     if (!h || m < 1 || m > ESMF_MAX_DENSITIES || !D || !J || !K) { set_error("bad autotune arguments"); return ESMF_ERR_INVALID_ARG; }
+    if (h->mode == ESMF_MODE_DF) { set_error("density-fitted handles have nothing to tune"); return ESMF_ERR_UNSUPPORTED; }
     DeviceGuard g(h->device);
     if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
     const bool tensor = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2 && h->path != ESMF_PATH_CUDA_CORE;
@@ -1055,6 +1266,10 @@ int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, in
                            bool *split) {
     if (h->tol_d > 0.0) {
         set_error("density-weighted screening needs per-build work memory; the no-alloc entry does not apply it");
+        return ESMF_ERR_UNSUPPORTED;
+    }
+    if (h->mode == ESMF_MODE_DF) {
+        set_error("density-fitted builds need per-build GEMM work memory; the no-alloc entry does not run them");
         return ESMF_ERR_UNSUPPORTED;
     }
     a->b = h->dev(); a->Q = h->S; a->tol = h->tol_s; a->bricks = h->bricks; a->nbricks = h->nbricks;

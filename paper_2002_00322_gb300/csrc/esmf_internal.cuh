@@ -133,6 +133,24 @@ int launch_finalize(const DevBasis &b, int m, const double *D, const double *Jac
                     const double *Kacc, double *J, double *K, double *F, double *tsum,
                     cudaStream_t s);
 
+// ---- df.cu (density-fitted J and K)
+struct DfBuild {
+    void *cublas;
+    int n, naux, m, fp32;
+    const void *B, *B2;          // B[P][p][q] and B''[p][P][q] in the arithmetic type
+    const double *D;             // caller's densities (m x n x n)
+    void *Dt, *Jt, *Kt, *g, *Y;  // work: arithmetic-type D (FP32 only), J, K, g, Y
+    double *J, *K, *F, *traces;  // caller's outputs
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+};
+int launch_df_integrals(const DevBasis &b, int naux, const double *acen, const double *aexp, double *T, double *V,
+                        cudaStream_t s);
+int launch_df_layouts(int naux, int n, const double *B, int fp32, void *Bout, void *B2, cudaStream_t s);
+int df_gemm_fold(void *cublas, int naux, int64_t nn, const double *Linv, const double *T, double *B, cudaStream_t s);
+int df_build(const DfBuild &a, cudaStream_t s);
+int df_cublas_create(void **out);
+void df_cublas_destroy(void *h);
+
 // ---- energy.cu (ESMF energy and gradient around the grouped build)
 struct EnergyWork {
     double *D, *J, *K, *F;               // 3 x N x N each: P, T, A and their J, K, F

@@ -22,7 +22,7 @@ ESMF_ERR_CUDA = -3
 ESMF_ERR_TIMEOUT = -4
 ESMF_ERR_UNSUPPORTED = -5
 
-MODES = {"stored": 0, "direct": 1, "auto": 2}
+MODES = {"stored": 0, "direct": 1, "auto": 2, "df": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16x2": 2, "bf16x2": 3}
 MAX_PRIM = 4
 
@@ -32,7 +32,7 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
            "esmf_fock_autotune", "esmf_fock_create_screened", "esmf_fock_build_batch",
-           "esmf_measure_fma_peak", "esmf_fock_set_density_screening"]
+           "esmf_measure_fma_peak", "esmf_fock_set_density_screening", "esmf_fock_create_df"]
 MAX_BATCH = 16
 SCREENINGS = {"schwarz": 0, "pair_max": 1}
 PATHS = {"auto": 0, "cuda_core": 1}
@@ -55,6 +55,10 @@ class esmf_basis_t(C.Structure):
     _fields_ = [("n_basis", C.c_int32), ("center", C.POINTER(C.c_double)),
                 ("n_prim", C.POINTER(C.c_int32)), ("exps", C.POINTER(C.c_double)),
                 ("coefs", C.POINTER(C.c_double))]
+
+
+class esmf_aux_t(C.Structure):
+    _fields_ = [("n_aux", C.c_int32), ("center", C.POINTER(C.c_double)), ("exps", C.POINTER(C.c_double))]
 
 
 class esmf_stats_t(C.Structure):
@@ -119,6 +123,9 @@ def load(path=None):
         L.esmf_gvp_gradient.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, C.c_double, C.c_double,
                                         C.c_double, vp, vp, vp, vp]
         L.esmf_gvp_gradient.restype = C.c_int
+        L.esmf_fock_create_df.argtypes = [C.POINTER(esmf_basis_t), C.POINTER(esmf_aux_t), C.c_int, C.c_int,
+                                          C.POINTER(vp)]
+        L.esmf_fock_create_df.restype = C.c_int
         L.esmf_fock_set_density_screening.argtypes = [vp, C.c_double]
         L.esmf_fock_set_density_screening.restype = C.c_int
         L.esmf_measure_fma_peak.argtypes = [C.c_int, C.c_int, dp]
@@ -173,6 +180,27 @@ def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device
         rc = L.esmf_fock_create_screened(C.byref(b), float(schwarz_tol), sc, m, p, int(device),
                                          int(budget_bytes), C.byref(h))
     _check(rc, "esmf_fock_create")
+    return h
+
+
+def esmf_fock_create_df(basis, aux_center, aux_exps, precision="fp64", device=0):
+    """Density-fitted handle (include/esmf_fock.h, esmf_fock_create_df): the
+    auxiliary s Gaussians exp(-aux_exps[P] |r - aux_center[P]|^2)."""
+    L = load()
+    center = np.ascontiguousarray(basis.center, dtype=np.float64)
+    nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)
+    exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
+    coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
+    b = esmf_basis_t(int(center.shape[0]), center.ctypes.data_as(C.POINTER(C.c_double)),
+                     nprim.ctypes.data_as(C.POINTER(C.c_int32)),
+                     exps.ctypes.data_as(C.POINTER(C.c_double)),
+                     coefs.ctypes.data_as(C.POINTER(C.c_double)))
+    ac = np.ascontiguousarray(aux_center, dtype=np.float64).reshape(-1, 3)
+    ae = np.ascontiguousarray(aux_exps, dtype=np.float64).ravel()
+    a = esmf_aux_t(int(ae.size), ac.ctypes.data_as(C.POINTER(C.c_double)), ae.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(L.esmf_fock_create_df(C.byref(b), C.byref(a), p, int(device), C.byref(h)), "esmf_fock_create_df")
     return h
 
 
@@ -320,13 +348,20 @@ class FockBuilder:
     """Owns one handle; D, J, K are torch float64 CUDA tensors (m, N, N)."""
 
     def __init__(self, basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0,
-                 screening="schwarz"):
+                 screening="schwarz", aux=None):
+        """mode "df" builds with density-fitted integrals over aux = (centers,
+        exponents) of auxiliary s Gaussians (schwarz_tol unused)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("FockBuilder needs a CUDA device")
         self.n = int(basis.center.shape[0])
         self.device = int(device)
-        self.h = esmf_fock_create(basis, schwarz_tol, mode, precision, device, budget_bytes, screening)
+        if mode == "df":
+            if aux is None:
+                raise ValueError("mode 'df' needs aux = (centers, exponents)")
+            self.h = esmf_fock_create_df(basis, aux[0], aux[1], precision, device)
+        else:
+            self.h = esmf_fock_create(basis, schwarz_tol, mode, precision, device, budget_bytes, screening)
 
     def stats(self):
         return esmf_fock_stats(self.h)

@@ -43,17 +43,23 @@ class Basis:
     nprim: np.ndarray
     exps: np.ndarray
     coefs: np.ndarray
+    cart: np.ndarray = None       # (N,) int32 Cartesian label: 0 s, 1..3 p_x, p_y, p_z (None: all s)
 
     @property
     def n(self) -> int:
         return int(self.center.shape[0])
+
+    @property
+    def has_p(self) -> bool:
+        return self.cart is not None and bool(np.any(np.asarray(self.cart) != 0))
 
     def subset(self, idx) -> "Basis":
         idx = np.asarray(idx, dtype=np.int64)
         off = np.concatenate([[0], np.cumsum(self.nprim)])
         sel = np.concatenate([np.arange(off[i], off[i + 1]) for i in idx])
         return Basis(self.center[idx].copy(), self.nprim[idx].copy(),
-                     self.exps[sel].copy(), self.coefs[sel].copy())
+                     self.exps[sel].copy(), self.coefs[sel].copy(),
+                     None if self.cart is None else np.asarray(self.cart)[idx].copy())
 
 
 @dataclass
@@ -109,6 +115,41 @@ def s_basis(rng, centers, per_center=2, nprim=3, lo=0.1, hi=10.0) -> Basis:
                  coefs.astype(np.float64))
 
 
+def sp_basis(rng, centers, nprim=3, lo=0.1, hi=10.0) -> Basis:
+    """One s shell and one p shell (p_x, p_y, p_z sharing exponents and
+    coefficients) per center, the shape of a minimal basis with p functions;
+    exponents log-uniform in [lo, hi] bohr^-2, coefficients uniform in (0.1, 1]."""
+    ncen = centers.shape[0]
+    center, npr, exps, coefs, cart = [], [], [], [], []
+    for c in centers:
+        es = np.exp(rng.uniform(np.log(lo), np.log(hi), size=nprim))
+        cs = 1.0 - rng.uniform(0.0, 0.9, size=nprim)
+        ep = np.exp(rng.uniform(np.log(lo), np.log(hi), size=nprim))
+        cp = 1.0 - rng.uniform(0.0, 0.9, size=nprim)
+        for lab, e, co in ((0, es, cs), (1, ep, cp), (2, ep, cp), (3, ep, cp)):
+            center.append(c)
+            npr.append(nprim)
+            exps.extend(e)
+            coefs.extend(co)
+            cart.append(lab)
+    return Basis(np.asarray(center, dtype=np.float64), np.asarray(npr, dtype=np.int32),
+                 np.asarray(exps, dtype=np.float64), np.asarray(coefs, dtype=np.float64),
+                 np.asarray(cart, dtype=np.int32))
+
+
+def sp_random(n_centers, m, seed, tol=1e-10, edge=None, min_dist=1.4) -> Workload:
+    """Random molecule of s and p shells (4 functions per center) for the
+    angular-momentum tests, densities from the same recipes."""
+    rng = rng_for(BASE_SEED + 300 + seed)
+    if edge is None:
+        edge = 10.0 * (n_centers / 100.0) ** (1.0 / 3.0)
+    cen = cube_centers(rng, n_centers, edge, min_dist)
+    b = sp_basis(rng, cen)
+    nocc = max(1, b.n // 5)
+    D = esmf_densities(rng, b.n, nocc, m)
+    return Workload(f"sp_n{b.n}_m{m}_s{seed}", b, D, tol, nocc)
+
+
 # ---------------------------------------------------------------- densities
 def orbitals(rng, n):
     """Rows are orthonormal orbitals (V = U^T C with U = I, C a Q factor)."""
@@ -155,6 +196,15 @@ def esmf_densities(rng, n, nocc, m, first=None):
             s = _unit(rng, (nocc, nv))
             out.append(Th.T @ s @ Ga)
     return np.ascontiguousarray(np.stack(out[:m]).astype(np.float64))
+
+
+def even_tempered_aux(basis: Basis, count=7, first=0.2, ratio=2.5):
+    """Auxiliary set for density fitting: on every distinct center, `count`
+    s Gaussians with exponents first * ratio^k bohr^-2 (k < count).  Returns
+    (centers (n_aux, 3), exponents (n_aux,))."""
+    cen = np.unique(basis.center, axis=0)
+    et = first * ratio ** np.arange(count)
+    return np.repeat(cen, et.size, axis=0), np.tile(et, cen.shape[0])
 
 
 # ---------------------------------------------------------------- ESMF state
