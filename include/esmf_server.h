@@ -73,6 +73,12 @@ typedef struct {
  */
 #define ESMF_SERVER_GRAPHS 1
 #define ESMF_SERVER_BATCH  2
+/* ESMF_SERVER_EVICT_LARGEST: when memory must be freed, evict the largest
+ * idle molecule first (among those with no queued request) instead of the
+ * least recently used.  Re-creating a handle costs about the same per byte
+ * of store, so freeing the room with fewer, larger evictions means fewer
+ * re-creations when requests are spread evenly over the molecules. */
+#define ESMF_SERVER_EVICT_LARGEST 4
 int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int precision,
                        int flags, esmf_server_t **out);
 

@@ -39,6 +39,7 @@ struct esmf_fock {
     // basis (device)
     double *center = nullptr, *exps = nullptr, *w = nullptr, *coefs = nullptr;
     int *nprim = nullptr, *poff = nullptr;
+    int *cart = nullptr;           // Cartesian labels (device, np), null when every function is s
     double *Q = nullptr;
     // screening table and threshold of the quartet rule S_pq S_rs >= tol_s:
     // the Schwarz table itself (S = Q, tol_s = tol), or the 0/1 table of the
@@ -101,6 +102,7 @@ struct esmf_fock {
         DevBasis b;
         b.n = n; b.np = np; b.nb = nb;
         b.center = center; b.nprim = nprim; b.poff = poff; b.exps = exps; b.w = w;
+        b.cart = cart;
         return b;
     }
 };
@@ -212,7 +214,7 @@ std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
 void release(esmf_fock *h) {
     if (!h) return;
     cudaFree(h->center); cudaFree(h->exps); cudaFree(h->w); cudaFree(h->coefs);
-    cudaFree(h->nprim); cudaFree(h->poff);
+    cudaFree(h->nprim); cudaFree(h->poff); cudaFree(h->cart);
     if (h->S != h->Q) cudaFree(h->S);
     cudaFree(h->Q);
     cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts);
@@ -311,9 +313,17 @@ int check_basis(const esmf_basis_t *basis, int64_t *nprim_tot_out) {
 
 // Device copies of the basis (padded to the block size), normalised weights
 // and the Schwarz table, on stream cs.
-int upload_basis(esmf_fock *h, const esmf_basis_t *basis, int64_t nprim_tot, cudaStream_t cs) {
+int upload_basis(esmf_fock *h, const esmf_basis_t *basis, int64_t nprim_tot, cudaStream_t cs,
+                 const int32_t *cart = nullptr) {
     const int n = h->n, np = h->np;
     int rc;
+    std::vector<int> hcart;
+    if (cart) {
+        hcart.assign(np, 0);
+        for (int i = 0; i < n; ++i) hcart[i] = cart[i];
+        if ((rc = dalloc(h, &h->cart, np))) return rc;
+        CKR(cudaMemcpyAsync(h->cart, hcart.data(), sizeof(int) * np, cudaMemcpyHostToDevice, cs));
+    }
     std::vector<double> hc((size_t)np * 3, 0.0);
     std::vector<int> hn(np, 0), ho(np, 0);
     std::memcpy(hc.data(), basis->center, sizeof(double) * 3 * n);
@@ -333,14 +343,22 @@ int upload_basis(esmf_fock *h, const esmf_basis_t *basis, int64_t nprim_tot, cud
     CKR(cudaMemcpyAsync(h->exps, basis->exps, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs));
     CKR(cudaMemcpyAsync(h->coefs, basis->coefs, sizeof(double) * nprim_tot, cudaMemcpyHostToDevice, cs));
     const DevBasis db = h->dev();
-    RET(launch_normalize(db, h->coefs, h->w, cs));
-    RET(launch_schwarz(db, h->Q, cs));
+    if (h->cart) {
+        RET(launch_normalize_l(db, h->coefs, h->w, cs));
+        RET(launch_schwarz_l(db, h->Q, cs));
+    } else {
+        RET(launch_normalize(db, h->coefs, h->w, cs));
+        RET(launch_schwarz(db, h->Q, cs));
+    }
     // the host copies above must outlive the copies
     CKR(cudaStreamSynchronize(cs));
     return ESMF_OK;
 }
 
 }  // namespace
+
+static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double tol, int screening, int mode,
+                       int precision, int device, int64_t budget_bytes, esmf_fock_t **out);
 
 extern "C" {
 
@@ -365,6 +383,29 @@ int esmf_fock_create(const esmf_basis_t *basis, double tol, int mode, int precis
 
 int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screening, int mode, int precision,
                               int device, int64_t budget_bytes, esmf_fock_t **out) {
+    return create_impl(basis, nullptr, tol, screening, mode, precision, device, budget_bytes, out);
+}
+
+int esmf_fock_create_cart(const esmf_basis_t *basis, const int32_t *cart, double tol, int mode, int precision,
+                          int device, int64_t budget_bytes, esmf_fock_t **out) {
+    if (!basis || !cart || basis->n_basis <= 0) { set_error("basis and cart are required"); return ESMF_ERR_INVALID_ARG; }
+    bool any_p = false;
+    for (int i = 0; i < basis->n_basis; ++i) {
+        if (cart[i] < 0 || cart[i] > 3) { set_error("cart[%d] = %d outside [0, 3]", i, cart[i]); return ESMF_ERR_INVALID_ARG; }
+        any_p |= cart[i] != 0;
+    }
+    if (!any_p) cart = nullptr;          // all s: the s-type path
+    else if (mode == ESMF_MODE_DIRECT) {
+        set_error("p functions need stored integrals (integral-direct builds evaluate s functions only)");
+        return ESMF_ERR_UNSUPPORTED;
+    }
+    return create_impl(basis, cart, tol, ESMF_SCREEN_SCHWARZ, mode, precision, device, budget_bytes, out);
+}
+
+}  // extern "C"
+
+static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double tol, int screening, int mode,
+                       int precision, int device, int64_t budget_bytes, esmf_fock_t **out) {
     const auto t0 = std::chrono::steady_clock::now();
     if (!out) { set_error("out is NULL"); return ESMF_ERR_INVALID_ARG; }
     if (screening != ESMF_SCREEN_SCHWARZ && screening != ESMF_SCREEN_PAIR_MAX) {
@@ -415,7 +456,7 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     auto fail = [&](int code) { cudaStreamSynchronize(cs); cudaGetLastError(); release(h); return code; };
     int rc;
 
-    if ((rc = upload_basis(h, basis, nprim_tot, cs))) return fail(rc);
+    if ((rc = upload_basis(h, basis, nprim_tot, cs, cart))) return fail(rc);
     cudaStream_t s = cs;
     auto ck = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess) { set_error("%s: %s", what, cudaGetErrorString(e)); return false; }
@@ -594,6 +635,11 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     if (mode == ESMF_MODE_AUTO) {
         use_mode = (budget_bytes == 0 || h->device_bytes + h->store_bytes <= budget_bytes) ? ESMF_MODE_STORED
                                                                                           : ESMF_MODE_DIRECT;
+        if (use_mode == ESMF_MODE_DIRECT && h->cart) {
+            set_error("the store of a basis with p functions (%lld bytes) exceeds the budget, and integral-direct "
+                      "builds evaluate s functions only", (long long)h->store_bytes);
+            return fail(ESMF_ERR_UNSUPPORTED);
+        }
         if (use_mode == ESMF_MODE_DIRECT && precision >= ESMF_PREC_FP16X2) h->prec = ESMF_PREC_FP32;
     } else if (mode == ESMF_MODE_STORED && budget_bytes > 0 && h->device_bytes + h->store_bytes > budget_bytes) {
         set_error("stored integrals need %lld bytes, budget %lld", (long long)h->store_bytes, (long long)budget_bytes);
@@ -619,9 +665,13 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
             if (!ck(cudaMemcpyAsync(h->offsets, offs.data(), sizeof(int64_t) * (h->nbricks + 1), cudaMemcpyHostToDevice, cs), "copy offsets"))
                 return fail(ESMF_ERR_CUDA);
             if (!ck(cudaMemsetAsync(h->store, 0, (size_t)h->store_bytes, cs), "clear store")) return fail(ESMF_ERR_CUDA);
-            if ((rc = launch_brick_generate(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec,
-                                            h->store, h->vscale, s)))
-                return fail(rc);
+            if (h->cart)
+                rc = launch_brick_generate_l(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec, h->store,
+                                             h->vscale, s);
+            else
+                rc = launch_brick_generate(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec, h->store,
+                                           h->vscale, s);
+            if (rc) return fail(rc);
         } else {
             // integral-direct: the primitive pairs of every block pair that a
             // kept brick uses as bra or ket, formed once here instead of in
@@ -656,6 +706,8 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
     *out = h;
     return ESMF_OK;
 }
+
+extern "C" {
 
 // Cholesky factor V = L L^T (lower, row-major, FP64) and L^-1, on the host;
 // false when V is not numerically positive definite (a pivot at or below

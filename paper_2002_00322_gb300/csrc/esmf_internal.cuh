@@ -54,6 +54,7 @@ struct DevBasis {
     const int *poff;       // np
     const double *exps;    // primitives
     const double *w;       // normalised raw-Gaussian weights
+    const int *cart = nullptr;  // np Cartesian labels (0 s, 1..3 p_x..p_z); null: all s
 };
 
 void set_error(const char *fmt, ...);
@@ -69,6 +70,13 @@ int launch_brick_count(const DevBasis &b, const double *Q, double tol, const Bri
 int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                           int64_t nbricks, const int64_t *offsets, int precision, void *store,
                           float vscale, cudaStream_t s);
+
+// ---- angular.cu (bases with Cartesian p functions)
+int launch_normalize_l(const DevBasis &b, const double *coefs, double *w, cudaStream_t s);
+int launch_schwarz_l(const DevBasis &b, double *Q, cudaStream_t s);
+int launch_brick_generate_l(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
+                            int64_t nbricks, const int64_t *offsets, int precision, void *store, float vscale,
+                            cudaStream_t s);
 
 // ---- jk_cuda.cu (CUDA-core contraction)
 // primitive-pair table of integral-direct handles: one entry per function-

@@ -74,6 +74,7 @@ struct esmf_server {
     int precision = ESMF_PREC_FP16X2;
     bool use_graphs = false;
     bool batch = false;              // batched ticks
+    bool evict_largest = false;      // eviction order: largest idle first (else LRU)
     cudaStream_t tick_stream = nullptr;
     cudaEvent_t tick_ev = nullptr;
     std::mutex mu;
@@ -177,7 +178,9 @@ void make_room(esmf_server *s, int idx) {
             if (victim < 0) { victim = (int)i; continue; }
             const Molecule &v = s->mols[victim];
             const bool cq = c.queued > 0, vq = v.queued > 0;
-            if ((cq != vq && !cq) || (cq == vq && c.last_use < v.last_use)) victim = (int)i;
+            const bool better = s->evict_largest ? (c.bytes > v.bytes || (c.bytes == v.bytes && c.last_use < v.last_use))
+                                                 : c.last_use < v.last_use;
+            if ((cq != vq && !cq) || (cq == vq && better)) victim = (int)i;
         }
         if (victim < 0) return;
         evict(s, victim);
@@ -501,7 +504,8 @@ extern "C" {
 int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int precision, int flags,
                        esmf_server_t **out) {
     if (!out || budget_bytes <= 0 || max_inflight < 1 || max_inflight > 64 || precision < ESMF_PREC_FP64 ||
-        precision > ESMF_PREC_BF16X2 || (flags & ~(ESMF_SERVER_GRAPHS | ESMF_SERVER_BATCH)) != 0) {
+        precision > ESMF_PREC_BF16X2 ||
+        (flags & ~(ESMF_SERVER_GRAPHS | ESMF_SERVER_BATCH | ESMF_SERVER_EVICT_LARGEST)) != 0) {
         set_error("bad server arguments");
         return ESMF_ERR_INVALID_ARG;
     }
@@ -521,6 +525,7 @@ int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int p
     s->precision = precision;
     s->use_graphs = (flags & ESMF_SERVER_GRAPHS) != 0;
     s->batch = (flags & ESMF_SERVER_BATCH) != 0;
+    s->evict_largest = (flags & ESMF_SERVER_EVICT_LARGEST) != 0;
     s->slots.resize(max_inflight);
     if (s->batch && (cudaStreamCreateWithFlags(&s->tick_stream, cudaStreamNonBlocking) != cudaSuccess ||
                      cudaEventCreateWithFlags(&s->tick_ev, cudaEventDisableTiming) != cudaSuccess)) {

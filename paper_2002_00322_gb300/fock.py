@@ -32,7 +32,8 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_set_timing", "esmf_fock_kernel_time", "esmf_fock_build_noalloc",
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
            "esmf_fock_autotune", "esmf_fock_create_screened", "esmf_fock_build_batch",
-           "esmf_measure_fma_peak", "esmf_fock_set_density_screening", "esmf_fock_create_df"]
+           "esmf_measure_fma_peak", "esmf_fock_set_density_screening", "esmf_fock_create_df",
+           "esmf_fock_create_cart"]
 MAX_BATCH = 16
 SCREENINGS = {"schwarz": 0, "pair_max": 1}
 PATHS = {"auto": 0, "cuda_core": 1}
@@ -123,6 +124,9 @@ def load(path=None):
         L.esmf_gvp_gradient.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, C.c_double, C.c_double,
                                         C.c_double, vp, vp, vp, vp]
         L.esmf_gvp_gradient.restype = C.c_int
+        L.esmf_fock_create_cart.argtypes = [C.POINTER(esmf_basis_t), C.POINTER(C.c_int32), C.c_double, C.c_int,
+                                            C.c_int, C.c_int, C.c_int64, C.POINTER(vp)]
+        L.esmf_fock_create_cart.restype = C.c_int
         L.esmf_fock_create_df.argtypes = [C.POINTER(esmf_basis_t), C.POINTER(esmf_aux_t), C.c_int, C.c_int,
                                           C.POINTER(vp)]
         L.esmf_fock_create_df.restype = C.c_int
@@ -174,6 +178,16 @@ def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     sc = SCREENINGS[screening] if isinstance(screening, str) else int(screening)
+    cart = getattr(basis, "cart", None)
+    if cart is not None and np.any(np.asarray(cart) != 0):
+        # s and Cartesian p functions: esmf_fock_create_cart (Schwarz screening)
+        if sc != 0:
+            raise ValueError("bases with p functions use Schwarz screening")
+        ca = np.ascontiguousarray(cart, dtype=np.int32)
+        rc = L.esmf_fock_create_cart(C.byref(b), ca.ctypes.data_as(C.POINTER(C.c_int32)), float(schwarz_tol), m, p,
+                                     int(device), int(budget_bytes), C.byref(h))
+        _check(rc, "esmf_fock_create_cart")
+        return h
     if sc == 0:
         rc = L.esmf_fock_create(C.byref(b), float(schwarz_tol), m, p, int(device), int(budget_bytes), C.byref(h))
     else:
@@ -185,7 +199,9 @@ def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device
 
 def esmf_fock_create_df(basis, aux_center, aux_exps, precision="fp64", device=0):
     """Density-fitted handle (include/esmf_fock.h, esmf_fock_create_df): the
-    auxiliary s Gaussians exp(-aux_exps[P] |r - aux_center[P]|^2)."""
+    auxiliary s Gaussians exp(-aux_exps[P] |r - aux_center[P]|^2); s bases."""
+    if getattr(basis, "cart", None) is not None and np.any(np.asarray(basis.cart) != 0):
+        raise ValueError("density fitting takes bases of s functions")
     L = load()
     center = np.ascontiguousarray(basis.center, dtype=np.float64)
     nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)

@@ -13,6 +13,7 @@ from . import fock
 
 SERVER_GRAPHS = 1      # ESMF_SERVER_GRAPHS
 SERVER_BATCH = 2       # ESMF_SERVER_BATCH
+SERVER_EVICT_LARGEST = 4   # ESMF_SERVER_EVICT_LARGEST
 
 SERVER_EXPORTS = ["esmf_server_create", "esmf_server_register", "esmf_server_submit",
                   "esmf_server_wait", "esmf_server_stats", "esmf_server_reset_stats",
@@ -59,13 +60,15 @@ class Server:
     """Requests use host numpy arrays; keep them alive until wait() returns."""
 
     def __init__(self, budget_bytes, max_inflight=4, precision="fp16x2", use_graphs=True, device=0,
-                 batch=False):
+                 batch=False, evict_largest=False):
         """use_graphs: replay single builds from CUDA graphs; batch: build the
-        tensor-path requests admitted together in one batched launch."""
+        tensor-path requests admitted together in one batched launch;
+        evict_largest: free memory by evicting the largest idle molecule first."""
         L = _lib()
         self.h = C.c_void_p()
         p = fock.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        flags = (SERVER_GRAPHS if use_graphs else 0) | (SERVER_BATCH if batch else 0)
+        flags = (SERVER_GRAPHS if use_graphs else 0) | (SERVER_BATCH if batch else 0) | \
+            (SERVER_EVICT_LARGEST if evict_largest else 0)
         fock._check(L.esmf_server_create(int(device), int(budget_bytes), int(max_inflight), p,
                                          flags, C.byref(self.h)), "esmf_server_create")
         self._keep = {}

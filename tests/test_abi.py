@@ -66,7 +66,7 @@ def test_strerror_and_host_side_argument_errors(lib):
     # server: unknown flag bits, bad slot count and budget are rejected before any CUDA call
     from paper_2002_00322_gb300 import server
     server._lib()
-    for args in ((0, 1 << 30, 4, 2, 4), (0, 1 << 30, 0, 2, server.SERVER_BATCH), (0, 0, 4, 2, 1)):
+    for args in ((0, 1 << 30, 4, 2, 8), (0, 1 << 30, 0, 2, server.SERVER_BATCH), (0, 0, 4, 2, 1)):
         assert lib.esmf_server_create(*args, C.byref(h)) == fock.ESMF_ERR_INVALID_ARG
 
 
