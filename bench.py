@@ -242,6 +242,26 @@ def sub_direct(fock, W, dev, stream, alu_peaks, steps=2):
                              "flops_per_quartet": "81 primitive quartets x 25 + 20 m"}}
 
 
+def sub_sp(fock, W, dev, stream, steps=5):
+    """A molecule of s and p shells (25 centers x (s, p_x, p_y, p_z) = 100
+    functions, m = 16, tol 1e-10): Obara-Saika store creation and builds on
+    the split FP16 tensor-core path and the FP64 CUDA-core path."""
+    import torch
+    w = W.sp_random(25, 16, 11)
+    out = {"n_basis": int(w.basis.n), "m": int(w.m), "shells": "25 centers x (s, p)"}
+    for prec in ("fp16x2", "fp64"):
+        with fock.FockBuilder(w.basis, w.tol, "stored", prec, device=dev.index) as fb:
+            st = fb.stats()
+            D = torch.from_numpy(w.D).to(dev)
+            J, K, F = torch.empty_like(D), torch.empty_like(D), torch.empty_like(D)
+            t = torch.empty(w.m, dtype=torch.float64, device=dev)
+            ms, ks = timed_builds(fock, fb, w.m, D, J, K, F, t, stream, steps, 2)
+            out[prec] = {"dtype": DTYPES[prec], "ms_per_step": round(ms, 4), "value": round(1e3 / ms, 3),
+                         "setup_ms": round(st["create_ms"], 1), "quartets_kept": st["n_quartets_kept"],
+                         "store_bytes": st["store_bytes"], "kernel_ms": round(ks * 1e3, 4)}
+    return out
+
+
 def sub_df(fock, W, dev, stream, alu_peaks, steps=3):
     """stored_n200_m16 with density-fitted integrals (7 even-tempered s
     auxiliaries per center): builds/s in FP64 and FP32 GEMMs, and the fit's
@@ -437,6 +457,7 @@ def run_ours(args):
         subs["precision_n400_m64_fp16x2"] = sub_precision(fock, W, dev, stream)
         subs["direct_n2000_m32_fp32"] = sub_direct(fock, W, dev, stream, alu_peaks)
         subs["stored_n200_m16_density_fitted"] = sub_df(fock, W, dev, stream, alu_peaks)
+        subs["sp_n100_m16"] = sub_sp(fock, W, dev, stream)
         subs["batched_uneven_fp16x2"] = run_batched(fock, W, dev, stream, "fp16x2")
         out["configs"] = subs
         if rank == 0 and world == 1 and not args.no_serving:

@@ -247,11 +247,17 @@ int esmf_fock_build_batch(int count, esmf_fock_t *const *h, const int *m,
 
 /*
  * esmf_fock_build_shard -- the part of esmf_fock_build contributed by shard
- * `shard` of `nshards` equal contiguous slices of the handle's kept brick
- * list.  J, K, F and the traces are linear in the integrals, so the element-
- * wise sum of the outputs of all shards (e.g. one all-reduce across GPUs, each
- * holding a handle for the same basis) equals the full build.  Same buffers,
- * asynchrony and errors as esmf_fock_build; INVALID_ARG for a bad shard.
+ * `shard` of `nshards` contiguous slices of the handle's kept brick list.
+ * The slices hold equal shares of the estimated contraction cost (the
+ * per-brick cost model of the tensor kernel's CTA split), each cut moved to
+ * the next item boundary of the brick order; on the tensor-core path each
+ * shard gets its own cost-balanced CTA split (formed on the first build of
+ * that shard: that build allocates a few hundred bytes).  J, K, F and the
+ * traces are linear in the integrals, so the element-wise sum of the outputs
+ * of all shards (e.g. one all-reduce across GPUs, each holding a handle for
+ * the same basis) equals the full build.  Same buffers, asynchrony and
+ * errors as esmf_fock_build; INVALID_ARG for a bad shard; UNSUPPORTED for
+ * density-fitted handles.
  */
 int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const double *D,
                           double *J, double *K, double *F, double *traces, void *stream);

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <thread>
 #include <vector>
@@ -77,6 +78,12 @@ struct esmf_fock {
     // CTAs: CTA g takes bricks [parts[g], parts[g+1]) (device, nparts + 1)
     int64_t *parts = nullptr;
     int nparts = 0;
+    // host copy of the brick list's estimated cost prefix (cost_prefix[i] =
+    // cost of bricks [0, i)) and item starts, for cost-balanced shards; the
+    // per-CTA split of each shard's range is built on first use
+    std::vector<double> cost_prefix;
+    std::vector<BrickDesc> hbricks;
+    std::map<std::pair<int64_t, int64_t>, std::pair<int64_t *, int>> shard_parts;
     // tensor-core path work memory
     uint16_t *kbank = nullptr, *jbank = nullptr;
     unsigned int *dmax = nullptr;
@@ -178,11 +185,8 @@ void dfree(esmf_fock *h, T **p, size_t count) {
 // per brick plus 0.84K per flushed 16 x 64 block.
 constexpr double kCostBrick = 1900.0, kCostView = 100.0, kCostBlock = 840.0;
 
-std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
+std::vector<double> cost_prefix(const std::vector<BrickDesc> &kept) {
     const int64_t n = (int64_t)kept.size();
-    if (G > n) G = (int)n;
-    std::vector<int64_t> parts;
-    if (G < 1) return parts;
     std::vector<double> pre(n + 1, 0.0);
     unsigned t3 = 0, t4 = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -198,6 +202,15 @@ std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
         const int views = 2 + (pq ? 1 : 0) + (rs ? 1 : 0) + (pq && rs ? 1 : 0);
         pre[i + 1] = pre[i] + kCostBrick + kCostView * views + kCostBlock * blocks;
     }
+    return pre;
+}
+
+std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
+    const int64_t n = (int64_t)kept.size();
+    if (G > n) G = (int)n;
+    std::vector<int64_t> parts;
+    if (G < 1) return parts;
+    const std::vector<double> pre = cost_prefix(kept);
     parts.resize(G + 1);
     parts[0] = 0;
     int64_t j = 0;
@@ -218,6 +231,7 @@ void release(esmf_fock *h) {
     if (h->S != h->Q) cudaFree(h->S);
     cudaFree(h->Q);
     cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts);
+    for (auto &sp : h->shard_parts) cudaFree(sp.second.first);
     cudaFree(h->ptab); cudaFree(h->pslot); cudaFree(h->pblocks);
     cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
     if (h->err_host) cudaFreeHost(h->err_host);
@@ -625,6 +639,8 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
     if (!ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count"))
         return fail(ESMF_ERR_CUDA);
     const std::vector<int64_t> parts = balance_parts(kept, h->num_sms);
+    h->cost_prefix = cost_prefix(kept);
+    h->hbricks = kept;
     h->nbricks = (int64_t)kept.size();
     h->n_kept_unique = unique;
     h->n_stored = 0;
@@ -952,7 +968,22 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
             L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev;
             L.ev_start = e0; L.ev_stop = e1;
             L.chunk = chunk ? chunk : 16;
-            if (b0 == 0 && b1 == h->nbricks && h->parts) { L.part = h->parts; L.nparts = h->nparts; }
+            if (b0 == 0 && b1 == h->nbricks && h->parts) {
+                L.part = h->parts; L.nparts = h->nparts;
+            } else if (b1 - b0 >= 1 && (int64_t)h->hbricks.size() == h->nbricks) {
+                // a shard: its own cost-balanced split over the CTAs, built once
+                auto key = std::make_pair(b0, b1);
+                auto it = h->shard_parts.find(key);
+                if (it == h->shard_parts.end()) {
+                    std::vector<BrickDesc> sub(h->hbricks.begin() + b0, h->hbricks.begin() + b1);
+                    const std::vector<int64_t> sp = balance_parts(sub, h->num_sms);
+                    int64_t *dp = nullptr;
+                    RET(dalloc(h, &dp, sp.size()));
+                    CKR(cudaMemcpy(dp, sp.data(), sizeof(int64_t) * sp.size(), cudaMemcpyHostToDevice));
+                    it = h->shard_parts.emplace(key, std::make_pair(dp, (int)sp.size() - 1)).first;
+                }
+                L.part = it->second.first; L.nparts = it->second.second;
+            }
             RET(launch_jk_umma(L, s));
             return launch_finalize_blocked(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s);
         }
@@ -1129,7 +1160,20 @@ int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const d
         return ESMF_ERR_INVALID_ARG;
     }
     if (h->mode == ESMF_MODE_DF) { set_error("density-fitted handles are not sharded"); return ESMF_ERR_UNSUPPORTED; }
-    const int64_t b0 = h->nbricks * shard / nshards, b1 = h->nbricks * (shard + 1) / nshards;
+    // shard s takes bricks [cut(s), cut(s + 1)): equal shares of the estimated
+    // cost (the tensor-kernel cost model of the per-CTA split), each cut moved
+    // forward to the next item start so that no item is divided between shards
+    auto cut = [&](int k) -> int64_t {
+        const int64_t n = h->nbricks;
+        if (k <= 0) return 0;
+        if (k >= nshards || (int64_t)h->cost_prefix.size() != n + 1) return k >= nshards ? n : n * k / nshards;
+        const double target = h->cost_prefix[n] * k / nshards;
+        int64_t j = std::lower_bound(h->cost_prefix.begin(), h->cost_prefix.end(), target) - h->cost_prefix.begin();
+        if (j > n) j = n;
+        while (j < n && !(h->hbricks[j].pad & BRICK_ITEM_FIRST)) ++j;
+        return j;
+    };
+    const int64_t b0 = cut(shard), b1 = std::max(b0, cut(shard + 1));
     return build_range(h, b0, b1, m, D, J, K, F, traces, stream);
 }
 

@@ -21,10 +21,11 @@ def molecules():
     return [W.small_random(n, 1, 40 + i, tol=1e-10, edge=4.0 + n / 5) for i, n in enumerate((24, 37, 52))]
 
 
-@pytest.mark.parametrize("prec,graphs,batch,budget,inflight", [
-    ("fp16x2", True, False, 1 << 34, 4), ("fp64", False, False, 1 << 34, 4), ("fp16x2", True, False, 0, 1),
-    ("fp16x2", False, True, 1 << 34, 8), ("fp16x2", True, True, 0, 3)])
-def test_mixed_requests_equal_standalone(esmf, prec, graphs, batch, budget, inflight):
+@pytest.mark.parametrize("prec,graphs,batch,budget,inflight,largest", [
+    ("fp16x2", True, False, 1 << 34, 4, False), ("fp64", False, False, 1 << 34, 4, False),
+    ("fp16x2", True, False, 0, 1, False), ("fp16x2", False, True, 1 << 34, 8, False),
+    ("fp16x2", True, True, 0, 3, False), ("fp16x2", True, True, 0, 1, True)])
+def test_mixed_requests_equal_standalone(esmf, prec, graphs, batch, budget, inflight, largest):
     import torch
     from paper_2002_00322_gb300.server import Server
     mols = molecules()
@@ -44,7 +45,8 @@ def test_mixed_requests_equal_standalone(esmf, prec, graphs, batch, budget, infl
         m = int(rng.integers(1, 20))
         D = rng.standard_normal((m, mols[i].basis.n, mols[i].basis.n))
         reqs.append((i, D))
-    with Server(budget, max_inflight=inflight, precision=prec, use_graphs=graphs, batch=batch) as srv:
+    with Server(budget, max_inflight=inflight, precision=prec, use_graphs=graphs, batch=batch,
+                evict_largest=largest) as srv:
         ids = [srv.register(w.basis, w.tol) for w in mols]
         tickets = [srv.submit(ids[i], D) for i, D in reqs]
         outs = [srv.wait(t, 600000) for t in tickets]

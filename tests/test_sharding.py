@@ -58,10 +58,14 @@ def test_sharded_allreduce_on_cpu_ranks():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp16x2", 1e-6)])
-def test_sequential_shards_sum_to_full_build(esmf, prec, tol):
+@pytest.mark.parametrize("prec,tol,case", [("fp64", 1e-12, "small"), ("fp16x2", 1e-6, "small"),
+                                           ("fp16x2", 1e-6, "stored_n200_m16")])
+def test_sequential_shards_sum_to_full_build(esmf, prec, tol, case):
+    """Shards are cut at equal estimated cost on item boundaries, and on the
+    tensor-core path each shard has its own cost-balanced CTA split: the
+    shards still sum to the whole build."""
     import torch
-    w = W.small_random(45, 4, 9, tol=1e-10, edge=12.0)
+    w = W.small_random(45, 4, 9, tol=1e-10, edge=12.0) if case == "small" else W.stored()
     D = torch.from_numpy(w.D).cuda()
     with esmf.FockBuilder(w.basis, w.tol, "stored", prec) as fb:
         J, K, F, t = fb.build(D, want_F=True)
