@@ -114,8 +114,9 @@ def ncu_traffic(kernel, precision):
 
 
 # ------------------------------------------------------------------ ours
-DTYPES = {"fp64": "f64", "fp32": "f32", "fp16x2": "f16x2+f32acc", "bf16x2": "bf16x2+f32acc"}
-ELEM_BYTES = {"fp64": 8, "fp32": 4, "fp16x2": 4, "bf16x2": 4}
+DTYPES = {"fp64": "f64", "fp32": "f32", "fp16x2": "f16x2+f32acc", "bf16x2": "bf16x2+f32acc",
+          "f32x2": "f32x2 (double-FP32 hi+lo, error-free products)"}
+ELEM_BYTES = {"fp64": 8, "fp32": 4, "fp16x2": 4, "bf16x2": 4, "f32x2": 8}
 
 
 def measured_alu_peaks(local):
@@ -132,6 +133,15 @@ def contraction_roofline(prec, st, m, n, kern_s, alu_peaks):
     density); split 16-bit stores: HBM, counting kept quartets x 4 B + D in +
     J, K out."""
     kname = "k_jk_umma" if prec in ("fp16x2", "bf16x2") else "k_jk_cuda"
+    if prec == "f32x2":
+        # each double-FP32 product-add is 12 FP32 instructions (1 mul, 3 FMA, 8 add/sub)
+        flops = st["n_quartets_kept"] * 20 * m
+        ach = flops / kern_s / 1e12
+        pk = round(alu_peaks["fp32"] * 2 / 12 / 2, 3)     # FMA rate / 12 instructions, 2 flops per product-add
+        return {"bound": "alu", "achieved": round(ach, 3), "peak": pk, "unit": "TFLOP/s",
+                "frac": round(ach / pk, 4), "traffic": None,
+                "peak_source": "derived: measured FP32 FMA rate / 12 FP32 instructions per double-FP32 product-add",
+                "kernel": kname, "kernel_ms": round(kern_s * 1e3, 4), "algorithmic_flops": flops}
     if prec in ("fp64", "fp32"):
         flops = st["n_quartets_kept"] * 20 * m
         ach = flops / kern_s / 1e12
@@ -451,7 +461,7 @@ def run_ours(args):
         # 64-density split build, the integral-direct ribbon, batched uneven
         # molecules and the serving stream, each with its own roofline
         subs = {}
-        for prec in ("fp64", "fp32", "fp16x2"):
+        for prec in ("fp64", "f32x2", "fp32", "fp16x2"):
             if prec != args.precision:
                 subs[f"stored_n200_m16_{prec}"] = sub_stored(fock, W, dev, stream, prec, alu_peaks)
         subs["precision_n400_m64_fp16x2"] = sub_precision(fock, W, dev, stream)
@@ -877,7 +887,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16x2", "bf16x2"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "fp16x2", "bf16x2", "f32x2"],
                     help="store precision of the headline build (default FP64, the paper's arithmetic)")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the other configurations (sub-records under 'configs')")

@@ -57,6 +57,11 @@ extern "C" {
 #define ESMF_PREC_FP16X2  2   /* integrals as scaled FP16 hi+lo pairs, tensor */
                               /* cores with FP32 accumulation (stored only)   */
 #define ESMF_PREC_BF16X2  3   /* as FP16X2 with BF16 halves (ablation)        */
+#define ESMF_PREC_F32X2   4   /* FP64 integrals contracted in double-FP32     */
+                              /* (hi+lo) arithmetic on CUDA cores: error-free */
+                              /* products (FMA) and compensated sums (TwoSum),*/
+                              /* about 2^-44 relative, at FP32-pipe rates;    */
+                              /* stored only                                   */
 
 /*
  * Basis of N contracted s-type Gaussians.  All pointers are HOST memory,

@@ -335,6 +335,7 @@ int launch_brick_generate_l(const DevBasis &b, const double *Q, double tol, cons
     const int grid = grid_a(nbricks, 1, 152 * 8);
     switch (precision) {
         case ESMF_PREC_FP64:
+        case ESMF_PREC_F32X2:     // FP64 values in the store
             k_brick_generate_l<0><<<grid, 256, 0, s>>>(b, Q, tol, bricks, nbricks, offsets, store, vscale);
             break;
         case ESMF_PREC_FP32:

@@ -252,6 +252,7 @@ int elem_bytes(int prec) {
     switch (prec) {
         case ESMF_PREC_FP64: return 8;
         case ESMF_PREC_FP32: return 4;
+        case ESMF_PREC_F32X2: return 8;     // FP64 values, split into FP32 hi + lo on chip
         default: return 4;   // hi+lo 16-bit pair
     }
 }
@@ -266,7 +267,7 @@ bool is_device_ptr(const void *p) {
 }
 
 int ensure_work(esmf_fock *h, int m) {
-    if (h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2 && !h->kbank) {
+    if (h->mode == ESMF_MODE_STORED && is_split16(h->prec) && !h->kbank) {
         RET(dalloc(h, (unsigned char **)&h->kbank, umma_kbank_bytes(h->nb)));
         RET(dalloc(h, (unsigned char **)&h->jbank, umma_jbank_bytes(h->nb)));
         RET(dalloc(h, &h->dmax, 1));
@@ -430,13 +431,13 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
     if (!basis) { set_error("basis missing or empty"); return ESMF_ERR_INVALID_ARG; }
     if (!(tol >= 0.0) || !is_finite(tol)) { set_error("schwarz_tol must be finite and >= 0"); return ESMF_ERR_INVALID_ARG; }
     if (mode < ESMF_MODE_STORED || mode > ESMF_MODE_AUTO) { set_error("bad mode %d", mode); return ESMF_ERR_INVALID_ARG; }
-    if (precision < ESMF_PREC_FP64 || precision > ESMF_PREC_BF16X2) { set_error("bad precision %d", precision); return ESMF_ERR_INVALID_ARG; }
+    if (precision < ESMF_PREC_FP64 || precision > ESMF_PREC_F32X2) { set_error("bad precision %d", precision); return ESMF_ERR_INVALID_ARG; }
     if (budget_bytes < 0) { set_error("budget_bytes < 0"); return ESMF_ERR_INVALID_ARG; }
     const int n = basis->n_basis;
     int64_t nprim_tot = 0;
     RET(check_basis(basis, &nprim_tot));
     if (mode == ESMF_MODE_DIRECT && precision >= ESMF_PREC_FP16X2) {
-        set_error("split 16-bit precisions need stored integrals");
+        set_error("split 16-bit and double-FP32 precisions need stored integrals");
         return ESMF_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -567,7 +568,7 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
     std::vector<int64_t> offs;
     const int eb = elem_bytes(precision);
     const int align_elems = 16 / eb;     // every brick's record starts on 16 bytes
-    const bool split16 = precision >= ESMF_PREC_FP16X2;
+    const bool split16 = is_split16(precision);
     const int head = MASK_BYTES / eb;            // keep mask ahead of the values
     int64_t unique = 0;
     std::vector<int64_t> order;
@@ -656,7 +657,8 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
                       "builds evaluate s functions only", (long long)h->store_bytes);
             return fail(ESMF_ERR_UNSUPPORTED);
         }
-        if (use_mode == ESMF_MODE_DIRECT && precision >= ESMF_PREC_FP16X2) h->prec = ESMF_PREC_FP32;
+        if (use_mode == ESMF_MODE_DIRECT && is_split16(precision)) h->prec = ESMF_PREC_FP32;
+        if (use_mode == ESMF_MODE_DIRECT && precision == ESMF_PREC_F32X2) h->prec = ESMF_PREC_FP64;
     } else if (mode == ESMF_MODE_STORED && budget_bytes > 0 && h->device_bytes + h->store_bytes > budget_bytes) {
         set_error("stored integrals need %lld bytes, budget %lld", (long long)h->store_bytes, (long long)budget_bytes);
         return fail(ESMF_ERR_UNSUPPORTED);
@@ -771,7 +773,7 @@ int esmf_fock_create_df(const esmf_basis_t *basis, const esmf_aux_t *aux, int pr
     }
     if (precision != ESMF_PREC_FP64 && precision != ESMF_PREC_FP32) {
         set_error("density fitting runs in FP64 or FP32");
-        return precision >= ESMF_PREC_FP16X2 && precision <= ESMF_PREC_BF16X2 ? ESMF_ERR_UNSUPPORTED : ESMF_ERR_INVALID_ARG;
+        return precision >= ESMF_PREC_FP16X2 && precision <= ESMF_PREC_F32X2 ? ESMF_ERR_UNSUPPORTED : ESMF_ERR_INVALID_ARG;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -953,7 +955,7 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
             for (auto &t : h->tuned)
                 if (t.first == m) chunk = t.second;
         a.mc = chunk;
-        const bool split16 = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
+        const bool split16 = h->mode == ESMF_MODE_STORED && is_split16(h->prec);
         if (h->tol_d > 0.0) {
             // density-weighted screening runs on the CUDA-core kernels
             RET(launch_density_weight(h->dev(), m, D, h->dw, h->dwb, s));
@@ -1022,7 +1024,7 @@ int esmf_fock_build_batch(int count, esmf_fock_t *const *hs, const int *ms, cons
         if (h->device != dev) { set_error("batch: handles on different devices"); return ESMF_ERR_INVALID_ARG; }
         if (ms[i] < 1 || ms[i] > ESMF_MAX_DENSITIES) { set_error("batch: m[%d] = %d", i, ms[i]); return ESMF_ERR_INVALID_ARG; }
         if (!Ds[i] || !Js[i] || !Ks[i]) { set_error("batch: D, J, K of entry %d are required", i); return ESMF_ERR_INVALID_ARG; }
-        if (!(h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2) || h->path == ESMF_PATH_CUDA_CORE ||
+        if (!(h->mode == ESMF_MODE_STORED && is_split16(h->prec)) || h->path == ESMF_PATH_CUDA_CORE ||
             h->tol_d > 0.0) {
             set_error("batch: handle %d is not on the tensor-core path (stored FP16X2/BF16X2, no density "
                       "screening)", i);
@@ -1245,10 +1247,10 @@ int esmf_fock_autotune(esmf_fock_t *h, int m, const double *D, double *J, double
     if (h->mode == ESMF_MODE_DF) { set_error("density-fitted handles have nothing to tune"); return ESMF_ERR_UNSUPPORTED; }
     DeviceGuard g(h->device);
     if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
-    const bool tensor = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2 && h->path != ESMF_PATH_CUDA_CORE;
+    const bool tensor = h->mode == ESMF_MODE_STORED && is_split16(h->prec) && h->path != ESMF_PATH_CUDA_CORE;
     std::vector<int> cand;
     if (tensor) { cand.push_back(16); if (m > 8) cand.push_back(8); }
-    else if (h->prec == ESMF_PREC_FP64) { cand.push_back(8); cand.push_back(4); }
+    else if (h->prec == ESMF_PREC_FP64 || h->prec == ESMF_PREC_F32X2) { cand.push_back(8); cand.push_back(4); }
     else { cand.push_back(16); cand.push_back(8); cand.push_back(4); }
     if (reps < 1) reps = 3;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1382,7 +1384,7 @@ int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, in
             if (t.first == m) chunk = t.second;
     a->mc = chunk;
     *device = h->device;
-    *split = h->mode == ESMF_MODE_STORED && h->prec >= ESMF_PREC_FP16X2;
+    *split = h->mode == ESMF_MODE_STORED && is_split16(h->prec);
     return ESMF_OK;
 }
 

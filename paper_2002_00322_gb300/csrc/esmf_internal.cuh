@@ -17,6 +17,9 @@ namespace esmf {
 // (p q | r s) with p in P, q in Q, r in R, s in S at local index
 // ((p*8 + q)*8 + r)*8 + s, of which only the Schwarz-kept ones are stored
 // (packed, in local-index order).
+// Split 16-bit store precisions (FP16X2, BF16X2): the tensor-core path.
+inline bool is_split16(int prec) { return prec == ESMF_PREC_FP16X2 || prec == ESMF_PREC_BF16X2; }
+
 constexpr int BLK = 8;
 constexpr int BRICK = BLK * BLK * BLK * BLK;   // 4096
 constexpr int MAXP = ESMF_MAX_PRIM;

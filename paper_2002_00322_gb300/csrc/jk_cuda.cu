@@ -48,6 +48,37 @@ __constant__ int c_slot[10][4] = {{0, 2, 1, 3}, {1, 2, 0, 3}, {0, 3, 1, 2}, {1, 
                                   {2, 0, 3, 1}, {3, 0, 2, 1}, {2, 1, 3, 0}, {3, 1, 2, 0},
                                   {0, 1, 2, 3}, {2, 3, 0, 1}};
 
+// Double-FP32 arithmetic (ESMF_PREC_F32X2): a value is an unevaluated sum
+// hi + lo of two floats (48 significand bits).  Products are formed without
+// error in their leading part (p = fl(a.hi b.hi), e = fma(a.hi, b.hi, -p),
+// the error-free product of Ogita, Rump and Oishi 2005) plus the two cross
+// terms, and added to the running sum with Knuth's TwoSum, the rounding error
+// of every addition kept in lo: about 2^-44 relative over a 64-term dot
+// product, at the FP32 pipe's rate (12 FP32 operations per product-add).
+struct f32x2 {
+    float hi, lo;
+    f32x2() = default;
+    __device__ __forceinline__ f32x2(double v) {
+        hi = __double2float_rn(v);
+        lo = __double2float_rn(v - (double)hi);
+    }
+    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ void macc(float &acc, float v, float d) { acc = fmaf(v, d, acc); }
+__device__ __forceinline__ void macc(double &acc, double v, double d) { acc = fma(v, d, acc); }
+__device__ __forceinline__ void macc(f32x2 &acc, const f32x2 &a, const f32x2 &b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+
 __device__ __forceinline__ bool kept_e(const double *qb, const double *qk, int e, double tol, int n,
                                        int P, int Q, int R, int S) {
     const int p = e >> 9, q = (e >> 6) & 7, r = (e >> 3) & 7, s = e & 7;
@@ -129,7 +160,8 @@ constexpr int jk_ctas_per_sm() {
     return k < 1 ? 1 : (k > 4 ? 4 : k);
 }
 
-// SRC: 0 fp64 store, 1 fp32 store, 2 fp16 hi+lo, 3 bf16 hi+lo, 4 direct (evaluated in TA)
+// SRC: 0 fp64 store, 1 fp32 store, 2 fp16 hi+lo, 3 bf16 hi+lo, 4 direct (evaluated in TA),
+// 5 fp64 store contracted in double-FP32 (TA = f32x2)
 template <typename TA, int MC, int SRC>
 __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cuda(JKArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -209,7 +241,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
         {
             const int e0 = threadIdx.x * 16;
             unsigned mask = 0, dmask = 0xffffu;
-            constexpr int EB = SRC == 0 ? 8 : 4;   // bytes per store element
+            constexpr int EB = (SRC == 0 || SRC == 5) ? 8 : 4;   // bytes per store element
             if (dens) {
                 // element-level rule: Q_pq Q_rs times the largest weight of the
                 // quartet's six index pairs must reach tol_d
@@ -263,7 +295,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                             sm.V[tile_swizzle(e0 + j)] = TA(0);
                             continue;
                         }
-                        if (SRC == 0) v = (TA)reinterpret_cast<const double *>(a.store)[i];
+                        if (SRC == 0 || SRC == 5) v = (TA)reinterpret_cast<const double *>(a.store)[i];
                         else if (SRC == 1) v = (TA)reinterpret_cast<const float *>(a.store)[i];
                         else {
                             const uint32_t u = reinterpret_cast<const uint32_t *>(a.store)[i];
@@ -328,7 +360,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                         const TA v = sm.V[bx ^ ((y & 1) ? t1 : 0) ^ ((y & 2) ? t2 : 0) ^ ((y & 4) ? t4 : 0)];
                         const TA *dp = sm.Ds[slot][x * 8 + y];
 #pragma unroll
-                        for (int dd = 0; dd < MC; ++dd) acc[dd] += v * dp[dd];
+                        for (int dd = 0; dd < MC; ++dd) macc(acc[dd], v, dp[dd]);
                     }
                 }
                 double *out = slot >= 8 ? a.Jacc : a.Kacc;
@@ -367,7 +399,7 @@ static int jk_launch(const JKArgs &a, cudaStream_t s) {
 // 2.22 s at 16).
 template <typename TA, int SRC>
 static int jk_launch_mc(const JKArgs &a, cudaStream_t s) {
-    const int mc = a.mc ? a.mc : (SRC == 4 ? 4 : (SRC <= 1 ? 8 : 16));
+    const int mc = a.mc ? a.mc : (SRC == 4 ? 4 : ((SRC <= 1 || SRC == 5) ? 8 : 16));
     if (sizeof(TA) == 8) {
         if (mc == 4) return jk_launch<TA, 4, SRC>(a, s);
         return jk_launch<TA, 8, SRC>(a, s);
@@ -389,6 +421,7 @@ int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
     switch (a.precision) {
         case ESMF_PREC_FP64: return jk_launch_mc<double, 0>(a, s);
         case ESMF_PREC_FP32: return jk_launch_mc<float, 1>(a, s);
+        case ESMF_PREC_F32X2: return jk_launch_mc<f32x2, 5>(a, s);
         default: break;
     }
     set_error("launch_jk_cuda: precision %d needs the split-precision path", a.precision);

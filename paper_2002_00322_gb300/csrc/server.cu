@@ -294,7 +294,7 @@ void fail_slot(esmf_server *s, int slot_idx, int rc) {
 
 bool on_tensor_path(esmf_fock_t *h) {
     esmf_stats_t st;
-    return esmf_fock_stats(h, &st) == ESMF_OK && st.mode == ESMF_MODE_STORED && st.precision >= ESMF_PREC_FP16X2;
+    return esmf_fock_stats(h, &st) == ESMF_OK && st.mode == ESMF_MODE_STORED && is_split16(st.precision);
 }
 
 // Most batched-tick compositions kept as instantiated graphs; beyond it the
@@ -504,7 +504,7 @@ extern "C" {
 int esmf_server_create(int device, int64_t budget_bytes, int max_inflight, int precision, int flags,
                        esmf_server_t **out) {
     if (!out || budget_bytes <= 0 || max_inflight < 1 || max_inflight > 64 || precision < ESMF_PREC_FP64 ||
-        precision > ESMF_PREC_BF16X2 ||
+        precision > ESMF_PREC_F32X2 ||
         (flags & ~(ESMF_SERVER_GRAPHS | ESMF_SERVER_BATCH | ESMF_SERVER_EVICT_LARGEST)) != 0) {
         set_error("bad server arguments");
         return ESMF_ERR_INVALID_ARG;

@@ -423,6 +423,7 @@ int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const 
                           float vscale, cudaStream_t s) {
     switch (precision) {
         case ESMF_PREC_FP64: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
+        case ESMF_PREC_F32X2: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
         case ESMF_PREC_FP32: return gen_launch<float, 1>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
         case ESMF_PREC_FP16X2: return gen_launch<float, 2>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
         case ESMF_PREC_BF16X2: return gen_launch<float, 3>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);

@@ -23,7 +23,7 @@ ESMF_ERR_TIMEOUT = -4
 ESMF_ERR_UNSUPPORTED = -5
 
 MODES = {"stored": 0, "direct": 1, "auto": 2, "df": 3}
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp16x2": 2, "bf16x2": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16x2": 2, "bf16x2": 3, "f32x2": 4}
 MAX_PRIM = 4
 
 # every symbol include/esmf_fock.h declares

@@ -11,7 +11,7 @@ results (tests/golden/make_golden.py writes them from oracle/ alone).
 
 Metric: relative Frobenius error of each J_k and K_k (for the row sets: of
 the selected rows, relative to the rows' reference norm), at the tolerances
-of the arithmetic: FP64 1e-10, FP32 and split FP16 2e-6, BF16 hi+lo 3e-5.
+of the arithmetic: FP64 and double-FP32 1e-10, FP32 and split FP16 2e-6, BF16 hi+lo 3e-5.
 """
 import os
 
@@ -23,7 +23,7 @@ from paper_2002_00322_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
-TOL = {"fp64": 1e-10, "fp32": 2e-6, "fp16x2": 2e-6, "bf16x2": 3e-5}
+TOL = {"fp64": 1e-10, "f32x2": 1e-10, "fp32": 2e-6, "fp16x2": 2e-6, "bf16x2": 3e-5}
 
 
 def fingerprint(w):
@@ -72,9 +72,9 @@ def c2():
 
 
 @pytest.mark.parametrize("mode,prec,path", [
-    ("stored", "fp64", "auto"), ("stored", "fp32", "auto"), ("stored", "fp16x2", "auto"),
-    ("stored", "bf16x2", "auto"), ("stored", "fp16x2", "cuda_core"), ("direct", "fp32", "auto"),
-    ("direct", "fp64", "auto")])
+    ("stored", "fp64", "auto"), ("stored", "f32x2", "auto"), ("stored", "fp32", "auto"),
+    ("stored", "fp16x2", "auto"), ("stored", "bf16x2", "auto"), ("stored", "fp16x2", "cuda_core"),
+    ("direct", "fp32", "auto"), ("direct", "fp64", "auto")])
 def test_stored_n200_m16_whole_matrices(esmf, c2, mode, prec, path):
     w, Jr, Kr, tr, n_kept = c2
     J, K, F, t, st = build(esmf, w, mode, prec, path)
@@ -108,7 +108,7 @@ def rows_check(esmf, w, g, mode, prec, path="auto"):
 
 @pytest.mark.parametrize("mode,prec,path", [
     ("stored", "fp16x2", "auto"), ("stored", "bf16x2", "auto"), ("stored", "fp32", "auto"),
-    ("stored", "fp64", "auto"), ("direct", "fp32", "auto")])
+    ("stored", "fp64", "auto"), ("stored", "f32x2", "auto"), ("direct", "fp32", "auto")])
 def test_precision_n400_m64_rows(esmf, mode, prec, path):
     w = W.precision()
     g = load("c4_precision_n400_m64.npz", w)
