@@ -410,10 +410,6 @@ int esmf_fock_create_cart(const esmf_basis_t *basis, const int32_t *cart, double
         any_p |= cart[i] != 0;
     }
     if (!any_p) cart = nullptr;          // all s: the s-type path
-    else if (mode == ESMF_MODE_DIRECT) {
-        set_error("p functions need stored integrals (integral-direct builds evaluate s functions only)");
-        return ESMF_ERR_UNSUPPORTED;
-    }
     return create_impl(basis, cart, tol, ESMF_SCREEN_SCHWARZ, mode, precision, device, budget_bytes, out);
 }
 
@@ -652,11 +648,6 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
     if (mode == ESMF_MODE_AUTO) {
         use_mode = (budget_bytes == 0 || h->device_bytes + h->store_bytes <= budget_bytes) ? ESMF_MODE_STORED
                                                                                           : ESMF_MODE_DIRECT;
-        if (use_mode == ESMF_MODE_DIRECT && h->cart) {
-            set_error("the store of a basis with p functions (%lld bytes) exceeds the budget, and integral-direct "
-                      "builds evaluate s functions only", (long long)h->store_bytes);
-            return fail(ESMF_ERR_UNSUPPORTED);
-        }
         if (use_mode == ESMF_MODE_DIRECT && is_split16(precision)) h->prec = ESMF_PREC_FP32;
         if (use_mode == ESMF_MODE_DIRECT && precision == ESMF_PREC_F32X2) h->prec = ESMF_PREC_FP64;
     } else if (mode == ESMF_MODE_STORED && budget_bytes > 0 && h->device_bytes + h->store_bytes > budget_bytes) {

@@ -23,6 +23,7 @@
 
 #include <type_traits>
 
+#include "angular.cuh"
 #include "esmf_internal.cuh"
 #include "integrals.cuh"
 
@@ -161,7 +162,8 @@ constexpr int jk_ctas_per_sm() {
 }
 
 // SRC: 0 fp64 store, 1 fp32 store, 2 fp16 hi+lo, 3 bf16 hi+lo, 4 direct (evaluated in TA),
-// 5 fp64 store contracted in double-FP32 (TA = f32x2)
+// 5 fp64 store contracted in double-FP32 (TA = f32x2), 6 direct with p functions
+// (Obara-Saika integrals evaluated in FP64, converted to TA)
 template <typename TA, int MC, int SRC>
 __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cuda(JKArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
             sm.nslots = ns;
         }
         const bool dens = a.dw != nullptr;
-        if ((SRC == 4 || dens) && threadIdx.x < 64) {
+        if ((SRC == 4 || SRC == 6 || dens) && threadIdx.x < 64) {
             const int t = threadIdx.x;
             sm.qb[t] = a.Q[(int64_t)(d.P * 8 + (t >> 3)) * np + d.Q * 8 + (t & 7)];
             sm.qk[t] = a.Q[(int64_t)(d.R * 8 + (t >> 3)) * np + d.S * 8 + (t & 7)];
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                     if (sm.qb[p * 8 + q] * sm.qk[r * 8 + s_] * wt >= a.tol_d) dmask |= 1u << j;
                 }
             }
-            if constexpr (SRC == 4) {
+            if constexpr (SRC == 4 || SRC == 6) {
                 for (int j = 0; j < 16; ++j)
                     if (kept_e(sm.qb, sm.qk, e0 + j, a.tol, n, d.P, d.Q, d.R, d.S)) mask |= 1u << j;
                 mask &= dmask;
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                 const unsigned char *mk = reinterpret_cast<const unsigned char *>(a.store) + a.offsets[bi] * EB;
                 mask = (unsigned)mk[2 * threadIdx.x] | ((unsigned)mk[2 * threadIdx.x + 1] << 8);
             }
-            if constexpr (SRC == 4) {
+            if constexpr (SRC == 4 || SRC == 6) {
                 // kept local indices listed in ascending order (in the density
                 // tiles' space, unused until the first chunk's barrier), then
                 // evaluated round-robin: a warp takes 32 consecutive kept
@@ -279,9 +281,19 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                     else sm.V[tile_swizzle(e)] = TA(0);
                 }
                 __syncthreads();
-                for (int i = threadIdx.x; i < total; i += blockDim.x) {
-                    const int e = klist[i];
-                    sm.V[tile_swizzle(e)] = contracted_eri<TA, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
+                if constexpr (SRC == 6) {
+                    // p functions: the Obara-Saika integral in FP64 from the basis arrays
+                    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                        const int e = klist[i];
+                        sm.V[tile_swizzle(e)] = (TA)angular::contracted_l(
+                            a.b, d.P * 8 + (e >> 9), d.Q * 8 + ((e >> 6) & 7), d.R * 8 + ((e >> 3) & 7),
+                            d.S * 8 + (e & 7));
+                    }
+                } else {
+                    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                        const int e = klist[i];
+                        sm.V[tile_swizzle(e)] = contracted_eri<TA, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
+                    }
                 }
             } else {
                 int pos = scan256(__popc(mask), sm.wsum);
@@ -399,7 +411,7 @@ static int jk_launch(const JKArgs &a, cudaStream_t s) {
 // 2.22 s at 16).
 template <typename TA, int SRC>
 static int jk_launch_mc(const JKArgs &a, cudaStream_t s) {
-    const int mc = a.mc ? a.mc : (SRC == 4 ? 4 : ((SRC <= 1 || SRC == 5) ? 8 : 16));
+    const int mc = a.mc ? a.mc : ((SRC == 4 || SRC == 6) ? 4 : ((SRC <= 1 || SRC == 5) ? 8 : 16));
     if (sizeof(TA) == 8) {
         if (mc == 4) return jk_launch<TA, 4, SRC>(a, s);
         return jk_launch<TA, 8, SRC>(a, s);
@@ -414,6 +426,10 @@ int launch_jk_cuda(const JKArgs &a, cudaStream_t s) {
         if (a.nbricks > 0 && (!a.ptab || !a.pslot)) {
             set_error("launch_jk_cuda: integral-direct build without a pair table");
             return ESMF_ERR_INVALID_ARG;
+        }
+        if (a.b.cart) {
+            if (a.precision == ESMF_PREC_FP64) return jk_launch_mc<double, 6>(a, s);
+            return jk_launch_mc<float, 6>(a, s);
         }
         if (a.precision == ESMF_PREC_FP64) return jk_launch_mc<double, 4>(a, s);
         return jk_launch_mc<float, 4>(a, s);

@@ -1,7 +1,8 @@
 """Bases with Cartesian p functions (esmf_fock_create_cart) on the GPU
 against the oracle's Obara-Saika integrals: the Schwarz table, kept-quartet
 counts and J, K, F, traces of every store precision, including the
-tensor-core path; the entries that evaluate s functions only must refuse."""
+tensor-core path, and integral-direct builds; the entries that take s
+functions only (pair-max rule, density fitting) must refuse."""
 import numpy as np
 import pytest
 
@@ -64,10 +65,22 @@ def test_screened_sp_molecule(esmf, prec):
         assert rel(J[k], Jr[k]) <= TOL[prec] and rel(K[k], Kr[k]) <= TOL[prec], (prec, k, rel(K[k], Kr[k]))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_integral_direct_sp(esmf, sp_tiny, prec):
+    """Integral-direct builds evaluate the p integrals inside every build."""
+    import torch
+    w, o, D, Jr, Kr = sp_tiny
+    with esmf.FockBuilder(w.basis, 0.0, "direct", prec) as fb:
+        J, K, _, _ = fb.build(torch.from_numpy(D).cuda())
+        torch.cuda.synchronize()
+    J, K = J.cpu().numpy(), K.cpu().numpy()
+    for k in range(D.shape[0]):
+        assert rel(J[k], Jr[k]) <= TOL[prec] and rel(K[k], Kr[k]) <= TOL[prec], (prec, k)
+
+
 def test_paths_without_p_integrals_refuse(esmf):
     w = W.sp_random(2, 1, 5)
-    with pytest.raises(esmf.EsmfError) as e:
-        esmf.FockBuilder(w.basis, 1e-10, "direct", "fp32")
-    assert e.value.code == esmf.ESMF_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         esmf.FockBuilder(w.basis, 1e-10, "stored", "fp64", screening="pair_max")
+    with pytest.raises(ValueError):
+        esmf.FockBuilder(w.basis, 0.0, "df", "fp64", aux=W.even_tempered_aux(w.basis))
