@@ -830,9 +830,10 @@ def run_serving(args, quick=False):
            "n_gpus": 1, "higher_is_better": True, "dtype": "f16x2+f32acc", "data": "synthetic",
            "config": {"workload": f"serving_{len(reqs)}req_pool{len(mols)}_n50-{args.serve_nmax}_m4-32",
                       "budget_gb": args.serve_budget_gb, "max_inflight": args.serve_inflight,
-                      "precision": "fp16x2", "graphs": True, "batched_ticks": True}}
+                      "precision": "fp16x2", "graphs": True, "batched_ticks": True,
+                      "eviction": "largest idle first"}}
     with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True, batch=True,
-                device=local) as srv:
+                evict_largest=True, device=local) as srv:
         ids = [srv.register(w.basis, w.tol) for w in mols]
         # closed loop
         t0 = time.perf_counter()

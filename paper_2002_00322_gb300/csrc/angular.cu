@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_brick_generate_l(DevBasis b, const doub
         const int total = wsum[0];
         for (int j = 0; j < 16; ++j)
             if (mask & (1u << j)) klist[pos++] = (unsigned short)(e0 + j);
-        constexpr int EB = PREC == 0 ? 8 : 4;
+        constexpr int EB = (PREC == 0 || PREC == 4) ? 8 : 4;
         const int64_t base = offsets[bi];
         unsigned char *mk = reinterpret_cast<unsigned char *>(store) + base * EB;
         mk[2 * threadIdx.x] = (unsigned char)(mask & 0xffu);
@@ -131,6 +131,9 @@ __global__ void __launch_bounds__(256) k_brick_generate_l(DevBasis b, const doub
                 reinterpret_cast<double *>(store)[vbase + i] = v;
             } else if (PREC == 1) {
                 reinterpret_cast<float *>(store)[vbase + i] = (float)v;
+            } else if (PREC == 4) {
+                const float hi = __double2float_rn(v);
+                reinterpret_cast<float2 *>(store)[vbase + i] = make_float2(hi, __double2float_rn(v - (double)hi));
             } else {
                 const double xs = v * (double)vscale;
                 uint16_t hb, lb;
@@ -170,8 +173,10 @@ int launch_brick_generate_l(const DevBasis &b, const double *Q, double tol, cons
     const int grid = grid_a(nbricks, 1, 152 * 8);
     switch (precision) {
         case ESMF_PREC_FP64:
-        case ESMF_PREC_F32X2:     // FP64 values in the store
             k_brick_generate_l<0><<<grid, 256, 0, s>>>(b, Q, tol, bricks, nbricks, offsets, store, vscale);
+            break;
+        case ESMF_PREC_F32X2:
+            k_brick_generate_l<4><<<grid, 256, 0, s>>>(b, Q, tol, bricks, nbricks, offsets, store, vscale);
             break;
         case ESMF_PREC_FP32:
             k_brick_generate_l<1><<<grid, 256, 0, s>>>(b, Q, tol, bricks, nbricks, offsets, store, vscale);

@@ -91,6 +91,7 @@ struct esmf_fock {
     int64_t n_stored = 0, store_bytes = 0, n_kept_unique = 0;
     // work (device)
     double *Jacc = nullptr, *Kacc = nullptr;
+    void *Dt = nullptr;            // D in the CUDA-core arithmetic type (FP32 / double-FP32), work_m densities
     double *ework = nullptr;       // ESMF energy / gradient work memory
     size_t ework_n = 0;
     int work_m = 0;
@@ -235,7 +236,7 @@ void release(esmf_fock *h) {
     cudaFree(h->ptab); cudaFree(h->pslot); cudaFree(h->pblocks);
     cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
     if (h->err_host) cudaFreeHost(h->err_host);
-    cudaFree(h->Jacc); cudaFree(h->Kacc); cudaFree(h->ework);
+    cudaFree(h->Jacc); cudaFree(h->Kacc); cudaFree(h->ework); cudaFree(h->Dt);
     cudaFree(h->dw); cudaFree(h->dwb);
     cudaFree(h->dfB); cudaFree(h->dfB2); cudaFree(h->dfDt); cudaFree(h->dfJt); cudaFree(h->dfKt);
     cudaFree(h->dfg); cudaFree(h->dfY);
@@ -252,7 +253,7 @@ int elem_bytes(int prec) {
     switch (prec) {
         case ESMF_PREC_FP64: return 8;
         case ESMF_PREC_FP32: return 4;
-        case ESMF_PREC_F32X2: return 8;     // FP64 values, split into FP32 hi + lo on chip
+        case ESMF_PREC_F32X2: return 8;     // FP64 values as FP32 hi + lo pairs
         default: return 4;   // hi+lo 16-bit pair
     }
 }
@@ -278,11 +279,14 @@ int ensure_work(esmf_fock *h, int m) {
     }
     if (m <= h->work_m) return ESMF_OK;
     const size_t cnt = (size_t)m * h->np * h->np;
+    const size_t tb = density_typed_bytes(h->prec);
     dfree(h, &h->Jacc, (size_t)h->work_m * h->np * h->np);
     dfree(h, &h->Kacc, (size_t)h->work_m * h->np * h->np);
+    dfree(h, (unsigned char **)&h->Dt, (size_t)h->work_m * h->n * h->n * tb);
     h->work_m = 0;
     RET(dalloc(h, &h->Jacc, cnt));
     RET(dalloc(h, &h->Kacc, cnt));
+    if (tb) RET(dalloc(h, (unsigned char **)&h->Dt, (size_t)m * h->n * h->n * tb));
     h->work_m = m;
     return ESMF_OK;
 }
@@ -979,6 +983,10 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
             }
             RET(launch_jk_umma(L, s));
             return launch_finalize_blocked(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s);
+        }
+        if (h->Dt) {
+            RET(launch_density_typed(h->prec, (int64_t)m * h->n * h->n, D, h->Dt, s));
+            a.Dt = h->Dt;
         }
         if (e0) CKR(cudaEventRecord(e0, s));
         if (split16) RET(launch_jk_cuda_split(a, s));

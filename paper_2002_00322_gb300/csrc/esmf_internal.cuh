@@ -109,7 +109,13 @@ struct JKArgs {
     // max_k max(|D_k[x][y]|, |D_k[y][x]|), dwb = nb x nb block maxima of dw
     const double *dw = nullptr, *dwb = nullptr;
     double tol_d = 0.0;
+    // D in the contraction's arithmetic type (FP32 or double-FP32), formed once
+    // per build; null: the kernel converts FP64 D as it loads its tiles
+    const void *Dt = nullptr;
 };
+// bytes per element of the typed density copy of a precision (0: none, FP64)
+size_t density_typed_bytes(int precision);
+int launch_density_typed(int precision, int64_t cnt, const double *D, void *Dt, cudaStream_t s);
 int launch_jk_cuda(const JKArgs &a, cudaStream_t s);
 // density weights of one build for density-weighted screening (dwb zeroed here)
 int launch_density_weight(const DevBasis &b, int m, const double *D, double *dw, double *dwb, cudaStream_t s);

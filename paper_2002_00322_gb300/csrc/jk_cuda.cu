@@ -66,6 +66,24 @@ struct f32x2 {
     __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
+__device__ __forceinline__ f32x2 make_f32x2(float hi, float lo) {
+    f32x2 r;
+    r.hi = hi;
+    r.lo = lo;
+    return r;
+}
+
+// sums of two density elements (the symmetrised Coulomb tiles), in the
+// arithmetic type; the double-FP32 sum keeps TwoSum's error in lo
+__device__ __forceinline__ float add_ta(float a, float b) { return a + b; }
+__device__ __forceinline__ double add_ta(double a, double b) { return a + b; }
+__device__ __forceinline__ f32x2 add_ta(const f32x2 &a, const f32x2 &b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return make_f32x2(s, __fadd_rn(__fadd_rn(a.lo, b.lo), err));
+}
+
 __device__ __forceinline__ void macc(float &acc, float v, float d) { acc = fmaf(v, d, acc); }
 __device__ __forceinline__ void macc(double &acc, double v, double d) { acc = fma(v, d, acc); }
 __device__ __forceinline__ void macc(f32x2 &acc, const f32x2 &a, const f32x2 &b) {
@@ -307,7 +325,11 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                             sm.V[tile_swizzle(e0 + j)] = TA(0);
                             continue;
                         }
-                        if (SRC == 0 || SRC == 5) v = (TA)reinterpret_cast<const double *>(a.store)[i];
+                        if (SRC == 0) v = (TA)reinterpret_cast<const double *>(a.store)[i];
+                        else if constexpr (SRC == 5) {
+                            const float2 u = reinterpret_cast<const float2 *>(a.store)[i];
+                            v = make_f32x2(u.x, u.y);
+                        }
                         else if (SRC == 1) v = (TA)reinterpret_cast<const float *>(a.store)[i];
                         else {
                             const uint32_t u = reinterpret_cast<const uint32_t *>(a.store)[i];
@@ -334,18 +356,22 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                 const int x = ij >> 3, y = ij & 7;
                 TA v = TA(0);
                 if (d0 + dd < a.m) {
-                    const double *Dk = a.D + (int64_t)(d0 + dd) * nn;
+                    // the per-build copy of D in the arithmetic type when there is
+                    // one (no conversion on the FP64 pipe here), else D itself
+                    const TA *Dt = reinterpret_cast<const TA *>(a.Dt);
+                    const int64_t kofs = (int64_t)(d0 + dd) * nn;
+                    auto at = [&](int64_t idx) -> TA { return Dt ? Dt[kofs + idx] : (TA)a.D[kofs + idx]; };
                     if (tile < 8) {
                         const int ra = sm.blk[c_tuple[tile][1]] * 8 + x, cb = sm.blk[c_tuple[tile][3]] * 8 + y;
-                        if (ra < n && cb < n) v = (TA)Dk[(int64_t)ra * n + cb];
+                        if (ra < n && cb < n) v = at((int64_t)ra * n + cb);
                     } else {
                         // Dj of the summed blocks (C, E): D[C,E] + [C != E] D[E,C]^T
                         const int C = sm.blk[tile == 8 ? 2 : 0], E = sm.blk[tile == 8 ? 3 : 1];
                         const int ra = C * 8 + x, cb = E * 8 + y;
                         if (ra < n && cb < n) {
-                            double w = Dk[(int64_t)ra * n + cb];
-                            if (C != E) w += Dk[(int64_t)cb * n + ra];
-                            v = (TA)w;
+                            if (C == E) v = at((int64_t)ra * n + cb);
+                            else if (Dt) v = add_ta(Dt[kofs + (int64_t)ra * n + cb], Dt[kofs + (int64_t)cb * n + ra]);
+                            else v = (TA)(a.D[kofs + (int64_t)ra * n + cb] + a.D[kofs + (int64_t)cb * n + ra]);
                         }
                     }
                 }
@@ -450,6 +476,30 @@ int launch_jk_cuda_split(const JKArgs &a, cudaStream_t s) {
     if (a.precision == ESMF_PREC_BF16X2) return jk_launch_mc<float, 3>(a, s);
     set_error("launch_jk_cuda_split: bad precision %d", a.precision);
     return ESMF_ERR_INVALID_ARG;
+}
+
+// ---------------------------------------------------------------- typed densities
+// D (FP64, m x n x n) once per build in the contraction's arithmetic type.
+template <typename T>
+__global__ void k_density_typed(int64_t cnt, const double *D, T *Dt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        Dt[i] = T(D[i]);
+}
+
+size_t density_typed_bytes(int precision) {
+    return precision == ESMF_PREC_F32X2 ? sizeof(f32x2) : (precision == ESMF_PREC_FP64 ? 0 : sizeof(float));
+}
+
+int launch_density_typed(int precision, int64_t cnt, const double *D, void *Dt, cudaStream_t s) {
+    int64_t g = (cnt + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    if (precision == ESMF_PREC_F32X2)
+        k_density_typed<f32x2><<<(int)g, 256, 0, s>>>(cnt, D, reinterpret_cast<f32x2 *>(Dt));
+    else
+        k_density_typed<float><<<(int)g, 256, 0, s>>>(cnt, D, reinterpret_cast<float *>(Dt));
+    CK(cudaGetLastError());
+    return ESMF_OK;
 }
 
 // ---------------------------------------------------------------- density weights

@@ -293,7 +293,8 @@ struct GenSmem {
     unsigned short klist[BRICK];   // local indices of the kept elements, ascending
 };
 
-// precision: 0 FP64 store (T = double), 1 FP32 store, 2 FP16 hi+lo, 3 BF16 hi+lo
+// precision: 0 FP64 store (T = double), 1 FP32 store, 2 FP16 hi+lo, 3 BF16 hi+lo,
+// 4 double-FP32 hi+lo floats (T = double)
 template <typename T, int PREC>
 __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double *Q, double tol,
                                                         const BrickDesc *bricks, int64_t nbricks,
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
         // record: 512-byte keep mask, then the kept values (FP64 / FP32, or
         // (hi | lo << 16) words of the value times the store's power-of-two
         // scale); offsets count store elements of sizeof(element) bytes
-        constexpr int EB = PREC == 0 ? 8 : 4;
+        constexpr int EB = (PREC == 0 || PREC == 4) ? 8 : 4;
         const int64_t base = offsets[bi];
         unsigned char *mk = reinterpret_cast<unsigned char *>(store) + base * EB;
         mk[2 * threadIdx.x] = (unsigned char)(mask & 0xffu);
@@ -346,6 +347,10 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
             const T v = contracted_eri<T, 128, MAXPP>(sm.pairs, e >> 6, sm.pairs, 64 + (e & 63));
             if (PREC == 0 || PREC == 1) {
                 reinterpret_cast<T *>(store)[vbase + i] = v;
+            } else if (PREC == 4) {
+                // double-FP32 store: the FP64 value as hi + lo floats
+                const float hi = __double2float_rn((double)v);
+                reinterpret_cast<float2 *>(store)[vbase + i] = make_float2(hi, __double2float_rn((double)v - (double)hi));
             } else {
                 const double xs = (double)v * (double)vscale;
                 uint16_t hb, lb;
@@ -423,7 +428,7 @@ int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const 
                           float vscale, cudaStream_t s) {
     switch (precision) {
         case ESMF_PREC_FP64: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
-        case ESMF_PREC_F32X2: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
+        case ESMF_PREC_F32X2: return gen_launch<double, 4>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
         case ESMF_PREC_FP32: return gen_launch<float, 1>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
         case ESMF_PREC_FP16X2: return gen_launch<float, 2>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
         case ESMF_PREC_BF16X2: return gen_launch<float, 3>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
