@@ -769,7 +769,10 @@ def serve_against_plain_fp64(args, mols, reqs, dens, budget, local):
         t0 = time.perf_counter()
         k = 0
         for (i, _, _), D in zip(reqs, dens):
-            if k and time.perf_counter() - t0 >= args.serve_fp64_seconds:
+            if args.serve_fp64_requests > 0:
+                if k >= args.serve_fp64_requests:
+                    break
+            elif k and time.perf_counter() - t0 >= args.serve_fp64_seconds:
                 break
             if i not in ids:
                 ids[i] = srv.register(mols[i].basis, mols[i].tol)
@@ -905,6 +908,8 @@ def main():
     ap.add_argument("--serve-nmax", type=int, default=600)
     ap.add_argument("--serve-budget-gb", type=float, default=60.0)
     ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-fp64-requests", type=int, default=0,
+                    help="serve exactly this prefix of the stream in the plain FP64 leg (0: bound by time)")
     ap.add_argument("--serve-fp64-seconds", type=float, default=45.0,
                     help="time bound of the plain FP64 leg of --serving (a prefix of the stream)")
     args = ap.parse_args()
