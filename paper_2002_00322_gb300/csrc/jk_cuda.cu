@@ -66,6 +66,23 @@ struct f32x2 {
     __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
+// FP32 -> FP64 widening by the IEEE-754 formats alone (sign, rebiased exponent,
+// mantissa shifted into place), on the integer pipe instead of GB300's narrow
+// FP64 pipe; exact for every normal float, zero for zero and subnormals
+// (below 1.2e-38, far under every contribution here).
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const uint64_t d = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                       ((uint64_t)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// a brick's partial sum as the FP64 value its accumulator receives
+__device__ __forceinline__ double flush_value(float v) { return widen(v); }
+__device__ __forceinline__ double flush_value(double v) { return v; }
+
 __device__ __forceinline__ f32x2 make_f32x2(float hi, float lo) {
     f32x2 r;
     r.hi = hi;
@@ -83,6 +100,8 @@ __device__ __forceinline__ f32x2 add_ta(const f32x2 &a, const f32x2 &b) {
     const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
     return make_f32x2(s, __fadd_rn(__fadd_rn(a.lo, b.lo), err));
 }
+
+__device__ __forceinline__ double flush_value(const f32x2 &v) { return widen(v.hi) + widen(v.lo); }
 
 __device__ __forceinline__ void macc(float &acc, float v, float d) { acc = fmaf(v, d, acc); }
 __device__ __forceinline__ void macc(double &acc, double v, double d) { acc = fma(v, d, acc); }
@@ -404,7 +423,7 @@ __global__ void __launch_bounds__(256, (jk_ctas_per_sm<TA, MC, SRC>())) k_jk_cud
                 double *out = slot >= 8 ? a.Jacc : a.Kacc;
 #pragma unroll
                 for (int dd = 0; dd < MC; ++dd)
-                    if (d0 + dd < a.m) atomicAdd(out + (int64_t)(d0 + dd) * npnp + (int64_t)orow * np + ocol, (double)acc[dd]);
+                    if (d0 + dd < a.m) atomicAdd(out + (int64_t)(d0 + dd) * npnp + (int64_t)orow * np + ocol, flush_value(acc[dd]));
             }
         }
     }
