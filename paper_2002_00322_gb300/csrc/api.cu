@@ -678,17 +678,11 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
             if (!ck(cudaMemcpyAsync(h->offsets, offs.data(), sizeof(int64_t) * (h->nbricks + 1), cudaMemcpyHostToDevice, cs), "copy offsets"))
                 return fail(ESMF_ERR_CUDA);
             if (!ck(cudaMemsetAsync(h->store, 0, (size_t)h->store_bytes, cs), "clear store")) return fail(ESMF_ERR_CUDA);
-            if (h->cart)
-                rc = launch_brick_generate_l(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec, h->store,
-                                             h->vscale, s);
-            else
-                rc = launch_brick_generate(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec, h->store,
-                                           h->vscale, s);
-            if (rc) return fail(rc);
-        } else {
-            // integral-direct: the primitive pairs of every block pair that a
-            // kept brick uses as bra or ket, formed once here instead of in
-            // every brick of every build
+        }
+        if (use_mode != ESMF_MODE_STORED || !h->cart) {
+            // the primitive pairs of every block pair that a kept brick uses as
+            // bra or ket, formed once here instead of in every brick (of the store
+            // generation, or of every integral-direct build)
             pslot_h.assign((size_t)h->nb * h->nb, -1);
             auto use = [&](int X, int Y) {
                 int &e = pslot_h[(size_t)X * h->nb + Y];
@@ -707,6 +701,21 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
                 !ck(cudaMemcpyAsync(h->pblocks, pblocks_h.data(), sizeof(int) * pblocks_h.size(), cudaMemcpyHostToDevice, cs), "copy pair blocks"))
                 return fail(ESMF_ERR_CUDA);
             if ((rc = launch_pair_table(db, h->pblocks, h->n_ptab, h->prec, h->ptab, s))) return fail(rc);
+        }
+        if (use_mode == ESMF_MODE_STORED) {
+            if (h->cart)
+                rc = launch_brick_generate_l(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec, h->store,
+                                             h->vscale, s);
+            else
+                rc = launch_brick_generate(db, h->S, tol_s, h->bricks, h->nbricks, h->offsets, h->prec, h->store,
+                                           h->vscale, s, h->ptab, h->pslot);
+            if (rc) return fail(rc);
+            // a stored handle needs the pair table only for the generation
+            if (h->ptab && !ck(cudaStreamSynchronize(cs), "store generation")) return fail(ESMF_ERR_CUDA);
+            dfree(h, (unsigned char **)&h->ptab, (size_t)h->n_ptab * pair_table_entry_bytes(h->prec));
+            dfree(h, &h->pslot, pslot_h.size());
+            dfree(h, &h->pblocks, pblocks_h.size());
+            h->n_ptab = 0;
         }
     }
     if (!ck(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming), "event")) return fail(ESMF_ERR_CUDA);

@@ -70,9 +70,11 @@ int launch_pair_rule(const DevBasis &b, const double *Q, double thr, const int2 
                      cudaStream_t s);
 int launch_brick_count(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                        int64_t nbricks, int32_t *counts, cudaStream_t s);
+// ptab / pslot: the create-time primitive-pair table of the block pairs the
+// bricks use (as for integral-direct handles); null: pairs formed per brick
 int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                           int64_t nbricks, const int64_t *offsets, int precision, void *store,
-                          float vscale, cudaStream_t s);
+                          float vscale, cudaStream_t s, const void *ptab = nullptr, const int *pslot = nullptr);
 
 // ---- angular.cu (bases with Cartesian p functions)
 int launch_normalize_l(const DevBasis &b, const double *coefs, double *w, cudaStream_t s);

@@ -299,7 +299,7 @@ template <typename T, int PREC>
 __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double *Q, double tol,
                                                         const BrickDesc *bricks, int64_t nbricks,
                                                         const int64_t *offsets, void *store,
-                                                        float vscale) {
+                                                        float vscale, const void *ptab, const int *pslot) {
     extern __shared__ __align__(16) unsigned char smraw[];
     GenSmem<T> &sm = *reinterpret_cast<GenSmem<T> *>(smraw);
     for (int64_t bi = blockIdx.x; bi < nbricks; bi += gridDim.x) {
@@ -309,10 +309,17 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
         // coordinate differences small)
         const int o = d.P * 8;
         const double ox = b.center[3 * o], oy = b.center[3 * o + 1], oz = b.center[3 * o + 2];
-        fill_pairs<T, MAXPP>(sm.pairs, 0, d.P, d.Q, b.center, b.nprim, b.poff, b.exps, b.w, b.np,
-                             ox, oy, oz);
-        fill_pairs<T, MAXPP>(sm.pairs, 64, d.R, d.S, b.center, b.nprim, b.poff, b.exps, b.w, b.np,
-                             ox, oy, oz);
+        if (ptab) {
+            // primitive pairs of (P,Q) and (R,S) from the create-time table (formed
+            // once per block pair, not once per brick)
+            const PairTable<T, MAXPP> *tab = reinterpret_cast<const PairTable<T, MAXPP> *>(ptab);
+            load_pairs<T, MAXPP>(sm.pairs, tab[pslot[d.P * b.nb + d.Q]], tab[pslot[d.R * b.nb + d.S]], ox, oy, oz);
+        } else {
+            fill_pairs<T, MAXPP>(sm.pairs, 0, d.P, d.Q, b.center, b.nprim, b.poff, b.exps, b.w, b.np,
+                                 ox, oy, oz);
+            fill_pairs<T, MAXPP>(sm.pairs, 64, d.R, d.S, b.center, b.nprim, b.poff, b.exps, b.w, b.np,
+                                 ox, oy, oz);
+        }
         if (threadIdx.x < 64) {
             const int t = threadIdx.x;
             sm.qb[t] = Q[(int64_t)(d.P * 8 + (t >> 3)) * b.np + d.Q * 8 + (t & 7)];
@@ -395,14 +402,17 @@ __global__ void __launch_bounds__(64) k_pair_table(DevBasis b, const int *blocks
     te.npp[t] = cnt;
 }
 
+// FP64 and double-FP32 stores evaluate in FP64 (double tables), the others in FP32
+static bool table_fp64(int precision) { return precision == ESMF_PREC_FP64 || precision == ESMF_PREC_F32X2; }
+
 size_t pair_table_entry_bytes(int precision) {
-    return precision == ESMF_PREC_FP64 ? sizeof(PairTable<double, MAXPP>) : sizeof(PairTable<float, MAXPP>);
+    return table_fp64(precision) ? sizeof(PairTable<double, MAXPP>) : sizeof(PairTable<float, MAXPP>);
 }
 
 int launch_pair_table(const DevBasis &b, const int *blocks, int nentries, int precision, void *tab,
                       cudaStream_t s) {
     if (nentries < 1) return ESMF_OK;
-    if (precision == ESMF_PREC_FP64)
+    if (table_fp64(precision))
         k_pair_table<double><<<nentries, 64, 0, s>>>(b, blocks, nentries, (PairTable<double, MAXPP> *)tab);
     else
         k_pair_table<float><<<nentries, 64, 0, s>>>(b, blocks, nentries, (PairTable<float, MAXPP> *)tab);
@@ -413,25 +423,25 @@ int launch_pair_table(const DevBasis &b, const int *blocks, int nentries, int pr
 template <typename T, int PREC>
 static int gen_launch(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                       int64_t nbricks, const int64_t *offsets, void *store, float vscale,
-                      cudaStream_t s) {
+                      const void *ptab, const int *pslot, cudaStream_t s) {
     const size_t smem = sizeof(GenSmem<T>);
     CK(cudaFuncSetAttribute(k_brick_generate<T, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem));
     k_brick_generate<T, PREC><<<grid_for(nbricks, 1, 152 * 4), 256, smem, s>>>(
-        b, Q, tol, bricks, nbricks, offsets, store, vscale);
+        b, Q, tol, bricks, nbricks, offsets, store, vscale, ptab, pslot);
     CK(cudaGetLastError());
     return ESMF_OK;
 }
 
 int launch_brick_generate(const DevBasis &b, const double *Q, double tol, const BrickDesc *bricks,
                           int64_t nbricks, const int64_t *offsets, int precision, void *store,
-                          float vscale, cudaStream_t s) {
+                          float vscale, cudaStream_t s, const void *ptab, const int *pslot) {
     switch (precision) {
-        case ESMF_PREC_FP64: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
-        case ESMF_PREC_F32X2: return gen_launch<double, 4>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
-        case ESMF_PREC_FP32: return gen_launch<float, 1>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
-        case ESMF_PREC_FP16X2: return gen_launch<float, 2>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
-        case ESMF_PREC_BF16X2: return gen_launch<float, 3>(b, Q, tol, bricks, nbricks, offsets, store, vscale, s);
+        case ESMF_PREC_FP64: return gen_launch<double, 0>(b, Q, tol, bricks, nbricks, offsets, store, vscale, ptab, pslot, s);
+        case ESMF_PREC_F32X2: return gen_launch<double, 4>(b, Q, tol, bricks, nbricks, offsets, store, vscale, ptab, pslot, s);
+        case ESMF_PREC_FP32: return gen_launch<float, 1>(b, Q, tol, bricks, nbricks, offsets, store, vscale, ptab, pslot, s);
+        case ESMF_PREC_FP16X2: return gen_launch<float, 2>(b, Q, tol, bricks, nbricks, offsets, store, vscale, ptab, pslot, s);
+        case ESMF_PREC_BF16X2: return gen_launch<float, 3>(b, Q, tol, bricks, nbricks, offsets, store, vscale, ptab, pslot, s);
     }
     set_error("unknown precision %d", precision);
     return ESMF_ERR_INVALID_ARG;
