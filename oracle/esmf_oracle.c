@@ -10,6 +10,8 @@
  *   - contracted s-type Gaussians normalised to <phi|phi> = 1 (textbook,
  *     Szabo & Ostlund App. A, the text the paper cites for integrals);
  *   - primitive (ss|ss) integrals through the Boys function F0 closed form;
+ *   - Cartesian p and d functions (labels 1..9) by the Obara-Saika vertical
+ *     and Head-Gordon-Pople horizontal recurrences over F_0 .. F_8;
  *   - Schwarz factors Q_pq = sqrt((pq|pq));
  *   - generalized J, K and F of Eq. (J_and_K), Sec. II.B.1:
  *       J[D]_pq = sum_rs D_rs (rs|pq),  K[D]_pq = sum_rs D_rs (pr|qs),
@@ -96,9 +98,11 @@ static double prim_eri(double a, const double *A, double b, const double *B,
 }
 
 /*
- * Cartesian p functions (angular momentum 1).  A function's Cartesian label
- * cart = 0 (s), 1, 2, 3 (p_x, p_y, p_z) makes its primitives
- * (r - A)_i exp(-a |r - A|^2).  Integrals over them follow the Obara-Saika
+ * Cartesian p and d functions (angular momentum 1 and 2).  A function's
+ * Cartesian label cart = 0 (s), 1, 2, 3 (p_x, p_y, p_z), 4, 5, 6 (d_xx, d_yy,
+ * d_zz), 7, 8, 9 (d_xy, d_xz, d_yz) makes its primitives
+ * (x - A_x)^lx (y - A_y)^ly (z - A_z)^lz exp(-a |r - A|^2) with the exponent
+ * triple (lx, ly, lz) of the label.  Integrals over them follow the Obara-Saika
  * recurrences (Obara & Saika, J. Chem. Phys. 84, 3963 (1986)): the vertical
  * recurrence builds [e0|f0]^(m) from the Boys functions F_m, the horizontal
  * one (Head-Gordon & Pople, J. Chem. Phys. 89, 5777 (1988)) moves angular
@@ -138,11 +142,33 @@ double oracle_boys(int m, double T)
 }
 
 typedef struct {
-    double PA[3], WP[3], QC[3], WQ[3], p, q, rho, K, F[8];
+    double PA[3], WP[3], QC[3], WQ[3], p, q, rho, K, F[16];
+    /* values of [e0|f0]^(m) already formed for this primitive quartet, over
+     * the box e <= E, f <= G (componentwise), m <= L; NAN = not yet formed */
+    int E[3], G[3], L;
+    double *memo;
 } osdata;
 
-/* [e0|f0]^(m) by the vertical recurrence (e, f: Cartesian exponent triples) */
+static int vrr_slot(const osdata *o, const int *e, const int *f, int m)
+{
+    int ie = (e[0] * (o->E[1] + 1) + e[1]) * (o->E[2] + 1) + e[2];
+    int nf = (o->G[0] + 1) * (o->G[1] + 1) * (o->G[2] + 1);
+    int jf = (f[0] * (o->G[1] + 1) + f[1]) * (o->G[2] + 1) + f[2];
+    return (ie * nf + jf) * (o->L + 1) + m;
+}
+
+static double os_vrr_formed(const osdata *o, const int *e, const int *f, int m);
+
+/* [e0|f0]^(m) by the vertical recurrence (e, f: Cartesian exponent triples);
+ * each value is formed once per primitive quartet and kept in o->memo */
 static double os_vrr(const osdata *o, const int *e, const int *f, int m)
+{
+    int k = vrr_slot(o, e, f, m);
+    if (isnan(o->memo[k])) o->memo[k] = os_vrr_formed(o, e, f, m);
+    return o->memo[k];
+}
+
+static double os_vrr_formed(const osdata *o, const int *e, const int *f, int m)
 {
     int i;
     for (i = 0; i < 3 && e[i] == 0; ++i) {}
@@ -197,9 +223,13 @@ static double os_hrr(const osdata *o, const double *AB, const double *CD,
     return os_vrr(o, a, c, 0);
 }
 
+/* exponent triple of a Cartesian label (0 s; 1-3 p_x, p_y, p_z; 4-6 d_xx,
+ * d_yy, d_zz; 7-9 d_xy, d_xz, d_yz) */
 static void cart_vec(int cart, int *v)
 {
-    v[0] = cart == 1; v[1] = cart == 2; v[2] = cart == 3;
+    static const int tab[10][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                                   {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+    v[0] = tab[cart][0]; v[1] = tab[cart][1]; v[2] = tab[cart][2];
 }
 
 /* primitive [ab|cd] over raw Cartesian primitives with labels la..ld */
@@ -224,10 +254,22 @@ static double prim_eri_l(double a, const double *A, int la, double b, const doub
     }
     o.p = p; o.q = q; o.rho = p * q / (p + q);
     o.K = 2.0 * pow(OR_PI, 2.5) / (p * q * sqrt(p + q)) * exp(-a * b / p * ab2) * exp(-c * d / q * cd2);
-    int L = (la > 0) + (lb > 0) + (lc > 0) + (ld > 0);
-    boys_all(L, o.rho * pq2, o.F);
     int va[3], vb[3], vc[3], vd[3];
     cart_vec(la, va); cart_vec(lb, vb); cart_vec(lc, vc); cart_vec(ld, vd);
+    /* the horizontal recurrence moves b onto a and d onto c, so the vertical
+     * one needs e <= a + b and f <= c + d, and orders m <= |a+b| + |c+d| */
+    int L = 0;
+    for (int x = 0; x < 3; ++x) {
+        o.E[x] = va[x] + vb[x];
+        o.G[x] = vc[x] + vd[x];
+        L += o.E[x] + o.G[x];
+    }
+    o.L = L;
+    boys_all(L, o.rho * pq2, o.F);
+    double memo[13 * 13 * 9];   /* |a+b|, |c+d| <= 4: at most 12 triples per box, L <= 8 */
+    int nmemo = (o.E[0] + 1) * (o.E[1] + 1) * (o.E[2] + 1) * (o.G[0] + 1) * (o.G[1] + 1) * (o.G[2] + 1) * (L + 1);
+    for (int k = 0; k < nmemo; ++k) memo[k] = NAN;
+    o.memo = memo;
     return os_hrr(&o, AB, CD, va, vb, vc, vd);
 }
 
@@ -708,30 +750,42 @@ int oracle_eri2(int naux, const double *acenter, const double *aexp, double *out
 }
 
 /*
- * Entry points for bases with Cartesian p functions (cart[i] in 0..3).
- * Normalisation (textbook): a p primitive N (x - A_x) exp(-a r^2) has
- * <g|g> = 1 for N = (2a/pi)^{3/4} 2 sqrt(a); two p_x primitives on one centre
- * overlap N_k N_l (pi/(a_k+a_l))^{3/2} / (2 (a_k + a_l)).  w_k = c d_k N_k.
+ * Entry points for bases with Cartesian p and d functions (cart[i] in 0..9).
+ * Normalisation (textbook Gaussian moments, int x^{2n} exp(-s x^2) dx =
+ * (2n-1)!! / (2s)^n sqrt(pi/s)): a primitive with exponent triple (lx, ly, lz),
+ * l = lx + ly + lz, has <g|g> = 1 for
+ *   N = (2a/pi)^{3/4} (4a)^{l/2} / sqrt((2lx-1)!! (2ly-1)!! (2lz-1)!!),
+ * and two primitives of one label on one centre overlap
+ *   N_k N_j (pi/s)^{3/2} (2lx-1)!! (2ly-1)!! (2lz-1)!! / (2s)^l,  s = a_k + a_j.
+ * w_k = c d_k N_k with c making the contracted function's norm one.
  */
+static double dfact_odd(int l) /* (2l-1)!! for l = 0, 1, 2 */
+{
+    return l == 2 ? 3.0 : 1.0;
+}
+
 int oracle_normalize_l(int n, const int32_t *nprim, const double *exps,
                        const double *coefs, const int32_t *cart, double *w)
 {
     if (n <= 0) return -1;
     int64_t *off = prim_offsets(n, nprim);
     for (int mu = 0; mu < n; ++mu) {
-        int l = cart[mu] ? 1 : 0;
+        int v[3];
+        cart_vec(cart[mu], v);
+        int l = v[0] + v[1] + v[2];
+        double df = dfact_odd(v[0]) * dfact_odd(v[1]) * dfact_odd(v[2]);
         double s = 0.0;
         for (int64_t k = off[mu]; k < off[mu + 1]; ++k)
             for (int64_t j = off[mu]; j < off[mu + 1]; ++j) {
-                double ak = exps[k], aj = exps[j];
-                double nk = pow(2.0 * ak / OR_PI, 0.75) * (l ? 2.0 * sqrt(ak) : 1.0);
-                double nj = pow(2.0 * aj / OR_PI, 0.75) * (l ? 2.0 * sqrt(aj) : 1.0);
-                double ov = pow(OR_PI / (ak + aj), 1.5) * (l ? 1.0 / (2.0 * (ak + aj)) : 1.0);
+                double ak = exps[k], aj = exps[j], sk = ak + aj;
+                double nk = pow(2.0 * ak / OR_PI, 0.75) * pow(4.0 * ak, 0.5 * l) / sqrt(df);
+                double nj = pow(2.0 * aj / OR_PI, 0.75) * pow(4.0 * aj, 0.5 * l) / sqrt(df);
+                double ov = pow(OR_PI / sk, 1.5) * df / pow(2.0 * sk, l);
                 s += coefs[k] * coefs[j] * nk * nj * ov;
             }
         double c = 1.0 / sqrt(s);
         for (int64_t k = off[mu]; k < off[mu + 1]; ++k)
-            w[k] = c * coefs[k] * pow(2.0 * exps[k] / OR_PI, 0.75) * (l ? 2.0 * sqrt(exps[k]) : 1.0);
+            w[k] = c * coefs[k] * pow(2.0 * exps[k] / OR_PI, 0.75) * pow(4.0 * exps[k], 0.5 * l) / sqrt(df);
     }
     free(off);
     return 0;

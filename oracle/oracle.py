@@ -102,7 +102,7 @@ class Oracle:
         self.exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
         self.coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
         self.w = np.zeros_like(self.exps)
-        # Cartesian p functions (basis.cart): the Obara-Saika integrals
+        # Cartesian p and d functions (basis.cart, labels 1..9): the Obara-Saika integrals
         self.cart = None
         if getattr(basis, "cart", None) is not None and np.any(np.asarray(basis.cart) != 0):
             self.cart = np.ascontiguousarray(basis.cart, dtype=np.int32)

@@ -43,7 +43,8 @@ class Basis:
     nprim: np.ndarray
     exps: np.ndarray
     coefs: np.ndarray
-    cart: np.ndarray = None       # (N,) int32 Cartesian label: 0 s, 1..3 p_x, p_y, p_z (None: all s)
+    cart: np.ndarray = None       # (N,) int32 Cartesian label: 0 s, 1..3 p_x, p_y, p_z,
+                                  # 4..6 d_xx, d_yy, d_zz, 7..9 d_xy, d_xz, d_yz (None: all s)
 
     @property
     def n(self) -> int:
@@ -51,7 +52,12 @@ class Basis:
 
     @property
     def has_p(self) -> bool:
+        """True when any function has angular momentum (p or d)."""
         return self.cart is not None and bool(np.any(np.asarray(self.cart) != 0))
+
+    @property
+    def has_d(self) -> bool:
+        return self.cart is not None and bool(np.any(np.asarray(self.cart) >= 4))
 
     def subset(self, idx) -> "Basis":
         idx = np.asarray(idx, dtype=np.int64)
@@ -135,6 +141,43 @@ def sp_basis(rng, centers, nprim=3, lo=0.1, hi=10.0) -> Basis:
     return Basis(np.asarray(center, dtype=np.float64), np.asarray(npr, dtype=np.int32),
                  np.asarray(exps, dtype=np.float64), np.asarray(coefs, dtype=np.float64),
                  np.asarray(cart, dtype=np.int32))
+
+
+def spd_basis(rng, centers, nprim=3, lo=0.1, hi=10.0) -> Basis:
+    """One s, one p and one Cartesian d shell per center (1 + 3 + 6 = 10
+    functions; the components of a shell share exponents and coefficients),
+    the shape of a polarised basis such as cc-pVDZ; exponents log-uniform in
+    [lo, hi] bohr^-2, coefficients uniform in (0.1, 1]."""
+    center, npr, exps, coefs, cart = [], [], [], [], []
+    for c in centers:
+        shells = []
+        for labels in ((0,), (1, 2, 3), (4, 5, 6, 7, 8, 9)):
+            e = np.exp(rng.uniform(np.log(lo), np.log(hi), size=nprim))
+            co = 1.0 - rng.uniform(0.0, 0.9, size=nprim)
+            shells.append((labels, e, co))
+        for labels, e, co in shells:
+            for lab in labels:
+                center.append(c)
+                npr.append(nprim)
+                exps.extend(e)
+                coefs.extend(co)
+                cart.append(lab)
+    return Basis(np.asarray(center, dtype=np.float64), np.asarray(npr, dtype=np.int32),
+                 np.asarray(exps, dtype=np.float64), np.asarray(coefs, dtype=np.float64),
+                 np.asarray(cart, dtype=np.int32))
+
+
+def spd_random(n_centers, m, seed, tol=1e-10, edge=None, min_dist=1.4, nprim=3) -> Workload:
+    """Random molecule of s, p and d shells (10 functions per center) for the
+    angular-momentum tests, densities from the same recipes."""
+    rng = rng_for(BASE_SEED + 400 + seed)
+    if edge is None:
+        edge = 10.0 * (n_centers / 100.0) ** (1.0 / 3.0)
+    cen = cube_centers(rng, n_centers, edge, min_dist)
+    b = spd_basis(rng, cen, nprim=nprim)
+    nocc = max(1, b.n // 5)
+    D = esmf_densities(rng, b.n, nocc, m)
+    return Workload(f"spd_n{b.n}_m{m}_s{seed}", b, D, tol, nocc)
 
 
 def sp_random(n_centers, m, seed, tol=1e-10, edge=None, min_dist=1.4) -> Workload:
