@@ -252,13 +252,13 @@ def sub_direct(fock, W, dev, stream, alu_peaks, steps=2):
                              "flops_per_quartet": "81 primitive quartets x 25 + 20 m"}}
 
 
-def sub_sp(fock, W, dev, stream, steps=5):
-    """A molecule of s and p shells (25 centers x (s, p_x, p_y, p_z) = 100
-    functions, m = 16, tol 1e-10): Obara-Saika store creation and builds on
-    the split FP16 tensor-core path and the FP64 CUDA-core path."""
+def sub_angular(fock, W, dev, stream, w, shells, steps=5):
+    """A molecule with p (and d) shells, m = 16, tol 1e-10: store creation
+    (Obara-Saika for s and p quartets, McMurchie-Davidson for quartets with a
+    d function, FP64) and builds on the split FP16 tensor-core path and the
+    FP64 CUDA-core path."""
     import torch
-    w = W.sp_random(25, 16, 11)
-    out = {"n_basis": int(w.basis.n), "m": int(w.m), "shells": "25 centers x (s, p)"}
+    out = {"n_basis": int(w.basis.n), "m": int(w.m), "shells": shells}
     for prec in ("fp16x2", "fp64"):
         with fock.FockBuilder(w.basis, w.tol, "stored", prec, device=dev.index) as fb:
             st = fb.stats()
@@ -467,7 +467,9 @@ def run_ours(args):
         subs["precision_n400_m64_fp16x2"] = sub_precision(fock, W, dev, stream)
         subs["direct_n2000_m32_fp32"] = sub_direct(fock, W, dev, stream, alu_peaks)
         subs["stored_n200_m16_density_fitted"] = sub_df(fock, W, dev, stream, alu_peaks)
-        subs["sp_n100_m16"] = sub_sp(fock, W, dev, stream)
+        subs["sp_n100_m16"] = sub_angular(fock, W, dev, stream, W.sp_random(25, 16, 11), "25 centers x (s, p), 3 primitives")
+        subs["spd_n100_m16"] = sub_angular(fock, W, dev, stream, W.spd_random(10, 16, 11, nprim=2),
+                                           "10 centers x (s, p, Cartesian d), 2 primitives")
         subs["batched_uneven_fp16x2"] = run_batched(fock, W, dev, stream, "fp16x2")
         out["configs"] = subs
         if rank == 0 and world == 1 and not args.no_serving:

@@ -146,24 +146,26 @@ int esmf_fock_create_screened(const esmf_basis_t *basis, double tol, int screeni
                               int64_t budget_bytes, esmf_fock_t **out);
 
 /*
- * esmf_fock_create_cart -- esmf_fock_create for a basis that mixes s and
- * Cartesian p functions, the angular momenta of split-valence and cc-pVDZ-
- * type bases (the paper's molecules use cc-pVDZ, Sec. III.A).  Function i has
- * the Cartesian label cart[i]: 0 for s, 1/2/3 for p_x/p_y/p_z, i.e. primitives
- * (r - A)_i exp(-a |r - A|^2) normalised to one (each contraction to one);
- * the three functions of a p shell are listed separately with the same
- * centre, exponents and coefficients.  Integrals over p functions come from
- * the Obara-Saika / Head-Gordon-Pople recurrences in FP64 at create time; the
- * Schwarz table, screening, store and every build kernel are those of s
- * bases (the contraction works on integral values by function index), so all
- * precisions and the tensor-core path apply.
- *   cart     host array of n_basis labels in [0, 3] (all zero: an s basis)
+ * esmf_fock_create_cart -- esmf_fock_create for a basis that mixes s, p and
+ * d Cartesian functions, the angular momenta of polarised bases such as
+ * cc-pVDZ (the paper's molecules use cc-pVDZ, Sec. III.A).  Function i has the
+ * Cartesian label cart[i]: 0 for s, 1/2/3 for p_x/p_y/p_z, 4/5/6 for
+ * d_xx/d_yy/d_zz and 7/8/9 for d_xy/d_xz/d_yz, i.e. primitives
+ * (x - A_x)^lx (y - A_y)^ly (z - A_z)^lz exp(-a |r - A|^2), each component
+ * normalised to one (each contraction to one); the functions of a shell are
+ * listed separately with the same centre, exponents and coefficients.
+ * Integrals come in FP64 from the Obara-Saika / Head-Gordon-Pople
+ * recurrences (s and p quartets) and the McMurchie-Davidson scheme (quartets
+ * with a d function), at create time for stored handles and inside every
+ * build for integral-direct ones (a correctness path: the s-type direct
+ * kernel is the fast one).  The Schwarz table, screening, store and every
+ * build kernel are those of s bases (the contraction works on integral
+ * values by function index), so all precisions and the tensor-core path
+ * apply.
+ *   cart     host array of n_basis labels in [0, 9] (all zero: an s basis)
  *   others   as esmf_fock_create, Schwarz screening
- * Errors: as esmf_fock_create; INVALID_ARG for a label outside [0, 3];
- * UNSUPPORTED for ESMF_MODE_DIRECT with p functions (integral-direct builds
- * evaluate s functions only), and for ESMF_MODE_AUTO when the store of a
- * basis with p functions does not fit budget_bytes.  esmf_fock_create_df and
- * the pair-max rule take s bases only.
+ * Errors: as esmf_fock_create; INVALID_ARG for a label outside [0, 9].
+ * esmf_fock_create_df and the pair-max rule take s bases only.
  */
 int esmf_fock_create_cart(const esmf_basis_t *basis, const int32_t *cart, double schwarz_tol,
                           int mode, int precision, int device, int64_t budget_bytes,

@@ -1,11 +1,10 @@
-// Contracted Cartesian p functions on the device: normalisation, the Schwarz
-// table and the integral store for bases that mix s and p shells.  The
-// integrals follow the Obara-Saika vertical recurrence (Obara & Saika, J.
-// Chem. Phys. 84, 3963 (1986)) and the horizontal recurrence of Head-Gordon
-// & Pople (J. Chem. Phys. 89, 5777 (1988)), written out for angular momentum
-// at most one per function (at most two per pair), in FP64.  Every other
-// step of a build (screening, the contraction kernels, finalisation) works on
-// the integral values by function index and is the same as for s functions.
+// Contracted Cartesian p and d functions on the device: normalisation, the
+// Schwarz table and the integral store for bases that mix s, p and d shells.
+// The integrals (angular.cuh) follow the Obara-Saika and Head-Gordon-Pople
+// recurrences for s and p functions and the McMurchie-Davidson scheme for
+// quartets with a d function, in FP64.  Every other step of a build
+// (screening, the contraction kernels, finalisation) works on the integral
+// values by function index and is the same as for s functions.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -33,23 +32,29 @@ int grid_a(int64_t work, int per_block, int cap = 152 * 32) {
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-// normalisation: a p primitive N (x - A_x) exp(-a r^2) has unit norm for
-// N = (2a/pi)^{3/4} 2 sqrt(a); two of one component on one centre overlap
-// N_k N_l (pi/(a_k + a_l))^{3/2} / (2 (a_k + a_l))
+// normalisation: a primitive N x^lx y^ly z^lz exp(-a r^2) (l = lx + ly + lz,
+// powers of the offsets from its centre) has unit norm for
+// N = (2a/pi)^{3/4} (4a)^{l/2} / sqrt((2lx-1)!! (2ly-1)!! (2lz-1)!!); two of
+// one label on one centre overlap N_k N_l (pi/s)^{3/2} (2lx-1)!! (2ly-1)!!
+// (2lz-1)!! / (2s)^l with s = a_k + a_l (the Gaussian moments
+// int x^{2n} exp(-s x^2) dx = (2n-1)!! / (2s)^n sqrt(pi/s)).
 __global__ void k_normalize_l(int n, const int *nprim, const int *poff, const int *cart, const double *exps,
                               const double *coefs, double *w) {
     const int mu = blockIdx.x * blockDim.x + threadIdx.x;
     if (mu >= n) return;
     const int o = poff[mu], np_ = nprim[mu];
-    const bool pf = cart[mu] != 0;
+    int v[3];
+    label_exps(cart[mu], v);
+    const int l = v[0] + v[1] + v[2];
+    const double df = (v[0] == 2 ? 3.0 : 1.0) * (v[1] == 2 ? 3.0 : 1.0) * (v[2] == 2 ? 3.0 : 1.0);
     const double pi = 3.14159265358979323846;
-    auto nrm = [&](double a) { return pow(2.0 * a / pi, 0.75) * (pf ? 2.0 * sqrt(a) : 1.0); };
+    auto nrm = [&](double a) { return pow(2.0 * a / pi, 0.75) * pow(4.0 * a, 0.5 * l) / sqrt(df); };
     double s = 0.0;
     for (int k = 0; k < np_; ++k)
-        for (int l = 0; l < np_; ++l) {
-            const double ak = exps[o + k], al = exps[o + l], sum = ak + al;
-            const double ov = pow(pi / sum, 1.5) * (pf ? 1.0 / (2.0 * sum) : 1.0);
-            s += coefs[o + k] * coefs[o + l] * nrm(ak) * nrm(al) * ov;
+        for (int j = 0; j < np_; ++j) {
+            const double ak = exps[o + k], aj = exps[o + j], sum = ak + aj;
+            const double ov = pow(pi / sum, 1.5) * df / pow(2.0 * sum, (double)l);
+            s += coefs[o + k] * coefs[o + j] * nrm(ak) * nrm(aj) * ov;
         }
     const double c = rsqrt(s);
     for (int k = 0; k < np_; ++k) w[o + k] = c * coefs[o + k] * nrm(exps[o + k]);

@@ -410,7 +410,7 @@ int esmf_fock_create_cart(const esmf_basis_t *basis, const int32_t *cart, double
     if (!basis || !cart || basis->n_basis <= 0) { set_error("basis and cart are required"); return ESMF_ERR_INVALID_ARG; }
     bool any_p = false;
     for (int i = 0; i < basis->n_basis; ++i) {
-        if (cart[i] < 0 || cart[i] > 3) { set_error("cart[%d] = %d outside [0, 3]", i, cart[i]); return ESMF_ERR_INVALID_ARG; }
+        if (cart[i] < 0 || cart[i] > 9) { set_error("cart[%d] = %d outside [0, 9]", i, cart[i]); return ESMF_ERR_INVALID_ARG; }
         any_p |= cart[i] != 0;
     }
     if (!any_p) cart = nullptr;          // all s: the s-type path

@@ -180,7 +180,7 @@ def esmf_fock_create(basis, schwarz_tol, mode="stored", precision="fp64", device
     sc = SCREENINGS[screening] if isinstance(screening, str) else int(screening)
     cart = getattr(basis, "cart", None)
     if cart is not None and np.any(np.asarray(cart) != 0):
-        # s and Cartesian p functions: esmf_fock_create_cart (Schwarz screening)
+        # s, Cartesian p and d functions: esmf_fock_create_cart (Schwarz screening)
         if sc != 0:
             raise ValueError("bases with p functions use Schwarz screening")
         ca = np.ascontiguousarray(cart, dtype=np.int32)
