@@ -102,3 +102,26 @@ def test_invalid_basis_rejected(lib, bad):
     expect = fock.ESMF_ERR_UNSUPPORTED if bad == "direct16" else fock.ESMF_ERR_INVALID_ARG
     assert rc == expect, (bad, rc, fock.esmf_last_error())
     assert not h.value
+
+
+@pytest.mark.parametrize("label", [-1, 10])
+def test_cartesian_label_outside_s_p_d_rejected(lib, label):
+    """esmf_fock_create_cart takes labels 0..9 (s, p_x..p_z, d_xx..d_yz) and
+    rejects any other on the host, before any device work."""
+    from paper_2002_00322_gb300 import fock
+    from paper_2002_00322_gb300 import workloads as W
+    w = W.spd_random(1, 1, 0)
+    b = w.basis
+    cart = np.ascontiguousarray(b.cart, dtype=np.int32).copy()
+    cart[3] = label
+    center = np.ascontiguousarray(b.center)
+    nprim, exps, coefs = (np.ascontiguousarray(x) for x in (b.nprim, b.exps, b.coefs))
+    cb = fock.esmf_basis_t(b.n, center.ctypes.data_as(C.POINTER(C.c_double)),
+                           nprim.ctypes.data_as(C.POINTER(C.c_int32)),
+                           exps.ctypes.data_as(C.POINTER(C.c_double)),
+                           coefs.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    rc = lib.esmf_fock_create_cart(C.byref(cb), cart.ctypes.data_as(C.POINTER(C.c_int32)), 0.0, 0, 0, 0, 0,
+                                   C.byref(h))
+    assert rc == fock.ESMF_ERR_INVALID_ARG, (label, rc)
+    assert not h.value
