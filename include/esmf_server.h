@@ -7,7 +7,11 @@
  * The server keeps each registered molecule's screening data and integral
  * store resident (a handle from esmf_fock_create) while they fit a device-
  * memory budget, evicting idle molecules least-recently-used first and
- * re-creating them on their next request.  A worker thread admits queued
+ * re-creating them on their next request.  Molecules that still have queued
+ * requests are evicted last: while other builds are in flight, a request
+ * whose molecule has no handle waits (up to 30 s) for room rather than
+ * evict one of them, and when it must, the molecule whose next queued request
+ * comes latest goes first.  A worker thread admits queued
  * requests whenever an execution slot, the molecule and enough memory are
  * free, so requests that arrive while others run start as soon as resources
  * allow and their work overlaps on the device (one non-blocking CUDA stream

@@ -38,6 +38,7 @@ struct Molecule {
     double tol = 0.0;
     esmf_fock_t *h = nullptr;
     int64_t bytes = 0;        // device bytes of the handle
+    int64_t known_bytes = 0;  // largest device bytes a handle of this molecule has had (0: never created)
     uint64_t last_use = 0;
     bool busy = false;
     int queued = 0;           // requests waiting for this molecule
@@ -160,29 +161,57 @@ void evict(esmf_server *s, int idx) {
     ++s->evictions;
 }
 
-// free device memory for a handle of molecule idx: evict idle handles until
-// the upper bound of its store fits, taking molecules with no queued requests
-// first and, among equals, the least recently used
-void make_room(esmf_server *s, int idx) {
+// How long a request for a molecule without a handle may wait for room
+// rather than evict a molecule that still has queued requests (a bound that
+// only guarantees progress: queues of resident molecules drain long before).
+constexpr double kPatienceMs = 30000.0;
+
+// Free device memory for a handle of molecule idx: evict idle handles until
+// its size fits — the size its handle had before (with 1/16 to spare for a
+// larger density count), or, on first creation, the upper bound of its store.  Molecules with no queued request go
+// first (the largest or the least recently used first, by the server's
+// order); molecules with queued requests only when allow_queued is set, the
+// one whose next request comes latest in the queue first (the furthest next
+// use, which is the eviction that costs the fewest re-creations).  Returns
+// true when the bound fits.
+bool make_room(esmf_server *s, int idx, bool allow_queued) {
     const Molecule &mol = s->mols[idx];
     const int64_t np = (mol.n + 7) / 8 * 8;
     const int64_t P = np * (np + 1) / 2;
-    const int64_t bound = (P * (P + 1) / 2) * 4 + (P * (P + 1) / 2) / 8 + np * np * 64;
+    const int64_t bound = mol.known_bytes > 0 ? mol.known_bytes + mol.known_bytes / 16
+                                              : (P * (P + 1) / 2) * 4 + (P * (P + 1) / 2) / 8 + np * np * 64;
+    std::vector<int64_t> next_use;
     for (;;) {
         const int64_t freeb = s->budget - resident_bytes(s);
-        if (freeb >= bound) return;
+        if (freeb >= bound) return true;
         int victim = -1;
         for (size_t i = 0; i < s->mols.size(); ++i) {
             const Molecule &c = s->mols[i];
-            if ((int)i == idx || !c.h || c.busy) continue;
+            if ((int)i == idx || !c.h || c.busy || c.queued > 0) continue;
             if (victim < 0) { victim = (int)i; continue; }
             const Molecule &v = s->mols[victim];
-            const bool cq = c.queued > 0, vq = v.queued > 0;
             const bool better = s->evict_largest ? (c.bytes > v.bytes || (c.bytes == v.bytes && c.last_use < v.last_use))
                                                  : c.last_use < v.last_use;
-            if ((cq != vq && !cq) || (cq == vq && better)) victim = (int)i;
+            if (better) victim = (int)i;
         }
-        if (victim < 0) return;
+        if (victim < 0 && allow_queued) {
+            if (next_use.empty()) {
+                next_use.assign(s->mols.size(), INT64_MAX);
+                int64_t pos = 0;
+                for (const auto &r : s->pending) {
+                    if (next_use[r->mol] == INT64_MAX) next_use[r->mol] = pos;
+                    ++pos;
+                }
+            }
+            for (size_t i = 0; i < s->mols.size(); ++i) {
+                const Molecule &c = s->mols[i];
+                if ((int)i == idx || !c.h || c.busy) continue;
+                if (victim < 0 || next_use[i] > next_use[victim] ||
+                    (next_use[i] == next_use[victim] && c.bytes > s->mols[victim].bytes))
+                    victim = (int)i;
+            }
+        }
+        if (victim < 0) return false;
         evict(s, victim);
     }
 }
@@ -402,13 +431,21 @@ bool try_admit(esmf_server *s, const std::shared_ptr<Request> &r, std::vector<in
     for (size_t i = 0; i < s->slots.size(); ++i)
         if (!s->slots[i].req) { slot_idx = (int)i; break; }
     if (slot_idx < 0) return false;
+    if (!mol.h) {
+        // While other builds are in flight (so the server makes progress) a
+        // new handle waits, up to kPatienceMs, rather than evict a molecule
+        // that still has queued requests: that eviction would only be undone
+        // by a re-creation a few requests later.
+        const double waited = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
+        const bool patient = s->inflight > 0 && waited < kPatienceMs;
+        if (!make_room(s, r->mol, !patient) && patient) return false;
+    }
     Slot &sl = s->slots[slot_idx];
     sl.req = r;
     ++s->inflight;
     s->peak_inflight = std::max<int64_t>(s->peak_inflight, s->inflight);
     int rc = ESMF_OK;
     if (!mol.h) {
-        make_room(s, r->mol);
         esmf_basis_t b;
         b.n_basis = mol.n; b.center = mol.center.data(); b.n_prim = mol.nprim.data();
         b.exps = mol.exps.data(); b.coefs = mol.coefs.data();
@@ -423,6 +460,7 @@ bool try_admit(esmf_server *s, const std::shared_ptr<Request> &r, std::vector<in
         esmf_fock_stats(mol.h, &after);
         if (after.device_bytes != before.device_bytes) drop_graphs_of(s, r->mol);   // work memory moved
         mol.bytes = after.device_bytes;
+        mol.known_bytes = std::max(mol.known_bytes, mol.bytes);
     }
     if (rc == ESMF_OK) rc = ensure_slot(s, slot_idx, (size_t)r->m * mol.n * mol.n, r->m);
     mol.busy = true;
