@@ -229,27 +229,38 @@ def sub_precision(fock, W, dev, stream, steps=10):
         return out
 
 
-def sub_direct(fock, W, dev, stream, alu_peaks, steps=2):
-    """direct_n2000_m32 (integral-direct FP32 on the 2000-function ribbon)."""
+def sub_direct(fock, W, dev, stream, alu_peaks, prec="fp32", steps=2):
+    """direct_n2000_m32 (integral-direct on the 2000-function ribbon): FP32
+    evaluation and contraction on CUDA cores ("fp32"), or FP32 evaluation into
+    split FP16 records chunk by chunk with the contraction on the tensor cores
+    ("fp16x2").  The roofline counts the same algorithmic work for both (81
+    primitive quartets x 25 flops per kept quartet for the integrals, 20 m for
+    the contraction) against the measured FP32 rate: the integral evaluation,
+    on CUDA cores either way, is most of the time."""
     import torch
     w = W.direct()
     n, m = w.basis.n, w.m
-    with fock.FockBuilder(w.basis, w.tol, "direct", "fp32", device=dev.index) as fb:
+    with fock.FockBuilder(w.basis, w.tol, "direct", prec, device=dev.index) as fb:
         st = fb.stats()
         D = torch.from_numpy(w.D).to(dev)
         J, K = torch.empty_like(D), torch.empty_like(D)
         ms, ks = timed_builds(fock, fb, m, D, J, K, None, None, stream, steps, 1)
         flops = st["n_quartets_kept"] * (81 * 25 + 20 * m)
         ach = flops / ks / 1e12
-        return {"dtype": "f32", "ms_per_step": round(ms, 3), "value": round(1e3 / ms, 4),
-                "quartets_per_s": round(st["n_quartets_kept"] / (ms / 1e3), 1),
-                "setup_ms": round(st["create_ms"], 1), "quartets_kept": st["n_quartets_kept"],
-                "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": alu_peaks["fp32"],
-                             "unit": "TFLOP/s", "frac": round(ach / alu_peaks["fp32"], 4), "traffic": None,
-                             "peak_source": "measured FP32 FMA rate (esmf_measure_fma_peak, this process)",
-                             "kernel": "k_jk_cuda", "kernel_ms": round(ks * 1e3, 3),
-                             "algorithmic_flops": flops,
-                             "flops_per_quartet": "81 primitive quartets x 25 + 20 m"}}
+        out = {"dtype": DTYPES[prec], "ms_per_step": round(ms, 3), "value": round(1e3 / ms, 4),
+               "quartets_per_s": round(st["n_quartets_kept"] / (ms / 1e3), 1),
+               "setup_ms": round(st["create_ms"], 1), "quartets_kept": st["n_quartets_kept"],
+               "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": alu_peaks["fp32"],
+                            "unit": "TFLOP/s", "frac": round(ach / alu_peaks["fp32"], 4), "traffic": None,
+                            "peak_source": "measured FP32 FMA rate (esmf_measure_fma_peak, this process)",
+                            "kernel": "k_jk_cuda" if prec == "fp32" else "k_brick_generate + k_jk_umma per chunk",
+                            "kernel_ms": round(ks * 1e3, 3),
+                            "algorithmic_flops": flops,
+                            "flops_per_quartet": "81 primitive quartets x 25 + 20 m"}}
+        if prec != "fp32":
+            out["chunks"] = st["n_chunks"]
+            out["scratch_bytes"] = st["scratch_bytes"]
+        return out
 
 
 def sub_angular(fock, W, dev, stream, w, shells, steps=5):
@@ -466,6 +477,7 @@ def run_ours(args):
                 subs[f"stored_n200_m16_{prec}"] = sub_stored(fock, W, dev, stream, prec, alu_peaks)
         subs["precision_n400_m64_fp16x2"] = sub_precision(fock, W, dev, stream)
         subs["direct_n2000_m32_fp32"] = sub_direct(fock, W, dev, stream, alu_peaks)
+        subs["direct_n2000_m32_fp16x2"] = sub_direct(fock, W, dev, stream, alu_peaks, prec="fp16x2")
         subs["stored_n200_m16_density_fitted"] = sub_df(fock, W, dev, stream, alu_peaks)
         subs["sp_n100_m16"] = sub_angular(fock, W, dev, stream, W.sp_random(25, 16, 11), "25 centers x (s, p), 3 primitives")
         subs["spd_n100_m16"] = sub_angular(fock, W, dev, stream, W.spd_random(10, 16, 11, nprim=2),

@@ -100,6 +100,9 @@ typedef struct {
     double  create_ms;          /* wall time of esmf_fock_create               */
     int32_t screening;          /* ESMF_SCREEN_*                               */
     int64_t n_pairs_kept;       /* pairs in at least one kept quartet          */
+    int64_t n_chunks;           /* integral-direct FP16X2/BF16X2: chunks each  */
+                                /* build regenerates (0 otherwise)             */
+    int64_t scratch_bytes;      /* their scratch buffer (part of device_bytes) */
 } esmf_stats_t;
 
 /*
@@ -114,9 +117,18 @@ typedef struct {
  *   device       CUDA device ordinal the handle lives on
  *   budget_bytes device-memory budget for AUTO mode (0 = no limit)
  *   out          receives the handle (NULL on failure)
+ * Integral-direct handles in FP16X2 / BF16X2 (s bases) contract on the
+ * tensor cores: every build evaluates the kept integrals in FP32 chunk by
+ * chunk (whole items of the brick list, at most 2 GiB of split records per
+ * chunk, or a quarter of budget_bytes when it is given) into a scratch buffer
+ * the handle owns, and contracts each chunk with the tensor-core kernel of
+ * the stored split precisions; the FP64 accumulators sum over the chunks.
+ * Their CUDA-core path (ESMF_PATH_CUDA_CORE, density-weighted screening, the
+ * no-allocation entry) is the FP32 integral-direct kernel.  ESMF_MODE_AUTO
+ * keeps choosing FP32 integral-direct builds when a split store does not fit.
  * Runs on the device's legacy default stream and returns after it has
- * finished.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED (FP16X2/BF16X2
- * requested in direct mode, or stored mode beyond budget_bytes).
+ * finished.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED (F32X2 requested in
+ * direct mode, or stored mode beyond budget_bytes).
  */
 int esmf_fock_create(const esmf_basis_t *basis, double schwarz_tol, int mode,
                      int precision, int device, int64_t budget_bytes,

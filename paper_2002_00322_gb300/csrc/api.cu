@@ -60,6 +60,16 @@ struct esmf_fock {
     int *pslot = nullptr, *pblocks = nullptr;
     int n_ptab = 0;
     float vscale = 1.0f;           // power-of-two scale of split 16-bit stores
+    // integral-direct builds on the tensor cores (FP16X2 / BF16X2 direct
+    // handles): the brick list cut at item boundaries into chunks whose packed
+    // records fit the scratch buffer; chunk c is bricks [chunks[c], chunks[c+1]),
+    // its records regenerated into `scratch` by every build (offsets above are
+    // then relative to the chunk's first brick).  Generation and contraction
+    // of a chunk are not overlapped with the next chunk's: both kernels fill
+    // every SM, so on two streams they only interleave (measured no faster).
+    std::vector<int64_t> chunks;
+    void *scratch = nullptr;
+    int64_t scratch_bytes = 0;
     int path = ESMF_PATH_AUTO;
     // density-weighted screening threshold (0: off) and its per-build weights
     double tol_d = 0.0;
@@ -231,7 +241,7 @@ void release(esmf_fock *h) {
     cudaFree(h->nprim); cudaFree(h->poff); cudaFree(h->cart);
     if (h->S != h->Q) cudaFree(h->S);
     cudaFree(h->Q);
-    cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts);
+    cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts); cudaFree(h->scratch);
     for (auto &sp : h->shard_parts) cudaFree(sp.second.first);
     cudaFree(h->ptab); cudaFree(h->pslot); cudaFree(h->pblocks);
     cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
@@ -267,8 +277,12 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// integral-direct handle whose builds regenerate split 16-bit records chunk by
+// chunk and contract them on the tensor cores
+bool tensor_direct(const esmf_fock *h) { return h->mode == ESMF_MODE_DIRECT && is_split16(h->prec) && h->scratch; }
+
 int ensure_work(esmf_fock *h, int m) {
-    if (h->mode == ESMF_MODE_STORED && is_split16(h->prec) && !h->kbank) {
+    if ((h->mode == ESMF_MODE_STORED || tensor_direct(h)) && is_split16(h->prec) && !h->kbank) {
         RET(dalloc(h, (unsigned char **)&h->kbank, umma_kbank_bytes(h->nb)));
         RET(dalloc(h, (unsigned char **)&h->jbank, umma_jbank_bytes(h->nb)));
         RET(dalloc(h, &h->dmax, 1));
@@ -436,8 +450,8 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
     const int n = basis->n_basis;
     int64_t nprim_tot = 0;
     RET(check_basis(basis, &nprim_tot));
-    if (mode == ESMF_MODE_DIRECT && precision >= ESMF_PREC_FP16X2) {
-        set_error("split 16-bit and double-FP32 precisions need stored integrals");
+    if (mode == ESMF_MODE_DIRECT && (precision == ESMF_PREC_F32X2 || (is_split16(precision) && cart))) {
+        set_error("double-FP32 needs stored integrals, and split 16-bit integral-direct builds take s bases");
         return ESMF_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -671,6 +685,46 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
             if (!ck(cudaMemcpyAsync(h->parts, parts.data(), sizeof(int64_t) * parts.size(), cudaMemcpyHostToDevice, cs), "copy parts"))
                 return fail(ESMF_ERR_CUDA);
             h->nparts = (int)parts.size() - 1;
+        }
+        if (use_mode == ESMF_MODE_DIRECT && is_split16(h->prec) && !h->cart) {
+            // integral-direct on the tensor cores: chunks of whole items whose
+            // records fit the scratch buffer (2 GiB, or a quarter of the budget;
+            // an item larger than that is a chunk of its own)
+            int64_t cap = (int64_t)2 << 30;
+            if (budget_bytes > 0) cap = std::min<int64_t>(cap, budget_bytes / 4);
+            const int64_t nk = h->nbricks;
+            std::vector<int64_t> ch{0};
+            int64_t prev = 0;                        // the last item start seen
+            for (int64_t i = 1; i <= nk; ++i) {
+                if (i < nk && !(kept[i].pad & BRICK_ITEM_FIRST)) continue;
+                if ((offs[i] - offs[ch.back()]) * eb > cap && prev > ch.back()) ch.push_back(prev);
+                prev = i;
+            }
+            if (ch.back() != nk) ch.push_back(nk);
+            std::vector<int64_t> roff(nk + 1, 0);
+            int64_t most = 0;
+            for (size_t c = 0; c + 1 < ch.size(); ++c) {
+                for (int64_t i = ch[c]; i < ch[c + 1]; ++i) roff[i] = offs[i] - offs[ch[c]];
+                most = std::max(most, (offs[ch[c + 1]] - offs[ch[c]]) * eb);
+            }
+            h->chunks = ch;
+            h->scratch_bytes = most;
+            if ((rc = dalloc(h, &h->offsets, nk + 1))) return fail(rc);
+            if ((rc = dalloc(h, (unsigned char **)&h->scratch, (size_t)h->scratch_bytes))) return fail(rc);
+            if (!ck(cudaMemcpyAsync(h->offsets, roff.data(), sizeof(int64_t) * (nk + 1), cudaMemcpyHostToDevice, cs), "copy chunk offsets") ||
+                !ck(cudaMemsetAsync(h->scratch, 0, (size_t)h->scratch_bytes, cs), "clear scratch"))
+                return fail(ESMF_ERR_CUDA);
+            // each chunk's cost-balanced split over the tensor kernel's CTAs
+            for (size_t c = 0; c + 1 < ch.size(); ++c) {
+                std::vector<BrickDesc> sub(kept.begin() + ch[c], kept.begin() + ch[c + 1]);
+                const std::vector<int64_t> sp = balance_parts(sub, h->num_sms);
+                int64_t *dp = nullptr;
+                if ((rc = dalloc(h, &dp, sp.size()))) return fail(rc);
+                h->shard_parts.emplace(std::make_pair(ch[c], ch[c + 1]), std::make_pair(dp, (int)sp.size() - 1));
+                if (!ck(cudaMemcpyAsync(dp, sp.data(), sizeof(int64_t) * sp.size(), cudaMemcpyHostToDevice, cs), "copy chunk parts") ||
+                    !ck(cudaStreamSynchronize(cs), "chunk parts"))
+                    return fail(ESMF_ERR_CUDA);
+            }
         }
         if (use_mode == ESMF_MODE_STORED) {
             if ((rc = dalloc(h, &h->offsets, h->nbricks + 1))) return fail(rc);
@@ -960,37 +1014,64 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
                 if (t.first == m) chunk = t.second;
         a.mc = chunk;
         const bool split16 = h->mode == ESMF_MODE_STORED && is_split16(h->prec);
+        const bool tdirect = tensor_direct(h);
         if (h->tol_d > 0.0) {
             // density-weighted screening runs on the CUDA-core kernels
             RET(launch_density_weight(h->dev(), m, D, h->dw, h->dwb, s));
             a.dw = h->dw; a.dwb = h->dwb; a.tol_d = h->tol_d;
         }
-        if (split16 && h->path != ESMF_PATH_CUDA_CORE && h->tol_d == 0.0) {
+        if ((split16 || tdirect) && h->path != ESMF_PATH_CUDA_CORE && h->tol_d == 0.0) {
             UmmaLaunch L;
-            L.bricks = h->bricks + b0; L.nbricks = b1 - b0; L.offsets = h->offsets + b0;
-            L.store = (const uint32_t *)h->store; L.kbank = h->kbank; L.jbank = h->jbank;
+            L.kbank = h->kbank; L.jbank = h->jbank;
             L.dmax_bits = h->dmax; L.D = D; L.n = h->n; L.np = h->np; L.nb = h->nb; L.m = m;
             L.bf16 = h->prec == ESMF_PREC_BF16X2; L.num_sms = h->num_sms; L.vscale = h->vscale;
             L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev;
-            L.ev_start = e0; L.ev_stop = e1;
             L.chunk = chunk ? chunk : 16;
-            if (b0 == 0 && b1 == h->nbricks && h->parts) {
-                L.part = h->parts; L.nparts = h->nparts;
-            } else if (b1 - b0 >= 1 && (int64_t)h->hbricks.size() == h->nbricks) {
-                // a shard: its own cost-balanced split over the CTAs, built once
-                auto key = std::make_pair(b0, b1);
-                auto it = h->shard_parts.find(key);
-                if (it == h->shard_parts.end()) {
-                    std::vector<BrickDesc> sub(h->hbricks.begin() + b0, h->hbricks.begin() + b1);
-                    const std::vector<int64_t> sp = balance_parts(sub, h->num_sms);
-                    int64_t *dp = nullptr;
-                    RET(dalloc(h, &dp, sp.size()));
-                    CKR(cudaMemcpy(dp, sp.data(), sizeof(int64_t) * sp.size(), cudaMemcpyHostToDevice));
-                    it = h->shard_parts.emplace(key, std::make_pair(dp, (int)sp.size() - 1)).first;
+            // CTA split of bricks [r0, r1): the whole list's, or the range's own
+            // cost-balanced one (chunks and shards), built once
+            auto set_parts = [&](int64_t r0, int64_t r1) -> int {
+                if (r0 == 0 && r1 == h->nbricks && h->parts && !tdirect) {
+                    L.part = h->parts; L.nparts = h->nparts;
+                } else if (r1 - r0 >= 1 && (int64_t)h->hbricks.size() == h->nbricks) {
+                    auto key = std::make_pair(r0, r1);
+                    auto it = h->shard_parts.find(key);
+                    if (it == h->shard_parts.end()) {
+                        std::vector<BrickDesc> sub(h->hbricks.begin() + r0, h->hbricks.begin() + r1);
+                        const std::vector<int64_t> sp = balance_parts(sub, h->num_sms);
+                        int64_t *dp = nullptr;
+                        RET(dalloc(h, &dp, sp.size()));
+                        CKR(cudaMemcpy(dp, sp.data(), sizeof(int64_t) * sp.size(), cudaMemcpyHostToDevice));
+                        it = h->shard_parts.emplace(key, std::make_pair(dp, (int)sp.size() - 1)).first;
+                    }
+                    L.part = it->second.first; L.nparts = it->second.second;
                 }
-                L.part = it->second.first; L.nparts = it->second.second;
+                return ESMF_OK;
+            };
+            if (!tdirect) {
+                L.bricks = h->bricks + b0; L.nbricks = b1 - b0; L.offsets = h->offsets + b0;
+                L.store = (const uint32_t *)h->store;
+                L.ev_start = e0; L.ev_stop = e1;
+                RET(set_parts(b0, b1));
+                RET(launch_jk_umma(L, s));
+            } else {
+                // integral-direct: per chunk, the packed split records of its bricks
+                // into the scratch buffer, then the tensor-core contraction of them;
+                // the FP64 accumulators sum over the chunks
+                if (e0) CKR(cudaEventRecord(e0, s));
+                const DevBasis db = h->dev();
+                for (size_t c = 0; c + 1 < h->chunks.size(); ++c) {
+                    const int64_t r0 = std::max(b0, h->chunks[c]), r1 = std::min(b1, h->chunks[c + 1]);
+                    if (r1 <= r0) continue;
+                    RET(launch_brick_generate(db, h->S, h->tol_s, h->bricks + r0, r1 - r0, h->offsets + r0, h->prec,
+                                              h->scratch, h->vscale, s, h->ptab, h->pslot));
+                    L.bricks = h->bricks + r0; L.nbricks = r1 - r0; L.offsets = h->offsets + r0;
+                    L.store = (const uint32_t *)h->scratch;
+                    L.part = nullptr; L.nparts = 0;
+                    RET(set_parts(r0, r1));
+                    RET(launch_jk_umma(L, s));
+                }
+                if (e1) CKR(cudaEventRecord(e1, s));
             }
-            RET(launch_jk_umma(L, s));
             return launch_finalize_blocked(h->dev(), m, D, h->Jacc, h->Kacc, J, K, F, traces, s);
         }
         if (h->Dt) {
@@ -1255,7 +1336,8 @@ int esmf_fock_autotune(esmf_fock_t *h, int m, const double *D, double *J, double
     if (h->mode == ESMF_MODE_DF) { set_error("density-fitted handles have nothing to tune"); return ESMF_ERR_UNSUPPORTED; }
     DeviceGuard g(h->device);
     if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
-    const bool tensor = h->mode == ESMF_MODE_STORED && is_split16(h->prec) && h->path != ESMF_PATH_CUDA_CORE;
+    const bool tensor = (h->mode == ESMF_MODE_STORED || tensor_direct(h)) && is_split16(h->prec) &&
+                        h->path != ESMF_PATH_CUDA_CORE;
     std::vector<int> cand;
     if (tensor) { cand.push_back(16); if (m > 8) cand.push_back(8); }
     else if (h->prec == ESMF_PREC_FP64 || h->prec == ESMF_PREC_F32X2) { cand.push_back(8); cand.push_back(4); }
@@ -1344,6 +1426,8 @@ int esmf_fock_stats(const esmf_fock_t *h, esmf_stats_t *out) {
     out->create_ms = h->create_ms;
     out->screening = h->screening;
     out->n_pairs_kept = h->n_pairs_kept;
+    out->n_chunks = h->chunks.empty() ? 0 : (int64_t)h->chunks.size() - 1;
+    out->scratch_bytes = h->scratch_bytes;
     return ESMF_OK;
 }
 

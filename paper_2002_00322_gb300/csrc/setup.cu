@@ -358,6 +358,22 @@ __global__ void __launch_bounds__(256) k_brick_generate(DevBasis b, const double
                 // double-FP32 store: the FP64 value as hi + lo floats
                 const float hi = __double2float_rn((double)v);
                 reinterpret_cast<float2 *>(store)[vbase + i] = make_float2(hi, __double2float_rn((double)v - (double)hi));
+            } else if constexpr (sizeof(T) == 4) {
+                // FP32-evaluated value: the power-of-two scale is exact in FP32 and
+                // the residual of the 16-bit rounding too (Sterbenz), so the FP32
+                // split equals the FP64 one and keeps off GB300's narrow FP64 pipe
+                const float xs = v * vscale;
+                uint16_t hb, lb;
+                if (PREC == 2) {
+                    const __half h = __float2half_rn(xs);
+                    hb = __half_as_ushort(h);
+                    lb = __half_as_ushort(__float2half_rn(xs - __half2float(h)));
+                } else {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(xs);
+                    hb = __bfloat16_as_ushort(h);
+                    lb = __bfloat16_as_ushort(__float2bfloat16_rn(xs - __bfloat162float(h)));
+                }
+                rec[i] = (uint32_t)hb | ((uint32_t)lb << 16);
             } else {
                 const double xs = (double)v * (double)vscale;
                 uint16_t hb, lb;

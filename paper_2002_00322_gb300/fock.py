@@ -67,7 +67,8 @@ class esmf_stats_t(C.Structure):
                 ("n_quartets_kept", C.c_int64), ("n_bricks", C.c_int64), ("n_stored", C.c_int64),
                 ("store_bytes", C.c_int64), ("device_bytes", C.c_int64), ("mode", C.c_int32),
                 ("precision", C.c_int32), ("schwarz_tol", C.c_double), ("create_ms", C.c_double),
-                ("screening", C.c_int32), ("n_pairs_kept", C.c_int64)]
+                ("screening", C.c_int32), ("n_pairs_kept", C.c_int64), ("n_chunks", C.c_int64),
+                ("scratch_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

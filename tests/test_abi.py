@@ -70,7 +70,7 @@ def test_strerror_and_host_side_argument_errors(lib):
         assert lib.esmf_server_create(*args, C.byref(h)) == fock.ESMF_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("bad", ["exp", "nprim", "coef", "tol", "mode", "prec", "direct16"])
+@pytest.mark.parametrize("bad", ["exp", "nprim", "coef", "tol", "mode", "prec", "direct_f32x2"])
 def test_invalid_basis_rejected(lib, bad):
     from paper_2002_00322_gb300 import fock
     from paper_2002_00322_gb300 import workloads as W
@@ -90,8 +90,8 @@ def test_invalid_basis_rejected(lib, bad):
         mode = 7
     elif bad == "prec":
         prec = 9
-    elif bad == "direct16":
-        mode, prec = 1, 2
+    elif bad == "direct_f32x2":
+        mode, prec = 1, 4
     center = np.ascontiguousarray(b.center)
     cb = fock.esmf_basis_t(b.n, center.ctypes.data_as(C.POINTER(C.c_double)),
                            nprim.ctypes.data_as(C.POINTER(C.c_int32)),
@@ -99,7 +99,7 @@ def test_invalid_basis_rejected(lib, bad):
                            coefs.ctypes.data_as(C.POINTER(C.c_double)))
     h = C.c_void_p()
     rc = lib.esmf_fock_create(C.byref(cb), tol, mode, prec, 0, 0, C.byref(h))
-    expect = fock.ESMF_ERR_UNSUPPORTED if bad == "direct16" else fock.ESMF_ERR_INVALID_ARG
+    expect = fock.ESMF_ERR_UNSUPPORTED if bad == "direct_f32x2" else fock.ESMF_ERR_INVALID_ARG
     assert rc == expect, (bad, rc, fock.esmf_last_error())
     assert not h.value
 

@@ -47,9 +47,9 @@ def rel(x, r):
     return float(np.linalg.norm(x - r)) / max(float(np.linalg.norm(r)), 1e-300)
 
 
-def build(esmf, w, mode, prec, path="auto"):
+def build(esmf, w, mode, prec, path="auto", budget=0):
     import torch
-    with esmf.FockBuilder(w.basis, w.tol, mode, prec) as fb:
+    with esmf.FockBuilder(w.basis, w.tol, mode, prec, budget_bytes=budget) as fb:
         if path != "auto":
             fb.set_path(path)
         J, K, F, t = fb.build(torch.from_numpy(np.ascontiguousarray(w.D)).cuda(), want_F=True)
@@ -74,10 +74,17 @@ def c2():
 @pytest.mark.parametrize("mode,prec,path", [
     ("stored", "fp64", "auto"), ("stored", "f32x2", "auto"), ("stored", "fp32", "auto"),
     ("stored", "fp16x2", "auto"), ("stored", "bf16x2", "auto"), ("stored", "fp16x2", "cuda_core"),
-    ("direct", "fp32", "auto"), ("direct", "fp64", "auto")])
+    ("direct", "fp32", "auto"), ("direct", "fp64", "auto"), ("direct", "fp16x2", "auto"),
+    ("direct", "fp16x2", "chunks")])
 def test_stored_n200_m16_whole_matrices(esmf, c2, mode, prec, path):
+    """Every path against the whole oracle matrices.  direct/fp16x2 regenerates
+    the split records into scratch and contracts them on the tensor cores; with
+    a 64 MB budget its scratch is 16 MB, so a build runs in dozens of chunks."""
     w, Jr, Kr, tr, n_kept = c2
-    J, K, F, t, st = build(esmf, w, mode, prec, path)
+    chunked = path == "chunks"
+    J, K, F, t, st = build(esmf, w, mode, prec, "auto" if chunked else path, budget=(64 << 20) if chunked else 0)
+    if mode == "direct" and prec == "fp16x2":
+        assert st["n_chunks"] >= (20 if chunked else 1) and st["scratch_bytes"] <= (16 << 20 if chunked else 1 << 31)
     tol = TOL[prec]
     ej = np.array([rel(J[k], Jr[k]) for k in range(w.m)])
     ek = np.array([rel(K[k], Kr[k]) for k in range(w.m)])
@@ -108,14 +115,15 @@ def rows_check(esmf, w, g, mode, prec, path="auto"):
 
 @pytest.mark.parametrize("mode,prec,path", [
     ("stored", "fp16x2", "auto"), ("stored", "bf16x2", "auto"), ("stored", "fp32", "auto"),
-    ("stored", "fp64", "auto"), ("stored", "f32x2", "auto"), ("direct", "fp32", "auto")])
+    ("stored", "fp64", "auto"), ("stored", "f32x2", "auto"), ("direct", "fp32", "auto"),
+    ("direct", "fp16x2", "auto")])
 def test_precision_n400_m64_rows(esmf, mode, prec, path):
     w = W.precision()
     g = load("c4_precision_n400_m64.npz", w)
     rows_check(esmf, w, g, mode, prec, path)
 
 
-@pytest.mark.parametrize("mode,prec", [("direct", "fp32"), ("stored", "fp16x2")])
+@pytest.mark.parametrize("mode,prec", [("direct", "fp32"), ("stored", "fp16x2"), ("direct", "fp16x2")])
 def test_direct_n2000_m32_rows(esmf, mode, prec):
     w = W.direct()
     g = load("c3_direct_n2000_m32.npz", w)

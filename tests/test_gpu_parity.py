@@ -60,7 +60,7 @@ def tiny_ref():
 
 @pytest.mark.parametrize("mode,prec", [("stored", "fp64"), ("stored", "fp32"), ("direct", "fp64"),
                                        ("direct", "fp32"), ("stored", "fp16x2"), ("stored", "bf16x2"),
-                                       ("stored", "f32x2")])
+                                       ("stored", "f32x2"), ("direct", "fp16x2"), ("direct", "bf16x2")])
 def test_tiny_all_paths(esmf, tiny_ref, mode, prec):
     w, o, Jr, Kr = tiny_ref
     J, K, F, t, st = gpu_build(esmf, w, mode, prec)
@@ -79,7 +79,7 @@ def test_schwarz_table(esmf, tiny_ref):
 @pytest.mark.parametrize("n,m,tol,seed", [(1, 1, 0.0, 1), (8, 2, 0.0, 2), (9, 3, 1e-9, 3),
                                           (21, 5, 1e-7, 4), (37, 4, 1e-10, 5)])
 @pytest.mark.parametrize("mode,prec", [("stored", "fp64"), ("direct", "fp32"), ("stored", "fp16x2"),
-                                       ("direct", "fp64"), ("stored", "f32x2")])
+                                       ("direct", "fp64"), ("stored", "f32x2"), ("direct", "fp16x2")])
 def test_ragged_sizes(esmf, n, m, tol, seed, mode, prec):
     w = W.small_random(n, m, seed, tol=tol, edge=4.0 + n / 4)
     rng = np.random.default_rng(seed)
