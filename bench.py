@@ -497,8 +497,10 @@ def run_ours(args):
 
 def run_direct(args):
     """The integral-direct path on the 4 x L ribbon (L = --direct-length; 250
-    gives the 2000-function workload), m = 32, FP32: integrals are recomputed
-    inside every build, so the bound is FP32 ALU + SFU, not memory."""
+    gives the 2000-function workload), m = 32: integrals are recomputed inside
+    every build in FP32, so the bound is FP32 ALU + SFU, not memory; the
+    contraction runs on CUDA cores (--direct-precision fp32) or, chunk by
+    chunk from split FP16 records, on the tensor cores (fp16x2)."""
     import torch
     from paper_2002_00322_gb300 import fock
     from paper_2002_00322_gb300 import workloads as W
@@ -507,7 +509,8 @@ def run_direct(args):
     dev = torch.device("cuda", local)
     w = W.direct(length=args.direct_length, m=32)
     n, m = w.basis.n, w.m
-    fb = fock.FockBuilder(w.basis, w.tol, "direct", "fp32", device=local)
+    prec = args.direct_precision
+    fb = fock.FockBuilder(w.basis, w.tol, "direct", prec, device=local)
     st = fb.stats()
     D = torch.from_numpy(w.D).to(dev)
     J, K = torch.empty_like(D), torch.empty_like(D)
@@ -537,19 +540,22 @@ def run_direct(args):
     achieved = flops / kern_s / 1e12
     out = {"metric": METRIC, "value": round(1e3 / ms_step, 4), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec],
            "data": "synthetic (seeded s-type basis on a ribbon; stands in for cc-pVDZ molecules)",
            "config": {"workload": f"direct_n{n}_m{m}", "n_basis": n, "m": m, "schwarz_tol": w.tol,
-                      "mode": "direct", "precision": "fp32", "quartets_kept": st["n_quartets_kept"],
+                      "mode": "direct", "precision": prec, "quartets_kept": st["n_quartets_kept"],
                       "bricks": st["n_bricks"], "setup_ms": round(st["create_ms"], 1),
                       "densities_per_pass": chunk},
            "quartets_per_s": round(st["n_quartets_kept"] / (ms_step / 1e3), 1),
            "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                         "peak_source": "measured FP32 FMA rate (esmf_measure_fma_peak, this process)",
-                        "kernel": "k_jk_cuda", "kernel_ms": round(kern_s * 1e3, 3),
-                        "algorithmic_flops": flops},
-           "gpu_launches": 2 * args.steps, "clocks": clk.summary()}
+                        "kernel": "k_jk_cuda" if prec == "fp32" else "k_brick_generate + k_jk_umma per chunk",
+                        "kernel_ms": round(kern_s * 1e3, 3), "algorithmic_flops": flops},
+           # CUDA cores: contraction + finalisation; tensor cores: per chunk the
+           # generation, k_dmax and per 16-density pass k_dbank + k_jk_umma
+           "gpu_launches": (2 if prec == "fp32" else st["n_chunks"] * (2 + 2 * ((m + 15) // 16)) + 1) * args.steps,
+           "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(out), flush=True)
     fb.close()
@@ -917,6 +923,7 @@ def main():
     ap.add_argument("--workload", default="stored", choices=["stored", "direct"],
                     help="stored: the 200-function stored build (default); direct: the integral-direct ribbon")
     ap.add_argument("--direct-length", type=int, default=250)
+    ap.add_argument("--direct-precision", default="fp32", choices=["fp32", "fp16x2", "bf16x2"])
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--serve-nmax", type=int, default=600)
