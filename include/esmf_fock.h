@@ -369,7 +369,10 @@ int esmf_fock_kernel_time(esmf_fock_t *h, double *ms, int64_t *launches, int res
  * run the CUDA-core kernel over that store here, not the tensor-core kernel
  * (which needs per-handle density tiles in work memory): their results equal
  * esmf_fock_build's within the precision's tolerance (2e-6 relative for
- * FP16X2, 3e-5 for BF16X2), and the call is slower.  The FP64 J/K
+ * FP16X2, 3e-5 for BF16X2), and the call is slower.  Integral-direct
+ * FP16X2 / BF16X2 handles (which contract on the tensor cores in
+ * esmf_fock_build) run the FP32 integral-direct CUDA-core kernel here: their
+ * results equal esmf_fock_build's within the same tolerances.  The FP64 J/K
  * accumulators are taken from one static device array of
  * ESMF_NOALLOC_MAX_SCRATCH_DOUBLES doubles (32 MiB) that the library holds on
  * every device it is loaded on until the process exits; nothing is allocated
