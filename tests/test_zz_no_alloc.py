@@ -27,7 +27,8 @@ def relerr(x, r):
 
 
 @pytest.mark.parametrize("case,mode,prec", [("tiny", "stored", "fp64"), ("ragged", "stored", "fp64"),
-                                            ("ragged", "stored", "fp16x2"), ("ragged", "direct", "fp32")])
+                                            ("ragged", "stored", "fp16x2"), ("ragged", "direct", "fp32"),
+                                            ("ragged", "direct", "fp16x2")])
 def test_noalloc_matches_build_twice(esmf, case, mode, prec):
     import torch
     if case == "tiny":
