@@ -36,20 +36,21 @@ __device__ __forceinline__ void boys_upto4(double T, double *F) {
     for (int m = 0; m < 4; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) / (2.0 * T);
 }
 
-// F_m(T), m = 0..M (M <= 8): below T = 3 the Taylor series of every order
-// (40 terms, truncation < 1e-28, alternating terms below 5 in size); above,
-// F_0 from erf and the upward recurrence, whose error grows by at most
-// prod_m (2m+1)/(2T) < 1.3 over eight steps at T = 3.
+// F_m(T), m = 0..M (M <= 8): below T = 3 the Taylor series of the top order
+// (40 terms, truncation < 1e-28, alternating terms below 5 in size) and the
+// downward recurrence F_{m-1} = (2T F_m + exp(-T)) / (2m-1), which damps
+// errors; above, F_0 from erf and the upward recurrence, whose error grows by
+// at most prod_m (2m+1)/(2T) < 1.3 over eight steps at T = 3.
 __device__ inline void boys_upto8(int M, double T, double *F) {
     if (T < 3.0) {
-        for (int m = 0; m <= M; ++m) {
-            double term = 1.0, sum = 1.0 / (2 * m + 1);
-            for (int k = 1; k < 40; ++k) {
-                term *= -T / k;
-                sum += term / (2 * m + 2 * k + 1);
-            }
-            F[m] = sum;
+        double term = 1.0, sum = 1.0 / (2 * M + 1);
+        for (int k = 1; k < 40; ++k) {
+            term *= -T / k;
+            sum += term / (2 * M + 2 * k + 1);
         }
+        F[M] = sum;
+        const double e = exp(-T);
+        for (int m = M; m > 0; --m) F[m - 1] = (2.0 * T * F[m] + e) / (2 * m - 1);
         return;
     }
     const double e = exp(-T), x = sqrt(T);
@@ -89,8 +90,8 @@ __device__ inline void hermite_e(int i, int j, double PA, double PB, double p, d
 // v <= TZ (TX + TY + TZ = L <= 8, so at most 4 x 4 x 3 = 48 of them):
 //   R^n_000 = (-2 alpha)^n F_n(alpha |PQ|^2),
 //   R^n_{t+1,u,v} = t R^{n+1}_{t-1,u,v} + X_PQ R^{n+1}_{t,u,v}   (and for u, v),
-// level by level from n = L down to 0 (entries above t+u+v = L - n at level n
-// are never used by a valid one).  R is indexed (t (TY+1) + u)(TZ+1) + v.
+// level by level from n = L down to 0; entries above t+u+v = L - n at level n
+// are never used and not formed.  R is indexed (t (TY+1) + u)(TZ+1) + v.
 __device__ inline void hermite_r(int TX, int TY, int TZ, double alpha, double X, double Y, double Z,
                                  const double *F, double *R) {
     const int L = TX + TY + TZ, NY = TY + 1, NZ = TZ + 1, nbox = (TX + 1) * NY * NZ;
@@ -103,6 +104,7 @@ __device__ inline void hermite_r(int TX, int TY, int TZ, double alpha, double X,
         for (int t = 0; t <= TX; ++t)
             for (int u = 0; u <= TY; ++u)
                 for (int v = 0; v <= TZ; ++v) {
+                    if (t + u + v > L - n) break;
                     const int k = (t * NY + u) * NZ + v;
                     double r;
                     if (t > 0) r = (t > 1 ? (t - 1) * prev[k - 2 * NY * NZ] : 0.0) + X * prev[k - NY * NZ];
