@@ -59,15 +59,19 @@ def test_sharded_allreduce_on_cpu_ranks():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec,tol,case", [("fp64", 1e-12, "small"), ("fp16x2", 1e-6, "small"),
-                                           ("fp16x2", 1e-6, "stored_n200_m16")])
+                                           ("fp16x2", 1e-6, "stored_n200_m16"),
+                                           ("fp16x2", 1e-6, "direct_stored_n200_m16")])
 def test_sequential_shards_sum_to_full_build(esmf, prec, tol, case):
     """Shards are cut at equal estimated cost on item boundaries, and on the
     tensor-core path each shard has its own cost-balanced CTA split: the
-    shards still sum to the whole build."""
+    shards still sum to the whole build.  The integral-direct tensor-core
+    case (a 64 MB budget: many chunks) cuts shards across its chunks."""
     import torch
     w = W.small_random(45, 4, 9, tol=1e-10, edge=12.0) if case == "small" else W.stored()
     D = torch.from_numpy(w.D).cuda()
-    with esmf.FockBuilder(w.basis, w.tol, "stored", prec) as fb:
+    direct = case.startswith("direct")
+    with esmf.FockBuilder(w.basis, w.tol, "direct" if direct else "stored", prec,
+                          budget_bytes=(64 << 20) if direct else 0) as fb:
         J, K, F, t = fb.build(D, want_F=True)
         acc = [torch.zeros_like(J), torch.zeros_like(K), torch.zeros_like(F), torch.zeros_like(t)]
         for s in range(4):
