@@ -22,12 +22,17 @@
 // and K{Q,R} over a run (double-buffered by run), and the Coulomb views are
 // flushed per brick (double-buffered; their FP32 sums over longer spans lose
 // accuracy when transition densities cancel).  Flushes add into FP64
-// accumulators with reductions.
+// accumulators with reductions straight from the registers that the
+// tensor-memory loads fill: each epilogue warp reads its 16 accumulator rows
+// in the 16x32bx2 shape (threads 0-15 the first half of the density columns,
+// threads 16-31 the second), so every lane carries data and a warp's
+// reduction covers 2 x 16 consecutive FP64 values of a block (the D^T parts,
+// written transposed, 16 values in 8 pairs); no shared-memory staging.
 //
 // Warp roles (320 threads): warp 0 producer (bulk copies of the packed brick
 // record and the six density tiles), warp 1 tensor-memory owner and MMA
 // issuer, warps 2-5 expand packed records into the operand tiles, warps 6-9
-// read accumulators and flush them.  Every mbarrier wait is bounded; on
+// read accumulators and reduce them into the FP64 accumulators.  Every mbarrier wait is bounded; on
 // timeout the kernel records an error and all roles leave.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -53,16 +58,11 @@ constexpr int OFF_B5 = OFF_B1 + 4 * KB_BYTES_MAX; // two Coulomb tiles
 constexpr int OFF_IN = OFF_B5 + 2 * JB_BYTES_MAX;
 constexpr int STAGE_BYTES = ((OFF_IN + IN_BYTES + 1023) / 1024) * 1024;
 constexpr int CTRL_BYTES = 4096;
-// epilogue staging of flushed output blocks: two exchange views (D and D^T
-// parts, 2 x 16 x 64 floats each), the J2 view and the hi and lo words of the
-// compensated J1 sum (16 x 64 floats each)
-constexpr int STAGE_K_FLOATS = 2 * MPMAX * 64;
-constexpr int EPI_BYTES = (2 * STAGE_K_FLOATS + 3 * MPMAX * 64) * 4;
-constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES + EPI_BYTES;
+constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES;
 
 struct Ctrl {
     uint64_t full[2], conv[2], mmad[2], acce[2], runfree[2];
-    // window region w has been staged at the end of wstaged[w] / 4 items (each
+    // window region w has been read at the end of wstaged[w] / 4 items (each
     // epilogue warp adds one); monotonic, so a waiter can be any number of
     // items behind (an mbarrier phase parity could alias two completions)
     unsigned wstaged[SWIN];
@@ -196,28 +196,26 @@ __device__ __forceinline__ void entry_range(const UmmaEntry &E, int64_t &beg, in
 
 namespace {
 
-// Load one accumulator region (this thread's TMEM lane) and write it, scaled,
-// to the staging area in block order.  Exchange regions hold [D part | D^T
-// part] (2 MP columns): the D part goes to [k][x][y] and the D^T part to
-// [k][y][x] (row = x*8 + y of the view's output block); Coulomb regions hold
-// MP columns.
-template <int MP, bool KVIEW>
-__device__ __forceinline__ void stage_view(uint32_t taddr, bool live, int row, int m, float inv, float *st) {
-    constexpr int NC = KVIEW ? 2 * MP : MP;
-    float v[NC < 16 ? 16 : NC];
+// 16 lanes x 32-bit from the warp's lane quarter, two halves: threads 0-15
+// take lane (base + t) at columns [0, N), threads 16-31 lane (base + t - 16) at
+// columns [N, 2N) (split offset N), N = 8 or 4 registers.
+__device__ __forceinline__ void tmem_ld_half8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], 8;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 #pragma unroll
-    for (int c0 = 0; c0 < NC; c0 += 16) tmem_ld16(taddr + c0, v + c0);
-    if (NC < 16) tmem_ld8(taddr, v);
-    tmem_wait_ld();
-    if (!live) return;
-    const int x = row >> 3, y = row & 7;
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_half4(uint32_t taddr, float *v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.16x32bx2.x4.b32 {%0,%1,%2,%3}, [%4], 4;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
 #pragma unroll
-    for (int k = 0; k < MP; ++k) {
-        if (k < m) {
-            st[k * 64 + x * 8 + y] = v[k] * inv;
-            if (KVIEW) st[MPMAX * 64 + k * 64 + y * 8 + x] = v[MP + k] * inv;
-        }
-    }
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+#pragma unroll
+    for (int i = 4; i < 8; ++i) v[i] = 0.f;
 }
 
 // Error-free sum (Knuth's TwoSum) of the running value hi and the term t:
@@ -230,53 +228,6 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float t) {
     const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
     hi = s;
     lo = __fadd_rn(lo, err);
-}
-
-// Add one Coulomb accumulator row (this thread's TMEM lane, MP columns),
-// scaled, into the thread's compensated running sums.
-template <int MP>
-__device__ __forceinline__ void accumulate_row(uint32_t taddr, bool live, float inv, float *hi, float *lo) {
-    float v[16];
-    if (MP == 16) tmem_ld16(taddr, v);
-    else tmem_ld8(taddr, v);
-    tmem_wait_ld();
-    if (!live) return;
-#pragma unroll
-    for (int k = 0; k < MP; ++k) two_sum_acc(hi[k], lo[k], __fmul_rn(v[k], inv));
-}
-
-// Coalesced reduction of one staged block (m x 64 values, m <= 16) into the
-// block-major accumulator at dst (contiguous m*64 doubles): all shared loads
-// of a thread are issued before its reductions so their latencies overlap.
-__device__ __forceinline__ void flush_block(const float *st, double *dst, int m, int et) {
-    const int cnt = m * 64;
-    float v[MPMAX / 2];
-#pragma unroll
-    for (int j = 0; j < MPMAX / 2; ++j) {
-        const int i = et + 128 * j;
-        v[j] = (i < cnt) ? st[i] : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < MPMAX / 2; ++j) {
-        const int i = et + 128 * j;
-        if (i < cnt) atomicAdd(dst + i, (double)v[j]);
-    }
-}
-
-// As flush_block for a block staged as hi and lo words: adds hi + lo in FP64.
-__device__ __forceinline__ void flush_block2(const float *hi, const float *lo, double *dst, int m, int et) {
-    const int cnt = m * 64;
-    double v[MPMAX / 2];
-#pragma unroll
-    for (int j = 0; j < MPMAX / 2; ++j) {
-        const int i = et + 128 * j;
-        v[j] = (i < cnt) ? (double)hi[i] + (double)lo[i] : 0.0;
-    }
-#pragma unroll
-    for (int j = 0; j < MPMAX / 2; ++j) {
-        const int i = et + 128 * j;
-        if (i < cnt) atomicAdd(dst + i, v[j]);
-    }
 }
 
 }  // namespace
@@ -407,7 +358,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
                 if (frun && run >= 2 && !__all_sync(~0u, mbar_wait(&c.runfree[rb], ((run - 2) >> 1) & 1, abort_flag))) { fail(5); stop = true; break; }
                 if (fitem) { touched3 = 0; touched4 = 0; }
                 // window region w (V3[w] and V4[w]) is free once the epilogue has
-                // staged it at the end of the previous item
+                // read it at the end of the previous item
                 const int wreg = d.S % SWIN;
                 if (d.R != d.S && item >= 1 && !((touched3 | touched4) & (1u << wreg)) &&
                     !__all_sync(~0u, counter_wait(&c.wstaged[wreg], 4u * (unsigned)item, abort_flag))) { fail(10); stop = true; break; }
@@ -525,32 +476,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
     } else if (nloc > 0 && warp >= 6) {
         // ------------------------------------------------ epilogue
         const int slice = warp & 3;
-        const int row = slice * 16 + (lane & 15);       // accumulator row of this thread (lane < 16)
-        const bool live = lane < 16;
-        const int et = threadIdx.x - 192;               // 0..127
         const uint32_t tl = tmem + ((uint32_t)(slice * 32) << 16);
         const uint32_t RW = 2 * mp, WV = 2 * SWIN * RW, WJ = WV + 4 * RW;
-        float *stA = reinterpret_cast<float *>(sm + 2 * STAGE_BYTES + CTRL_BYTES);
-        float *stB = stA + STAGE_K_FLOATS;
-        float *stJ = stB + STAGE_K_FLOATS;
-        float *stJ1 = stJ + MPMAX * 64, *stJ1lo = stJ1 + MPMAX * 64;
         // compensated running sum of J1 -> J[P,Q] over the item (P, Q fixed)
-        float j1h[MPMAX], j1l[MPMAX];
+        float j1h[MPMAX / 2], j1l[MPMAX / 2];
 #pragma unroll
-        for (int k = 0; k < MPMAX; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
+        for (int k = 0; k < MPMAX / 2; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
+        const int jrow = slice * 16 + (lane & 15);      // accumulator row of this thread (all lanes)
         // per-entry constants (refreshed when the stream enters a new entry)
         int m = 0, nb = 0, mtot = 0, d0 = 0;
         float inv = 1.0f;
         double *Jacc = nullptr, *Kacc = nullptr;
         auto blk = [&](double *base, int X, int Y) { return base + ((int64_t)(X * nb + Y) * mtot + d0) * 64; };
-        auto stage = [&](uint32_t col, bool kview, float *dst) {
-            if (mp == 16) {
-                if (kview) stage_view<16, true>(tl + col, live, row, m, inv, dst);
-                else stage_view<16, false>(tl + col, live, row, m, inv, dst);
-            } else {
-                if (kview) stage_view<8, true>(tl + col, live, row, m, inv, dst);
-                else stage_view<8, false>(tl + col, live, row, m, inv, dst);
-            }
+        const int trow = (jrow & 7) * 8 + (jrow >> 3);  // its place in a transposed block
+        // an exchange region [D part | D^T part] read in the half layout: this
+        // thread's densities cb .. cb + mp/2 - 1 of both parts
+        auto ld_x = [&](uint32_t col, float *vd, float *vt) {
+            if (mp == 16) { tmem_ld_half8(tl + col, vd); tmem_ld_half8(tl + col + mp, vt); }
+            else { tmem_ld_half4(tl + col, vd); tmem_ld_half4(tl + col + mp, vt); }
+        };
+        // reductions of a loaded region into K[A,C] (D part) and K[C,A] (D^T part)
+        auto red_x = [&](const float *vd, const float *vt, int A, int C, bool with_t) {
+            const int half = mp / 2, cb = lane < 16 ? 0 : half;
+            double *dd = blk(Kacc, A, C) + jrow, *dt = blk(Kacc, C, A) + trow;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j < half && cb + j < m) {
+                    atomicAdd(dd + (cb + j) * 64, (double)(vd[j] * inv));
+                    if (with_t) atomicAdd(dt + (cb + j) * 64, (double)(vt[j] * inv));
+                }
         };
         auto release = [&](uint64_t *bar) {
             tc_fence_before();
@@ -584,70 +538,66 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
                 if (!mbar_wait(&c.mmad[s], (i >> 1) & 1, abort_flag)) fail(7);
                 // leave together: every epilogue thread must reach the same named barriers
                 named_bar_sync(2, 128);
-                if (et == 0) c.edecide = *abort_flag;
+                if (threadIdx.x == 192) c.edecide = *abort_flag;
                 named_bar_sync(2, 128);
                 if (c.edecide) { stop = true; break; }
                 tc_fence_after();
                 // per brick: Coulomb view J2 -> J[R,S] (not for the (PQ|PQ) brick) is
                 // flushed; J1 -> J[P,Q] joins the item's compensated sum
-                stage(WJ + b * 2 * mp, false, stJ);
-                if (mp == 16) accumulate_row<16>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
-                else accumulate_row<8>(tl + WJ + b * 2 * mp + mp, live, inv, j1h, j1l);
-                release(&c.acce[b]);
-                if (!diag) {
-                    named_bar_sync(2, 128);
-                    flush_block(stJ, blk(Jacc, d.R, d.S), m, et);
+                {
+                    float vj2[8], vj1[8];
+                    if (mp == 16) { tmem_ld_half8(tl + WJ + b * 2 * mp, vj2); tmem_ld_half8(tl + WJ + b * 2 * mp + mp, vj1); }
+                    else { tmem_ld_half4(tl + WJ + b * 2 * mp, vj2); tmem_ld_half4(tl + WJ + b * 2 * mp + mp, vj1); }
+                    tmem_wait_ld();
+                    release(&c.acce[b]);
+                    const int half = mp / 2, cb = lane < 16 ? 0 : half;
+                    if (!diag) {
+                        double *dst = blk(Jacc, d.R, d.S) + jrow;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (j < half && cb + j < m) atomicAdd(dst + (cb + j) * 64, (double)(vj2[j] * inv));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j < half) two_sum_acc(j1h[j], j1l[j], __fmul_rn(vj1[j], inv));
                 }
-                named_bar_sync(2, 128);
                 if (lrun) {
                     // V1 -> K[P,R] (and K[R,P] unless (PQ|PQ)), V2 -> K[Q,R], K[R,Q] (P != Q)
                     const int rb = run & 1;
-                    stage(WV + rb * 2 * RW, true, stA);
-                    if (pq_diff) stage(WV + rb * 2 * RW + RW, true, stB);
+                    float a1[8], a2[8], b1[8], b2[8];
+                    ld_x(WV + rb * 2 * RW, a1, a2);
+                    if (pq_diff) ld_x(WV + rb * 2 * RW + RW, b1, b2);
+                    tmem_wait_ld();
                     release(&c.runfree[rb]);
-                    named_bar_sync(2, 128);
-                    flush_block(stA, blk(Kacc, d.P, d.R), m, et);
-                    if (!diag) flush_block(stA + MPMAX * 64, blk(Kacc, d.R, d.P), m, et);
-                    if (pq_diff) {
-                        flush_block(stB, blk(Kacc, d.Q, d.R), m, et);
-                        if (!diag) flush_block(stB + MPMAX * 64, blk(Kacc, d.R, d.Q), m, et);
-                    }
-                    named_bar_sync(2, 128);
+                    red_x(a1, a2, d.P, d.R, !diag);
+                    if (pq_diff) red_x(b1, b2, d.Q, d.R, !diag);
                     ++run;
                 }
                 if (litem) {
-                    if (live) {
+                    {
+                        const int half = mp / 2, cb = lane < 16 ? 0 : half;
+                        double *dst = blk(Jacc, d.P, d.Q) + jrow;
 #pragma unroll
-                        for (int k = 0; k < MPMAX; ++k)
-                            if (k < m) { stJ1[k * 64 + row] = j1h[k]; stJ1lo[k * 64 + row] = j1l[k]; }
+                        for (int j = 0; j < 8; ++j)
+                            if (j < half && cb + j < m) atomicAdd(dst + (cb + j) * 64, (double)j1h[j] + (double)j1l[j]);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) { j1h[j] = 0.f; j1l[j] = 0.f; }
                     }
-#pragma unroll
-                    for (int k = 0; k < MPMAX; ++k) { j1h[k] = 0.f; j1l[k] = 0.f; }
-                    named_bar_sync(2, 128);
-                    flush_block2(stJ1, stJ1lo, blk(Jacc, d.P, d.Q), m, et);
-                    named_bar_sync(2, 128);
                     // window regions: V3 -> K[P,S], K[S,P]; V4 -> K[Q,S], K[S,Q] (D^T parts
                     // not for the (PQ|PQ) item)
                     const int S0 = d.S - d.S % SWIN;
                     for (int w = 0; w < SWIN; ++w) {
                         const bool h3 = touched3 & (1u << w), h4 = touched4 & (1u << w);
-                        if (h3) stage(RW * w, true, stA);
-                        if (h4) stage(RW * (SWIN + w), true, stB);
+                        float a1[8], a2[8], b1[8], b2[8];
+                        if (h3) ld_x(RW * w, a1, a2);
+                        if (h4) ld_x(RW * (SWIN + w), b1, b2);
+                        if (h3 || h4) tmem_wait_ld();
                         tc_fence_before();                  // every region, once per item
                         __syncwarp();
                         if (lane == 0) counter_release_add(&c.wstaged[w]);
-                        if (!h3 && !h4) continue;
-                        named_bar_sync(2, 128);
                         const int S = S0 + w;
-                        if (h3) {
-                            flush_block(stA, blk(Kacc, d.P, S), m, et);
-                            if (!diag) flush_block(stA + MPMAX * 64, blk(Kacc, S, d.P), m, et);
-                        }
-                        if (h4) {
-                            flush_block(stB, blk(Kacc, d.Q, S), m, et);
-                            if (!diag) flush_block(stB + MPMAX * 64, blk(Kacc, S, d.Q), m, et);
-                        }
-                        named_bar_sync(2, 128);
+                        if (h3) red_x(a1, a2, d.P, S, !diag);
+                        if (h4) red_x(b1, b2, d.Q, S, !diag);
                     }
                 }
             }
