@@ -97,15 +97,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def ncu_traffic(kernel, precision):
-    """DRAM traffic per launch from the committed ncu capture, or None when the
-    kernel's source has changed since that capture (or no capture exists)."""
+def ncu_traffic(kernel, precision, workload="stored_n200_m16"):
+    """DRAM traffic per launch from the committed ncu capture of this kernel on
+    this workload in this precision, or None when the kernel's source has
+    changed since that capture (or no such capture exists)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p)).get(kernel)
-    if not rec or precision not in rec.get("workload", ""):
+    if not rec or rec.get("workload", "") != f"{workload} {precision}":
         return None
     h = hashlib.sha1()
     for f in rec["files"]:
@@ -126,7 +127,7 @@ def measured_alu_peaks(local):
     return {p: round(max(fock.esmf_measure_fma_peak(p, local) for _ in range(2)), 2) for p in ("fp64", "fp32")}
 
 
-def contraction_roofline(prec, st, m, n, kern_s, alu_peaks):
+def contraction_roofline(prec, st, m, n, kern_s, alu_peaks, workload="stored_n200_m16"):
     """Roofline of the contraction kernel of one stored build.  FP64 / FP32
     stores: CUDA-core FMAs against the measured FMA rate, counting the
     algorithmic 20 m flops per kept unique quartet (2 J + 8 K FMAs per
@@ -147,14 +148,14 @@ def contraction_roofline(prec, st, m, n, kern_s, alu_peaks):
         ach = flops / kern_s / 1e12
         pk = alu_peaks[prec]
         return {"bound": "alu", "achieved": round(ach, 3), "peak": pk, "unit": "TFLOP/s",
-                "frac": round(ach / pk, 4), "traffic": ncu_traffic(kname, prec),
+                "frac": round(ach / pk, 4), "traffic": ncu_traffic(kname, prec, workload),
                 "peak_source": f"measured {prec.upper()} FMA rate (esmf_measure_fma_peak, this process)",
                 "kernel": kname, "kernel_ms": round(kern_s * 1e3, 4), "algorithmic_flops": flops}
     alg_bytes = st["n_quartets_kept"] * ELEM_BYTES[prec] + 3 * m * n * n * 8
     hbm, src, _ = peaks()
     ach = alg_bytes / kern_s / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(ach / hbm, 4), "traffic": ncu_traffic(kname, prec), "peak_source": src,
+            "frac": round(ach / hbm, 4), "traffic": ncu_traffic(kname, prec, workload), "peak_source": src,
             "kernel": kname, "kernel_ms": round(kern_s * 1e3, 4), "stored_bytes": st["store_bytes"],
             "algorithmic_bytes": alg_bytes}
 
@@ -215,7 +216,7 @@ def sub_precision(fock, W, dev, stream, steps=10):
                "density_builds_per_s": round(m * 1e3 / ms, 1), "densities_per_pass": chunk,
                "quartets_per_s": round(st["n_quartets_kept"] / (ms / 1e3), 1),
                "setup_ms": round(st["create_ms"], 1), "store_bytes": st["store_bytes"],
-               "roofline": contraction_roofline("fp16x2", st, m, n, ks, None)}
+               "roofline": contraction_roofline("fp16x2", st, m, n, ks, None, workload="precision_n400_m64")}
         g = os.path.join(ROOT, "tests", "golden", "c4_precision_n400_m64.npz")
         if os.path.exists(g):
             gd = np.load(g)
