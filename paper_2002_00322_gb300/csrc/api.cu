@@ -84,8 +84,9 @@ struct esmf_fock {
     std::vector<std::pair<int, int>> tuned;   // (m, densities per pass) picked by esmf_fock_autotune
     int force_chunk = 0;                      // set while the autotuner times a candidate
     int num_sms = 0;
-    // cost-balanced split of the whole brick list over the tensor kernel's
-    // CTAs: CTA g takes bricks [parts[g], parts[g+1]) (device, nparts + 1)
+    // cost-balanced chunks of the whole brick list for the tensor kernel:
+    // chunk g is bricks [parts[g], parts[g+1]) (device, nparts + 1), and the
+    // kernel's CTAs take chunks dynamically
     int64_t *parts = nullptr;
     int nparts = 0;
     // host copy of the brick list's estimated cost prefix (cost_prefix[i] =
@@ -97,6 +98,7 @@ struct esmf_fock {
     // tensor-core path work memory
     uint16_t *kbank = nullptr, *jbank = nullptr;
     unsigned int *dmax = nullptr;
+    unsigned *sched = nullptr;     // the tensor kernel's work counter
     int *err_host = nullptr, *err_dev = nullptr;   // mapped page-locked flag
     int64_t n_stored = 0, store_bytes = 0, n_kept_unique = 0;
     // work (device)
@@ -187,13 +189,13 @@ void dfree(esmf_fock *h, T **p, size_t count) {
     *p = nullptr;
 }
 
-// Relative cost of each brick in the tensor-core contraction, for splitting
-// the list over CTAs: a base cost, one unit per issued exchange/Coulomb view
-// and one per output block whose flush the brick triggers (its Coulomb J2
-// block; at a run end the run's V1/V2 blocks; at an item end the J1 block and
-// the window's V3/V4 blocks).  The coefficients are a least-squares fit of
-// per-CTA cycle counts on GB300 (stored_n200_m16, 152 CTAs): about 1.9K cycles
-// per brick plus 0.84K per flushed 16 x 64 block.
+// Relative cost of each brick in the tensor-core contraction, for cutting the
+// list into chunks: a base cost, one unit per issued exchange/Coulomb view and
+// one per output block whose flush the brick triggers (its Coulomb J2 block;
+// at a run end the run's V1/V2 blocks; at an item end the J1 block and the
+// window's V3/V4 blocks).  The coefficients came from a least-squares fit of
+// per-CTA cycle counts on GB300 (stored_n200_m16, 152 CTAs); the chunks are
+// taken dynamically, so the model only has to keep them of similar size.
 constexpr double kCostBrick = 1900.0, kCostView = 100.0, kCostBlock = 840.0;
 
 std::vector<double> cost_prefix(const std::vector<BrickDesc> &kept) {
@@ -216,6 +218,11 @@ std::vector<double> cost_prefix(const std::vector<BrickDesc> &kept) {
     return pre;
 }
 
+// Brick ranges of equal estimated cost for the tensor kernel, kChunksPerSM
+// per SM: its CTAs take them dynamically (a launch-wide counter), so a CTA
+// that runs slow for reasons the cost model does not see takes fewer.
+constexpr int kChunksPerSM = 4;
+
 std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
     const int64_t n = (int64_t)kept.size();
     if (G > n) G = (int)n;
@@ -228,7 +235,11 @@ std::vector<int64_t> balance_parts(const std::vector<BrickDesc> &kept, int G) {
     for (int g = 1; g < G; ++g) {
         const double target = pre[n] * g / G;
         while (j < n && pre[j] < target) ++j;
-        parts[g] = std::max(j, parts[g - 1] + 1);      // every CTA gets a brick
+        // cuts need not fall on item starts: a chunk that splits an item
+        // flushes the item's resident output blocks at its end, and cutting at
+        // item starts instead leaves chunks too uneven where items are about
+        // as long as chunks (measured slower)
+        parts[g] = std::max(j, parts[g - 1] + 1);      // every chunk gets a brick
     }
     parts[G] = n;
     for (int g = G - 1; g >= 1; --g) parts[g] = std::min(parts[g], parts[g + 1] - 1);
@@ -244,7 +255,7 @@ void release(esmf_fock *h) {
     cudaFree(h->bricks); cudaFree(h->offsets); cudaFree(h->store); cudaFree(h->parts); cudaFree(h->scratch);
     for (auto &sp : h->shard_parts) cudaFree(sp.second.first);
     cudaFree(h->ptab); cudaFree(h->pslot); cudaFree(h->pblocks);
-    cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax);
+    cudaFree(h->kbank); cudaFree(h->jbank); cudaFree(h->dmax); cudaFree(h->sched);
     if (h->err_host) cudaFreeHost(h->err_host);
     cudaFree(h->Jacc); cudaFree(h->Kacc); cudaFree(h->ework); cudaFree(h->Dt);
     cudaFree(h->dw); cudaFree(h->dwb);
@@ -286,6 +297,7 @@ int ensure_work(esmf_fock *h, int m) {
         RET(dalloc(h, (unsigned char **)&h->kbank, umma_kbank_bytes(h->nb)));
         RET(dalloc(h, (unsigned char **)&h->jbank, umma_jbank_bytes(h->nb)));
         RET(dalloc(h, &h->dmax, 1));
+        RET(dalloc(h, &h->sched, 1));
     }
     if (h->tol_d > 0.0 && !h->dw) {
         RET(dalloc(h, &h->dw, (size_t)h->np * h->np));
@@ -653,7 +665,7 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
     }
     if (!ck(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device), "SM count"))
         return fail(ESMF_ERR_CUDA);
-    const std::vector<int64_t> parts = balance_parts(kept, h->num_sms);
+    const std::vector<int64_t> parts = balance_parts(kept, kChunksPerSM * h->num_sms);
     h->cost_prefix = cost_prefix(kept);
     h->hbricks = kept;
     h->nbricks = (int64_t)kept.size();
@@ -717,7 +729,7 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
             // each chunk's cost-balanced split over the tensor kernel's CTAs
             for (size_t c = 0; c + 1 < ch.size(); ++c) {
                 std::vector<BrickDesc> sub(kept.begin() + ch[c], kept.begin() + ch[c + 1]);
-                const std::vector<int64_t> sp = balance_parts(sub, h->num_sms);
+                const std::vector<int64_t> sp = balance_parts(sub, kChunksPerSM * h->num_sms);
                 int64_t *dp = nullptr;
                 if ((rc = dalloc(h, &dp, sp.size()))) return fail(rc);
                 h->shard_parts.emplace(std::make_pair(ch[c], ch[c + 1]), std::make_pair(dp, (int)sp.size() - 1));
@@ -1025,7 +1037,7 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
             L.kbank = h->kbank; L.jbank = h->jbank;
             L.dmax_bits = h->dmax; L.D = D; L.n = h->n; L.np = h->np; L.nb = h->nb; L.m = m;
             L.bf16 = h->prec == ESMF_PREC_BF16X2; L.num_sms = h->num_sms; L.vscale = h->vscale;
-            L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev;
+            L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev; L.counter = h->sched;
             L.chunk = chunk ? chunk : 16;
             // CTA split of bricks [r0, r1): the whole list's, or the range's own
             // cost-balanced one (chunks and shards), built once
@@ -1037,7 +1049,7 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
                     auto it = h->shard_parts.find(key);
                     if (it == h->shard_parts.end()) {
                         std::vector<BrickDesc> sub(h->hbricks.begin() + r0, h->hbricks.begin() + r1);
-                        const std::vector<int64_t> sp = balance_parts(sub, h->num_sms);
+                        const std::vector<int64_t> sp = balance_parts(sub, kChunksPerSM * h->num_sms);
                         int64_t *dp = nullptr;
                         RET(dalloc(h, &dp, sp.size()));
                         CKR(cudaMemcpy(dp, sp.data(), sizeof(int64_t) * sp.size(), cudaMemcpyHostToDevice));
@@ -1143,7 +1155,7 @@ int esmf_fock_build_batch(int count, esmf_fock_t *const *hs, const int *ms, cons
         l.store = (const uint32_t *)h->store; l.kbank = h->kbank; l.jbank = h->jbank;
         l.dmax_bits = h->dmax; l.D = Ds[i]; l.n = h->n; l.np = h->np; l.nb = h->nb; l.m = m;
         l.bf16 = h->prec == ESMF_PREC_BF16X2; l.num_sms = h->num_sms; l.vscale = h->vscale;
-        l.Jacc = h->Jacc; l.Kacc = h->Kacc; l.error = h->err_dev;
+        l.Jacc = h->Jacc; l.Kacc = h->Kacc; l.error = h->err_dev; l.counter = h->sched;
         l.chunk = 16;
         if (h->parts) { l.part = h->parts; l.nparts = h->nparts; }
     }

@@ -138,8 +138,9 @@ struct UmmaLaunch {
     int *error;                  // device flag, 0 = ok
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr;   // optional timing
     int chunk = 16;              // densities per tensor-core pass (8 or 16)
-    const int64_t *part = nullptr;   // optional per-CTA brick ranges (nparts + 1 entries)
-    int nparts = 0;
+    const int64_t *part = nullptr;   // optional brick ranges (nparts + 1 entries) that CTAs take
+    int nparts = 0;                  // dynamically, several per CTA
+    unsigned *counter = nullptr;     // device work counter of the launch (zeroed per launch)
 };
 int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s);
 int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s);   // count <= 16

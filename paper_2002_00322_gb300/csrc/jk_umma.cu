@@ -58,6 +58,9 @@ constexpr int OFF_B5 = OFF_B1 + 4 * KB_BYTES_MAX; // two Coulomb tiles
 constexpr int OFF_IN = OFF_B5 + 2 * JB_BYTES_MAX;
 constexpr int STAGE_BYTES = ((OFF_IN + IN_BYTES + 1023) / 1024) * 1024;
 constexpr int CTRL_BYTES = 4096;
+constexpr int CQ = 16;                 // chunk queue slots
+constexpr int MAX_ENTRIES_CTRL = 16;   // entries per launch (MAX_ENTRIES)
+constexpr int CHUNKS_PER_CTA = 4;      // chunks of an entry without a part list, per CTA
 constexpr int SMEM_TOTAL = 2 * STAGE_BYTES + CTRL_BYTES;
 
 struct Ctrl {
@@ -71,6 +74,12 @@ struct Ctrl {
     int cdecide, edecide;   // group-uniform copies of abort_flag (converters, epilogue)
     int scan[8];
     int vpos[512];
+    // dynamic work: the producer takes chunk indices from the launch's counter
+    // and publishes them in order (cq_pub counts published slots, cq_done four
+    // per chunk the epilogue has finished); -1 ends the sequence
+    int cq[CQ];
+    unsigned cq_pub, cq_done;
+    int cbase[MAX_ENTRIES_CTRL + 1];   // first global chunk index of each entry
 };
 static_assert(sizeof(Ctrl) <= CTRL_BYTES, "control block");
 
@@ -173,22 +182,28 @@ constexpr int MAX_ENTRIES = 16;
 struct UmmaParams {
     UmmaEntry e[MAX_ENTRIES];
     int nentries, mp;              // mp: density columns per pass, the same for every entry
+    unsigned *counter;             // chunks taken so far (zero at launch)
 };
+static_assert(MAX_ENTRIES == MAX_ENTRIES_CTRL, "entries per launch");
 
 namespace {
 
-// This CTA's brick range of entry E.
-__device__ __forceinline__ void entry_range(const UmmaEntry &E, int64_t &beg, int64_t &end) {
+// Chunks of entry E: its part list (cost-balanced brick ranges, several per
+// CTA), or CHUNKS_PER_CTA even ranges per CTA.  CTAs take chunks dynamically,
+// in the order of a launch-wide counter.
+__device__ __forceinline__ int entry_chunks(const UmmaEntry &E) {
+    if (E.part) return E.nparts;
+    const int64_t k = (int64_t)CHUNKS_PER_CTA * gridDim.x;
+    return (int)(E.nbricks < k ? E.nbricks : k);
+}
+__device__ __forceinline__ void chunk_range(const UmmaEntry &E, int j, int64_t &beg, int64_t &end) {
     if (E.part) {
-        if ((int)blockIdx.x < E.nparts) {
-            beg = E.part[blockIdx.x];
-            end = E.part[blockIdx.x + 1];
-        } else {
-            beg = end = 0;
-        }
+        beg = E.part[j];
+        end = E.part[j + 1];
     } else {
-        beg = E.nbricks * blockIdx.x / gridDim.x;
-        end = E.nbricks * (blockIdx.x + 1) / gridDim.x;
+        const int nc = entry_chunks(E);
+        beg = E.nbricks * j / nc;
+        end = E.nbricks * (j + 1) / nc;
     }
 }
 
@@ -236,12 +251,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
     extern __shared__ __align__(1024) unsigned char sm[];
     Ctrl &c = *reinterpret_cast<Ctrl *>(sm + 2 * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int nloc = 0;                  // this CTA's bricks over all entries
-    for (int e = 0; e < P.nentries; ++e) {
-        int64_t b0, b1;
-        entry_range(P.e[e], b0, b1);
-        nloc += (int)(b1 - b0);
-    }
     const int mp = P.mp;
     const uint32_t kbytes = 512u * mp, jbytes = 256u * mp;
     volatile int *abort_flag = &c.abort_flag;
@@ -257,6 +266,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
         mbar_init(&c.runfree[1], 4);
         for (int w = 0; w < SWIN; ++w) c.wstaged[w] = 0;
         c.abort_flag = 0;
+        c.cq_pub = 0;
+        c.cq_done = 0;
+        c.cbase[0] = 0;
+        for (int e = 0; e < P.nentries; ++e) c.cbase[e + 1] = c.cbase[e] + entry_chunks(P.e[e]);
         mbar_fence_init();
     }
     if (warp == 1) tmem_alloc(&c.tmem_base, 512);
@@ -271,19 +284,50 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
         for (int e = 0; e < P.nentries; ++e)
             if (P.e[e].error) atomicExch(P.e[e].error, code);
     };
+    const int nchunks = c.cbase[P.nentries];
+    // global chunk ch -> entry e and its brick range
+    auto resolve = [&](int ch, int &e, int64_t &beg, int64_t &end) {
+        e = 0;
+        while (e + 1 < P.nentries && ch >= c.cbase[e + 1]) ++e;
+        chunk_range(P.e[e], ch - c.cbase[e], beg, end);
+    };
+    // the qr-th chunk of this CTA, as the producer published it; false at the
+    // end of the sequence or when the wait gives up
+    auto take_chunk = [&](int qr, int &e, int64_t &beg, int64_t &end) -> bool {
+        if (!counter_wait(&c.cq_pub, (unsigned)qr + 1u, abort_flag)) {
+            if (!*abort_flag) fail(11);
+            return false;
+        }
+        const int ch = c.cq[qr % CQ];
+        if (ch < 0) return false;
+        resolve(ch, e, beg, end);
+        return true;
+    };
 
-    if (nloc > 0 && warp == 0 && lane == 0) {
+    if (warp == 0 && lane == 0) {
         // ------------------------------------------------ producer
         int issued = 0;
         // the next brick's descriptor and record offset are loaded one
         // iteration ahead, so their latency overlaps the wait for a free stage
         int i = 0;
         bool stop = false;
-        for (int e = 0; e < P.nentries && !stop; ++e) {
-            const UmmaEntry &E = P.e[e];
+        for (int qr = 0; !stop; ++qr) {
+            // take the next chunk of the launch and publish it to the other
+            // roles (its queue slot is free once the epilogue finished chunk qr - CQ)
+            if (qr >= CQ && !counter_wait(&c.cq_done, 4u * (unsigned)(qr - CQ + 1), abort_flag)) {
+                if (!*abort_flag) fail(12);
+                break;
+            }
+            int ch = (int)atomicAdd(P.counter, 1u);
+            if (ch >= nchunks) ch = -1;
+            c.cq[qr % CQ] = ch;
+            counter_release_add(&c.cq_pub);
+            if (ch < 0) break;
+            int e;
             int64_t beg, end;
-            entry_range(E, beg, end);
+            resolve(ch, e, beg, end);
             if (beg >= end) continue;
+            const UmmaEntry &E = P.e[e];
             const BrickDesc *bricks = E.bricks;
             const int64_t *offsets = E.offsets;
             const uint32_t *store = E.store;
@@ -317,7 +361,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
         // no copy may still be landing when the CTA leaves
         for (int k = (issued > 2 ? issued - 2 : 0); k < issued; ++k)
             mbar_wait(&c.full[k & 1], (k >> 1) & 1, abort_flag);
-    } else if (nloc > 0 && warp == 1) {
+    } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         // The whole warp runs the loop and takes every wait (decisions made
         // warp-uniform); one elected lane issues the MMAs and the commit.
@@ -333,11 +377,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
         unsigned touched3 = 0, touched4 = 0;
         int i = 0;
         bool stop = false;
-        for (int e = 0; e < P.nentries && !stop; ++e) {
-            const UmmaEntry &E = P.e[e];
+        for (int qr = 0; !stop; ++qr) {
+            int e;
             int64_t beg, end;
-            entry_range(E, beg, end);
+            if (!take_chunk(qr, e, beg, end)) break;
             if (beg >= end) continue;
+            const UmmaEntry &E = P.e[e];
             const BrickDesc *bricks = E.bricks;
             // instruction descriptors of the entry (FP16 or BF16 halves)
             const uint32_t id_k = idesc_f16(64, RW, 0, E.bf16), idm_k = idesc_f16(64, RW, 1, E.bf16);
@@ -410,10 +455,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
             const int i = committed - 1;
             mbar_wait(&c.mmad[i & 1], (i >> 1) & 1, abort_flag);
         }
-    } else if (nloc > 0 && warp >= 2 && warp < 6) {
+    } else if (warp >= 2 && warp < 6) {
         // ------------------------------------------------ converters
         const int ct = threadIdx.x - 64;
-        for (int i = 0; i < nloc; ++i) {
+        int i = 0;                     // bricks of this CTA so far
+        int64_t left = 0;              // bricks left in the current chunk
+        for (int qr = 0;; ++i, --left) {
+            while (left == 0) {
+                int e;
+                int64_t beg, end;
+                if (!take_chunk(qr++, e, beg, end)) break;
+                left = end - beg;
+            }
+            if (left == 0) break;
             const int s = i & 1;
             if (!mbar_wait(&c.full[s], (i >> 1) & 1, abort_flag)) fail(6);
             // leave together: every converter thread must reach the same named barriers
@@ -473,7 +527,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
             if (lane == 0) mbar_arrive(&c.conv[s]);
             named_bar_sync(1, 128);   // vpos / scan reused by the next brick
         }
-    } else if (nloc > 0 && warp >= 6) {
+    } else if (warp >= 6) {
         // ------------------------------------------------ epilogue
         const int slice = warp & 3;
         const uint32_t tl = tmem + ((uint32_t)(slice * 32) << 16);
@@ -515,11 +569,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
         unsigned touched3 = 0, touched4 = 0;
         int i = 0;
         bool stop = false;
-        for (int e = 0; e < P.nentries && !stop; ++e) {
-            const UmmaEntry &E = P.e[e];
+        for (int qr = 0; !stop; ++qr) {
+            int e;
             int64_t beg, end;
-            entry_range(E, beg, end);
-            if (beg >= end) continue;
+            if (!take_chunk(qr, e, beg, end)) break;
+            const UmmaEntry &E = P.e[e];
             const BrickDesc *bricks = E.bricks;
             m = E.m; nb = E.nb; mtot = E.mtot; d0 = E.d0; Jacc = E.Jacc; Kacc = E.Kacc;
             inv = 1.0f / (E.vscale * density_scale(E.dmax_bits));
@@ -601,6 +655,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
                     }
                 }
             }
+            // this chunk's queue slot may be reused
+            __syncwarp();
+            if (lane == 0) counter_release_add(&c.cq_done);
         }
     }
     tc_fence_before();
@@ -630,7 +687,7 @@ int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s) {
         if (e != cudaSuccess) { set_error("memset dmax: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
         k_dmax<<<256, 256, 0, s>>>(L.D, (int64_t)L.m * nn, L.dmax_bits);
         mmax = L.m > mmax ? L.m : mmax;
-        const int g = L.part ? L.nparts : (L.nbricks < L.num_sms ? (int)L.nbricks : L.num_sms);
+        const int g = L.nbricks < L.num_sms ? (int)L.nbricks : L.num_sms;
         grid = g > grid ? g : grid;
     }
     e = cudaGetLastError();
@@ -656,6 +713,9 @@ int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s) {
         e = cudaGetLastError();
         if (e != cudaSuccess) { set_error("k_dbank: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
         if (p.nentries == 0) continue;
+        p.counter = Ls[0].counter;
+        e = cudaMemsetAsync(p.counter, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) { set_error("memset chunk counter: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
         k_jk_umma<<<grid, NTHREADS, SMEM_TOTAL, s>>>(p);
         e = cudaGetLastError();
         if (e != cudaSuccess) { set_error("k_jk_umma: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
@@ -696,7 +756,9 @@ int launch_jk_umma(const UmmaLaunch &L, cudaStream_t s) {
         E.error = L.error;
         int grid = L.num_sms;
         if (grid > L.nbricks) grid = (int)L.nbricks;
-        if (L.part) grid = L.nparts;
+        p.counter = L.counter;
+        e = cudaMemsetAsync(L.counter, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) { set_error("memset chunk counter: %s", cudaGetErrorString(e)); return ESMF_ERR_CUDA; }
         if (L.ev_start && d0 == 0) cudaEventRecord(L.ev_start, s);
         k_jk_umma<<<grid, NTHREADS, SMEM_TOTAL, s>>>(p);
         if (L.ev_stop && d0 + chunk >= L.m) cudaEventRecord(L.ev_stop, s);
