@@ -239,7 +239,7 @@ int esmf_fock_build(esmf_fock_t *h, int m, const double *D, double *J,
  * esmf_fock_build_batch -- esmf_fock_build for several handles (molecules of
  * different sizes, each with its own density count) in ONE persistent
  * tensor-core launch per pass of 16 densities (a single launch when every
- * m <= 16): every CTA walks its cost-balanced slice of each handle's bricks
+ * m <= 16): the CTAs take cost-balanced chunks of every handle's bricks
  * in turn, so small molecules share the GPU instead of each filling a launch
  * of its own.  The whole call allocates nothing once each handle has built
  * with at least its m before, and can then be captured in a CUDA graph.
@@ -268,9 +268,9 @@ int esmf_fock_build_batch(int count, esmf_fock_t *const *h, const int *m,
  * esmf_fock_build_shard -- the part of esmf_fock_build contributed by shard
  * `shard` of `nshards` contiguous slices of the handle's kept brick list.
  * The slices hold equal shares of the estimated contraction cost (the
- * per-brick cost model of the tensor kernel's CTA split), each cut moved to
+ * per-brick cost model of the tensor kernel's chunks), each cut moved to
  * the next item boundary of the brick order; on the tensor-core path each
- * shard gets its own cost-balanced CTA split (formed on the first build of
+ * shard gets its own cost-balanced chunks (formed on the first build of
  * that shard: that build allocates a few hundred bytes).  J, K, F and the
  * traces are linear in the integrals, so the element-wise sum of the outputs
  * of all shards (e.g. one all-reduce across GPUs, each holding a handle for

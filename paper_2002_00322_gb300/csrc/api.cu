@@ -91,7 +91,7 @@ struct esmf_fock {
     int nparts = 0;
     // host copy of the brick list's estimated cost prefix (cost_prefix[i] =
     // cost of bricks [0, i)) and item starts, for cost-balanced shards; the
-    // per-CTA split of each shard's range is built on first use
+    // chunks of each shard's range are built on first use
     std::vector<double> cost_prefix;
     std::vector<BrickDesc> hbricks;
     std::map<std::pair<int64_t, int64_t>, std::pair<int64_t *, int>> shard_parts;
@@ -726,7 +726,7 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
             if (!ck(cudaMemcpyAsync(h->offsets, roff.data(), sizeof(int64_t) * (nk + 1), cudaMemcpyHostToDevice, cs), "copy chunk offsets") ||
                 !ck(cudaMemsetAsync(h->scratch, 0, (size_t)h->scratch_bytes, cs), "clear scratch"))
                 return fail(ESMF_ERR_CUDA);
-            // each chunk's cost-balanced split over the tensor kernel's CTAs
+            // each scratch chunk's cost-balanced chunks for the tensor kernel
             for (size_t c = 0; c + 1 < ch.size(); ++c) {
                 std::vector<BrickDesc> sub(kept.begin() + ch[c], kept.begin() + ch[c + 1]);
                 const std::vector<int64_t> sp = balance_parts(sub, kChunksPerSM * h->num_sms);
@@ -1039,8 +1039,8 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
             L.bf16 = h->prec == ESMF_PREC_BF16X2; L.num_sms = h->num_sms; L.vscale = h->vscale;
             L.Jacc = h->Jacc; L.Kacc = h->Kacc; L.error = h->err_dev; L.counter = h->sched;
             L.chunk = chunk ? chunk : 16;
-            // CTA split of bricks [r0, r1): the whole list's, or the range's own
-            // cost-balanced one (chunks and shards), built once
+            // chunks of bricks [r0, r1) for the tensor kernel: the whole list's, or
+            // the range's own cost-balanced ones (scratch chunks and shards), built once
             auto set_parts = [&](int64_t r0, int64_t r1) -> int {
                 if (r0 == 0 && r1 == h->nbricks && h->parts && !tdirect) {
                     L.part = h->parts; L.nparts = h->nparts;

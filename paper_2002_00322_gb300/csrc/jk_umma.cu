@@ -164,14 +164,14 @@ __global__ void k_dbank(const double *D, int n, int nb, int m, int d0, int mp, c
 // One entry of a launch: the bricks of one handle contracted with one chunk of
 // at most 16 of its densities.  A launch holds up to MAX_ENTRIES entries
 // (several molecules, uneven basis sizes and density counts) and every CTA
-// walks its own slice of every entry in turn.
+// takes chunks of the entries from a launch-wide counter.
 struct UmmaEntry {
     const BrickDesc *bricks;
     int64_t nbricks;
     const int64_t *offsets;        // record start, in 32-bit words
     const uint32_t *store;
     const uint16_t *kbank, *jbank;
-    const int64_t *part;           // per-CTA brick ranges (nparts + 1), or null: even split by count
+    const int64_t *part;           // chunk brick ranges (nparts + 1), or null: even chunks by count
     int nparts, nb, m, d0, mtot, bf16;
     float vscale;
     const unsigned int *dmax_bits;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = c.tmem_base;
-    // A CTA that gives up leaves the rest of its slice of every entry
+    // A CTA that gives up leaves the rest of its chunks of every entry
     // unprocessed, so every entry of the launch is marked incomplete.
     auto fail = [&](int code) {
         *abort_flag = 1;
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_jk_umma(const __grid_constant__
 // Several handles in one persistent launch per pass of 16 densities: pass c
 // contracts density chunk c of every handle with more than 16c densities
 // (one launch when every m <= 16).  Each handle keeps its own density bank
-// and accumulators; every CTA walks its cost-balanced slice of each handle.
+// and accumulators; the CTAs take cost-balanced chunks of every handle.
 int launch_jk_umma_batch(const UmmaLaunch *Ls, int count, cudaStream_t s) {
     if (count < 1 || count > MAX_ENTRIES) {
         set_error("batch of %d handles outside [1, %d]", count, MAX_ENTRIES);
