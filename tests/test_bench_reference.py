@@ -23,3 +23,17 @@ def test_reference_arm_line():
     assert d["e2e"] == {"value": d["value"], "unit": "builds/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "stored_n200_m16"
+
+
+def test_traffic_record_matches_workload_and_source():
+    """The DRAM traffic the bench reports comes from the committed ncu record
+    of the same kernel, workload and precision, and only while the kernel's
+    source is the one that was captured; the committed records are current."""
+    sys.path.insert(0, ROOT)
+    import bench
+    recs = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    for kernel, rec in recs.items():
+        workload, prec = rec["workload"].rsplit(" ", 1)
+        assert bench.ncu_traffic(kernel, prec, workload) == rec["traffic_bytes_per_launch"], kernel
+        assert bench.ncu_traffic(kernel, prec, "precision_n400_m64") is None
+        assert bench.ncu_traffic(kernel, "bf16x2" if prec != "bf16x2" else "fp64", workload) is None
