@@ -855,7 +855,8 @@ def run_serving(args, quick=False):
            "config": {"workload": f"serving_{len(reqs)}req_pool{len(mols)}_n50-{args.serve_nmax}_m4-32",
                       "budget_gb": args.serve_budget_gb, "max_inflight": args.serve_inflight,
                       "precision": "fp16x2", "graphs": True, "batched_ticks": True,
-                      "eviction": "largest idle first"}}
+                      "eviction": "idle molecules largest first; a molecule with queued requests only "
+                                  "after a new handle has waited 30 s, furthest next use first"}}
     with Server(budget, max_inflight=args.serve_inflight, precision="fp16x2", use_graphs=True, batch=True,
                 evict_largest=True, device=local) as srv:
         ids = [srv.register(w.basis, w.tol) for w in mols]
@@ -889,6 +890,7 @@ def run_serving(args, quick=False):
                           "creates": st_closed["creates"], "evictions": st_closed["evictions"],
                           "graph_launches": st_closed["graph_launches"],
                           "batch_launches": st_closed["batch_launches"],
+                          "tick_graph_launches": st_closed["tick_graph_launches"],
                           "batched_builds": st_closed["batched_builds"],
                           "peak_inflight": st_closed["peak_inflight"], "p50_ms": round(st_closed["p50_ms"], 2),
                           "p99_ms": round(st_closed["p99_ms"], 2)}
@@ -898,6 +900,7 @@ def run_serving(args, quick=False):
                         "creates": st_open["creates"], "evictions": st_open["evictions"],
                         "graph_launches": st_open["graph_launches"],
                         "batch_launches": st_open["batch_launches"],
+                        "tick_graph_launches": st_open["tick_graph_launches"],
                         "peak_inflight": st_open["peak_inflight"], "failed": st_open["failed"]}
     out["density_builds"] = int(sum(m for (_, m, _) in reqs))
     if quick:
