@@ -279,6 +279,61 @@ class Oracle:
         K = np.einsum("Ppr,krs,Pqs->kpq", B, D, B, optimize=True)
         return J, K
 
+    def collocation(self, points):
+        """X[p, P] = phi_p(r_P), the normalised contracted s function p at grid
+        point r_P: sum_k w_pk exp(-a_pk |r_P - A_p|^2), a plain loop."""
+        self._no_p("collocation")
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+        off = np.concatenate([[0], np.cumsum(self.nprim)])
+        X = np.zeros((self.n, pts.shape[0]))
+        for p in range(self.n):
+            d2 = ((pts - self.center[p]) ** 2).sum(axis=1)
+            for k in range(off[p], off[p + 1]):
+                X[p] += self.w[k] * np.exp(-self.exps[k] * d2)
+        return X
+
+    def thc_fit(self, points, tol, ridge):
+        """Least-squares tensor hypercontraction of the kept integrals, the
+        other acceleration route the paper names (Sec. I), in the LS-THC form
+        of Parrish, Hohenstein, Martinez and Sherrill (J. Chem. Phys. 137,
+        224106, 2012), restated:
+            (pq|rs) ~ sum_PQ X_pP X_qP Z_PQ X_rQ X_sQ,   X_pP = phi_p(r_P),
+        Z minimising the Frobenius error over the kept integrals through its
+        normal equations S Z S = E, with
+            E_PQ = sum_pqrs X_pP X_qP (pq|rs) X_rQ X_sQ   (Schwarz-kept quartets),
+            S_PQ = (sum_p X_pP X_pQ)^2,
+        regularised as Z = (S + lam I)^-1 E (S + lam I)^-1, lam = ridge * max_P S_PP
+        (ridge 0: the plain least-squares fit), symmetrised as (Z + Z^T)/2.  E is formed from the grouped
+        Coulomb build over the rank-one densities x_Q x_Q^T (one per grid point):
+        E_PQ = x_P^T J[x_Q x_Q^T] x_P.  Returns (X, Z)."""
+        X = self.collocation(points)
+        G = X.shape[1]
+        DQ = np.einsum("pQ,qQ->Qpq", X, X)
+        JQ, _, _ = self.jk_unique(DQ, tol)
+        E = np.einsum("pP,qP,Qpq->PQ", X, X, JQ)
+        S = (X.T @ X) ** 2
+        Sr = S + ridge * S.diagonal().max() * np.eye(G)
+        Z = np.linalg.solve(Sr, np.linalg.solve(Sr, E).T).T
+        return X, 0.5 * (Z + Z.T)          # Z is symmetric; drop the solves' rounding asymmetry
+
+    @staticmethod
+    def thc_tensor(X, Z):
+        """The hypercontracted integral tensor V[p, q, r, s] = sum_PQ X_pP X_qP Z_PQ X_rQ X_sQ."""
+        n, G = X.shape
+        X2 = np.einsum("pP,qP->pqP", X, X).reshape(n * n, G)
+        return (X2 @ Z @ X2.T).reshape(n, n, n, n)
+
+    def jk_thc(self, D, points, tol, ridge):
+        """J and K of Eq. (J_and_K) over the hypercontracted integrals of
+        thc_fit: J_k[p][q] = sum_rs D_k[r][s] V_pqrs, K_k[p][r] = sum_qs
+        D_k[q][s] V_pqrs (the brute loop's index order, any D).  Returns (J, K)."""
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        X, Z = self.thc_fit(points, tol, ridge)
+        V = self.thc_tensor(X, Z)
+        J = np.einsum("pqrs,krs->kpq", V, D)
+        K = np.einsum("pqrs,kqs->kpr", V, D)
+        return J, K
+
     @staticmethod
     def fock_traces(D, J, K):
         D = np.ascontiguousarray(D, dtype=np.float64)

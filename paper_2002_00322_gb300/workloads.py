@@ -250,6 +250,25 @@ def even_tempered_aux(basis: Basis, count=7, first=0.2, ratio=2.5):
     return np.repeat(cen, et.size, axis=0), np.tile(et, cen.shape[0])
 
 
+def thc_grid(basis: Basis, radii=(0.6, 1.4), corner=1.0):
+    """Grid points for tensor hypercontraction: on every distinct center, the
+    center itself, the six points +-x, +-y, +-z at each radius (bohr) and, if
+    corner > 0, the eight cube-corner directions at distance corner (21
+    points per center with the defaults).  Returns (n_points, 3)."""
+    cen = np.unique(basis.center, axis=0)
+    axes = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=np.float64)
+    corners = np.array([[a, b, c] for a in (-1, 1) for b in (-1, 1) for c in (-1, 1)],
+                       dtype=np.float64) / np.sqrt(3.0)
+    pts = []
+    for c in cen:
+        pts.append(c[None, :])
+        for r in radii:
+            pts.append(c + r * axes)
+        if corner > 0:
+            pts.append(c + corner * corners)
+    return np.ascontiguousarray(np.concatenate(pts, axis=0), dtype=np.float64)
+
+
 # ---------------------------------------------------------------- ESMF state
 @dataclass
 class EsmfState:
