@@ -325,6 +325,68 @@ def sub_df(fock, W, dev, stream, alu_peaks, steps=3):
     return out
 
 
+def sub_thc(fock, W, dev, stream, alu_peaks, steps=3):
+    """stored_n200_m16 with least-squares tensor-hypercontracted integrals over
+    13 grid points per center (the center, +-x, +-y, +-z at 0.6 and 1.4 bohr:
+    1300 points; ridge 1e-8; the fit from the Schwarz-kept integrals at the
+    workload's tol): builds/s in FP64 and FP32 GEMMs, create time (the fit's
+    exact grouped builds and Cholesky factor included), and the fit's error
+    against the stored exact FP64 oracle build."""
+    import torch
+    w = W.stored()
+    n, m = w.basis.n, w.m
+    pts = W.thc_grid(w.basis, radii=(0.6, 1.4), corner=0.0)
+    G = int(pts.shape[0])
+    ridge = 1e-8
+    g = os.path.join(ROOT, "tests", "golden", "c2_stored_n200_m16.npz")
+    gd = np.load(g) if os.path.exists(g) else None
+    out = {"n_grid": G, "grid": "13 points per center: the center and +-x, +-y, +-z at 0.6 and 1.4 bohr",
+           "ridge": ridge}
+    for prec in ("fp64", "fp32"):
+        with fock.FockBuilder(w.basis, w.tol, "thc", prec, device=dev.index, grid=pts, ridge=ridge) as fb:
+            st = fb.stats()
+            D = torch.from_numpy(w.D).to(dev)
+            J, K, F = torch.empty_like(D), torch.empty_like(D), torch.empty_like(D)
+            t = torch.empty(m, dtype=torch.float64, device=dev)
+            ms, ks = timed_builds(fock, fb, m, D, J, K, F, t, stream, steps, 1)
+            # per density: X^T D (2 G n^2), (X^T D) X (2 G^2 n), Z y (2 G^2),
+            # X diag(z) X^T (2 n^2 G), X (Z o M) (2 G^2 n), (.) X^T (2 n^2 G)
+            flops = m * (6 * G * n * n + 4 * G * G * n + 2 * G * G)
+            ach = flops / ks / 1e12
+            rec = {"dtype": DTYPES[prec], "ms_per_step": round(ms, 3), "value": round(1e3 / ms, 3),
+                   "setup_ms": round(st["create_ms"], 1), "factor_bytes": st["store_bytes"],
+                   "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": alu_peaks[prec],
+                                "unit": "TFLOP/s", "frac": round(ach / alu_peaks[prec], 4), "traffic": None,
+                                "peak_source": f"measured {prec.upper()} FMA rate (esmf_measure_fma_peak)",
+                                "kernel": "cuBLAS GEMMs (5 per density) + elementwise kernels",
+                                "kernel_ms": round(ks * 1e3, 3), "algorithmic_flops": flops}}
+            if gd is not None:
+                Jr = np.zeros((m, n, n))
+                il = np.tril_indices(n)
+                Jr[:, il[0], il[1]] = gd["J_lower"]
+                Jr[:, il[1], il[0]] = gd["J_lower"]
+                Jh, Kh = J.cpu().numpy(), K.cpu().numpy()
+                rel = lambda x, r: float(np.linalg.norm(x - r) / max(np.linalg.norm(r), 1e-300))
+                rec["fit_error_vs_exact_oracle"] = {"J_max": max(rel(Jh[k], Jr[k]) for k in range(m)),
+                                                    "K_max": max(rel(Kh[k], gd["K"][k]) for k in range(m))}
+            out[prec] = rec
+    return out
+
+
+def run_thc(args):
+    """The tensor-hypercontracted stored_n200_m16 sub-record alone (one JSON line)."""
+    import torch
+    from paper_2002_00322_gb300 import fock
+    from paper_2002_00322_gb300 import workloads as W
+    rank, world, local = env_rank()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rec = sub_thc(fock, W, dev, torch.cuda.current_stream(), measured_alu_peaks(local), steps=args.steps)
+    print(json.dumps({"workload": "stored_n200_m16_thc", **rec}), flush=True)
+
+
 def run_ours(args):
     import torch
     from paper_2002_00322_gb300 import fock
@@ -480,6 +542,7 @@ def run_ours(args):
         subs["direct_n2000_m32_fp32"] = sub_direct(fock, W, dev, stream, alu_peaks)
         subs["direct_n2000_m32_fp16x2"] = sub_direct(fock, W, dev, stream, alu_peaks, prec="fp16x2")
         subs["stored_n200_m16_density_fitted"] = sub_df(fock, W, dev, stream, alu_peaks)
+        subs["stored_n200_m16_thc"] = sub_thc(fock, W, dev, stream, alu_peaks)
         subs["sp_n100_m16"] = sub_angular(fock, W, dev, stream, W.sp_random(25, 16, 11), "25 centers x (s, p), 3 primitives")
         subs["spd_n100_m16"] = sub_angular(fock, W, dev, stream, W.spd_random(10, 16, 11, nprim=2),
                                            "10 centers x (s, p, Cartesian d), 2 primitives")
@@ -924,8 +987,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving", action="store_true", help="run the serving workload instead")
-    ap.add_argument("--workload", default="stored", choices=["stored", "direct"],
-                    help="stored: the 200-function stored build (default); direct: the integral-direct ribbon")
+    ap.add_argument("--workload", default="stored", choices=["stored", "direct", "thc"],
+                    help="stored: the 200-function stored build (default); direct: the integral-direct ribbon; "
+                         "thc: its tensor-hypercontracted sub-record alone")
     ap.add_argument("--direct-length", type=int, default=250)
     ap.add_argument("--direct-precision", default="fp32", choices=["fp32", "fp16x2", "bf16x2"])
     ap.add_argument("--serve-requests", type=int, default=256)
@@ -944,6 +1008,8 @@ def main():
         run_reference(args)
     elif args.workload == "direct":
         run_direct(args)
+    elif args.workload == "thc":
+        run_thc(args)
     else:
         run_ours(args)
 

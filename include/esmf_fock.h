@@ -50,6 +50,7 @@ extern "C" {
 #define ESMF_MODE_DIRECT  1   /* integrals recomputed inside every build      */
 #define ESMF_MODE_AUTO    2   /* stored if it fits the device budget          */
 #define ESMF_MODE_DF      3   /* density fitting (esmf_fock_create_df)        */
+#define ESMF_MODE_THC     4   /* tensor hypercontraction (esmf_fock_create_thc) */
 
 /* arithmetic of the integral x density products (accumulation is FP64) */
 #define ESMF_PREC_FP64    0   /* FP64 integrals, FP64 products                */
@@ -94,7 +95,7 @@ typedef struct {
     int64_t n_stored;           /* integrals held in the store (stored mode)   */
     int64_t store_bytes;        /* bytes of the integral store                 */
     int64_t device_bytes;       /* all device memory held by the handle        */
-    int32_t mode;               /* ESMF_MODE_STORED or ESMF_MODE_DIRECT        */
+    int32_t mode;               /* ESMF_MODE_STORED, _DIRECT, _DF or _THC      */
     int32_t precision;          /* ESMF_PREC_*                                 */
     double  schwarz_tol;
     double  create_ms;          /* wall time of esmf_fock_create               */
@@ -213,6 +214,55 @@ typedef struct {
 } esmf_aux_t;
 int esmf_fock_create_df(const esmf_basis_t *basis, const esmf_aux_t *aux, int precision,
                         int device, esmf_fock_t **out);
+
+/*
+ * esmf_fock_create_thc -- a handle whose builds use least-squares tensor
+ * hypercontraction (THC) of the integrals, the other acceleration the paper
+ * names as future work (Sec. I), in the LS-THC form of Parrish, Hohenstein,
+ * Martinez and Sherrill (J. Chem. Phys. 137, 224106, 2012):
+ *   (pq|rs) ~ sum_PQ X_pP X_qP Z_PQ X_rQ X_sQ,   X_pP = phi_p(r_P),
+ * over caller-chosen grid points r_P.  At create time, in FP64: the
+ * collocation X on the device; the Coulomb matrix
+ *   E_PQ = sum_pqrs X_pP X_qP (pq|rs) X_rQ X_sQ   (Schwarz-kept quartets)
+ * from the library's own grouped builds over the rank-one densities
+ * x_Q x_Q^T (an internal ESMF_MODE_AUTO FP64 handle with schwarz_tol and
+ * budget_bytes, destroyed before return; 64 grid points per build);
+ * S_PQ = (sum_p X_pP X_pQ)^2; and the regularised least-squares fit
+ *   Z = (S + lam I)^-1 E (S + lam I)^-1,   lam = ridge * max_P S_PP,
+ * through a host Cholesky factor of S + lam I and four device triangular
+ * solves, symmetrised to the last bit.  Every build is then dense GEMMs and
+ * elementwise kernels (Eq. J_and_K over the fitted integrals, any D):
+ *   M_k = X^T D_k X,   J_k = X diag(Z diag(M_k)) X^T,   K_k = X (Z o M_k) X^T.
+ * esmf_fock_build and esmf_fock_build_host accept the handle (m densities per
+ * build as usual, in batches whose work fits about 1 GiB); the batched,
+ * shard, no-alloc and autotune entries reject it (UNSUPPORTED).
+ *   basis        as for esmf_fock_create (s functions)
+ *   grid         host grid points (read during this call)
+ *   schwarz_tol  >= 0: screening of the exact integrals behind E
+ *   ridge        >= 0, finite: relative regularisation (0: the plain least-
+ *                squares fit; 1e-8 keeps S + lam I conditioned to about 1e8,
+ *                so that rounding in E and S moves J and K by ~1e-8 relative)
+ *   precision    ESMF_PREC_FP64 or ESMF_PREC_FP32 (build GEMM arithmetic;
+ *                the fit is always formed in FP64)
+ *   device, budget_bytes, out   as for esmf_fock_create
+ * Cost: the fit takes n_grid / 64 exact grouped builds and O(n_grid^3) host
+ * work for the Cholesky factor.  Device memory: X (N n_grid) and Z
+ * (n_grid^2) in the build arithmetic, plus per-build work of about
+ * m (N n_grid + n_grid^2) elements (at most about 1 GiB); during create also
+ * the internal handle and four n_grid^2 FP64 matrices.
+ * Errors: INVALID_ARG (bad basis or grid, a negative or non-finite tol or
+ * ridge, or S + lam I not numerically positive definite: grid points that
+ * the others reproduce), UNSUPPORTED (split 16-bit precisions), OOM, CUDA,
+ * TIMEOUT (a bounded wait of the fit's builds expired).
+ */
+#define ESMF_MAX_GRID 8192
+typedef struct {
+    int32_t       n_grid;     /* number of grid points, 1 .. ESMF_MAX_GRID   */
+    const double *points;     /* n_grid x 3, bohr, finite                     */
+} esmf_grid_t;
+int esmf_fock_create_thc(const esmf_basis_t *basis, const esmf_grid_t *grid, double schwarz_tol,
+                         double ridge, int precision, int device, int64_t budget_bytes,
+                         esmf_fock_t **out);
 
 /*
  * esmf_fock_build -- one grouped pass over the (stored or recomputed)

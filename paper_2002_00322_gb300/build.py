@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libesmf_fock.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "setup.cu", "jk_cuda.cu", "jk_umma.cu", "noalloc.cu", "server.cu", "energy.cu", "peak.cu", "df.cu", "angular.cu"]
+SOURCES = ["api.cu", "setup.cu", "jk_cuda.cu", "jk_umma.cu", "noalloc.cu", "server.cu", "energy.cu", "peak.cu", "df.cu", "angular.cu", "thc.cu"]
 
 
 def nvcc():

@@ -81,6 +81,13 @@ struct esmf_fock {
     void *dfB = nullptr, *dfB2 = nullptr;
     void *dfDt = nullptr, *dfJt = nullptr, *dfKt = nullptr, *dfg = nullptr, *dfY = nullptr;
     int df_m = 0;
+    // tensor hypercontraction (mode ESMF_MODE_THC): grid size, collocation X
+    // and fitted Z (arithmetic type), per-build work for up to thc_m densities
+    int thc_G = 0;
+    void *thcX = nullptr, *thcZ = nullptr;
+    void *thcDt = nullptr, *thcA = nullptr, *thcM = nullptr, *thcy = nullptr, *thcz = nullptr;
+    void *thcJt = nullptr, *thcKt = nullptr;
+    int thc_m = 0;
     std::vector<std::pair<int, int>> tuned;   // (m, densities per pass) picked by esmf_fock_autotune
     int force_chunk = 0;                      // set while the autotuner times a candidate
     int num_sms = 0;
@@ -261,6 +268,8 @@ void release(esmf_fock *h) {
     cudaFree(h->dw); cudaFree(h->dwb);
     cudaFree(h->dfB); cudaFree(h->dfB2); cudaFree(h->dfDt); cudaFree(h->dfJt); cudaFree(h->dfKt);
     cudaFree(h->dfg); cudaFree(h->dfY);
+    cudaFree(h->thcX); cudaFree(h->thcZ); cudaFree(h->thcDt); cudaFree(h->thcA); cudaFree(h->thcM);
+    cudaFree(h->thcy); cudaFree(h->thcz); cudaFree(h->thcJt); cudaFree(h->thcKt);
     df_cublas_destroy(h->cublas);
     cudaFree(h->sD); cudaFree(h->sJ); cudaFree(h->sK); cudaFree(h->sF); cudaFree(h->st);
     if (h->done) cudaEventDestroy(h->done);
@@ -797,10 +806,11 @@ static int create_impl(const esmf_basis_t *basis, const int32_t *cart, double to
 
 extern "C" {
 
-// Cholesky factor V = L L^T (lower, row-major, FP64) and L^-1, on the host;
-// false when V is not numerically positive definite (a pivot at or below
-// 1e-13 of its diagonal element: an auxiliary that the others reproduce).
-static bool cholesky_inverse(int n, std::vector<double> &V, std::vector<double> &Linv) {
+// Cholesky factor V = L L^T in place (lower triangle, row-major, FP64; the
+// entries above the diagonal keep V's), on the host; false when V is not
+// numerically positive definite (a pivot at or below 1e-13 of its diagonal
+// element: a function that the others reproduce).
+static bool cholesky_factor(int n, std::vector<double> &V) {
     for (int j = 0; j < n; ++j) {
         const double vjj = V[(size_t)j * n + j];
         double d = vjj;
@@ -814,6 +824,12 @@ static bool cholesky_inverse(int n, std::vector<double> &V, std::vector<double> 
             V[(size_t)i * n + j] = x / l;
         }
     }
+    return true;
+}
+
+// Cholesky factor V = L L^T (as cholesky_factor) and L^-1, on the host.
+static bool cholesky_inverse(int n, std::vector<double> &V, std::vector<double> &Linv) {
+    if (!cholesky_factor(n, V)) return false;
     // forward substitution for each column of the identity: L X = I
     Linv.assign((size_t)n * n, 0.0);
     for (int c = 0; c < n; ++c)
@@ -936,9 +952,214 @@ int esmf_fock_create_df(const esmf_basis_t *basis, const esmf_aux_t *aux, int pr
     return ESMF_OK;
 }
 
+int esmf_fock_create_thc(const esmf_basis_t *basis, const esmf_grid_t *grid, double schwarz_tol, double ridge,
+                         int precision, int device, int64_t budget_bytes, esmf_fock_t **out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!out) { set_error("out is NULL"); return ESMF_ERR_INVALID_ARG; }
+    *out = nullptr;
+    int64_t nprim_tot = 0;
+    RET(check_basis(basis, &nprim_tot));
+    if (!grid || grid->n_grid <= 0 || grid->n_grid > ESMF_MAX_GRID || !grid->points) {
+        set_error("grid missing, empty or above %d points", ESMF_MAX_GRID);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    for (int P = 0; P < 3 * grid->n_grid; ++P)
+        if (!is_finite(grid->points[P])) { set_error("grid point %d not finite", P / 3); return ESMF_ERR_INVALID_ARG; }
+    if (!(schwarz_tol >= 0.0) || !is_finite(schwarz_tol) || !(ridge >= 0.0) || !is_finite(ridge) || budget_bytes < 0) {
+        set_error("schwarz_tol and ridge must be finite and >= 0, budget_bytes >= 0");
+        return ESMF_ERR_INVALID_ARG;
+    }
+    if (precision != ESMF_PREC_FP64 && precision != ESMF_PREC_FP32) {
+        set_error("tensor hypercontraction runs in FP64 or FP32");
+        return precision >= ESMF_PREC_FP16X2 && precision <= ESMF_PREC_F32X2 ? ESMF_ERR_UNSUPPORTED : ESMF_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("device %d not available (%d devices)", device, ndev);
+        return ESMF_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    if (!g.ok) { set_error("cudaSetDevice(%d) failed", device); return ESMF_ERR_CUDA; }
+    esmf_fock *h = new (std::nothrow) esmf_fock();
+    if (!h) { set_error("host allocation failed"); return ESMF_ERR_OOM; }
+    const int n = basis->n_basis, G = grid->n_grid;
+    h->device = device; h->n = n; h->prec = precision; h->mode = ESMF_MODE_THC; h->tol = schwarz_tol;
+    h->nb = (n + BLK - 1) / BLK;
+    h->np = h->nb * BLK;
+    h->thc_G = G;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_error("cudaStreamCreate failed");
+        return ESMF_ERR_CUDA;
+    }
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } cs_guard{cs};
+    // rank-one densities per grouped Coulomb build of the fit
+    const int MQ = G < 64 ? G : 64;
+    const size_t nn = (size_t)n * n, nG = (size_t)n * G, GG = (size_t)G * G;
+    const size_t es = precision == ESMF_PREC_FP32 ? 4 : 8;
+    double *pts = nullptr, *X = nullptr, *Dq = nullptr, *Jq = nullptr, *Kq = nullptr, *R = nullptr, *E = nullptr,
+           *C = nullptr, *L = nullptr;
+    esmf_fock_t *hx = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(cs);
+        if (hx) esmf_fock_destroy(hx);
+        hx = nullptr;
+        cudaFree(pts); cudaFree(X); cudaFree(Dq); cudaFree(Jq); cudaFree(Kq); cudaFree(R); cudaFree(E);
+        cudaFree(C); cudaFree(L);
+    };
+    auto fail = [&](int code) { cleanup(); cudaGetLastError(); release(h); return code; };
+    int rc;
+    if ((rc = upload_basis(h, basis, nprim_tot, cs))) return fail(rc);
+    if ((rc = df_cublas_create(&h->cublas))) return fail(rc);
+    if (cudaMalloc(&pts, sizeof(double) * 3 * G) || cudaMalloc(&X, sizeof(double) * nG) ||
+        cudaMalloc(&Dq, sizeof(double) * MQ * nn) || cudaMalloc(&Jq, sizeof(double) * MQ * nn) ||
+        cudaMalloc(&Kq, sizeof(double) * MQ * nn) || cudaMalloc(&R, sizeof(double) * MQ * nG) ||
+        cudaMalloc(&E, sizeof(double) * GG) || cudaMalloc(&C, sizeof(double) * GG) ||
+        cudaMalloc(&L, sizeof(double) * GG)) {
+        cudaGetLastError();
+        set_error("hypercontraction set-up memory (%zu bytes per grid matrix)", sizeof(double) * GG);
+        return fail(ESMF_ERR_OOM);
+    }
+    if (cudaMemcpyAsync(pts, grid->points, sizeof(double) * 3 * G, cudaMemcpyHostToDevice, cs)) {
+        set_error("copy grid failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    if ((rc = launch_thc_collocate(h->dev(), G, pts, X, cs))) return fail(rc);
+    // E from the exact screened integrals: grouped Coulomb builds over the
+    // rank-one densities x_Q x_Q^T, MQ grid points per build
+    if ((rc = esmf_fock_create(basis, schwarz_tol, ESMF_MODE_AUTO, ESMF_PREC_FP64, device, budget_bytes, &hx)))
+        return fail(rc);
+    for (int q0 = 0; q0 < G; q0 += MQ) {
+        const int mq = G - q0 < MQ ? G - q0 : MQ;
+        if ((rc = launch_thc_rank_one(n, G, q0, mq, X, Dq, cs))) return fail(rc);
+        if ((rc = esmf_fock_build(hx, mq, Dq, Jq, Kq, nullptr, nullptr, cs))) return fail(rc);
+        if ((rc = thc_coulomb_columns(h->cublas, n, G, q0, mq, X, Jq, R, E, cs))) return fail(rc);
+    }
+    h->n_kept_unique = hx->n_kept_unique;
+    if ((rc = thc_gram(h->cublas, n, G, X, C, cs))) return fail(rc);
+    std::vector<double> hS(GG), hE(GG);
+    if (cudaMemcpyAsync(hS.data(), C, sizeof(double) * GG, cudaMemcpyDeviceToHost, cs) ||
+        cudaMemcpyAsync(hE.data(), E, sizeof(double) * GG, cudaMemcpyDeviceToHost, cs) || cudaStreamSynchronize(cs)) {
+        set_error("fit matrices copy failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    if (*hx->err_host) {
+        set_error("a bounded wait expired in the Coulomb builds of the fit");
+        return fail(ESMF_ERR_TIMEOUT);
+    }
+    esmf_fock_destroy(hx);
+    hx = nullptr;
+    // S = (X^T X) o (X^T X) + lam I and E, both made exactly symmetric
+    double smax = 0.0;
+    for (int i = 0; i < G; ++i)
+        for (int j = 0; j <= i; ++j) {
+            const double c = 0.5 * (hS[(size_t)i * G + j] + hS[(size_t)j * G + i]);
+            const double e = 0.5 * (hE[(size_t)i * G + j] + hE[(size_t)j * G + i]);
+            hS[(size_t)i * G + j] = hS[(size_t)j * G + i] = c * c;
+            hE[(size_t)i * G + j] = hE[(size_t)j * G + i] = e;
+            if (i == j && c * c > smax) smax = c * c;
+        }
+    const double lam = ridge * smax;
+    for (int i = 0; i < G; ++i) hS[(size_t)i * G + i] += lam;
+    if (!cholesky_factor(G, hS)) {
+        set_error("S + lam I is not positive definite (grid points that the others reproduce; raise ridge)");
+        return fail(ESMF_ERR_INVALID_ARG);
+    }
+    if (cudaMemcpyAsync(L, hS.data(), sizeof(double) * GG, cudaMemcpyHostToDevice, cs) ||
+        cudaMemcpyAsync(E, hE.data(), sizeof(double) * GG, cudaMemcpyHostToDevice, cs)) {
+        set_error("copy of the fit matrices failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    if ((rc = dalloc(h, (unsigned char **)&h->thcZ, GG * es))) return fail(rc);
+    if ((rc = thc_solve_z(h->cublas, G, L, E, es == 4, h->thcZ, cs))) return fail(rc);
+    if (es == 4) {
+        if ((rc = dalloc(h, (unsigned char **)&h->thcX, nG * es))) return fail(rc);
+        if ((rc = launch_thc_convert((int64_t)nG, X, (float *)h->thcX, cs))) return fail(rc);
+    } else {
+        h->thcX = X;                      // the FP64 collocation itself
+        h->device_bytes += (int64_t)(nG * es);
+        X = nullptr;
+    }
+    h->store_bytes = (int64_t)((nG + GG) * es);
+    if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc((void **)&h->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&h->err_dev, h->err_host, 0) != cudaSuccess) {
+        set_error("event / error flag creation failed");
+        return fail(ESMF_ERR_CUDA);
+    }
+    *h->err_host = 0;
+    cleanup();
+    if (cudaGetLastError() != cudaSuccess) { set_error("hypercontraction set-up kernels failed"); release(h); return ESMF_ERR_CUDA; }
+    h->create_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return ESMF_OK;
+}
+
 }  // extern "C"
 
 namespace {
+
+// One hypercontracted build: per-build work grown for up to m densities
+// (batches of densities whose work stays within about 1 GiB), then the GEMM
+// sequence of thc.cu per batch.
+int build_thc(esmf_fock_t *h, int m, const double *D, double *J, double *K, double *F, double *traces,
+              cudaStream_t s) {
+    const size_t es = h->prec == ESMF_PREC_FP32 ? 4 : 8;
+    const size_t n = (size_t)h->n, G = (size_t)h->thc_G, nn = n * n, nG = n * G, GG = G * G;
+    const size_t per = nG + GG + 2 * G + 2 * nn + (es == 4 ? nn : 0);
+    int mc = (int)std::max<size_t>(1, std::min<size_t>((size_t)m, ((size_t)1 << 30) / (es * per)));
+    if (mc > h->thc_m) {
+        const size_t o = (size_t)h->thc_m;
+        dfree(h, (unsigned char **)&h->thcDt, es == 4 ? o * nn * es : 1);
+        dfree(h, (unsigned char **)&h->thcA, o * nG * es);
+        dfree(h, (unsigned char **)&h->thcM, o * GG * es);
+        dfree(h, (unsigned char **)&h->thcy, o * G * es);
+        dfree(h, (unsigned char **)&h->thcz, o * G * es);
+        dfree(h, (unsigned char **)&h->thcJt, o * nn * es);
+        dfree(h, (unsigned char **)&h->thcKt, o * nn * es);
+        h->thc_m = 0;
+        const size_t c = (size_t)mc;
+        RET(dalloc(h, (unsigned char **)&h->thcDt, es == 4 ? c * nn * es : 1));
+        RET(dalloc(h, (unsigned char **)&h->thcA, c * nG * es));
+        RET(dalloc(h, (unsigned char **)&h->thcM, c * GG * es));
+        RET(dalloc(h, (unsigned char **)&h->thcy, c * G * es));
+        RET(dalloc(h, (unsigned char **)&h->thcz, c * G * es));
+        RET(dalloc(h, (unsigned char **)&h->thcJt, c * nn * es));
+        RET(dalloc(h, (unsigned char **)&h->thcKt, c * nn * es));
+        h->thc_m = mc;
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (h->timing && h->ev_used < 65536) {
+        if (h->ev_used == h->ev_pool.size()) {
+            cudaEvent_t x, y;
+            CKR(cudaEventCreate(&x));
+            CKR(cudaEventCreate(&y));
+            h->ev_pool.push_back({x, y});
+        }
+        ev0 = h->ev_pool[h->ev_used].first;
+        ev1 = h->ev_pool[h->ev_used].second;
+        ++h->ev_used;
+        CKR(cudaEventRecord(ev0, s));
+    }
+    for (int k0 = 0; k0 < m; k0 += mc) {
+        const int kc = m - k0 < mc ? m - k0 : mc;
+        const size_t off = (size_t)k0 * nn;
+        ThcBuild a;
+        a.cublas = h->cublas; a.n = h->n; a.G = h->thc_G; a.m = kc; a.fp32 = es == 4;
+        a.X = h->thcX; a.Z = h->thcZ; a.D = D + off;
+        a.Dt = h->thcDt; a.A = h->thcA; a.M = h->thcM; a.y = h->thcy; a.z = h->thcz; a.Jt = h->thcJt; a.Kt = h->thcKt;
+        a.J = J + off; a.K = K + off; a.F = F ? F + off : nullptr; a.traces = traces ? traces + k0 : nullptr;
+        RET(thc_build(a, s));
+    }
+    if (ev1) CKR(cudaEventRecord(ev1, s));
+    return ESMF_OK;
+}
 
 // One density-fitted build: per-build work grown for m densities, then the
 // GEMM sequence of df.cu.
@@ -947,7 +1168,8 @@ int build_df(esmf_fock_t *h, int m, const double *D, double *J, double *K, doubl
     const size_t es = h->prec == ESMF_PREC_FP32 ? 4 : 8;
     const size_t nn = (size_t)h->n * h->n;
     if (m > h->df_m) {
-        dfree(h, (unsigned char **)&h->dfDt, h->df_m * nn * es); dfree(h, (unsigned char **)&h->dfJt, h->df_m * nn * es);
+        dfree(h, (unsigned char **)&h->dfDt, es == 4 ? h->df_m * nn * es : 1);
+        dfree(h, (unsigned char **)&h->dfJt, h->df_m * nn * es);
         dfree(h, (unsigned char **)&h->dfKt, h->df_m * nn * es); dfree(h, (unsigned char **)&h->dfg, (size_t)h->df_m * h->naux * es);
         h->df_m = 0;
         RET(dalloc(h, (unsigned char **)&h->dfDt, es == 4 ? m * nn * es : 1));
@@ -993,6 +1215,10 @@ int build_range(esmf_fock_t *h, int64_t b0, int64_t b1, int m, const double *D, 
     if (h->mode == ESMF_MODE_DF) {
         if (b0 != 0 || b1 != h->nbricks) { set_error("density-fitted handles build whole only"); return ESMF_ERR_UNSUPPORTED; }
         return build_df(h, m, D, J, K, F, traces, (cudaStream_t)stream);
+    }
+    if (h->mode == ESMF_MODE_THC) {
+        if (b0 != 0 || b1 != h->nbricks) { set_error("hypercontracted handles build whole only"); return ESMF_ERR_UNSUPPORTED; }
+        return build_thc(h, m, D, J, K, F, traces, (cudaStream_t)stream);
     }
     RET(ensure_work(h, m));
     cudaStream_t s = (cudaStream_t)stream;
@@ -1262,7 +1488,10 @@ int esmf_fock_build_shard(esmf_fock_t *h, int shard, int nshards, int m, const d
         set_error("shard %d of %d", shard, nshards);
         return ESMF_ERR_INVALID_ARG;
     }
-    if (h->mode == ESMF_MODE_DF) { set_error("density-fitted handles are not sharded"); return ESMF_ERR_UNSUPPORTED; }
+    if (h->mode == ESMF_MODE_DF || h->mode == ESMF_MODE_THC) {
+        set_error("density-fitted and hypercontracted handles are not sharded");
+        return ESMF_ERR_UNSUPPORTED;
+    }
     // shard s takes bricks [cut(s), cut(s + 1)): equal shares of the estimated
     // cost (the tensor-kernel cost model of the per-CTA split), each cut moved
     // forward to the next item start so that no item is divided between shards
@@ -1345,7 +1574,10 @@ int esmf_fock_set_path(esmf_fock_t *h, int path) {
 int esmf_fock_autotune(esmf_fock_t *h, int m, const double *D, double *J, double *K, int reps,
                        void *stream, int *chosen) {
     if (!h || m < 1 || m > ESMF_MAX_DENSITIES || !D || !J || !K) { set_error("bad autotune arguments"); return ESMF_ERR_INVALID_ARG; }
-    if (h->mode == ESMF_MODE_DF) { set_error("density-fitted handles have nothing to tune"); return ESMF_ERR_UNSUPPORTED; }
+    if (h->mode == ESMF_MODE_DF || h->mode == ESMF_MODE_THC) {
+        set_error("density-fitted and hypercontracted handles have nothing to tune");
+        return ESMF_ERR_UNSUPPORTED;
+    }
     DeviceGuard g(h->device);
     if (!g.ok) { set_error("cudaSetDevice failed"); return ESMF_ERR_CUDA; }
     const bool tensor = (h->mode == ESMF_MODE_STORED || tensor_direct(h)) && is_split16(h->prec) &&
@@ -1470,8 +1702,9 @@ int handle_prepare_noalloc(esmf_fock_t *h, int m, const double *D, JKArgs *a, in
         set_error("density-weighted screening needs per-build work memory; the no-alloc entry does not apply it");
         return ESMF_ERR_UNSUPPORTED;
     }
-    if (h->mode == ESMF_MODE_DF) {
-        set_error("density-fitted builds need per-build GEMM work memory; the no-alloc entry does not run them");
+    if (h->mode == ESMF_MODE_DF || h->mode == ESMF_MODE_THC) {
+        set_error("density-fitted and hypercontracted builds need per-build GEMM work memory; the no-alloc "
+                  "entry does not run them");
         return ESMF_ERR_UNSUPPORTED;
     }
     a->b = h->dev(); a->Q = h->S; a->tol = h->tol_s; a->bricks = h->bricks; a->nbricks = h->nbricks;

@@ -193,14 +193,19 @@ int df_build(const DfBuild &a, cudaStream_t s) {
                          zero, Kk, ty, n, ct, CUBLAS_GEMM_DEFAULT));
     }
     if (a.ev_stop) CKD(cudaEventRecord(a.ev_stop, s));
-    if (a.traces) CKD(cudaMemsetAsync(a.traces, 0, sizeof(double) * m, s));
+    return launch_factored_finalize(n, m, a.fp32, a.D, a.Jt, a.Kt, a.J, a.K, a.F, a.traces, s);
+}
+
+int launch_factored_finalize(int n, int m, int fp32, const double *D, const void *Jt, const void *Kt, double *J,
+                             double *K, double *F, double *traces, cudaStream_t s) {
+    if (traces) CKD(cudaMemsetAsync(traces, 0, sizeof(double) * m, s));
     const int threads = n <= 128 ? 128 : 256;
-    if (a.fp32)
-        k_df_finalize<float><<<dim3(n, m), threads, 0, s>>>(n, a.D, (const float *)a.Jt, (const float *)a.Kt, a.J,
-                                                            a.K, a.F, a.traces);
+    if (fp32)
+        k_df_finalize<float><<<dim3(n, m), threads, 0, s>>>(n, D, (const float *)Jt, (const float *)Kt, J, K, F,
+                                                            traces);
     else
-        k_df_finalize<double><<<dim3(n, m), threads, 0, s>>>(n, a.D, (const double *)a.Jt, (const double *)a.Kt,
-                                                             a.J, a.K, a.F, a.traces);
+        k_df_finalize<double><<<dim3(n, m), threads, 0, s>>>(n, D, (const double *)Jt, (const double *)Kt, J, K, F,
+                                                             traces);
     CKD(cudaGetLastError());
     return ESMF_OK;
 }

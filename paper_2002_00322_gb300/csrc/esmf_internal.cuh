@@ -170,6 +170,29 @@ int df_gemm_fold(void *cublas, int naux, int64_t nn, const double *Linv, const d
 int df_build(const DfBuild &a, cudaStream_t s);
 int df_cublas_create(void **out);
 void df_cublas_destroy(void *h);
+// F = 2 J - K and t_k = D_k . F_k from the arithmetic-type Jt, Kt of a
+// factored (density-fitted or hypercontracted) build of m densities; writes
+// the caller's FP64 J, K (and F), zeroes and fills the traces
+int launch_factored_finalize(int n, int m, int fp32, const double *D, const void *Jt, const void *Kt, double *J,
+                             double *K, double *F, double *traces, cudaStream_t s);
+
+// ---- thc.cu (tensor hypercontraction)
+struct ThcBuild {
+    void *cublas;
+    int n, G, m, fp32;
+    const void *X, *Z;           // X[p][P] (n x G) and Z[P][Q] (G x G) in the arithmetic type
+    const double *D;             // caller's densities (m x n x n)
+    void *Dt, *A, *M, *y, *z, *Jt, *Kt;   // work for m densities (see thc_build)
+    double *J, *K, *F, *traces;  // caller's outputs
+};
+int launch_thc_collocate(const DevBasis &b, int G, const double *pts, double *X, cudaStream_t s);
+int launch_thc_rank_one(int n, int G, int q0, int mq, const double *X, double *Dq, cudaStream_t s);
+int thc_coulomb_columns(void *cublas, int n, int G, int q0, int mq, const double *X, const double *Jq, double *R,
+                        double *E, cudaStream_t s);
+int thc_gram(void *cublas, int n, int G, const double *X, double *C, cudaStream_t s);
+int thc_solve_z(void *cublas, int G, const double *L, double *W, int fp32, void *Zout, cudaStream_t s);
+int launch_thc_convert(int64_t cnt, const double *src, float *dst, cudaStream_t s);
+int thc_build(const ThcBuild &a, cudaStream_t s);
 
 // ---- energy.cu (ESMF energy and gradient around the grouped build)
 struct EnergyWork {

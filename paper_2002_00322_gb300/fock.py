@@ -22,7 +22,7 @@ ESMF_ERR_CUDA = -3
 ESMF_ERR_TIMEOUT = -4
 ESMF_ERR_UNSUPPORTED = -5
 
-MODES = {"stored": 0, "direct": 1, "auto": 2, "df": 3}
+MODES = {"stored": 0, "direct": 1, "auto": 2, "df": 3, "thc": 4}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16x2": 2, "bf16x2": 3, "f32x2": 4}
 MAX_PRIM = 4
 
@@ -33,7 +33,7 @@ EXPORTS = ["esmf_fock_create", "esmf_fock_build", "esmf_fock_build_host", "esmf_
            "esmf_fock_set_path", "esmf_fock_device_error", "esmf_fock_build_shard",
            "esmf_fock_autotune", "esmf_fock_create_screened", "esmf_fock_build_batch",
            "esmf_measure_fma_peak", "esmf_fock_set_density_screening", "esmf_fock_create_df",
-           "esmf_fock_create_cart"]
+           "esmf_fock_create_cart", "esmf_fock_create_thc"]
 MAX_BATCH = 16
 SCREENINGS = {"schwarz": 0, "pair_max": 1}
 PATHS = {"auto": 0, "cuda_core": 1}
@@ -60,6 +60,10 @@ class esmf_basis_t(C.Structure):
 
 class esmf_aux_t(C.Structure):
     _fields_ = [("n_aux", C.c_int32), ("center", C.POINTER(C.c_double)), ("exps", C.POINTER(C.c_double))]
+
+
+class esmf_grid_t(C.Structure):
+    _fields_ = [("n_grid", C.c_int32), ("points", C.POINTER(C.c_double))]
 
 
 class esmf_stats_t(C.Structure):
@@ -131,6 +135,9 @@ def load(path=None):
         L.esmf_fock_create_df.argtypes = [C.POINTER(esmf_basis_t), C.POINTER(esmf_aux_t), C.c_int, C.c_int,
                                           C.POINTER(vp)]
         L.esmf_fock_create_df.restype = C.c_int
+        L.esmf_fock_create_thc.argtypes = [C.POINTER(esmf_basis_t), C.POINTER(esmf_grid_t), C.c_double, C.c_double,
+                                           C.c_int, C.c_int, C.c_int64, C.POINTER(vp)]
+        L.esmf_fock_create_thc.restype = C.c_int
         L.esmf_fock_set_density_screening.argtypes = [vp, C.c_double]
         L.esmf_fock_set_density_screening.restype = C.c_int
         L.esmf_measure_fma_peak.argtypes = [C.c_int, C.c_int, dp]
@@ -218,6 +225,29 @@ def esmf_fock_create_df(basis, aux_center, aux_exps, precision="fp64", device=0)
     h = C.c_void_p()
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _check(L.esmf_fock_create_df(C.byref(b), C.byref(a), p, int(device), C.byref(h)), "esmf_fock_create_df")
+    return h
+
+
+def esmf_fock_create_thc(basis, points, schwarz_tol, ridge, precision="fp64", device=0, budget_bytes=0):
+    """Tensor-hypercontracted handle (include/esmf_fock.h, esmf_fock_create_thc)
+    over the grid points (n_grid, 3); s bases."""
+    if getattr(basis, "cart", None) is not None and np.any(np.asarray(basis.cart) != 0):
+        raise ValueError("tensor hypercontraction takes bases of s functions")
+    L = load()
+    center = np.ascontiguousarray(basis.center, dtype=np.float64)
+    nprim = np.ascontiguousarray(basis.nprim, dtype=np.int32)
+    exps = np.ascontiguousarray(basis.exps, dtype=np.float64)
+    coefs = np.ascontiguousarray(basis.coefs, dtype=np.float64)
+    b = esmf_basis_t(int(center.shape[0]), center.ctypes.data_as(C.POINTER(C.c_double)),
+                     nprim.ctypes.data_as(C.POINTER(C.c_int32)),
+                     exps.ctypes.data_as(C.POINTER(C.c_double)),
+                     coefs.ctypes.data_as(C.POINTER(C.c_double)))
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    g = esmf_grid_t(int(pts.shape[0]), pts.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(L.esmf_fock_create_thc(C.byref(b), C.byref(g), float(schwarz_tol), float(ridge), p, int(device),
+                                  int(budget_bytes), C.byref(h)), "esmf_fock_create_thc")
     return h
 
 
@@ -365,9 +395,12 @@ class FockBuilder:
     """Owns one handle; D, J, K are torch float64 CUDA tensors (m, N, N)."""
 
     def __init__(self, basis, schwarz_tol, mode="stored", precision="fp64", device=0, budget_bytes=0,
-                 screening="schwarz", aux=None):
+                 screening="schwarz", aux=None, grid=None, ridge=1e-8):
         """mode "df" builds with density-fitted integrals over aux = (centers,
-        exponents) of auxiliary s Gaussians (schwarz_tol unused)."""
+        exponents) of auxiliary s Gaussians (schwarz_tol unused); mode "thc"
+        with the integrals hypercontracted over the grid points (n_grid, 3),
+        the fit regularised by ridge (schwarz_tol screens the exact integrals
+        behind the fit)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("FockBuilder needs a CUDA device")
@@ -377,6 +410,10 @@ class FockBuilder:
             if aux is None:
                 raise ValueError("mode 'df' needs aux = (centers, exponents)")
             self.h = esmf_fock_create_df(basis, aux[0], aux[1], precision, device)
+        elif mode == "thc":
+            if grid is None:
+                raise ValueError("mode 'thc' needs grid = points (n_grid, 3)")
+            self.h = esmf_fock_create_thc(basis, grid, schwarz_tol, ridge, precision, device, budget_bytes)
         else:
             self.h = esmf_fock_create(basis, schwarz_tol, mode, precision, device, budget_bytes, screening)
 

@@ -125,3 +125,49 @@ def test_cartesian_label_outside_s_p_d_rejected(lib, label):
                                    C.byref(h))
     assert rc == fock.ESMF_ERR_INVALID_ARG, (label, rc)
     assert not h.value
+
+
+@pytest.mark.parametrize("bad", ["empty", "too_many", "nan_point", "null_points", "ridge_neg", "ridge_nan",
+                                 "tol_neg", "budget_neg", "prec", "split"])
+def test_thc_arguments_rejected_on_the_host(lib, bad):
+    """esmf_fock_create_thc checks the grid, tolerance, ridge, budget and
+    precision before any device work: INVALID_ARG, or UNSUPPORTED for the
+    split 16-bit precisions."""
+    from paper_2002_00322_gb300 import fock
+    from paper_2002_00322_gb300 import workloads as W
+    w = W.small_random(6, 1, 1)
+    b = w.basis
+    pts = np.ascontiguousarray(W.thc_grid(b))
+    G, tol, ridge, budget, prec = pts.shape[0], 0.0, 1e-8, 0, 0
+    ptr = pts.ctypes.data_as(C.POINTER(C.c_double))
+    if bad == "empty":
+        G = 0
+    elif bad == "too_many":
+        G = 8193
+    elif bad == "nan_point":
+        pts[3, 1] = np.nan
+    elif bad == "null_points":
+        ptr = None
+    elif bad == "ridge_neg":
+        ridge = -1e-8
+    elif bad == "ridge_nan":
+        ridge = float("nan")
+    elif bad == "tol_neg":
+        tol = -1.0
+    elif bad == "budget_neg":
+        budget = -1
+    elif bad == "prec":
+        prec = 9
+    elif bad == "split":
+        prec = 2
+    center, nprim, exps, coefs = (np.ascontiguousarray(x) for x in (b.center, b.nprim, b.exps, b.coefs))
+    cb = fock.esmf_basis_t(b.n, center.ctypes.data_as(C.POINTER(C.c_double)),
+                           nprim.ctypes.data_as(C.POINTER(C.c_int32)),
+                           exps.ctypes.data_as(C.POINTER(C.c_double)),
+                           coefs.ctypes.data_as(C.POINTER(C.c_double)))
+    g = fock.esmf_grid_t(G, ptr)
+    h = C.c_void_p()
+    rc = lib.esmf_fock_create_thc(C.byref(cb), C.byref(g), tol, ridge, prec, 0, budget, C.byref(h))
+    expect = fock.ESMF_ERR_UNSUPPORTED if bad == "split" else fock.ESMF_ERR_INVALID_ARG
+    assert rc == expect, (bad, rc, fock.esmf_last_error())
+    assert not h.value
