@@ -245,6 +245,8 @@ int esmf_fock_create_df(const esmf_basis_t *basis, const esmf_aux_t *aux, int pr
  *   precision    ESMF_PREC_FP64 or ESMF_PREC_FP32 (build GEMM arithmetic;
  *                the fit is always formed in FP64)
  *   device, budget_bytes, out   as for esmf_fock_create
+ * esmf_fock_stats reports mode ESMF_MODE_THC, n_quartets_kept of the exact
+ * integrals behind E, and store_bytes of X and Z.
  * Cost: the fit takes n_grid / 64 exact grouped builds and O(n_grid^3) host
  * work for the Cholesky factor.  Device memory: X (N n_grid) and Z
  * (n_grid^2) in the build arithmetic, plus per-build work of about
