@@ -8,6 +8,7 @@ symmetries and positivity the fitted tensor keeps.  CPU only."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle.oracle import Oracle
 from paper_2002_00322_gb300 import workloads as W
@@ -159,3 +160,69 @@ def test_fitted_tensor_symmetries_and_positivity():
     P = (C @ C.T)[None]
     _, KP = o.jk_thc(P, pts, 0.0, 1e-8)
     assert np.sum(P[0] * KP[0]) >= 0
+
+
+def _fit_with(o, points, tol, ridge, slip):
+    """thc_fit with one plausible slip planted (the oracle itself is untouched)."""
+    X = o.collocation(points)
+    G = X.shape[1]
+    DQ = np.einsum("pQ,qQ->Qpq", X, X)
+    JQ, _, _ = o.jk_unique(DQ, tol)
+    E = np.einsum("pP,qP,Qpq->PQ", X, X, JQ)
+    if slip == "E_one_side":
+        E = np.einsum("pP,qQ,Qpq->PQ", X, X, JQ)
+    S = (X.T @ X) ** 2
+    if slip == "S_unsquared":
+        S = X.T @ X
+    lam = ridge * S.diagonal().max()
+    if slip == "ridge_absolute":
+        lam = ridge
+    Sr = S + lam * np.eye(G)
+    Z = np.linalg.solve(Sr, np.linalg.solve(Sr, E).T).T
+    if slip == "one_solve":
+        Z = np.linalg.solve(Sr, E)
+    return X, 0.5 * (Z + Z.T)
+
+
+_THC_TENSOR = Oracle.thc_tensor
+
+
+def _tensor_with(X, Z, slip):
+    if slip == "tensor_pairing":
+        return np.einsum("pP,qQ,PQ,rP,sQ->pqrs", X, X, Z, X, X)
+    return _THC_TENSOR(X, Z)
+
+
+@pytest.mark.parametrize("slip", ["S_unsquared", "E_one_side", "one_solve", "ridge_absolute",
+                                  "tensor_pairing", "exchange_transposed"])
+def test_pins_catch_planted_slips(monkeypatch, slip):
+    """Each slip planted in a copy of the THC oracle fails at least one pin."""
+    def fit(self, points, tol, ridge):
+        return _fit_with(self, points, tol, ridge, slip)
+
+    def tensor(X, Z):
+        return _tensor_with(X, Z, slip)
+
+    def jk(self, D, points, tol, ridge):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        X, Z = self.thc_fit(points, tol, ridge)
+        V = self.thc_tensor(X, Z)
+        J = np.einsum("pqrs,krs->kpq", V, D)
+        K = np.einsum("pqrs,kqs->kpr", V, D)
+        if slip == "exchange_transposed":
+            K = np.einsum("pqrs,ksq->kpr", V, D)
+        return J, K
+
+    monkeypatch.setattr(Oracle, "thc_fit", fit)
+    monkeypatch.setattr(Oracle, "thc_tensor", staticmethod(tensor))
+    monkeypatch.setattr(Oracle, "jk_thc", jk)
+    pins = [test_coulomb_matrix_from_rank_one_builds_equals_brute_sum, test_least_squares_against_a_generic_solver,
+            test_grid_spanning_every_pair_product_is_exact, test_nested_grids_never_worsen_the_fit,
+            test_fitted_tensor_symmetries_and_positivity]
+    failed = []
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"no pin caught the slip {slip}"
