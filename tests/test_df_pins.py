@@ -5,6 +5,7 @@ integrals when the auxiliary set spans every orbital product.  CPU only."""
 import math
 
 import numpy as np
+import pytest
 from scipy import special
 
 from oracle.oracle import Oracle
@@ -91,3 +92,38 @@ def test_fit_with_an_even_tempered_set_is_close_and_keeps_the_symmetries():
     np.testing.assert_allclose(Kt, K.transpose(0, 2, 1), atol=1e-13 * np.abs(K).max())
     J2, K2 = o.jk_df(2.0 * D[:1] - D[1:], ac, ae)
     np.testing.assert_allclose(K2, 2.0 * K[:1] - K[1:], atol=1e-12 * np.abs(K).max())
+
+
+@pytest.mark.parametrize("slip", ["upper_factor", "no_metric", "exchange_transposed", "coulomb_unfitted"])
+def test_pins_catch_planted_slips(monkeypatch, slip):
+    """Each slip planted in a copy of the density-fitting oracle fails at
+    least one pin."""
+    def jk_df(self, D, acenter, aexp):
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        T = self.eri3(acenter, aexp)
+        V = self.eri2(acenter, aexp)
+        L = np.linalg.cholesky(V)
+        Tm = T.reshape(T.shape[0], -1)
+        if slip == "upper_factor":
+            B = np.linalg.solve(L.T, Tm).reshape(T.shape)
+        elif slip == "no_metric":
+            B = T
+        else:
+            B = np.linalg.solve(L, Tm).reshape(T.shape)
+        g = np.einsum("Prs,krs->kP", T if slip == "coulomb_unfitted" else B, D)
+        J = np.einsum("Ppq,kP->kpq", B, g)
+        if slip == "exchange_transposed":
+            K = np.einsum("Ppr,ksr,Pqs->kpq", B, D, B, optimize=True)
+        else:
+            K = np.einsum("Ppr,krs,Pqs->kpq", B, D, B, optimize=True)
+        return J, K
+
+    monkeypatch.setattr(Oracle, "jk_df", jk_df)
+    failed = []
+    for pin in (test_fit_is_exact_when_the_auxiliaries_span_the_products,
+                test_fit_with_an_even_tempered_set_is_close_and_keeps_the_symmetries):
+        try:
+            pin()
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"no pin caught the slip {slip}"
