@@ -1,0 +1,60 @@
+"""The oracle's pins catch plausible mistakes: each case plants one slip in
+a copy of oracle/esmf_oracle.c (the first occurrence of the pattern, the
+s-function path; compiled into a temporary directory) and runs the pins of
+tests/test_oracle_pins.py against it in a child process, which must report
+failing tests.  The unmodified copy, built the same way, passes.  CPU only."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "esmf_oracle.c")
+
+MUTANTS = {
+    "boys_series_term": ("T * T / 10.0", "T * T / 5.0"),
+    "boys_erf_argument": ("* erf(sqrt(T));", "* erf(T);"),
+    "eri_prefactor": ("return 2.0 * pow(OR_PI, 2.5) / (p * q * sqrt(p + q)) *",
+                      "return 2.0 * pow(OR_PI, 2.0) / (p * q * sqrt(p + q)) *"),
+    "eri_exponent_sign": ("exp(-a * b / p * ab2) * exp(-c * d / q * cd2) * oracle_boys0(T);",
+                          "exp(-a * b / p * ab2) * exp(c * d / q * cd2) * oracle_boys0(T);"),
+    "product_center_weights": ("P[x] = (a * A[x] + b * B[x]) / p;", "P[x] = (b * A[x] + a * B[x]) / p;"),
+    "primitive_norm_power": ("w[k] = c * coefs[k] * pow(2.0 * exps[k] / OR_PI, 0.75);",
+                             "w[k] = c * coefs[k] * pow(2.0 * exps[k] / OR_PI, 0.5);"),
+    "contracted_overlap_power": ("double ov = pow(2.0 * sqrt(ak * al) / (ak + al), 1.5);",
+                                 "double ov = pow(2.0 * sqrt(ak * al) / (ak + al), 0.5);"),
+    "orbit_not_deduplicated": ("if (dup) continue;", "if (0 && dup) continue;"),
+    "unique_exchange_operand": ("K[k * nn + (int64_t)i0 * n + i2] += Dk[(int64_t)i1 * n + i3] * v;",
+                                "K[k * nn + (int64_t)i0 * n + i2] += Dk[(int64_t)i3 * n + i1] * v;"),
+    "brute_exchange_operand": ("K[k * nn + (int64_t)p * n + r] += Dk[(int64_t)q * n + s] * v;",
+                               "K[k * nn + (int64_t)p * n + r] += Dk[(int64_t)s * n + q] * v;"),
+}
+
+
+def run_pins(tmp_path, name, pat=None, new=None):
+    src = open(SRC).read()
+    if pat is not None:
+        assert pat in src, f"pattern of {name} not in the oracle"
+        src = src.replace(pat, new, 1)
+    c = tmp_path / f"{name}.c"
+    c.write_text(src)
+    so = tmp_path / f"{name}.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math", "-ffp-contract=off",
+                    str(c), "-o", str(so), "-lm"], check=True)
+    env = dict(os.environ, ESMF_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        "-x", "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
+def test_unmodified_copy_passes(tmp_path):
+    rc, out = run_pins(tmp_path, "unmodified")
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_slip_fails_a_pin(tmp_path, name):
+    rc, out = run_pins(tmp_path, name, *MUTANTS[name])
+    assert rc == 1 and "failed" in out, out
