@@ -1,8 +1,10 @@
 """The oracle's pins catch plausible mistakes: each case plants one slip in
-a copy of oracle/esmf_oracle.c (the first occurrence of the pattern, the
-s-function path; compiled into a temporary directory) and runs the pins of
-tests/test_oracle_pins.py against it in a child process, which must report
-failing tests.  The unmodified copy, built the same way, passes.  CPU only."""
+a copy of oracle/esmf_oracle.c (the first occurrence of the pattern;
+compiled into a temporary directory) and runs the pins of
+tests/test_oracle_pins.py (s functions) or tests/test_angular_pins.py (the
+Obara-Saika path of p and d functions) against it in a child process, which
+must report failing tests.  The unmodified copy, built the same way, passes
+both.  CPU only."""
 import os
 import subprocess
 import sys
@@ -32,7 +34,21 @@ MUTANTS = {
 }
 
 
-def run_pins(tmp_path, name, pat=None, new=None):
+# planted in the Obara-Saika path (p and d functions), caught by tests/test_angular_pins.py
+ANGULAR_MUTANTS = {
+    "vrr_bra_rho_sign": ("- o->rho / o->p * os_vrr(o, e2, f, m + 1)", "+ o->rho / o->p * os_vrr(o, e2, f, m + 1)"),
+    "vrr_cross_exponent": ("v += f[i] / (2.0 * (o->p + o->q)) * os_vrr(o, e1, f1, m + 1);",
+                           "v += f[i] / (2.0 * o->p) * os_vrr(o, e1, f1, m + 1);"),
+    "vrr_ket_boys_order": ("o->WQ[i] * os_vrr(o, e, f1, m + 1)", "o->WQ[i] * os_vrr(o, e, f1, m)"),
+    "hrr_bra_sign": ("+ AB[j] * os_hrr(o, AB, CD, a, b1, c, d)", "- AB[j] * os_hrr(o, AB, CD, a, b1, c, d)"),
+    "hrr_ket_sign": ("+ CD[j] * os_hrr(o, AB, CD, a, b, c, d1)", "- CD[j] * os_hrr(o, AB, CD, a, b, c, d1)"),
+    "d_double_factorial": ("return l == 2 ? 3.0 : 1.0;", "return l == 2 ? 2.0 : 1.0;"),
+    "d_label_table": ("{1, 1, 0}, {1, 0, 1}, {0, 1, 1}", "{1, 0, 1}, {1, 1, 0}, {0, 1, 1}"),
+    "gaussian_product_point_w": ("W[x] = (p * P[x] + q * Q[x]) / (p + q);", "W[x] = (q * P[x] + p * Q[x]) / (p + q);"),
+}
+
+
+def run_pins(tmp_path, name, pat=None, new=None, pins="test_oracle_pins.py"):
     src = open(SRC).read()
     if pat is not None:
         assert pat in src, f"pattern of {name} not in the oracle"
@@ -43,18 +59,25 @@ def run_pins(tmp_path, name, pat=None, new=None):
     subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math", "-ffp-contract=off",
                     str(c), "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, ESMF_ORACLE_LIB=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins),
                         "-x", "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True,
                        text=True, timeout=600)
     return r.returncode, r.stdout[-2000:]
 
 
-def test_unmodified_copy_passes(tmp_path):
-    rc, out = run_pins(tmp_path, "unmodified")
+@pytest.mark.parametrize("pins", ["test_oracle_pins.py", "test_angular_pins.py"])
+def test_unmodified_copy_passes(tmp_path, pins):
+    rc, out = run_pins(tmp_path, "unmodified", pins=pins)
     assert rc == 0, out
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_slip_fails_a_pin(tmp_path, name):
     rc, out = run_pins(tmp_path, name, *MUTANTS[name])
+    assert rc == 1 and "failed" in out, out
+
+
+@pytest.mark.parametrize("name", sorted(ANGULAR_MUTANTS))
+def test_planted_angular_slip_fails_a_pin(tmp_path, name):
+    rc, out = run_pins(tmp_path, name, *ANGULAR_MUTANTS[name], pins="test_angular_pins.py")
     assert rc == 1 and "failed" in out, out
