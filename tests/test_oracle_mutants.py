@@ -3,8 +3,10 @@ a copy of oracle/esmf_oracle.c (the first occurrence of the pattern;
 compiled into a temporary directory) and runs the pins of
 tests/test_oracle_pins.py (s functions) or tests/test_angular_pins.py (the
 Obara-Saika path of p and d functions) against it in a child process, which
-must report failing tests.  The unmodified copy, built the same way, passes
-both.  CPU only."""
+must report failing tests; likewise slips planted in a copy of
+oracle/esmf_energy.py, loaded in place of the module, against
+tests/test_energy_pins.py.  The unmodified copies, built and loaded the same
+way, pass.  CPU only."""
 import os
 import subprocess
 import sys
@@ -80,4 +82,60 @@ def test_planted_slip_fails_a_pin(tmp_path, name):
 @pytest.mark.parametrize("name", sorted(ANGULAR_MUTANTS))
 def test_planted_angular_slip_fails_a_pin(tmp_path, name):
     rc, out = run_pins(tmp_path, name, *ANGULAR_MUTANTS[name], pins="test_angular_pins.py")
+    assert rc == 1 and "failed" in out, out
+
+
+# planted in the energy / GVP oracle (oracle/esmf_energy.py), caught by tests/test_energy_pins.py
+ENERGY_MUTANTS = {
+    "norm_N2": ("N2 = c0 * c0 + 2.0 * float(np.sum(sigma * sigma))", "N2 = c0 * c0 + float(np.sum(sigma * sigma))"),
+    "e1_cross_coefficient": ("+ 4.0 * c0 * np.trace(Th @ G @ Ga.T @ sigma.T)",
+                             "+ 2.0 * c0 * np.trace(Th @ G @ Ga.T @ sigma.T)"),
+    "density_A_sign": ("A = Ga.T @ sigma.T @ sigma @ Ga - Th.T @ sigma @ sigma.T @ Th",
+                       "A = Ga.T @ sigma.T @ sigma @ Ga + Th.T @ sigma @ sigma.T @ Th"),
+    "fock_exchange_sign": ("return 2.0 * J - K", "return 2.0 * J + K"),
+    "dc0_normalisation_term": ("+ 2.0 * c0 * dot(FP, P) + 4.0 * dot(FP, T)) / N2 - 2.0 * c0 * E / N2",
+                               "+ 2.0 * c0 * dot(FP, P) + 4.0 * dot(FP, T)) / N2"),
+    "dsigma_exchange_sign": ("- 4.0 * (Th @ FP @ Th.T @ s)", "+ 4.0 * (Th @ FP @ Th.T @ s)"),
+    "dtheta_transpose": ("+ 4.0 * c0 * (Th @ (FT + FT.T))", "+ 4.0 * c0 * (Th @ (FT + FT))"),
+    "dgamma_transpose": ("+ 4.0 * (s.T @ Th @ FT)) / N2", "+ 4.0 * (s.T @ Th @ FT.T)) / N2"),
+    "gvp_rotation_norm": ("+ 0.5 * float(np.sum(Gx * Gx))", "+ 1.0 * float(np.sum(Gx * Gx))"),
+    "gvp_variance_sign": ("chi * (-2.0 * mu * (omega - E))", "chi * (2.0 * mu * (omega - E))"),
+    "gvp_tangent_half": ("- 0.5 * (Adir @ Gam + Gam @ Adir)", "- 1.0 * (Adir @ Gam + Gam @ Adir)"),
+}
+
+ENERGY_RUNNER = """
+import importlib.util, sys
+import pytest
+sys.path.insert(0, sys.argv[1])
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.esmf_energy", sys.argv[2])
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.esmf_energy"] = mod
+spec.loader.exec_module(mod)
+oracle.esmf_energy = mod
+sys.exit(pytest.main([sys.argv[3], "-x", "-q", "-p", "no:cacheprovider"]))
+"""
+
+
+def run_energy_pins(tmp_path, name, pat=None, new=None):
+    src = open(os.path.join(ROOT, "oracle", "esmf_energy.py")).read()
+    if pat is not None:
+        assert src.count(pat) == 1, f"pattern of {name} not once in the energy oracle"
+        src = src.replace(pat, new)
+    f = tmp_path / f"{name}.py"
+    f.write_text(src)
+    r = subprocess.run([sys.executable, "-c", ENERGY_RUNNER, ROOT, str(f),
+                        os.path.join(ROOT, "tests", "test_energy_pins.py")],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+def test_unmodified_energy_copy_passes(tmp_path):
+    rc, out = run_energy_pins(tmp_path, "unmodified")
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(ENERGY_MUTANTS))
+def test_planted_energy_slip_fails_a_pin(tmp_path, name):
+    rc, out = run_energy_pins(tmp_path, name, *ENERGY_MUTANTS[name])
     assert rc == 1 and "failed" in out, out
