@@ -1,8 +1,9 @@
 """The oracle's pins catch plausible mistakes: each case plants one slip in
 a copy of oracle/esmf_oracle.c (the first occurrence of the pattern;
 compiled into a temporary directory) and runs the pins of
-tests/test_oracle_pins.py (s functions) or tests/test_angular_pins.py (the
-Obara-Saika path of p and d functions) against it in a child process, which
+tests/test_oracle_pins.py (s functions), tests/test_angular_pins.py (the
+Obara-Saika path of p and d functions) or tests/test_screening_pins.py (the
+pair and density rules) against it in a child process, which
 must report failing tests; likewise slips planted in a copy of
 oracle/esmf_energy.py, loaded in place of the module, against
 tests/test_energy_pins.py.  The unmodified copies, built and loaded the same
@@ -31,6 +32,8 @@ MUTANTS = {
     "orbit_not_deduplicated": ("if (dup) continue;", "if (0 && dup) continue;"),
     "unique_exchange_operand": ("K[k * nn + (int64_t)i0 * n + i2] += Dk[(int64_t)i1 * n + i3] * v;",
                                 "K[k * nn + (int64_t)i0 * n + i2] += Dk[(int64_t)i3 * n + i1] * v;"),
+    "schwarz_without_root": ("Q[(int64_t)p * n + q] = sqrt(v > 0.0 ? v : 0.0);",
+                             "Q[(int64_t)p * n + q] = (v > 0.0 ? v : 0.0);"),
     "brute_exchange_operand": ("K[k * nn + (int64_t)p * n + r] += Dk[(int64_t)q * n + s] * v;",
                                "K[k * nn + (int64_t)p * n + r] += Dk[(int64_t)s * n + q] * v;"),
 }
@@ -47,6 +50,17 @@ ANGULAR_MUTANTS = {
     "d_double_factorial": ("return l == 2 ? 3.0 : 1.0;", "return l == 2 ? 2.0 : 1.0;"),
     "d_label_table": ("{1, 1, 0}, {1, 0, 1}, {0, 1, 1}", "{1, 0, 1}, {1, 1, 0}, {0, 1, 1}"),
     "gaussian_product_point_w": ("W[x] = (p * P[x] + q * Q[x]) / (p + q);", "W[x] = (q * P[x] + p * Q[x]) / (p + q);"),
+}
+
+
+# planted in the screening rules, caught by tests/test_screening_pins.py
+SCREENING_MUTANTS = {
+    "pair_max_one_pair_only": ("if (v > *a2) *a2 = v;", ";"),
+    "pair_max_skips_diagonal": ("if (r == p && s > q) continue;", "if (r == p && s >= q) continue;"),
+    "density_weight_untransposed": ("double b = fabs(D[k * nn + (int64_t)y * n + x]);",
+                                    "double b = fabs(D[k * nn + (int64_t)x * n + y]);"),
+    "density_weight_missing_pair": ("Wd[(int64_t)p * n + r]};", "Wd[(int64_t)r * n + s]};"),
+    "density_rule_factor": ("* wt < tol_d) continue;", "* wt * 0.25 < tol_d) continue;"),
 }
 
 
@@ -67,7 +81,7 @@ def run_pins(tmp_path, name, pat=None, new=None, pins="test_oracle_pins.py"):
     return r.returncode, r.stdout[-2000:]
 
 
-@pytest.mark.parametrize("pins", ["test_oracle_pins.py", "test_angular_pins.py"])
+@pytest.mark.parametrize("pins", ["test_oracle_pins.py", "test_angular_pins.py", "test_screening_pins.py"])
 def test_unmodified_copy_passes(tmp_path, pins):
     rc, out = run_pins(tmp_path, "unmodified", pins=pins)
     assert rc == 0, out
@@ -82,6 +96,12 @@ def test_planted_slip_fails_a_pin(tmp_path, name):
 @pytest.mark.parametrize("name", sorted(ANGULAR_MUTANTS))
 def test_planted_angular_slip_fails_a_pin(tmp_path, name):
     rc, out = run_pins(tmp_path, name, *ANGULAR_MUTANTS[name], pins="test_angular_pins.py")
+    assert rc == 1 and "failed" in out, out
+
+
+@pytest.mark.parametrize("name", sorted(SCREENING_MUTANTS))
+def test_planted_screening_slip_fails_a_pin(tmp_path, name):
+    rc, out = run_pins(tmp_path, name, *SCREENING_MUTANTS[name], pins="test_screening_pins.py")
     assert rc == 1 and "failed" in out, out
 
 
