@@ -10,8 +10,11 @@
  *     F[D]_pq = 2 J[D]_pq - K[D]_pq
  *
  * with the two-electron integrals (pq|rs) in chemists' (1122) order over a
- * basis of contracted s-type Gaussians, all m matrices in ONE pass over the
- * integrals ("grouping Fock builds", Sec. II.C), with Schwarz screening of
+ * basis of contracted Gaussians (s functions; Cartesian p and d functions
+ * through esmf_fock_create_cart), all m matrices in ONE pass over the
+ * integrals ("grouping Fock builds", Sec. II.C), or over approximate
+ * integrals by density fitting (esmf_fock_create_df) or tensor
+ * hypercontraction (esmf_fock_create_thc), with Schwarz screening of
  * integral quartets (kept iff Q_pq * Q_rs >= tol, Q_pq = sqrt((pq|pq)); the
  * bound-based form of the shell-pair screening of Sec. II.C).  It also forms
  * the inner products t_k = D_k . F_k = sum_pq D_k,pq F_k,pq (Table I).
@@ -360,7 +363,8 @@ int esmf_fock_build_host(esmf_fock_t *h, int m, const double *D_host,
  * screening on run the CUDA-core kernels (split 16-bit stores included) and
  * are not accepted by esmf_fock_build_batch (UNSUPPORTED) or
  * esmf_fock_build_noalloc (UNSUPPORTED: it needs per-build work memory).
- * Errors: INVALID_ARG (NULL handle, negative or non-finite tol_d).
+ * Errors: INVALID_ARG (NULL handle, negative or non-finite tol_d),
+ * UNSUPPORTED (density-fitted or hypercontracted handles: no quartets).
  */
 int esmf_fock_set_density_screening(esmf_fock_t *h, double tol_d);
 

@@ -1561,6 +1561,10 @@ int esmf_fock_set_density_screening(esmf_fock_t *h, double tol_d) {
         set_error("density screening needs a handle and a finite tol_d >= 0");
         return ESMF_ERR_INVALID_ARG;
     }
+    if (h->mode == ESMF_MODE_DF || h->mode == ESMF_MODE_THC) {
+        set_error("density-fitted and hypercontracted builds have no quartets to screen");
+        return ESMF_ERR_UNSUPPORTED;
+    }
     h->tol_d = tol_d;
     return ESMF_OK;
 }

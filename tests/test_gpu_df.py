@@ -75,7 +75,8 @@ def test_entries_without_a_fitted_path_refuse(esmf):
         for call in (lambda: esmf.esmf_fock_build_noalloc(fb.h, 2, Dt, J, K),
                      lambda: esmf.esmf_fock_build_shard(fb.h, 0, 2, 2, Dt, J, K),
                      lambda: fb.autotune(Dt),
-                     lambda: esmf.esmf_fock_build_batch([fb.h], [2], [Dt], [J], [K])):
+                     lambda: esmf.esmf_fock_build_batch([fb.h], [2], [Dt], [J], [K]),
+                     lambda: fb.set_density_screening(1e-6)):
             with pytest.raises(esmf.EsmfError) as e:
                 call()
             assert e.value.code == esmf.ESMF_ERR_UNSUPPORTED
